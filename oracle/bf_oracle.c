@@ -1,0 +1,214 @@
+/*
+ * Oracle for the batched panel-major BLAS/LAPACK path: plain, slow, obviously
+ * correct CPU routines in FP64.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call, link or
+ * load this file: only the test suite, the package smoke check and the
+ * benchmark's CPU-baseline leg do.  It shares no code, header, helper or
+ * constant with the CUDA library.
+ *
+ * Conventions
+ *   - Matrices are column-major: element (i, j) of A is A[i + j*lda].
+ *   - Every routine is the textbook definition written out as loops, in the
+ *     order the definition states, with no blocking or fusion.  Compile with
+ *     -O2 -ffp-contract=off so that no multiply-add is contracted and the
+ *     rounding is the plain IEEE-754 one of each written operation.
+ *   - Sizes equal to zero return at once and touch nothing.
+ *
+ * Readings of the paper where it is silent (each one is tested):
+ *   - beta == 0: C is not read (the BLAS convention), so NaN in C is ignored.
+ *   - syrk / potrf / syrk_potrf write only the lower triangle of D,
+ *     diagonal included; the strictly upper part of D is left untouched.
+ *   - potrf: the first column j whose pivot d fails (d > 0) (this includes a
+ *     NaN pivot) makes the routine return j+1 and stop; columns >= j of D are
+ *     then unspecified.  0 means success.
+ */
+#include <math.h>
+#include <stddef.h>
+#include <stdlib.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define EL(P, ld, i, j) (P)[(size_t)(i) + (size_t)(j) * (size_t)(ld)]
+
+/* gemm_nt (Appendix A.2.1, the gemm example; Sec. 5.2.2 "gemm_nt"):
+ *   D <- alpha * A * B^T + beta * C
+ * A is m x k, B is n x k, C and D are m x n; C and D may coincide. */
+void or_dgemm_nt(int m, int n, int k, double alpha, const double *A, int lda,
+                 const double *B, int ldb, double beta, const double *C, int ldc,
+                 double *D, int ldd) {
+  if (m <= 0 || n <= 0) return;
+  for (int j = 0; j < n; j++) {
+    for (int i = 0; i < m; i++) {
+      double s = 0.0;
+      for (int l = 0; l < k; l++) s += EL(A, lda, i, l) * EL(B, ldb, j, l);
+      double c = (beta == 0.0) ? 0.0 : beta * EL(C, ldc, i, j);
+      EL(D, ldd, i, j) = alpha * s + c;
+    }
+  }
+}
+
+/* syrk_ln (Sec. 5.2.2 "syrk_ln"): lower(D) <- alpha * A * B^T + beta * C,
+ * A and B are m x k and may differ, C and D are m x m.  Only i >= j is
+ * computed and written. */
+void or_dsyrk_ln(int m, int k, double alpha, const double *A, int lda,
+                 const double *B, int ldb, double beta, const double *C, int ldc,
+                 double *D, int ldd) {
+  if (m <= 0) return;
+  for (int j = 0; j < m; j++) {
+    for (int i = j; i < m; i++) {
+      double s = 0.0;
+      for (int l = 0; l < k; l++) s += EL(A, lda, i, l) * EL(B, ldb, j, l);
+      double c = (beta == 0.0) ? 0.0 : beta * EL(C, ldc, i, j);
+      EL(D, ldd, i, j) = alpha * s + c;
+    }
+  }
+}
+
+/* potrf_l (Sec. 5.2.2 "potrf_l"; Sec. 4.6 for the factorization as a
+ * sequence of column steps): the lower Cholesky factor L of the m x m SPD
+ * matrix C (only its lower triangle is read), C = L * L^T, stored in lower(D).
+ * Column by column (Cholesky-Crout order):
+ *   d       = C[j][j] - sum_{l<j} L[j][l]^2
+ *   L[j][j] = sqrt(d)                       (fails unless d > 0)
+ *   L[i][j] = (C[i][j] - sum_{l<j} L[i][l] L[j][l]) / L[j][j],  i > j
+ * If dinv is not NULL, dinv[j] = 1 / L[j][j] (the inverse diagonal that the
+ * factorization keeps for later solves, Sec. 4.7.1).
+ * C and D may coincide.  Returns 0, or j+1 for the first failing pivot. */
+int or_dpotrf_l(int m, const double *C, int ldc, double *D, int ldd, double *dinv) {
+  if (m <= 0) return 0;
+  for (int j = 0; j < m; j++) {
+    double d = EL(C, ldc, j, j);
+    for (int l = 0; l < j; l++) d -= EL(D, ldd, j, l) * EL(D, ldd, j, l);
+    if (!(d > 0.0)) return j + 1;
+    double ljj = sqrt(d);
+    EL(D, ldd, j, j) = ljj;
+    for (int i = j + 1; i < m; i++) {
+      double s = EL(C, ldc, i, j);
+      for (int l = 0; l < j; l++) s -= EL(D, ldd, i, l) * EL(D, ldd, j, l);
+      EL(D, ldd, i, j) = s / ljj;
+    }
+    if (dinv) dinv[j] = 1.0 / ljj;
+  }
+  return 0;
+}
+
+/* trsm_rltn (Sec. 5.2.2 "trsm_rltn"; right side, lower, transposed,
+ * non-unit): D = X with X * L^T = alpha * B, i.e. D <- alpha * B * L^{-T}.
+ * B and D are m x n, L is n x n lower triangular (strictly upper part not
+ * read).  Column by column:
+ *   X[i][j] = (alpha B[i][j] - sum_{l<j} X[i][l] L[j][l]) / L[j][j].
+ * B and D may coincide. */
+void or_dtrsm_rltn(int m, int n, double alpha, const double *L, int ldl,
+                   const double *B, int ldb, double *D, int ldd) {
+  if (m <= 0 || n <= 0) return;
+  for (int j = 0; j < n; j++) {
+    for (int i = 0; i < m; i++) {
+      double s = alpha * EL(B, ldb, i, j);
+      for (int l = 0; l < j; l++) s -= EL(D, ldd, i, l) * EL(L, ldl, j, l);
+      EL(D, ldd, i, j) = s / EL(L, ldl, j, j);
+    }
+  }
+}
+
+/* syrk_potrf_ln (Sec. 4.7.2 "Concatenating updates/downdates"; Sec. 5.3,
+ * the Riccati factorization step; Appendix A.3 routine list):
+ *   lower(D) <- chol(C + A * B^T),  A and B m x k, C and D m x m.
+ * Written as its definition: the syrk_ln sum with alpha = beta = 1 into a
+ * scratch matrix, then potrf_l of that matrix.  Returns potrf's info. */
+int or_dsyrk_dpotrf_ln(int m, int k, const double *A, int lda, const double *B, int ldb,
+                       const double *C, int ldc, double *D, int ldd, double *dinv) {
+  if (m <= 0) return 0;
+  double *T = (double *)malloc((size_t)m * (size_t)m * sizeof(double));
+  if (!T) return -1;
+  or_dsyrk_ln(m, k, 1.0, A, lda, B, ldb, 1.0, C, ldc, T, m);
+  int info = or_dpotrf_l(m, T, m, D, ldd, dinv);
+  free(T);
+  return info;
+}
+
+/* Panel-major format (Sec. 4.3.3): rows are grouped in panels of ps rows
+ * (ps a power of two); each panel is a column-major ps x cn block (lda = ps)
+ * and panels follow one another, ps*cn doubles apart.  Element (r, c) of the
+ * panel-major matrix therefore lies at
+ *   (r / ps) * ps * cn  +  c * ps  +  r % ps.
+ * pack copies the m x n column-major matrix A into the panel-major matrix pA
+ * at sub-matrix offset (ai, aj); unpack copies it back out. */
+static size_t pm_index(int r, int c, int ps, int cn) {
+  return (size_t)(r / ps) * (size_t)ps * (size_t)cn + (size_t)c * (size_t)ps + (size_t)(r % ps);
+}
+
+void or_pack(int m, int n, const double *A, int lda, int ps, int cn, double *pA, int ai, int aj) {
+  for (int j = 0; j < n; j++)
+    for (int i = 0; i < m; i++) pA[pm_index(ai + i, aj + j, ps, cn)] = EL(A, lda, i, j);
+}
+
+void or_unpack(int m, int n, int ps, int cn, const double *pA, int ai, int aj, double *A, int lda) {
+  for (int j = 0; j < n; j++)
+    for (int i = 0; i < m; i++) EL(A, lda, i, j) = pA[pm_index(ai + i, aj + j, ps, cn)];
+}
+
+/* ---- batched drivers: the same routines over independent problems ------
+ * Problem b's operand X starts at X + b*sX (strides in doubles).  The loop
+ * over problems runs on every OpenMP thread; the arithmetic of each problem
+ * is exactly the single-problem routine above. */
+int or_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+void or_set_num_threads(int t) {
+#ifdef _OPENMP
+  if (t > 0) omp_set_num_threads(t);
+#else
+  (void)t;
+#endif
+}
+
+void or_dgemm_nt_batch(int batch, int m, int n, int k, double alpha,
+                       const double *A, int lda, long sA, const double *B, int ldb, long sB,
+                       double beta, const double *C, int ldc, long sC, double *D, int ldd, long sD) {
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int b = 0; b < batch; b++)
+    or_dgemm_nt(m, n, k, alpha, A + (size_t)b * sA, lda, B + (size_t)b * sB, ldb, beta,
+                C + (size_t)b * sC, ldc, D + (size_t)b * sD, ldd);
+}
+
+void or_dsyrk_ln_batch(int batch, int m, int k, double alpha,
+                       const double *A, int lda, long sA, const double *B, int ldb, long sB,
+                       double beta, const double *C, int ldc, long sC, double *D, int ldd, long sD) {
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int b = 0; b < batch; b++)
+    or_dsyrk_ln(m, k, alpha, A + (size_t)b * sA, lda, B + (size_t)b * sB, ldb, beta,
+                C + (size_t)b * sC, ldc, D + (size_t)b * sD, ldd);
+}
+
+void or_dpotrf_l_batch(int batch, int m, const double *C, int ldc, long sC,
+                       double *D, int ldd, long sD, double *dinv, long sdinv, int *info) {
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int b = 0; b < batch; b++)
+    info[b] = or_dpotrf_l(m, C + (size_t)b * sC, ldc, D + (size_t)b * sD, ldd,
+                          dinv ? dinv + (size_t)b * sdinv : NULL);
+}
+
+void or_dtrsm_rltn_batch(int batch, int m, int n, double alpha, const double *L, int ldl, long sL,
+                         const double *B, int ldb, long sB, double *D, int ldd, long sD) {
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int b = 0; b < batch; b++)
+    or_dtrsm_rltn(m, n, alpha, L + (size_t)b * sL, ldl, B + (size_t)b * sB, ldb,
+                  D + (size_t)b * sD, ldd);
+}
+
+void or_dsyrk_dpotrf_ln_batch(int batch, int m, int k, const double *A, int lda, long sA,
+                              const double *B, int ldb, long sB, const double *C, int ldc, long sC,
+                              double *D, int ldd, long sD, double *dinv, long sdinv, int *info) {
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int b = 0; b < batch; b++)
+    info[b] = or_dsyrk_dpotrf_ln(m, k, A + (size_t)b * sA, lda, B + (size_t)b * sB, ldb,
+                                 C + (size_t)b * sC, ldc, D + (size_t)b * sD, ldd,
+                                 dinv ? dinv + (size_t)b * sdinv : NULL);
+}

@@ -1,0 +1,82 @@
+"""The pins must catch plausible mistakes in the oracle.
+
+Each case copies the oracle source, plants one mistake (a transposed operand,
+a wrong sign, a dropped term, a wrong index), builds the copy on the CPU and
+checks that at least one pin from test_oracle_pins fails against it.
+"""
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+import oracle
+from tests import test_oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "bf_oracle.c")
+
+MUTANTS = {
+    "gemm_transposed_B": ("s += EL(A, lda, i, l) * EL(B, ldb, j, l);\n      double c = (beta == 0.0) ? 0.0 : beta * EL(C, ldc, i, j);\n      EL(D, ldd, i, j) = alpha * s + c;\n    }\n  }\n}\n\n/* syrk_ln",
+                          "s += EL(A, lda, i, l) * EL(B, ldb, l, j);\n      double c = (beta == 0.0) ? 0.0 : beta * EL(C, ldc, i, j);\n      EL(D, ldd, i, j) = alpha * s + c;\n    }\n  }\n}\n\n/* syrk_ln"),
+    "gemm_sign": ("EL(D, ldd, i, j) = alpha * s + c;\n    }\n  }\n}\n\n/* syrk_ln",
+                  "EL(D, ldd, i, j) = alpha * s - c;\n    }\n  }\n}\n\n/* syrk_ln"),
+    "gemm_drops_last_k": ("for (int l = 0; l < k; l++) s += EL(A, lda, i, l) * EL(B, ldb, j, l);\n      double c = (beta == 0.0) ? 0.0 : beta * EL(C, ldc, i, j);\n      EL(D, ldd, i, j) = alpha * s + c;\n    }\n  }\n}\n\n/* syrk_ln",
+                          "for (int l = 0; l < k - 1; l++) s += EL(A, lda, i, l) * EL(B, ldb, j, l);\n      double c = (beta == 0.0) ? 0.0 : beta * EL(C, ldc, i, j);\n      EL(D, ldd, i, j) = alpha * s + c;\n    }\n  }\n}\n\n/* syrk_ln"),
+    "syrk_writes_upper": ("for (int i = j; i < m; i++) {", "for (int i = 0; i < m; i++) {"),
+    "potrf_dropped_term": ("for (int l = 0; l < j; l++) d -= EL(D, ldd, j, l) * EL(D, ldd, j, l);",
+                           "for (int l = 1; l < j; l++) d -= EL(D, ldd, j, l) * EL(D, ldd, j, l);"),
+    "potrf_multiplies": ("EL(D, ldd, i, j) = s / ljj;", "EL(D, ldd, i, j) = s * ljj;"),
+    "potrf_wrong_index": ("for (int l = 0; l < j; l++) s -= EL(D, ldd, i, l) * EL(D, ldd, j, l);\n      EL(D, ldd, i, j) = s / ljj;",
+                          "for (int l = 0; l < j; l++) s -= EL(D, ldd, i, l) * EL(D, ldd, l, j);\n      EL(D, ldd, i, j) = s / ljj;"),
+    "trsm_reads_upper": ("s -= EL(D, ldd, i, l) * EL(L, ldl, j, l);", "s -= EL(D, ldd, i, l) * EL(L, ldl, l, j);"),
+    "trsm_drops_alpha": ("double s = alpha * EL(B, ldb, i, j);", "double s = EL(B, ldb, i, j);"),
+    "syrk_potrf_drops_C": ("or_dsyrk_ln(m, k, 1.0, A, lda, B, ldb, 1.0, C, ldc, T, m);",
+                           "or_dsyrk_ln(m, k, 1.0, A, lda, B, ldb, 0.0, C, ldc, T, m);"),
+    "pack_row_in_panel": ("(size_t)c * (size_t)ps + (size_t)(r % ps)", "(size_t)c * (size_t)ps + (size_t)((r + 1) % ps)"),
+}
+
+
+def _battery():
+    """Run a representative subset of the pins; return True if all pass."""
+    checks = [
+        lambda: pins.test_gemm_nt_integer_exact(7, 5, 9, -2.0, 3.0),
+        lambda: pins.test_gemm_nt_transposition_is_detected(),
+        lambda: pins.test_syrk_ln_integer_exact_lower_only(9, 5),
+        lambda: pins.test_potrf_integer_factor_returns_exactly(13),
+        lambda: pins.test_potrf_2x2_closed_form(),
+        lambda: pins.test_trsm_integer_solution_returns_exactly(7, 3),
+        lambda: pins.test_syrk_potrf_exact_construction(8, 3),
+        lambda: pins.test_pack_is_the_3d_panel_view(8, 13, 17),
+        lambda: pins.test_golden_cholesky_3x3(),
+        lambda: pins.test_golden_trsm_3x3(),
+    ]
+    for c in checks:
+        try:
+            c()
+        except AssertionError:
+            return False
+    return True
+
+
+def test_unmutated_oracle_passes_battery():
+    assert _battery()
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation anchor for {name} not unique"
+    mpath = tmp_path / "mutant.c"
+    mpath.write_text(src.replace(old, new))
+    so = tmp_path / "libmutant.so"
+    subprocess.run(["gcc", *oracle.CFLAGS, "-o", str(so), str(mpath), "-lm"], check=True)
+    # run the battery in a child process so that a mutant cannot disturb this one
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("import sys; sys.path.insert(0, %r); import oracle; "
+            "oracle.build = lambda force=False: %r; "
+            "from tests.test_oracle_mutants import _battery; "
+            "sys.exit(0 if _battery() else 3)") % (root, str(so))
+    rc = subprocess.run([sys.executable, "-c", code], cwd=root).returncode
+    assert rc == 3, f"mutant {name} survived the pins (rc={rc})"
