@@ -1,0 +1,567 @@
+#!/usr/bin/env python3
+"""Benchmark: batched FP64 panel-major routines on one GB300 (or N, as replicas).
+
+Workload (one "step"): the FP64 routine sweep -- dgemm_nt, dsyrk_ln, dpotrf_l,
+dtrsm_rltn and the fused dsyrk_dpotrf_ln at square n in
+{4, 8, 16, 24, 32, 48, 64, 96, 128, 192, 256}, k = n, each point with a batch
+sized so that its inputs fill about 1 GiB of HBM (far larger than the 129 MB
+L2, so no L2 flush is needed between steps).  Entries iid N(0, 1); SPD
+inputs M M^T + n I; the trsm factor is the Cholesky factor of such an input;
+syrk_potrf computes chol(n I + M M^T).  All data synthetic and seeded.
+
+Metric: GFLOP/s of the whole step (sum of the routines' flop counts over the
+step time), with per-point GFLOP/s and roofline fraction.  Flop counts:
+gemm 2mnk, syrk k m(m+1), potrf n^3/3 + n^2/2 + n/6, trsm m n^2,
+syrk_potrf = syrk + potrf.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank runs the same workload on its own GPU
+(independent problems, no collective: replicas, weak scaling); rank 0 prints
+one JSON line.  --impl reference times the CPU oracle on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+SWEEP_N = (4, 8, 16, 24, 32, 48, 64, 96, 128, 192, 256)
+ROUTINES = ("dgemm_nt", "dsyrk_ln", "dpotrf_l", "dtrsm_rltn", "dsyrk_dpotrf_ln")
+
+# FP64 ALU peak of GB300 from unit counts and clock: 152 SMs x 2 FP64 FMA
+# lanes per SM and clock x 2 flop x 2.07 GHz.
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
+
+
+def flops(routine: str, n: int) -> float:
+    m = k = n
+    if routine == "dgemm_nt":
+        return 2.0 * m * n * k
+    if routine == "dsyrk_ln":
+        return float(k * m * (m + 1))
+    if routine == "dpotrf_l":
+        return n ** 3 / 3.0 + n ** 2 / 2.0 + n / 6.0
+    if routine == "dtrsm_rltn":
+        return float(m * n * n)
+    if routine == "dsyrk_dpotrf_ln":
+        return float(k * m * (m + 1)) + n ** 3 / 3.0 + n ** 2 / 2.0 + n / 6.0
+    raise ValueError(routine)
+
+
+def alg_bytes(routine: str, n: int) -> float:
+    """Bytes the method must move per problem: inputs read once, output written
+    once, triangles only for symmetric/triangular operands."""
+    m = k = n
+    if routine == "dgemm_nt":
+        return 8.0 * (m * k + n * k + 2 * m * n)
+    if routine == "dsyrk_ln":
+        return 8.0 * (2 * m * k + m * (m + 1))
+    if routine == "dpotrf_l":
+        return 8.0 * n * (n + 1)
+    if routine == "dtrsm_rltn":
+        return 8.0 * (n * (n + 1) / 2 + 2 * m * n)
+    if routine == "dsyrk_dpotrf_ln":
+        return 8.0 * (2 * n * k + n * (n + 1))
+    raise ValueError(routine)
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def roofline_gflops(routine, n, hbm_gbs):
+    return min(FP64_PEAK_GFLOPS, hbm_gbs * flops(routine, n) / alg_bytes(routine, n))
+
+
+WORKLOAD = ("FP64 routine sweep: dgemm_nt, dsyrk_ln, dpotrf_l, dtrsm_rltn, dsyrk_dpotrf_ln "
+            "at square n in {4,8,16,24,32,48,64,96,128,192,256}, k=n, batch sized so the "
+            "inputs of each point fill ~1 GiB; iid N(0,1), SPD inputs M M^T + n I")
+
+
+def config_dict(points):
+    return {
+        "workload": WORKLOAD,
+        "routines": list(ROUTINES),
+        "n": sorted({n for _, n in points}),
+        "batch_per_point_inputs_bytes": 1 << 30,
+        "layout": "panel-major, ps=4",
+        "l2": "inputs larger than L2 (1 GiB per point), no flush",
+    }
+
+
+# ------------------------------------------------------------------ clocks --
+
+class ClockSampler:
+    """nvidia-smi sampled every 200 ms during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(gpu_index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {
+            "sm_mhz": statistics.median(sm) if sm else None,
+            "sm_max_mhz": max(smax) if smax else None,
+            "reasons": sorted(reasons),
+            "samples": len(sm),
+        }
+
+
+# --------------------------------------------------------------- GPU arm ---
+
+class Point:
+    """One (routine, n) sweep point: resident panel-major inputs and outputs."""
+
+    def __init__(self, routine, n, dev, seed):
+        import torch
+
+        import paper_1704_02457_gb300 as bf
+        from paper_1704_02457_gb300 import inputs
+
+        self.routine, self.n = routine, n
+        self.batch = bt = inputs.sweep_batch(routine, n)
+        self.flops = flops(routine, n) * bt
+        self.roof = None
+        mk = lambda X: bf.DMatBatch.from_colmajor(X, tight=True)  # noqa: E731
+        if routine == "dgemm_nt":
+            self.A = mk(inputs.normal((bt, n, n), seed, dev))
+            self.B = mk(inputs.normal((bt, n, n), seed + 1, dev))
+            self.C = mk(inputs.normal((bt, n, n), seed + 2, dev))
+            self.D = bf.DMatBatch(bt, n, n, tight=True)
+        elif routine == "dsyrk_ln":
+            self.A = mk(inputs.normal((bt, n, n), seed, dev))
+            self.C = mk(inputs.normal((bt, n, n), seed + 2, dev))
+            self.D = bf.DMatBatch(bt, n, n, tight=True)
+        elif routine == "dpotrf_l":
+            self.C = mk(inputs.spd(bt, n, seed, dev))
+            self.D = bf.DMatBatch(bt, n, n, tight=True)
+            self.info = torch.zeros(bt, dtype=torch.int32, device=dev)
+        elif routine == "dtrsm_rltn":
+            self.L = mk(inputs.chol_factor(bt, n, seed, dev))
+            self.B = mk(inputs.normal((bt, n, n), seed + 1, dev))
+            self.D = bf.DMatBatch(bt, n, n, tight=True)
+        elif routine == "dsyrk_dpotrf_ln":
+            self.A = mk(inputs.normal((bt, n, n), seed, dev))
+            Q = torch.zeros(bt, n, n, dtype=torch.float64, device=dev)
+            Q.diagonal(dim1=1, dim2=2).fill_(float(n))
+            self.C = mk(Q)
+            del Q
+            self.D = bf.DMatBatch(bt, n, n, tight=True)
+            self.info = torch.zeros(bt, dtype=torch.int32, device=dev)
+        torch.cuda.synchronize()
+
+    def run(self, stream=None):
+        import paper_1704_02457_gb300 as bf
+        n = self.n
+        r = self.routine
+        if r == "dgemm_nt":
+            bf.dgemm_nt(n, n, n, 1.0, self.A, 0, 0, self.B, 0, 0, 1.0, self.C, 0, 0, self.D, 0, 0, stream=stream)
+        elif r == "dsyrk_ln":
+            bf.dsyrk_ln(n, n, 1.0, self.A, 0, 0, self.A, 0, 0, 1.0, self.C, 0, 0, self.D, 0, 0, stream=stream)
+        elif r == "dpotrf_l":
+            bf.dpotrf_l(n, self.C, 0, 0, self.D, 0, 0, dinv=False, info=self.info, stream=stream)
+        elif r == "dtrsm_rltn":
+            bf.dtrsm_rltn(n, n, 1.0, self.L, 0, 0, self.B, 0, 0, self.D, 0, 0, stream=stream)
+        elif r == "dsyrk_dpotrf_ln":
+            bf.dsyrk_dpotrf_ln(n, n, self.A, 0, 0, self.A, 0, 0, self.C, 0, 0, self.D, 0, 0, dinv=False,
+                               info=self.info, stream=stream)
+
+
+def cpu_sample_rates(points_spec, budget_s=0.25, max_threads=None):
+    """Oracle GFLOP/s per (routine, n) on a bounded sample; returns (rates, cores, desc)."""
+    import numpy as np
+
+    import oracle
+    from paper_1704_02457_gb300 import inputs
+
+    oracle.build()
+    if max_threads:
+        oracle.set_num_threads(max_threads)
+    cores = oracle.num_threads()
+    rates, sizes = {}, {}
+    for routine, n in points_spec:
+        f = flops(routine, n)
+        # probe with a tiny batch, then size the sample to the budget
+        count = max(1, min(inputs.sweep_batch(routine, n), int(2e7 / max(f, 1.0))))
+        for attempt in range(3):
+            t = _oracle_run(routine, n, count)
+            if t >= 0.5 * budget_s or count >= inputs.sweep_batch(routine, n):
+                break
+            count = min(inputs.sweep_batch(routine, n), int(count * min(64.0, budget_s / max(t, 1e-6))) + 1)
+        rates[(routine, n)] = f * count / t / 1e9
+        sizes[(routine, n)] = count
+    desc = ("oracle (plain C loops, -O2 -ffp-contract=off, OpenMP over problems) on a bounded "
+            "sample per point (" + ", ".join(f"{r}@{n}:{sizes[(r, n)]}" for r, n in points_spec[:3])
+            + ", ...), about %.2f s each; step time = sum over points of full-batch flops / sample rate"
+            % budget_s)
+    return rates, cores, desc, sizes
+
+
+def _oracle_run(routine, n, count):
+    import numpy as np
+
+    import oracle
+    rng = np.random.default_rng(7 + n)
+    A = rng.standard_normal((count, n, n))
+    if routine in ("dpotrf_l",):
+        S = A @ A.transpose(0, 2, 1) + n * np.eye(n)
+        t0 = time.perf_counter()
+        oracle.dpotrf_l(S)
+        return time.perf_counter() - t0
+    if routine == "dtrsm_rltn":
+        L = np.linalg.cholesky(A @ A.transpose(0, 2, 1) + n * np.eye(n))
+        B = rng.standard_normal((count, n, n))
+        t0 = time.perf_counter()
+        oracle.dtrsm_rltn(1.0, L, B)
+        return time.perf_counter() - t0
+    if routine == "dsyrk_dpotrf_ln":
+        Q = np.broadcast_to(n * np.eye(n), (count, n, n))
+        t0 = time.perf_counter()
+        oracle.dsyrk_dpotrf_ln(A, A, Q)
+        return time.perf_counter() - t0
+    B = rng.standard_normal((count, n, n))
+    C = rng.standard_normal((count, n, n))
+    t0 = time.perf_counter()
+    if routine == "dgemm_nt":
+        oracle.dgemm_nt(1.0, A, B, 1.0, C)
+    else:
+        oracle.dsyrk_ln(1.0, A, A, 1.0, C)
+    return time.perf_counter() - t0
+
+
+def run_gpu(args):
+    import torch
+
+    import paper_1704_02457_gb300 as bf
+    from paper_1704_02457_gb300.build import build
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    if rank == 0 or world == 1:
+        build()
+    if world > 1:
+        torch.distributed.barrier()
+    build()
+    bf.load()
+
+    spec = [(r, n) for n in SWEEP_N for r in ROUTINES]
+    if args.points:
+        keep = set(args.points.split(","))
+        spec = [(r, n) for r, n in spec if f"{r}@{n}" in keep or r in keep or str(n) in keep]
+    hbm, hbm_src = measured_peaks()
+    pts = []
+    for i, (r, n) in enumerate(spec):
+        pts.append(Point(r, n, dev, seed=5000 + 97 * i))
+        torch.cuda.empty_cache()
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        for j, p in enumerate(pts):
+            if ev is not None:
+                ev[j][0].record(stream)
+            p.run(stream)
+            if ev is not None:
+                ev[j][1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    K = args.steps
+    evs = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in pts]
+           for _ in range(K)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    time.sleep(0.3)
+    t0.record(stream)
+    for s in range(K):
+        step(evs[s])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    total_ms = t0.elapsed_time(t1)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / K
+    step_flops = sum(p.flops for p in pts)
+    value = step_flops * world / (ms_per_step * 1e-3) / 1e9
+
+    per_point = []
+    per_routine = {}
+    for j, p in enumerate(pts):
+        times = [evs[s][j][0].elapsed_time(evs[s][j][1]) for s in range(K)]
+        med = statistics.median(times)
+        mean = sum(times) / len(times)
+        g = p.flops / (med * 1e-3) / 1e9
+        roof = roofline_gflops(p.routine, p.n, hbm)
+        per_point.append({"routine": p.routine, "n": p.n, "batch": p.batch, "ms": round(med, 4),
+                          "gflops": round(g, 2), "roofline_frac": round(g / roof, 4)})
+        acc = per_routine.setdefault(p.routine, [0.0, 0.0, 0, 0.0])
+        acc[0] += p.flops
+        acc[1] += mean
+        acc[2] += 1
+        acc[3] += alg_bytes(p.routine, p.n) * p.batch
+
+    # dominant kernel: the routine with the largest share of step time
+    dom = max(per_routine, key=lambda r: per_routine[r][1])
+    fl, ms, nl, by = per_routine[dom]
+    achieved_tflops = fl / (ms * 1e-3) / 1e12
+    roof_obj = {
+        "kernel": {"dgemm_nt": "k_gemm_nt<false,true>", "dsyrk_ln": "k_gemm_nt<true,true>",
+                   "dpotrf_l": "k_chol_small/k_chol_rows", "dtrsm_rltn": "k_trsm_rltn",
+                   "dsyrk_dpotrf_ln": "k_chol_small/k_chol_rows (fused)"}[dom],
+        "routine": dom,
+        "bound": "alu",
+        "achieved": round(achieved_tflops, 4),
+        "peak": round(FP64_PEAK_GFLOPS / 1e3, 4),
+        "unit": "TFLOP/s",
+        "frac": round(achieved_tflops / (FP64_PEAK_GFLOPS / 1e3), 4),
+        "traffic": None,
+        "algorithmic_bytes_per_launch": round(by / nl),
+        "peak_source": "FP64 ALU peak derived from unit counts and clock (152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz); "
+                       "HBM roof uses %s %.0f GB/s" % (hbm_src, hbm),
+        "time_share": round(ms / sum(v[1] for v in per_routine.values()), 4),
+    }
+
+    result = {
+        "metric": "batched dsyrk_dpotrf/dgemm_nt GFLOP/s & roofline % vs n; mixed vs FP64 at 1e-12",
+        "value": round(value, 2),
+        "unit": "GFLOP/s",
+        "n_gpus": world,
+        "steps": K,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_per_step, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic (seeded iid N(0,1), SPD M M^T + n I)",
+        "config": config_dict(spec),
+        "gpu_launches": len(pts) * K,
+        "clocks": clocks,
+        "roofline": roof_obj,
+        "per_point": per_point,
+    }
+    result["per_routine_gflops"] = {r: round(v[0] / (v[1] * 1e-3) / 1e9, 2) for r, v in per_routine.items()}
+
+    if not args.no_e2e:
+        result["e2e"] = run_e2e(pts, args, dev, world)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rates, cores, desc, _ = cpu_sample_rates(spec, budget_s=args.cpu_budget)
+        t_cpu = sum(p.flops / (rates[(p.routine, p.n)] * 1e9) for p in pts)
+        result["cpu_baseline"] = {"value": round(step_flops / t_cpu / 1e9, 3), "unit": "GFLOP/s",
+                                  "cores": cores, "kind": "oracle", "sample": desc}
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(result))
+
+
+def run_e2e(pts, args, dev, world):
+    """The same step through the public API with host buffers.  Every step, for
+    every point: copy its inputs from pinned host memory (column-major, as a
+    user holds them) to the device, pack them (bf_pack), run the routine, unpack
+    the result (bf_unpack) and copy it back to pinned host memory.
+
+    Host inputs are kept in per-n pinned pools that the routines of that n
+    share: a pool of N(0,1) data (gemm A, B, C; syrk A, C; trsm B; syrk_potrf
+    M), a pool of SPD matrices (potrf), one of Cholesky factors (trsm) and one
+    of n*I (syrk_potrf).  Device staging buffers are reused across points."""
+    import torch
+
+    import paper_1704_02457_gb300 as bf
+    from paper_1704_02457_gb300 import inputs
+
+    stream = torch.cuda.current_stream()
+    by_n = {}
+    for p in pts:
+        by_n.setdefault(p.n, []).append(p)
+    pools = {}
+    for n, group in by_n.items():
+        pool = {}
+        need_norm = max(p.batch * n * n * {"dgemm_nt": 3, "dsyrk_ln": 2, "dtrsm_rltn": 1,
+                                             "dsyrk_dpotrf_ln": 1}.get(p.routine, 0) for p in group)
+        if need_norm:
+            h = torch.empty(need_norm, dtype=torch.float64, pin_memory=True)
+            h.copy_(inputs.normal((need_norm,), 7000 + n, dev))
+            pool["norm"] = h
+        for p in group:
+            bt = p.batch
+            if p.routine == "dpotrf_l":
+                h = torch.empty((bt, n, n), dtype=torch.float64, pin_memory=True)
+                h.copy_(inputs.spd(bt, n, 7100 + n, dev))
+                pool["spd"] = h
+            elif p.routine == "dtrsm_rltn":
+                h = torch.empty((bt, n, n), dtype=torch.float64, pin_memory=True)
+                h.copy_(inputs.chol_factor(bt, n, 7200 + n, dev).transpose(1, 2))
+                pool["fac"] = h
+            elif p.routine == "dsyrk_dpotrf_ln":
+                h = torch.zeros((bt, n, n), dtype=torch.float64, pin_memory=True)
+                h.diagonal(dim1=1, dim2=2).fill_(float(n))
+                pool["q"] = h
+        pools[n] = pool
+    plan = []
+    h2d = d2h = 0
+    for p in pts:
+        n, bt, pool = p.n, p.batch, pools[p.n]
+        sz = bt * n * n
+        norm = lambda i: pool["norm"][i * sz:(i + 1) * sz].view(bt, n, n)  # noqa: E731
+        ins = {"dgemm_nt": [("A", norm(0)), ("B", norm(1)), ("C", norm(2))],
+               "dsyrk_ln": [("A", norm(0)), ("C", norm(1))],
+               "dpotrf_l": [("C", pool.get("spd"))],
+               "dtrsm_rltn": [("L", pool.get("fac")), ("B", norm(0))],
+               "dsyrk_dpotrf_ln": [("A", norm(0)), ("C", pool.get("q"))]}[p.routine]
+        h2d += sum(h.numel() * 8 for _, h in ins)
+        d2h += sz * 8
+        plan.append((p, ins))
+    max_sz = max(p.batch * p.n * p.n for p in pts)
+    slots = [torch.empty(max_sz, dtype=torch.float64, device=dev) for _ in range(3)]
+    out_dev = torch.empty(max_sz, dtype=torch.float64, device=dev)
+    out_host = torch.empty(max_sz, dtype=torch.float64, pin_memory=True)
+    torch.cuda.synchronize()
+
+    def e2e_step():
+        for p, ins in plan:
+            sz = p.batch * p.n * p.n
+            for slot, (name, h) in zip(slots, ins):
+                buf = slot[:sz].view(p.batch, p.n, p.n)
+                buf.copy_(h, non_blocking=True)
+                bf.pack(buf, getattr(p, name), stream=stream)
+            p.run(stream)
+            ob = out_dev[:sz].view(p.batch, p.n, p.n)
+            bf.unpack(p.D, ob, stream=stream)
+            out_host[:sz].copy_(out_dev[:sz], non_blocking=True)
+
+    steps = max(1, min(args.steps, 2))
+    e2e_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / steps
+    if world > 1:
+        t = torch.tensor([dt], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        dt = float(t.item())
+    step_flops = sum(p.flops for p in pts)
+    return {"value": round(step_flops * world / dt / 1e9, 2), "unit": "GFLOP/s",
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": steps,
+            "ms_per_step": round(dt * 1e3, 2),
+            "path": "pinned host column-major -> H2D -> bf_pack -> routine -> bf_unpack -> D2H"}
+
+
+# ---------------------------------------------------------- reference arm --
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and rank != 0:
+        return
+    spec = [(r, n) for n in SWEEP_N for r in ROUTINES]
+    from paper_1704_02457_gb300 import inputs
+    budget = args.cpu_budget
+    rates = None
+    for _ in range(args.warmup):
+        rates, cores, desc, sizes = cpu_sample_rates(spec, budget_s=budget * 0.2)
+    step_times = []
+    for _ in range(args.steps):
+        rates, cores, desc, sizes = cpu_sample_rates(spec, budget_s=budget)
+        step_times.append(sum(flops(r, n) * inputs.sweep_batch(r, n) / (rates[(r, n)] * 1e9) for r, n in spec))
+    step_flops = sum(flops(r, n) * inputs.sweep_batch(r, n) for r, n in spec)
+    t = statistics.median(step_times)
+    value = step_flops / t / 1e9
+    print(json.dumps({
+        "impl": "reference",
+        "metric": "batched dsyrk_dpotrf/dgemm_nt GFLOP/s & roofline % vs n; mixed vs FP64 at 1e-12",
+        "value": round(value, 3), "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(t * 1e3, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded iid N(0,1), SPD M M^T + n I)", "config": config_dict(spec),
+        "cpu_baseline": {"value": round(value, 3), "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": round(value, 3), "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--points", default="", help="comma list of routine@n, routine or n (debug subsets)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=0.3, help="seconds of oracle time per point")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

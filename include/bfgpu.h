@@ -1,0 +1,208 @@
+/*
+ * bfgpu.h -- C ABI of the batched panel-major FP64 BLAS/LAPACK routines for
+ * GB300 (sm_103a).
+ *
+ * The routines are the level-3 BLAS- and LAPACK-like operations that BLASFEO
+ * (Frison et al., "BLASFEO: basic linear algebra subroutines for embedded
+ * optimization") builds on the panel-major matrix format: gemm_nt, syrk_ln,
+ * potrf_l, trsm_rltn and the fused syrk_potrf_ln.  Each routine exists in the
+ * paper's single-problem form and in a batched form that runs many
+ * independent problems of the same shape in one launch.
+ *
+ * Conventions shared by every entry point (Appendix A.2 of the paper):
+ *   - Sizes come first, then the operands.  A matrix operand is a descriptor
+ *     plus the row and column (ai, aj) of the first element of the
+ *     sub-matrix that is the actual operand.  Option letters (n/t, l/r, ...)
+ *     are part of the routine name.
+ *   - Routines are non-destructive: the output has its own operand, which
+ *     may coincide with an input where stated.
+ *   - All matrix memory is DEVICE memory owned by the caller.  The library
+ *     never allocates, frees or keeps a pointer past the call.
+ *   - Descriptors are plain host structs passed by pointer; only the memory
+ *     they point at lives on the device.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Every
+ *     call is asynchronous on that stream.
+ *   - Batched forms: problem b (0 <= b < batch) of operand X uses the matrix
+ *     whose storage starts at X->pA + b * strideX (stride in doubles).  All
+ *     problems share the sizes, the offsets and X's descriptor fields.
+ *
+ * Return value of every routine:
+ *     0               success (the work is queued on `stream`)
+ *    -i  (i >= 1)     argument i (1-based position in the call) is invalid;
+ *                     nothing was launched
+ *    BF_ERR_UNSUPPORTED  the sizes are valid but beyond what the kernels
+ *                     implement (see each routine)
+ *    > 0 otherwise    a cudaError_t returned by the launch
+ * Numerical failure of a factorization is not an error of the call: it is
+ * reported per problem in the `info` array (see bf_dpotrf_l_batched).
+ */
+#ifndef BFGPU_H
+#define BFGPU_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Panel height ps of the GPU panel-major format (Sec. 4.3.3).  A power of
+ * two, fixed at build time for every matrix, as the paper requires.  Four
+ * doubles (32 bytes, one DRAM sector per panel column) keeps the padding of
+ * the smallest matrices (n = 4) at zero. */
+#define BF_PS 4
+
+/* Memory alignment in bytes that bf_memsize_dmat rounds up to. */
+#define BF_ALIGN 256
+
+#define BF_ERR_UNSUPPORTED 100000
+
+/* Matrix descriptor: the blasfeo_dmat structure of Appendix A.1.1 with the
+ * members that the panel-major format needs (Sec. 4.3.3).
+ *   pA      device pointer to the first element of the storage; 32-byte
+ *           aligned.
+ *   dA      device pointer to room for min(m, n) doubles that a
+ *           factorization may fill with the inverse of the diagonal
+ *           (Sec. 4.7.1), or NULL.
+ *   m, n    rows and columns of the matrix.
+ *   pm      storage rows: m rounded up to a multiple of ps.
+ *   cn      storage columns, the panel length ("sda" in Sec. 4.3.3), >= n.
+ *   ps      panel height; must equal BF_PS.
+ *   memsize bytes of device memory addressed by the descriptor.
+ * Element (i, j) of the matrix lies at
+ *   pA[(i - i % ps) * cn + j * ps + i % ps]                      (Sec. 4.3.3)
+ */
+typedef struct bf_dmat {
+  double *pA;
+  double *dA;
+  int m;
+  int n;
+  int pm;
+  int cn;
+  int ps;
+  size_t memsize;
+} bf_dmat;
+
+/* ---- memory (Appendix A.1.2, externally provided memory) ----------------- */
+
+/* Bytes of device memory that bf_create_dmat needs for an m x n matrix:
+ * the panel-major storage (pm * cn doubles) followed by the inverse-diagonal
+ * array (min(m, n) doubles), rounded up to a multiple of BF_ALIGN so that
+ * consecutive matrices carved from one buffer stay aligned.  Returns 0 for
+ * negative sizes. */
+size_t bf_memsize_dmat(int m, int n);
+
+/* Fills *sA for an m x n matrix over caller-owned device memory `mem` of at
+ * least bf_memsize_dmat(m, n) bytes, aligned to BF_ALIGN.  Touches neither
+ * the memory nor the device.  Returns 0, or -1/-2/-3/-4 for a bad m, n, sA or
+ * mem (mem must be non-NULL and BF_ALIGN-aligned). */
+int bf_create_dmat(int m, int n, bf_dmat *sA, void *mem);
+
+/* Panel height of this build (BF_PS). */
+int bf_panel_height(void);
+
+/* ---- packing (Sec. 4.3.3; the packing routines of Appendix A.3) ---------- */
+
+/* Copies, for each of `batch` problems, the m x n column-major matrix at
+ * A + b*strideA (device memory, leading dimension lda >= max(1, m)) into the
+ * sub-matrix (bi, bj) of the panel-major matrix sB (problem stride strideB).
+ * Elements of sB outside the sub-matrix are not written. */
+int bf_pack_dmat_batched(int batch, int m, int n, const double *A, int lda, long long strideA,
+                         const bf_dmat *sB, int bi, int bj, long long strideB, void *stream);
+
+/* The inverse copy: sub-matrix (ai, aj) of sA into the column-major B. */
+int bf_unpack_dmat_batched(int batch, int m, int n, const bf_dmat *sA, int ai, int aj,
+                           long long strideA, double *B, int ldb, long long strideB, void *stream);
+
+/* ---- level-3 BLAS ---------------------------------------------------------- */
+
+/* gemm_nt (Appendix A.2.1; Sec. 5.2.2):
+ *     D <- alpha * A * B^T + beta * C
+ * A is m x k, B is n x k, C and D are m x n.  C and D may be the same
+ * sub-matrix of the same storage; no other overlap is allowed.  beta == 0
+ * means C is not read (it may hold NaN).  k == 0 gives D = beta * C.
+ * Any size >= 0 is supported. */
+int bf_dgemm_nt_batched(int batch, int m, int n, int k, double alpha,
+                        const bf_dmat *sA, int ai, int aj, long long strideA,
+                        const bf_dmat *sB, int bi, int bj, long long strideB, double beta,
+                        const bf_dmat *sC, int ci, int cj, long long strideC,
+                        const bf_dmat *sD, int di, int dj, long long strideD, void *stream);
+
+int bf_dgemm_nt(int m, int n, int k, double alpha, const bf_dmat *sA, int ai, int aj,
+                const bf_dmat *sB, int bi, int bj, double beta, const bf_dmat *sC, int ci, int cj,
+                const bf_dmat *sD, int di, int dj, void *stream);
+
+/* syrk_ln (Sec. 5.2.2):
+ *     lower(D) <- alpha * A * B^T + beta * C
+ * A and B are m x k and may be different matrices (or the same); C and D are
+ * m x m.  Only the lower triangle of D, diagonal included, is computed and
+ * written; the strictly upper part of D is left untouched.  C and D may
+ * coincide.  beta == 0 means C is not read. */
+int bf_dsyrk_ln_batched(int batch, int m, int k, double alpha,
+                        const bf_dmat *sA, int ai, int aj, long long strideA,
+                        const bf_dmat *sB, int bi, int bj, long long strideB, double beta,
+                        const bf_dmat *sC, int ci, int cj, long long strideC,
+                        const bf_dmat *sD, int di, int dj, long long strideD, void *stream);
+
+int bf_dsyrk_ln(int m, int k, double alpha, const bf_dmat *sA, int ai, int aj,
+                const bf_dmat *sB, int bi, int bj, double beta, const bf_dmat *sC, int ci, int cj,
+                const bf_dmat *sD, int di, int dj, void *stream);
+
+/* trsm_rltn (Sec. 5.2.2; right, lower, transposed, non-unit):
+ *     D <- alpha * B * L^{-T},  i.e. D = X with X * L^T = alpha * B
+ * L is the n x n lower triangle of sL at (li, lj) (its strictly upper part
+ * is not read); B and D are m x n and may coincide.  If dinv is not NULL it
+ * holds, for problem b, the n values 1/L[j][j] at dinv + b*strideDinv (as
+ * written by bf_dpotrf_l_batched) and the solve uses them instead of
+ * dividing (Sec. 4.7.1).  Supports n <= 4096; any m. */
+int bf_dtrsm_rltn_batched(int batch, int m, int n, double alpha,
+                          const bf_dmat *sL, int li, int lj, long long strideL,
+                          const double *dinv, long long strideDinv,
+                          const bf_dmat *sB, int bi, int bj, long long strideB,
+                          const bf_dmat *sD, int di, int dj, long long strideD, void *stream);
+
+int bf_dtrsm_rltn(int m, int n, double alpha, const bf_dmat *sL, int li, int lj,
+                  const bf_dmat *sB, int bi, int bj, const bf_dmat *sD, int di, int dj,
+                  void *stream);
+
+/* ---- LAPACK-like --------------------------------------------------------- */
+
+/* potrf_l (Sec. 5.2.2; Sec. 4.6):
+ *     lower(D) <- L,  L * L^T = C,  L lower triangular with positive diagonal
+ * C is m x m; only its lower triangle is read.  C and D may coincide.  The
+ * strictly upper part of D is left untouched.
+ * dinv (device, may be NULL): receives 1/L[j][j] for j < m at
+ *   dinv + b*strideDinv (Sec. 4.7.1).
+ * info (device, may be NULL): info[b] = 0 if problem b factorized, else the
+ *   1-based column j+1 of the first pivot that was not > 0 (NaN included);
+ *   columns >= j of that problem's D are then unspecified.  Other problems
+ *   are unaffected.
+ * Supports m <= 512. */
+int bf_dpotrf_l_batched(int batch, int m, const bf_dmat *sC, int ci, int cj, long long strideC,
+                        const bf_dmat *sD, int di, int dj, long long strideD,
+                        double *dinv, long long strideDinv, int *info, void *stream);
+
+int bf_dpotrf_l(int m, const bf_dmat *sC, int ci, int cj, const bf_dmat *sD, int di, int dj,
+                int *info, void *stream);
+
+/* syrk_potrf_ln (Sec. 4.7.2 "concatenating updates/downdates"; Sec. 5.3;
+ * routine list in Appendix A.3):
+ *     lower(D) <- chol(C + A * B^T)
+ * A and B are m x k (may coincide), C and D are m x m (may coincide).  The
+ * sum is formed inside the factorization kernel and never stored.  dinv and
+ * info as for bf_dpotrf_l_batched.  Supports m <= 512. */
+int bf_dsyrk_dpotrf_ln_batched(int batch, int m, int k,
+                               const bf_dmat *sA, int ai, int aj, long long strideA,
+                               const bf_dmat *sB, int bi, int bj, long long strideB,
+                               const bf_dmat *sC, int ci, int cj, long long strideC,
+                               const bf_dmat *sD, int di, int dj, long long strideD,
+                               double *dinv, long long strideDinv, int *info, void *stream);
+
+int bf_dsyrk_dpotrf_ln(int m, int k, const bf_dmat *sA, int ai, int aj,
+                       const bf_dmat *sB, int bi, int bj, const bf_dmat *sC, int ci, int cj,
+                       const bf_dmat *sD, int di, int dj, int *info, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BFGPU_H */

@@ -1,0 +1,192 @@
+"""Batched panel-major FP64 BLAS/LAPACK routines for GB300 (sm_103a).
+
+The routines of BLASFEO's level-3 hot path (gemm_nt, syrk_ln, potrf_l,
+trsm_rltn, syrk_potrf_ln) run as hand-written CUDA kernels in libbfgpu.so,
+behind the C ABI of include/bfgpu.h.  This package is the thin Python side:
+it loads the library (``_abi``), and ``DMatBatch`` keeps a batch of
+panel-major matrices in one torch device tensor and hands its descriptor to
+the C calls.  PyTorch only provides device memory and the current stream.
+
+Every call raises ``BfError`` on a non-zero return code.
+"""
+from __future__ import annotations
+
+import ctypes
+
+from . import _abi
+from ._abi import BF_ALIGN, BF_ERR_UNSUPPORTED, BF_PS, bf_dmat, load
+
+__all__ = [
+    "BF_PS", "BF_ALIGN", "BF_ERR_UNSUPPORTED", "BfError", "DMatBatch", "bf_dmat", "load",
+    "dgemm_nt", "dsyrk_ln", "dpotrf_l", "dtrsm_rltn", "dsyrk_dpotrf_ln", "pack", "unpack",
+]
+
+
+class BfError(RuntimeError):
+    def __init__(self, fn, code):
+        super().__init__(f"{fn} returned {code}")
+        self.code = code
+
+
+def _check(fn, code):
+    if code != 0:
+        raise BfError(fn, code)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class DMatBatch:
+    """``batch`` panel-major m x n FP64 matrices in one device tensor.
+
+    Problem b's matrix starts ``stride`` doubles after problem a-1's; the
+    stride is bf_memsize_dmat(m, n) / 8 so every matrix stays 256-byte
+    aligned, and ``desc`` is the descriptor of problem 0 (the batched C calls
+    take it together with ``stride``).  ``dinv`` views the per-problem
+    inverse-diagonal arrays that the factorizations can fill (Sec. 4.7.1).
+    """
+
+    def __init__(self, batch: int, m: int, n: int, device=None, fill: float | None = None,
+                 tight: bool = False):
+        torch = _torch()
+        lib = load()
+        self.batch, self.m, self.n = int(batch), int(m), int(n)
+        memsize = lib.bf_memsize_dmat(self.m, self.n)
+        pm = -(-self.m // BF_PS) * BF_PS
+        # tight: matrices back to back (16-byte aligned), no inverse-diagonal room
+        self.stride = (pm * self.n + 1) // 2 * 2 if tight else memsize // 8
+        nelem = max(1, self.batch * self.stride) + BF_ALIGN // 8
+        device = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+        raw = torch.empty(nelem, dtype=torch.float64, device=device)
+        off = (-raw.data_ptr() % BF_ALIGN) // 8
+        self._raw = raw
+        self.storage = raw[off:off + max(1, self.batch * self.stride)]
+        if fill is not None:
+            self.storage.fill_(fill)
+        self.desc = bf_dmat()
+        _check("bf_create_dmat", lib.bf_create_dmat(self.m, self.n, ctypes.byref(self.desc),
+                                                    ctypes.c_void_p(self.storage.data_ptr())))
+        if tight:
+            self.desc.dA = None
+        self.pm, self.cn = self.desc.pm, self.desc.cn
+
+    @property
+    def ref(self):
+        return ctypes.byref(self.desc)
+
+    @property
+    def dinv_ptr(self):
+        return ctypes.c_void_p(self.desc.dA) if self.desc.dA else None
+
+    def dinv(self):
+        """(batch, min(m, n)) view of the inverse-diagonal arrays (not for tight batches)."""
+        nd = min(self.m, self.n)
+        base = self.pm * self.cn
+        return self.storage.view(self.batch, self.stride)[:, base:base + nd]
+
+    def panels(self):
+        """(batch, pm*cn) view of the panel-major storage of each matrix."""
+        return self.storage.view(self.batch, self.stride)[:, : self.pm * self.cn]
+
+    @classmethod
+    def from_colmajor(cls, X, device=None, stream=None, tight: bool = False):
+        """Pack a (batch, m, n) float64 tensor (any device) into panel-major."""
+        torch = _torch()
+        bt, m, n = X.shape
+        out = cls(bt, m, n, device=device, fill=0.0, tight=tight)
+        cm = X.to(device=out.storage.device, dtype=torch.float64).transpose(1, 2).contiguous()
+        pack(cm, out, stream=stream)
+        return out
+
+    def to_colmajor(self, stream=None):
+        """Unpack into a new (batch, m, n) float64 device tensor."""
+        torch = _torch()
+        cm = torch.empty(self.batch, self.n, self.m, dtype=torch.float64, device=self.storage.device)
+        unpack(self, cm, stream=stream)
+        return cm.transpose(1, 2)
+
+
+def pack(cm, dst: DMatBatch, bi: int = 0, bj: int = 0, stream=None, m=None, n=None):
+    """cm: (batch, n, m) contiguous device tensor holding column-major m x n matrices."""
+    lib = load()
+    bt = cm.shape[0]
+    m = cm.shape[2] if m is None else m
+    n = cm.shape[1] if n is None else n
+    _check("bf_pack_dmat_batched", lib.bf_pack_dmat_batched(
+        bt, m, n, ctypes.c_void_p(cm.data_ptr()), cm.shape[2], cm.shape[1] * cm.shape[2],
+        dst.ref, bi, bj, dst.stride, _stream(stream)))
+
+
+def unpack(src: DMatBatch, cm, ai: int = 0, aj: int = 0, stream=None, m=None, n=None):
+    lib = load()
+    bt = cm.shape[0]
+    m = cm.shape[2] if m is None else m
+    n = cm.shape[1] if n is None else n
+    _check("bf_unpack_dmat_batched", lib.bf_unpack_dmat_batched(
+        bt, m, n, src.ref, ai, aj, src.stride, ctypes.c_void_p(cm.data_ptr()), cm.shape[2],
+        cm.shape[1] * cm.shape[2], _stream(stream)))
+
+
+def _op(X: DMatBatch | None, i=0, j=0):
+    if X is None:
+        return (None, 0, 0, 0)
+    return (X.ref, i, j, X.stride)
+
+
+def dgemm_nt(m, n, k, alpha, A, ai, aj, B, bi, bj, beta, C, ci, cj, D, di, dj, batch=None,
+             stream=None):
+    """D <- alpha * A * B^T + beta * C over the batch (bf_dgemm_nt_batched)."""
+    batch = D.batch if batch is None else batch
+    _check("bf_dgemm_nt_batched", load().bf_dgemm_nt_batched(
+        batch, m, n, k, alpha, *_op(A, ai, aj), *_op(B, bi, bj), beta, *_op(C, ci, cj),
+        *_op(D, di, dj), _stream(stream)))
+
+
+def dsyrk_ln(m, k, alpha, A, ai, aj, B, bi, bj, beta, C, ci, cj, D, di, dj, batch=None, stream=None):
+    """lower(D) <- alpha * A * B^T + beta * C (bf_dsyrk_ln_batched)."""
+    batch = D.batch if batch is None else batch
+    _check("bf_dsyrk_ln_batched", load().bf_dsyrk_ln_batched(
+        batch, m, k, alpha, *_op(A, ai, aj), *_op(B, bi, bj), beta, *_op(C, ci, cj),
+        *_op(D, di, dj), _stream(stream)))
+
+
+def dpotrf_l(m, C, ci, cj, D, di, dj, dinv=True, info=None, batch=None, stream=None):
+    """lower(D) <- chol(C) (bf_dpotrf_l_batched).  dinv=True stores 1/L_jj in D's
+    inverse-diagonal arrays; info: optional int32 device tensor of length batch."""
+    batch = D.batch if batch is None else batch
+    dptr = D.dinv_ptr if dinv else None
+    _check("bf_dpotrf_l_batched", load().bf_dpotrf_l_batched(
+        batch, m, *_op(C, ci, cj), *_op(D, di, dj), dptr, D.stride if dptr else 0,
+        ctypes.c_void_p(info.data_ptr()) if info is not None else None, _stream(stream)))
+
+
+def dsyrk_dpotrf_ln(m, k, A, ai, aj, B, bi, bj, C, ci, cj, D, di, dj, dinv=True, info=None,
+                    batch=None, stream=None):
+    """lower(D) <- chol(C + A * B^T) (bf_dsyrk_dpotrf_ln_batched)."""
+    batch = D.batch if batch is None else batch
+    dptr = D.dinv_ptr if dinv else None
+    _check("bf_dsyrk_dpotrf_ln_batched", load().bf_dsyrk_dpotrf_ln_batched(
+        batch, m, k, *_op(A, ai, aj), *_op(B, bi, bj), *_op(C, ci, cj), *_op(D, di, dj),
+        dptr, D.stride if dptr else 0,
+        ctypes.c_void_p(info.data_ptr()) if info is not None else None, _stream(stream)))
+
+
+def dtrsm_rltn(m, n, alpha, L, li, lj, B, bi, bj, D, di, dj, use_dinv=False, batch=None,
+               stream=None):
+    """D <- alpha * B * L^{-T} (bf_dtrsm_rltn_batched).  use_dinv: take 1/L_jj from
+    L's inverse-diagonal arrays (filled by a previous factorization)."""
+    batch = D.batch if batch is None else batch
+    dptr = L.dinv_ptr if use_dinv else None
+    if dptr is not None and (li != 0 or lj != 0):
+        raise ValueError("use_dinv needs the factor at offset (0, 0)")
+    _check("bf_dtrsm_rltn_batched", load().bf_dtrsm_rltn_batched(
+        batch, m, n, alpha, *_op(L, li, lj), dptr, L.stride if dptr else 0, *_op(B, bi, bj),
+        *_op(D, di, dj), _stream(stream)))

@@ -1,0 +1,295 @@
+// The C ABI of include/bfgpu.h: argument checking (the argument checks the
+// paper mentions for its wrapper implementation, Sec. 3.1) and dispatch to
+// the kernels.  Nothing here allocates memory or synchronizes.
+#include <cstdint>
+#include <initializer_list>
+
+#include "bf_internal.cuh"
+
+using namespace bf;
+
+namespace {
+
+inline bool aligned_to(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+// Checks one matrix operand of a batched call.  Returns 0 if valid, else
+// 1 (descriptor), 2 (row offset), 3 (column offset) or 4 (stride).
+int check_op(const bf_dmat *s, int ri, int cj, int rows, int cols, long long stride, int batch,
+             bool output) {
+  if (!s || s->ps != PS || !s->pA || !aligned_to(s->pA, 8) || s->m < 0 || s->n < 0 ||
+      s->pm < s->m || s->pm % PS != 0 || s->cn < s->n)
+    return 1;
+  if (ri < 0 || ri + rows > s->m) return 2;
+  if (cj < 0 || cj + cols > s->n) return 3;
+  if (stride < 0) return 4;
+  if (output && batch > 1 && stride < (long long)s->pm * s->cn) return 4;
+  return 0;
+}
+
+inline int pos_err(int which, int desc_pos) { return -(desc_pos + which - 1); }
+
+Op make_op(const bf_dmat *s, int ri, int cj, long long stride) {
+  Op o;
+  o.p = s ? s->pA : nullptr;
+  o.stride = stride;
+  o.cn = s ? s->cn : 0;
+  o.i0 = ri;
+  o.j0 = cj;
+  return o;
+}
+
+OpW make_opw(const bf_dmat *s, int ri, int cj, long long stride) {
+  OpW o;
+  o.p = s->pA;
+  o.stride = stride;
+  o.cn = s->cn;
+  o.i0 = ri;
+  o.j0 = cj;
+  return o;
+}
+
+// The vector-load fast path needs every operand's rows to start on a panel
+// top and every problem to start 16-byte aligned.
+bool fast_path(std::initializer_list<const Op *> ops) {
+  for (const Op *o : ops) {
+    if (!o->p) continue;
+    if ((o->i0 % PS) != 0 || (o->stride % 2) != 0 || !aligned_to(o->p, 16)) return false;
+  }
+  return true;
+}
+
+inline int status(cudaError_t e) { return e == cudaSuccess ? 0 : (int)e; }
+
+}  // namespace
+
+extern "C" {
+
+size_t bf_memsize_dmat(int m, int n) {
+  if (m < 0 || n < 0) return 0;
+  const size_t pm = ((size_t)m + PS - 1) / PS * PS;
+  const size_t cn = (size_t)n;
+  const size_t nd = (size_t)(m < n ? m : n);
+  const size_t bytes = (pm * cn + nd) * sizeof(double);
+  return (bytes + BF_ALIGN - 1) / BF_ALIGN * BF_ALIGN;
+}
+
+int bf_create_dmat(int m, int n, bf_dmat *sA, void *mem) {
+  if (m < 0) return -1;
+  if (n < 0) return -2;
+  if (!sA) return -3;
+  if (!mem || !aligned_to(mem, BF_ALIGN)) return -4;
+  const int pm = (m + PS - 1) / PS * PS;
+  sA->pA = (double *)mem;
+  sA->dA = (m < n ? m : n) > 0 ? (double *)mem + (size_t)pm * n : nullptr;
+  sA->m = m;
+  sA->n = n;
+  sA->pm = pm;
+  sA->cn = n;
+  sA->ps = PS;
+  sA->memsize = bf_memsize_dmat(m, n);
+  return 0;
+}
+
+int bf_panel_height(void) { return PS; }
+
+int bf_pack_dmat_batched(int batch, int m, int n, const double *A, int lda, long long strideA,
+                         const bf_dmat *sB, int bi, int bj, long long strideB, void *stream) {
+  if (batch < 0) return -1;
+  if (m < 0) return -2;
+  if (n < 0) return -3;
+  if (batch == 0 || m == 0 || n == 0) return 0;
+  if (!A || !aligned_to(A, 8)) return -4;
+  if (lda < m) return -5;
+  if (strideA < 0) return -6;
+  if (int w = check_op(sB, bi, bj, m, n, strideB, batch, true)) return pos_err(w, 7);
+  return status(launch_pack(batch, m, n, A, lda, strideA, make_opw(sB, bi, bj, strideB),
+                            (cudaStream_t)stream));
+}
+
+int bf_unpack_dmat_batched(int batch, int m, int n, const bf_dmat *sA, int ai, int aj,
+                           long long strideA, double *B, int ldb, long long strideB, void *stream) {
+  if (batch < 0) return -1;
+  if (m < 0) return -2;
+  if (n < 0) return -3;
+  if (batch == 0 || m == 0 || n == 0) return 0;
+  if (int w = check_op(sA, ai, aj, m, n, strideA, batch, false)) return pos_err(w, 4);
+  if (!B || !aligned_to(B, 8)) return -8;
+  if (ldb < m) return -9;
+  if (strideB < 0 || (batch > 1 && strideB < (long long)ldb * n)) return -10;
+  return status(launch_unpack(batch, m, n, make_op(sA, ai, aj, strideA), B, ldb, strideB,
+                              (cudaStream_t)stream));
+}
+
+// ---------------------------------------------------------------- gemm / syrk
+
+static int gemm_like(bool syrk, int batch, int m, int n, int k, double alpha, const bf_dmat *sA,
+                     int ai, int aj, long long strideA, const bf_dmat *sB, int bi, int bj,
+                     long long strideB, double beta, const bf_dmat *sC, int ci, int cj,
+                     long long strideC, const bf_dmat *sD, int di, int dj, long long strideD,
+                     void *stream) {
+  // argument positions differ by one between gemm (m, n, k) and syrk (m, k)
+  const int sh = syrk ? -1 : 0;
+  if (batch < 0) return -1;
+  if (m < 0) return -2;
+  if (n < 0) return -3;
+  if (k < 0) return -(4 + sh);
+  if (batch == 0 || m == 0 || n == 0) return 0;
+  if (k > 0) {
+    if (int w = check_op(sA, ai, aj, m, k, strideA, batch, false)) return pos_err(w, 6 + sh);
+    if (int w = check_op(sB, bi, bj, n, k, strideB, batch, false)) return pos_err(w, 10 + sh);
+  }
+  if (beta != 0.0)
+    if (int w = check_op(sC, ci, cj, m, n, strideC, batch, false)) return pos_err(w, 15 + sh);
+  if (int w = check_op(sD, di, dj, m, n, strideD, batch, true)) return pos_err(w, 19 + sh);
+  const Op A = make_op(k > 0 ? sA : nullptr, ai, aj, strideA);
+  const Op B = make_op(k > 0 ? sB : nullptr, bi, bj, strideB);
+  const Op C = make_op(beta != 0.0 ? sC : nullptr, ci, cj, strideC);
+  const OpW D = make_opw(sD, di, dj, strideD);
+  const Op Dr = make_op(sD, di, dj, strideD);
+  const bool fast = fast_path({&A, &B, &C, &Dr});
+  return status(launch_gemm_nt(syrk, batch, m, n, k, alpha, A, B, beta, C, D, fast,
+                               (cudaStream_t)stream));
+}
+
+int bf_dgemm_nt_batched(int batch, int m, int n, int k, double alpha, const bf_dmat *sA, int ai,
+                        int aj, long long strideA, const bf_dmat *sB, int bi, int bj,
+                        long long strideB, double beta, const bf_dmat *sC, int ci, int cj,
+                        long long strideC, const bf_dmat *sD, int di, int dj, long long strideD,
+                        void *stream) {
+  return gemm_like(false, batch, m, n, k, alpha, sA, ai, aj, strideA, sB, bi, bj, strideB, beta,
+                   sC, ci, cj, strideC, sD, di, dj, strideD, stream);
+}
+
+int bf_dgemm_nt(int m, int n, int k, double alpha, const bf_dmat *sA, int ai, int aj,
+                const bf_dmat *sB, int bi, int bj, double beta, const bf_dmat *sC, int ci, int cj,
+                const bf_dmat *sD, int di, int dj, void *stream) {
+  const int r = bf_dgemm_nt_batched(1, m, n, k, alpha, sA, ai, aj, 0, sB, bi, bj, 0, beta, sC,
+                                    ci, cj, 0, sD, di, dj, 0, stream);
+  // map batched argument positions back to this signature
+  if (r >= 0) return r;
+  static const int map[24] = {0, 0, 1, 2, 3, 4, 5, 6, 7, 0, 8, 9, 10, 0, 11, 12, 13, 14, 0, 15, 16, 17, 0, 18};
+  return -map[-r];
+}
+
+int bf_dsyrk_ln_batched(int batch, int m, int k, double alpha, const bf_dmat *sA, int ai, int aj,
+                        long long strideA, const bf_dmat *sB, int bi, int bj, long long strideB,
+                        double beta, const bf_dmat *sC, int ci, int cj, long long strideC,
+                        const bf_dmat *sD, int di, int dj, long long strideD, void *stream) {
+  if (batch < 0) return -1;
+  if (m < 0) return -2;
+  if (k < 0) return -3;
+  return gemm_like(true, batch, m, m, k, alpha, sA, ai, aj, strideA, sB, bi, bj, strideB, beta, sC,
+                   ci, cj, strideC, sD, di, dj, strideD, stream);
+}
+
+int bf_dsyrk_ln(int m, int k, double alpha, const bf_dmat *sA, int ai, int aj, const bf_dmat *sB,
+                int bi, int bj, double beta, const bf_dmat *sC, int ci, int cj, const bf_dmat *sD,
+                int di, int dj, void *stream) {
+  const int r = bf_dsyrk_ln_batched(1, m, k, alpha, sA, ai, aj, 0, sB, bi, bj, 0, beta, sC, ci, cj,
+                                    0, sD, di, dj, 0, stream);
+  if (r >= 0) return r;
+  static const int map[23] = {0, 0, 1, 2, 3, 4, 5, 6, 0, 7, 8, 9, 0, 10, 11, 12, 13, 0, 14, 15, 16, 0, 17};
+  return -map[-r];
+}
+
+// ------------------------------------------------------------------ trsm
+
+int bf_dtrsm_rltn_batched(int batch, int m, int n, double alpha, const bf_dmat *sL, int li, int lj,
+                          long long strideL, const double *dinv, long long strideDinv,
+                          const bf_dmat *sB, int bi, int bj, long long strideB, const bf_dmat *sD,
+                          int di, int dj, long long strideD, void *stream) {
+  if (batch < 0) return -1;
+  if (m < 0) return -2;
+  if (n < 0) return -3;
+  if (batch == 0 || m == 0 || n == 0) return 0;
+  if (n > TRSM_MAX_N) return BF_ERR_UNSUPPORTED;
+  if (int w = check_op(sL, li, lj, n, n, strideL, batch, false)) return pos_err(w, 5);
+  if (dinv && !aligned_to(dinv, 8)) return -9;
+  if (strideDinv < 0 || (dinv && batch > 1 && strideDinv < n && strideDinv != 0)) return -10;
+  if (int w = check_op(sB, bi, bj, m, n, strideB, batch, false)) return pos_err(w, 11);
+  if (int w = check_op(sD, di, dj, m, n, strideD, batch, true)) return pos_err(w, 15);
+  return status(launch_trsm_rltn(batch, m, n, alpha, make_op(sL, li, lj, strideL), dinv,
+                                 strideDinv, make_op(sB, bi, bj, strideB),
+                                 make_opw(sD, di, dj, strideD), (cudaStream_t)stream));
+}
+
+int bf_dtrsm_rltn(int m, int n, double alpha, const bf_dmat *sL, int li, int lj, const bf_dmat *sB,
+                  int bi, int bj, const bf_dmat *sD, int di, int dj, void *stream) {
+  const int r = bf_dtrsm_rltn_batched(1, m, n, alpha, sL, li, lj, 0, nullptr, 0, sB, bi, bj, 0, sD,
+                                      di, dj, 0, stream);
+  if (r >= 0) return r;
+  static const int map[19] = {0, 0, 1, 2, 3, 4, 5, 6, 0, 0, 0, 7, 8, 9, 0, 10, 11, 12, 0};
+  return -map[-r];
+}
+
+// -------------------------------------------------------- potrf / syrk_potrf
+
+static int chol_like(bool fused, int batch, int m, int k, const bf_dmat *sA, int ai, int aj,
+                     long long strideA, const bf_dmat *sB, int bi, int bj, long long strideB,
+                     const bf_dmat *sC, int ci, int cj, long long strideC, const bf_dmat *sD,
+                     int di, int dj, long long strideD, double *dinv, long long strideDinv,
+                     int *info, void *stream, int posC) {
+  // posC: argument position of sC; the rest of the positions follow it
+  if (batch == 0 || m == 0) return 0;
+  if (m > CHOL_MAX_N) return BF_ERR_UNSUPPORTED;
+  if (fused && k > 0) {
+    if (int w = check_op(sA, ai, aj, m, k, strideA, batch, false)) return pos_err(w, 4);
+    if (int w = check_op(sB, bi, bj, m, k, strideB, batch, false)) return pos_err(w, 8);
+  }
+  if (int w = check_op(sC, ci, cj, m, m, strideC, batch, false)) return pos_err(w, posC);
+  if (int w = check_op(sD, di, dj, m, m, strideD, batch, true)) return pos_err(w, posC + 4);
+  if (dinv && !aligned_to(dinv, 8)) return -(posC + 8);
+  if (strideDinv < 0 || (dinv && batch > 1 && strideDinv < m)) return -(posC + 9);
+  if (info && !aligned_to(info, 4)) return -(posC + 10);
+  const Op A = make_op(fused && k > 0 ? sA : nullptr, ai, aj, strideA);
+  const Op B = make_op(fused && k > 0 ? sB : nullptr, bi, bj, strideB);
+  const Op C = make_op(sC, ci, cj, strideC);
+  const OpW D = make_opw(sD, di, dj, strideD);
+  const Op Dr = make_op(sD, di, dj, strideD);
+  const bool fast = fast_path({&A, &B, &C, &Dr});
+  return status(launch_chol(fused && k > 0, batch, m, k, A, B, C, D, dinv, strideDinv, info, fast,
+                            (cudaStream_t)stream));
+}
+
+int bf_dpotrf_l_batched(int batch, int m, const bf_dmat *sC, int ci, int cj, long long strideC,
+                        const bf_dmat *sD, int di, int dj, long long strideD, double *dinv,
+                        long long strideDinv, int *info, void *stream) {
+  if (batch < 0) return -1;
+  if (m < 0) return -2;
+  return chol_like(false, batch, m, 0, nullptr, 0, 0, 0, nullptr, 0, 0, 0, sC, ci, cj, strideC, sD,
+                   di, dj, strideD, dinv, strideDinv, info, stream, 3);
+}
+
+int bf_dpotrf_l(int m, const bf_dmat *sC, int ci, int cj, const bf_dmat *sD, int di, int dj,
+                int *info, void *stream) {
+  const int r = bf_dpotrf_l_batched(1, m, sC, ci, cj, 0, sD, di, dj, 0, sD ? sD->dA : nullptr, 0,
+                                    info, stream);
+  if (r >= 0) return r;
+  static const int map[14] = {0, 0, 1, 2, 3, 4, 0, 5, 6, 7, 0, 5, 0, 8};
+  return -map[-r];
+}
+
+int bf_dsyrk_dpotrf_ln_batched(int batch, int m, int k, const bf_dmat *sA, int ai, int aj,
+                               long long strideA, const bf_dmat *sB, int bi, int bj,
+                               long long strideB, const bf_dmat *sC, int ci, int cj,
+                               long long strideC, const bf_dmat *sD, int di, int dj,
+                               long long strideD, double *dinv, long long strideDinv, int *info,
+                               void *stream) {
+  if (batch < 0) return -1;
+  if (m < 0) return -2;
+  if (k < 0) return -3;
+  return chol_like(true, batch, m, k, sA, ai, aj, strideA, sB, bi, bj, strideB, sC, ci, cj, strideC,
+                   sD, di, dj, strideD, dinv, strideDinv, info, stream, 12);
+}
+
+int bf_dsyrk_dpotrf_ln(int m, int k, const bf_dmat *sA, int ai, int aj, const bf_dmat *sB, int bi,
+                       int bj, const bf_dmat *sC, int ci, int cj, const bf_dmat *sD, int di, int dj,
+                       int *info, void *stream) {
+  const int r = bf_dsyrk_dpotrf_ln_batched(1, m, k, sA, ai, aj, 0, sB, bi, bj, 0, sC, ci, cj, 0, sD,
+                                           di, dj, 0, sD ? sD->dA : nullptr, 0, info, stream);
+  if (r >= 0) return r;
+  static const int map[23] = {0, 0, 1, 2, 3, 4, 5, 0, 6, 7, 8, 0, 9, 10, 11, 0, 12, 13, 14, 0, 12, 0, 15};
+  return -map[-r];
+}
+
+}  // extern "C"

@@ -1,0 +1,435 @@
+// potrf_l and the fused syrk_potrf_ln, batched, FP64, panel-major operands.
+//
+// potrf_l (Sec. 5.2.2, Sec. 4.6):         lower(D) <- chol(C)
+// syrk_potrf_ln (Sec. 4.7.2, Sec. 5.3):   lower(D) <- chol(C + A * B^T)
+//
+// The paper builds the factorization from kernels on register-resident
+// blocks, keeps 1/L[j][j] for later solves (Sec. 4.7.1) and, for
+// syrk_potrf, adds the A*B^T update inside the same kernel so that the sum is
+// never stored and reloaded (Sec. 4.7.2).  Both ideas carry over; what
+// changes on GB300 is where the lanes go.  A warp-wide FP64 instruction costs
+// the same with 1 or 32 active lanes, and the per-column square root and
+// reciprocal cost several FMAs each, so the sequential part of a small
+// Cholesky must be shared by many problems at once.  Two kernels:
+//
+//  k_chol_small (n <= 64): a warp holds Q = 32/G problems, G lanes per
+//    problem.  The lower triangles live packed in shared memory, problem q's
+//    element e at sm[e*Q + q].  The factorization runs column by column
+//    (Cholesky-Crout); the pivot's rsqrt is one warp instruction for all Q
+//    problems.  For syrk_potrf the A*B^T sum is added in 4x4 register blocks
+//    straight into the shared-memory triangle before the factorization.
+//
+//  k_chol_rows (n <= 512): one CTA per problem, one thread per row, blocks of
+//    up to 32 columns held in registers.  For block column [c0, c0+W):
+//      (a) acc = C[i][c0..]  (+ A[i][:] * B[c0..][:]^T for syrk_potrf)
+//      (b) acc -= L[i][0:c0] * L[c0..][0:c0]^T            (gemm_nt downdate)
+//      (c) the warp of rows c0..c0+31 factors the diagonal block in
+//          registers with warp shuffles (potrf_l kernel on a register block)
+//      (d) the rows below solve against it (trsm_rltn kernel)
+//    The operand rows shared by all threads, B[c0..][l..] and L[c0..][l..],
+//    are staged 32 columns at a time in shared memory and read as broadcasts.
+//
+// Non-SPD input: the first column j whose pivot is not > 0 (NaN included)
+// sets info = j+1; the arithmetic continues on NaNs without branching, so the
+// columns >= j are unspecified and no other problem is affected.
+#include "bf_internal.cuh"
+
+namespace bf {
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ void tri_index(int t, int &tr, int &tc) {
+  int r = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+  while (r * (r + 1) / 2 > t) r--;
+  while ((r + 1) * (r + 2) / 2 <= t) r++;
+  tr = r;
+  tc = t - r * (r + 1) / 2;
+}
+
+// packed lower column-major: column l starts at cs(l); element (i, l) at cs(l) + i
+__device__ __forceinline__ int col_start(int l, int n) { return (l * (2 * n - l + 1)) / 2 - l; }
+
+// ---------------------------------------------------------------------------
+// k_chol_small
+// ---------------------------------------------------------------------------
+template <int G, bool FUSED, bool ALIGNED>
+__global__ void __launch_bounds__(32)
+k_chol_small(int batch, int n, int k, Op A, Op B, Op C, OpW D, double *dinv, long long sdinv,
+             int *info) {
+  constexpr int Q = 32 / G;
+  extern __shared__ double sm[];
+  const int lane = threadIdx.x;
+  const int q = lane / G, s = lane % G;
+  const int b0 = blockIdx.x * Q;
+  const int b = b0 + q;
+  const bool valid = b < batch;
+
+  // ---- phase 1: lower triangle of C into shared memory (whole warp per problem)
+  for (int qq = 0; qq < Q; qq++) {
+    const int bb = b0 + qq;
+    if (bb >= batch) break;
+    const double *pc = C.p + bb * C.stride;
+    if (ALIGNED) {
+      for (int p = 0; p * PS < n; p++) {
+        const int ncol = min(n, p * PS + PS);
+        const double *pp = pc + (long long)(C.i0 + p * PS) * C.cn + (long long)C.j0 * PS;
+        for (int x = lane; x < ncol * PS; x += 32) {
+          const int j = x / PS, i = p * PS + (x % PS);
+          if (i < n && i >= j) sm[(col_start(j, n) + i) * Q + qq] = pp[x];
+        }
+      }
+    } else {
+      for (int x = lane; x < n * n; x += 32) {
+        const int j = x / n, i = x - j * n;
+        if (i >= j) sm[(col_start(j, n) + i) * Q + qq] = pc[pm_off(C.i0 + i, C.j0 + j, C.cn)];
+      }
+    }
+  }
+  __syncwarp();
+
+  // ---- syrk_potrf: add A*B^T in 4x4 register blocks of the lower block triangle
+  if (FUSED && valid) {
+    const double *pa = A.p + b * A.stride;
+    const double *pb = B.p + b * B.stride;
+    const int TR = (n + 3) / 4;
+    const int ntiles = TR * (TR + 1) / 2;
+    for (int t = s; t < ntiles; t += G) {
+      int tr, tc;
+      tri_index(t, tr, tc);
+      const int i0 = tr * 4, j0 = tc * 4;
+      double acc[4][4];
+#pragma unroll
+      for (int r = 0; r < 4; r++)
+#pragma unroll
+        for (int c = 0; c < 4; c++) acc[r][c] = 0.0;
+      if (ALIGNED) {
+        const double *ap = pa + (long long)(A.i0 + i0) * A.cn + (long long)A.j0 * PS;
+        const double *bp = pb + (long long)(B.i0 + j0) * B.cn + (long long)B.j0 * PS;
+#pragma unroll 4
+        for (int l = 0; l < k; l++) {
+          const double2 a01 = __ldg((const double2 *)(ap + l * PS));
+          const double2 a23 = __ldg((const double2 *)(ap + l * PS + 2));
+          const double2 b01 = __ldg((const double2 *)(bp + l * PS));
+          const double2 b23 = __ldg((const double2 *)(bp + l * PS + 2));
+          const double av[4] = {a01.x, a01.y, a23.x, a23.y};
+          const double bv[4] = {b01.x, b01.y, b23.x, b23.y};
+#pragma unroll
+          for (int r = 0; r < 4; r++)
+#pragma unroll
+            for (int c = 0; c < 4; c++) acc[r][c] = fma(av[r], bv[c], acc[r][c]);
+        }
+      } else {
+        const double *ar[4], *br[4];
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+          ar[r] = pa + pm_off(A.i0 + min(i0 + r, n - 1), A.j0, A.cn);
+          br[r] = pb + pm_off(B.i0 + min(j0 + r, n - 1), B.j0, B.cn);
+        }
+        for (int l = 0; l < k; l++) {
+          double av[4], bv[4];
+#pragma unroll
+          for (int r = 0; r < 4; r++) {
+            av[r] = __ldg(ar[r] + l * PS);
+            bv[r] = __ldg(br[r] + l * PS);
+          }
+#pragma unroll
+          for (int r = 0; r < 4; r++)
+#pragma unroll
+            for (int c = 0; c < 4; c++) acc[r][c] = fma(av[r], bv[c], acc[r][c]);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < 4; r++)
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+          const int i = i0 + r, j = j0 + c;
+          if (i < n && i >= j) sm[(col_start(j, n) + i) * Q + q] += acc[r][c];
+        }
+    }
+  }
+  __syncwarp();
+
+  // ---- phase 2: Cholesky-Crout, column by column; row i belongs to sub-lane i % G
+  int first_bad = 0;
+  for (int j = 0; j < n; j++) {
+    const int cj = col_start(j, n);
+    const int istart = j + ((s - (j % G)) + G) % G;
+    double dval = 0.0;
+    int i = istart;
+    // four rows at a time share the loads of row j
+    for (; i + 3 * G < n; i += 4 * G) {
+      double a0 = sm[(cj + i) * Q + q], a1 = sm[(cj + i + G) * Q + q];
+      double a2 = sm[(cj + i + 2 * G) * Q + q], a3 = sm[(cj + i + 3 * G) * Q + q];
+      int cl = 0;
+      for (int l = 0; l < j; l++) {
+        const double ljl = sm[(cl + j) * Q + q];
+        a0 = fma(-sm[(cl + i) * Q + q], ljl, a0);
+        a1 = fma(-sm[(cl + i + G) * Q + q], ljl, a1);
+        a2 = fma(-sm[(cl + i + 2 * G) * Q + q], ljl, a2);
+        a3 = fma(-sm[(cl + i + 3 * G) * Q + q], ljl, a3);
+        cl += n - l - 1;
+      }
+      if (i == j) dval = a0;
+      sm[(cj + i) * Q + q] = a0;
+      sm[(cj + i + G) * Q + q] = a1;
+      sm[(cj + i + 2 * G) * Q + q] = a2;
+      sm[(cj + i + 3 * G) * Q + q] = a3;
+    }
+    for (; i < n; i += G) {
+      double a0 = sm[(cj + i) * Q + q];
+      int cl = 0;
+      for (int l = 0; l < j; l++) {
+        a0 = fma(-sm[(cl + i) * Q + q], sm[(cl + j) * Q + q], a0);
+        cl += n - l - 1;
+      }
+      if (i == j) dval = a0;
+      sm[(cj + i) * Q + q] = a0;
+    }
+    // pivot of problem q comes from its sub-lane that owns row j
+    const double d = (G == 1) ? dval : __shfl_sync(FULL, dval, q * G + (j % G));
+    const double r = rsqrt(d);
+    if (!(d > 0.0) && first_bad == 0) first_bad = j + 1;
+    for (int ii = istart; ii < n; ii += G) {
+      if (ii == j)
+        sm[(cj + ii) * Q + q] = d * r;
+      else
+        sm[(cj + ii) * Q + q] *= r;
+    }
+    if (dinv && valid && s == (j % G)) dinv[b * sdinv + j] = r;
+    __syncwarp();
+  }
+
+  // ---- phase 3: lower triangle back to D (whole warp per problem)
+  for (int qq = 0; qq < Q; qq++) {
+    const int bb = b0 + qq;
+    if (bb >= batch) break;
+    double *pd = D.p + bb * D.stride;
+    if (ALIGNED) {
+      for (int p = 0; p * PS < n; p++) {
+        const int ncol = min(n, p * PS + PS);
+        double *pp = pd + (long long)(D.i0 + p * PS) * D.cn + (long long)D.j0 * PS;
+        for (int x = lane; x < ncol * PS; x += 32) {
+          const int j = x / PS, i = p * PS + (x % PS);
+          if (i < n && i >= j) pp[x] = sm[(col_start(j, n) + i) * Q + qq];
+        }
+      }
+    } else {
+      for (int x = lane; x < n * n; x += 32) {
+        const int j = x / n, i = x - j * n;
+        if (i >= j) pd[pm_off(D.i0 + i, D.j0 + j, D.cn)] = sm[(col_start(j, n) + i) * Q + qq];
+      }
+    }
+  }
+  if (info && valid && s == 0) info[b] = first_bad;
+}
+
+// ---------------------------------------------------------------------------
+// k_chol_rows
+// ---------------------------------------------------------------------------
+constexpr int KC = 32;  // columns per staged chunk
+
+struct RowsSmem {
+  double stage[KC][34];  // stage[ll][jj]: row c0+jj, column l0+ll of the shared operand
+                         // (even pitch: pairs (jj, jj+1) are read as one 16-byte load)
+  double Ls[32][33];     // diagonal block of L: Ls[jj][j]
+  double rinv[32];
+  int bad;
+};
+
+template <int W, bool FUSED, bool ALIGNED>
+__device__ __forceinline__ void rows_block(RowsSmem &S, int c0, int n, int k, const double *pa,
+                                           const double *pb, const double *pc, double *pd, Op A,
+                                           Op B, Op C, OpW D, double *dinv_b) {
+  const int i = threadIdx.x;
+  const int T = blockDim.x;
+  const int w = min(32, n - c0);
+  const bool active = (i < n) && (i >= c0);
+  double acc[W];
+
+  // (a) C[i][c0 + jj] for the lower part of the block column
+#pragma unroll
+  for (int jj = 0; jj < W; jj++) {
+    const int col = c0 + jj;
+    acc[jj] = (active && jj < w && i >= col) ? pc[pm_off(C.i0 + i, C.j0 + col, C.cn)] : 0.0;
+  }
+
+  // (a') syrk_potrf: += A[i][:] * B[c0..c0+w)[:]^T, B rows staged per chunk
+  if (FUSED) {
+    const double *arow = pa + pm_off(A.i0 + min(i, n - 1), A.j0, A.cn);
+    for (int l0 = 0; l0 < k; l0 += KC) {
+      const int kc = min(KC, k - l0);
+      __syncthreads();
+      for (int x = i; x < 32 * KC; x += T) {
+        const int r4 = x % PS, ll = (x / PS) % KC, pnl = x / (PS * KC);
+        const int jj = pnl * PS + r4;
+        S.stage[ll][jj] = (jj < w && ll < kc) ? __ldg(pb + pm_off(B.i0 + c0 + jj, B.j0 + l0 + ll, B.cn)) : 0.0;
+      }
+      __syncthreads();
+      if (active) {
+        for (int ll = 0; ll < kc; ll++) {
+          const double x = __ldg(arow + (long long)(l0 + ll) * PS);
+#pragma unroll
+          for (int jj = 0; jj < W; jj += 2) {
+            const double2 bv = *(const double2 *)&S.stage[ll][jj];
+            acc[jj] = fma(x, bv.x, acc[jj]);
+            if (jj + 1 < W) acc[jj + 1] = fma(x, bv.y, acc[jj + 1]);
+          }
+        }
+      }
+    }
+  }
+
+  // (b) downdate with the columns of L already computed: -= L[i][0:c0] L[c0..][0:c0]^T
+  {
+    const double *lrow = pd + pm_off(D.i0 + min(i, n - 1), D.j0, D.cn);
+    for (int l0 = 0; l0 < c0; l0 += KC) {
+      __syncthreads();
+      for (int x = i; x < 32 * KC; x += T) {
+        const int r4 = x % PS, ll = (x / PS) % KC, pnl = x / (PS * KC);
+        const int jj = pnl * PS + r4;
+        S.stage[ll][jj] = (jj < w) ? pd[pm_off(D.i0 + c0 + jj, D.j0 + l0 + ll, D.cn)] : 0.0;
+      }
+      __syncthreads();
+      if (active) {
+#pragma unroll 2
+        for (int ll = 0; ll < KC; ll++) {
+          const double x = lrow[(long long)(l0 + ll) * PS];
+#pragma unroll
+          for (int jj = 0; jj < W; jj += 2) {
+            const double2 lv = *(const double2 *)&S.stage[ll][jj];
+            acc[jj] = fma(-x, lv.x, acc[jj]);
+            if (jj + 1 < W) acc[jj + 1] = fma(-x, lv.y, acc[jj + 1]);
+          }
+        }
+      }
+    }
+  }
+
+  // (c) diagonal block: the warp holding rows c0..c0+31 factors it in registers
+  const int lane = i & 31;
+  if ((i >> 5) == (c0 >> 5)) {
+    int bad = 0;  // every lane sees every pivot, so every lane tracks the first bad one
+#pragma unroll
+    for (int j = 0; j < W; j++) {
+      if (j < w) {
+        const double d = __shfl_sync(FULL, acc[j], j);
+        const double r = rsqrt(d);
+        if (!(d > 0.0) && bad == 0) bad = c0 + j + 1;
+        if (lane == j) {
+          acc[j] = d * r;
+          S.rinv[j] = r;
+        } else {
+          acc[j] *= r;
+        }
+#pragma unroll
+        for (int jj = j + 1; jj < W; jj++) {
+          const double v = __shfl_sync(FULL, acc[j], jj);
+          acc[jj] = fma(-acc[j], v, acc[jj]);
+        }
+      }
+    }
+#pragma unroll
+    for (int jj = 0; jj < W; jj++) S.Ls[lane][jj] = acc[jj];
+    if (lane == 0 && bad != 0 && S.bad == 0) S.bad = bad;
+  }
+  __syncthreads();
+
+  // (d) rows below the diagonal block: substitution against it
+  if (active && i >= c0 + 32) {
+#pragma unroll
+    for (int j = 0; j < W; j++) {
+      acc[j] *= S.rinv[j];
+#pragma unroll
+      for (int jj = j + 1; jj < W; jj++) acc[jj] = fma(-acc[j], S.Ls[jj][j], acc[jj]);
+    }
+  }
+
+  // (e) store the block column
+  if (active) {
+    double *drow = pd + pm_off(D.i0 + i, D.j0, D.cn);
+#pragma unroll
+    for (int jj = 0; jj < W; jj++) {
+      const int col = c0 + jj;
+      if (jj < w && i >= col) drow[(long long)col * PS] = acc[jj];
+    }
+  }
+  if (dinv_b && i < w) dinv_b[c0 + i] = S.rinv[i];
+  __syncthreads();
+}
+
+template <bool FUSED, bool ALIGNED>
+__global__ void __launch_bounds__(512)
+k_chol_rows(int n, int k, Op A, Op B, Op C, OpW D, double *dinv, long long sdinv, int *info) {
+  __shared__ RowsSmem S;
+  const int b = blockIdx.x;
+  const double *pa = FUSED ? A.p + b * A.stride : nullptr;
+  const double *pb = FUSED ? B.p + b * B.stride : nullptr;
+  const double *pc = C.p + b * C.stride;
+  double *pd = D.p + b * D.stride;
+  double *dinv_b = dinv ? dinv + b * sdinv : nullptr;
+  if (threadIdx.x == 0) S.bad = 0;
+  __syncthreads();
+  for (int c0 = 0; c0 < n; c0 += 32) {
+    const int w8 = (min(32, n - c0) + 7) & ~7;
+    switch (w8) {
+      case 8: rows_block<8, FUSED, ALIGNED>(S, c0, n, k, pa, pb, pc, pd, A, B, C, D, dinv_b); break;
+      case 16: rows_block<16, FUSED, ALIGNED>(S, c0, n, k, pa, pb, pc, pd, A, B, C, D, dinv_b); break;
+      case 24: rows_block<24, FUSED, ALIGNED>(S, c0, n, k, pa, pb, pc, pd, A, B, C, D, dinv_b); break;
+      default: rows_block<32, FUSED, ALIGNED>(S, c0, n, k, pa, pb, pc, pd, A, B, C, D, dinv_b); break;
+    }
+  }
+  if (info && threadIdx.x == 0) info[b] = S.bad;
+}
+
+// smallest G whose shared-memory triangle for 32/G problems fits the budget
+int pick_small_g(int n) {
+  const long long ne = (long long)n * (n + 1) / 2;
+  for (int g = 1; g <= 32; g *= 2)
+    if (ne * (32 / g) * 8 <= 40 * 1024) return g;
+  return 0;
+}
+
+template <int G, bool FUSED>
+cudaError_t launch_small_g(bool aligned, int batch, int n, int k, Op A, Op B, Op C, OpW D,
+                           double *dinv, long long sdinv, int *info, cudaStream_t s) {
+  constexpr int Q = 32 / G;
+  const size_t smem = (size_t)n * (n + 1) / 2 * Q * sizeof(double);
+  const unsigned blocks = (unsigned)((batch + Q - 1) / Q);
+  if (aligned)
+    k_chol_small<G, FUSED, true><<<blocks, 32, smem, s>>>(batch, n, k, A, B, C, D, dinv, sdinv, info);
+  else
+    k_chol_small<G, FUSED, false><<<blocks, 32, smem, s>>>(batch, n, k, A, B, C, D, dinv, sdinv, info);
+  return cudaGetLastError();
+}
+
+template <bool FUSED>
+cudaError_t launch_chol_t(bool aligned, int batch, int n, int k, Op A, Op B, Op C, OpW D,
+                          double *dinv, long long sdinv, int *info, cudaStream_t s) {
+  const int g = (n <= 64) ? pick_small_g(n) : 0;
+  switch (g) {
+    case 1: return launch_small_g<1, FUSED>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
+    case 2: return launch_small_g<2, FUSED>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
+    case 4: return launch_small_g<4, FUSED>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
+    case 8: return launch_small_g<8, FUSED>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
+    case 16: return launch_small_g<16, FUSED>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
+    case 32: return launch_small_g<32, FUSED>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
+    default: break;
+  }
+  const int threads = (n + 31) & ~31;
+  if (aligned)
+    k_chol_rows<FUSED, true><<<batch, threads, 0, s>>>(n, k, A, B, C, D, dinv, sdinv, info);
+  else
+    k_chol_rows<FUSED, false><<<batch, threads, 0, s>>>(n, k, A, B, C, D, dinv, sdinv, info);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_chol(bool fused, int batch, int n, int k, Op A, Op B, Op C, OpW D,
+                        double *dinv, long long sdinv, int *info, bool aligned, cudaStream_t s) {
+  return fused ? launch_chol_t<true>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s)
+               : launch_chol_t<false>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
+}
+
+}  // namespace bf

@@ -1,0 +1,201 @@
+// gemm_nt and syrk_ln, batched, FP64, panel-major operands.
+//
+// gemm_nt (Appendix A.2.1; Sec. 5.2.2):  D <- alpha * A * B^T + beta * C
+// syrk_ln (Sec. 5.2.2):                  lower(D) <- alpha * A * B^T + beta * C
+//
+// Design.  On GB300 the FP64 pipe executes two FMA lanes per SM and clock, so
+// a warp-wide DFMA occupies the SM's FP64 units for 16 cycles whatever its
+// active mask, while loads, integer work and FP32 run on pipes that are an
+// order of magnitude wider.  The kernel therefore spends every FP64 lane on
+// useful work: each thread owns one 4x4 register block of one problem's D
+// (rows i0..i0+3 sit in one panel of height 4, Sec. 4.1 register blocking),
+// and threads are numbered over (problem, block) so that warps stay full
+// across problem boundaries.  Operand columns of the register block are one
+// 32-byte panel column each (Sec. 4.3.3: 'NT' reads both A and B along their
+// panels), fetched with two 16-byte loads through L1; the 16 FMAs per column
+// pair hide them.  syrk_ln numbers only the blocks of the lower block
+// triangle, the diagonal blocks storing their lower half.
+#include "bf_internal.cuh"
+
+namespace bf {
+namespace {
+
+// t -> (tr, tc) with tr >= tc and t = tr*(tr+1)/2 + tc.
+__device__ __forceinline__ void tri_index(int t, int &tr, int &tc) {
+  int r = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+  while (r * (r + 1) / 2 > t) r--;
+  while ((r + 1) * (r + 2) / 2 <= t) r++;
+  tr = r;
+  tc = t - r * (r + 1) / 2;
+}
+
+template <bool SYRK, bool ALIGNED>
+__global__ void __launch_bounds__(128)
+k_gemm_nt(int batch, int m, int n, int k, double alpha, Op A, Op B, double beta, Op C, OpW D,
+          int tiles_c, int tiles_pp) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)batch * tiles_pp) return;
+  const int b = (int)(t / tiles_pp);
+  const int tt = (int)(t - (long long)b * tiles_pp);
+  int tr, tc;
+  if (SYRK) {
+    tri_index(tt, tr, tc);
+  } else {
+    tr = tt / tiles_c;
+    tc = tt - tr * tiles_c;
+  }
+  const int i0 = tr * 4, j0 = tc * 4;
+  const double *pa = A.p + b * A.stride;
+  const double *pb = B.p + b * B.stride;
+  const double *pc = C.p ? C.p + b * C.stride : nullptr;
+  double *pd = D.p + b * D.stride;
+
+  const bool full = (i0 + 4 <= m) && (j0 + 4 <= n) && (!SYRK || tr != tc);
+  const bool a1 = (alpha == 1.0);
+  double acc[4][4];
+
+  // alpha == 1: start from beta*C so that the epilogue costs no FP64 work.
+  if (a1 && beta != 0.0) {
+    if (ALIGNED && full) {
+      const double *cp = pc + (long long)(C.i0 + i0) * C.cn + (long long)(C.j0 + j0) * PS;
+#pragma unroll
+      for (int c = 0; c < 4; c++) {
+        double2 lo = *(const double2 *)(cp + c * PS);
+        double2 hi = *(const double2 *)(cp + c * PS + 2);
+        acc[0][c] = lo.x; acc[1][c] = lo.y; acc[2][c] = hi.x; acc[3][c] = hi.y;
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < 4; r++)
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+          const int i = i0 + r, j = j0 + c;
+          acc[r][c] = (i < m && j < n && (!SYRK || i >= j)) ? pc[pm_off(C.i0 + i, C.j0 + j, C.cn)] : 0.0;
+        }
+    }
+    if (beta != 1.0) {
+#pragma unroll
+      for (int r = 0; r < 4; r++)
+#pragma unroll
+        for (int c = 0; c < 4; c++) acc[r][c] *= beta;
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < 4; r++)
+#pragma unroll
+      for (int c = 0; c < 4; c++) acc[r][c] = 0.0;
+  }
+
+  if (ALIGNED) {
+    // rows i0..i0+3 of A (and j0..j0+3 of B) are one panel: column l is 4
+    // consecutive doubles.  Rows past m inside the last panel exist in memory
+    // (storage is padded to whole panels); their results are never stored.
+    const double *ap = pa + (long long)(A.i0 + i0) * A.cn + (long long)A.j0 * PS;
+    const double *bp = pb + (long long)(B.i0 + j0) * B.cn + (long long)B.j0 * PS;
+#pragma unroll 4
+    for (int l = 0; l < k; l++) {
+      const double2 a01 = __ldg((const double2 *)(ap + l * PS));
+      const double2 a23 = __ldg((const double2 *)(ap + l * PS + 2));
+      const double2 b01 = __ldg((const double2 *)(bp + l * PS));
+      const double2 b23 = __ldg((const double2 *)(bp + l * PS + 2));
+      const double av[4] = {a01.x, a01.y, a23.x, a23.y};
+      const double bv[4] = {b01.x, b01.y, b23.x, b23.y};
+#pragma unroll
+      for (int r = 0; r < 4; r++)
+#pragma unroll
+        for (int c = 0; c < 4; c++) acc[r][c] = fma(av[r], bv[c], acc[r][c]);
+    }
+  } else {
+    // generic variant (Sec. 4.4.2): sub-matrix rows not aligned to a panel top
+    const double *ar[4], *br[4];
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+      const int ii = min(i0 + r, m - 1), jj = min(j0 + r, n - 1);
+      ar[r] = pa + pm_off(A.i0 + ii, A.j0, A.cn);
+      br[r] = pb + pm_off(B.i0 + jj, B.j0, B.cn);
+    }
+#pragma unroll 2
+    for (int l = 0; l < k; l++) {
+      double av[4], bv[4];
+#pragma unroll
+      for (int r = 0; r < 4; r++) {
+        av[r] = __ldg(ar[r] + l * PS);
+        bv[r] = __ldg(br[r] + l * PS);
+      }
+#pragma unroll
+      for (int r = 0; r < 4; r++)
+#pragma unroll
+        for (int c = 0; c < 4; c++) acc[r][c] = fma(av[r], bv[c], acc[r][c]);
+    }
+  }
+
+  // epilogue
+  if (ALIGNED && full) {
+    double *dp = pd + (long long)(D.i0 + i0) * D.cn + (long long)(D.j0 + j0) * PS;
+    const double *cp = (!a1 && beta != 0.0)
+                           ? pc + (long long)(C.i0 + i0) * C.cn + (long long)(C.j0 + j0) * PS
+                           : nullptr;
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+      double v[4];
+#pragma unroll
+      for (int r = 0; r < 4; r++) v[r] = acc[r][c];
+      if (!a1) {
+        if (cp) {
+          const double2 lo = *(const double2 *)(cp + c * PS);
+          const double2 hi = *(const double2 *)(cp + c * PS + 2);
+          v[0] = fma(alpha, v[0], beta * lo.x);
+          v[1] = fma(alpha, v[1], beta * lo.y);
+          v[2] = fma(alpha, v[2], beta * hi.x);
+          v[3] = fma(alpha, v[3], beta * hi.y);
+        } else {
+#pragma unroll
+          for (int r = 0; r < 4; r++) v[r] *= alpha;
+        }
+      }
+      *(double2 *)(dp + c * PS) = make_double2(v[0], v[1]);
+      *(double2 *)(dp + c * PS + 2) = make_double2(v[2], v[3]);
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < 4; r++)
+#pragma unroll
+      for (int c = 0; c < 4; c++) {
+        const int i = i0 + r, j = j0 + c;
+        if (i < m && j < n && (!SYRK || i >= j)) {
+          double v = acc[r][c];
+          if (!a1) {
+            v *= alpha;
+            if (beta != 0.0) v = fma(beta, pc[pm_off(C.i0 + i, C.j0 + j, C.cn)], v);
+          }
+          pd[pm_off(D.i0 + i, D.j0 + j, D.cn)] = v;
+        }
+      }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_gemm_nt(bool syrk, int batch, int m, int n, int k, double alpha, Op A, Op B,
+                           double beta, Op C, OpW D, bool aligned, cudaStream_t s) {
+  const int tr = (m + 3) / 4, tcn = (n + 3) / 4;
+  const int tiles_pp = syrk ? tr * (tr + 1) / 2 : tr * tcn;
+  const long long total = (long long)batch * tiles_pp;
+  const int threads = 128;
+  const long long blocks = (total + threads - 1) / threads;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  if (syrk) {
+    if (aligned)
+      k_gemm_nt<true, true><<<(unsigned)blocks, threads, 0, s>>>(batch, m, n, k, alpha, A, B, beta, C, D, tcn, tiles_pp);
+    else
+      k_gemm_nt<true, false><<<(unsigned)blocks, threads, 0, s>>>(batch, m, n, k, alpha, A, B, beta, C, D, tcn, tiles_pp);
+  } else {
+    if (aligned)
+      k_gemm_nt<false, true><<<(unsigned)blocks, threads, 0, s>>>(batch, m, n, k, alpha, A, B, beta, C, D, tcn, tiles_pp);
+    else
+      k_gemm_nt<false, false><<<(unsigned)blocks, threads, 0, s>>>(batch, m, n, k, alpha, A, B, beta, C, D, tcn, tiles_pp);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace bf

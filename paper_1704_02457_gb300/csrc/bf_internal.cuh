@@ -1,0 +1,60 @@
+// Internal declarations shared by the CUDA translation units of the library.
+//
+// Panel-major addressing (Sec. 4.3.3 of the paper): with panel height PS (a
+// power of two) and panel length cn, element (r, c) of a matrix lies at
+//   (r - r % PS) * cn + c * PS + r % PS.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "bfgpu.h"
+
+namespace bf {
+
+constexpr int PS = BF_PS;
+static_assert((PS & (PS - 1)) == 0, "panel height must be a power of two");
+
+// A read-only operand of a batched call: storage of problem 0, distance in
+// doubles between consecutive problems, panel length and the sub-matrix
+// offset of the operand.
+struct Op {
+  const double *p;
+  long long stride;
+  int cn;
+  int i0, j0;
+};
+
+// A written operand.
+struct OpW {
+  double *p;
+  long long stride;
+  int cn;
+  int i0, j0;
+};
+
+__host__ __device__ __forceinline__ long long pm_off(int r, int c, int cn) {
+  return (long long)(r & ~(PS - 1)) * cn + (long long)c * PS + (r & (PS - 1));
+}
+
+// ---- launchers (each returns the cudaError_t of its launch) ---------------
+
+cudaError_t launch_gemm_nt(bool syrk, int batch, int m, int n, int k, double alpha, Op A, Op B,
+                           double beta, Op C, OpW D, bool aligned, cudaStream_t s);
+
+// potrf_l (fused = false) and syrk_potrf_ln (fused = true, A and B used).
+cudaError_t launch_chol(bool fused, int batch, int n, int k, Op A, Op B, Op C, OpW D,
+                        double *dinv, long long sdinv, int *info, bool aligned, cudaStream_t s);
+
+cudaError_t launch_trsm_rltn(int batch, int m, int n, double alpha, Op L, const double *dinv,
+                             long long sdinv, Op B, OpW D, cudaStream_t s);
+
+cudaError_t launch_pack(int batch, int m, int n, const double *A, int lda, long long sA, OpW B,
+                        cudaStream_t s);
+cudaError_t launch_unpack(int batch, int m, int n, Op A, double *B, int ldb, long long sB,
+                          cudaStream_t s);
+
+// Largest order the factorization kernels accept.
+constexpr int CHOL_MAX_N = 512;
+constexpr int TRSM_MAX_N = 4096;
+
+}  // namespace bf

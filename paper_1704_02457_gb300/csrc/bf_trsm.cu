@@ -1,0 +1,173 @@
+// trsm_rltn, batched, FP64, panel-major operands (Sec. 5.2.2; right, lower,
+// transposed, non-unit):
+//     D <- alpha * B * L^{-T}   i.e. the X with X * L^T = alpha * B.
+//
+// Rows of X are independent: row i solves x_i L^T = alpha b_i by forward
+// substitution over the columns.  One thread owns one row and walks the
+// columns in blocks of up to 32 held in registers.  For block [c0, c0+W):
+//   (a) acc = alpha * B[i][c0..]
+//   (b) acc -= X[i][0:c0] * L[c0..][0:c0]^T     (the gemm_nt downdate, merged
+//       into the solve kernel as the paper does for trsm, Sec. 4.6)
+//   (d) substitution against the diagonal block L[c0..][c0..], multiplying
+//       by the inverse diagonal (Sec. 4.7.1): from the caller's dinv when
+//       given (as written by potrf), else one reciprocal per column computed
+//       once per CTA, so no thread divides in its inner loop.
+// L's rows are shared by all threads of a problem: the diagonal block and the
+// downdate chunks are staged in shared memory and read as broadcasts.  A CTA
+// packs the rows of several small problems so that warps stay full; a problem
+// with more than 256 rows is split over several CTAs.
+#include "bf_internal.cuh"
+
+namespace bf {
+namespace {
+
+constexpr int KC = 32;        // columns of L per staged downdate chunk
+constexpr int SPITCH = 34;    // stage row pitch (even: 16-byte pair loads)
+constexpr int MAX_ROWS = 256; // rows per CTA
+
+__host__ __device__ __forceinline__ int ls_region(int W) { return W * (W + 1) + W + 1; }
+
+template <int W>
+__device__ __forceinline__ void trsm_block(double *smem, int P, int R, int c0, int m, int n,
+                                           double alpha, int pb0, int batch, int r0, Op L,
+                                           const double *dinv, long long sdinv, Op B, OpW D) {
+  const int t = threadIdx.x;
+  const int T = blockDim.x;
+  const int w = min(32, n - c0);
+  const int RS = ls_region(W);
+  double *stage_base = smem + (((size_t)P * RS + 1) & ~(size_t)1);  // 16-byte aligned
+
+  const int p = t / R;
+  const int row = r0 + (t - p * R);
+  const int b = pb0 + p;
+  const bool active = (p < P) && (row < m) && (b < batch);
+  double *Ls = smem + (size_t)min(p, P - 1) * RS;  // Ls[jj*(W+1) + j], then rinv[W]
+  double *rinv = Ls + W * (W + 1);
+
+  // diagonal block of L and its inverse diagonal, for every problem of the CTA
+  for (int x = t; x < P * W * W; x += T) {
+    const int pp = x / (W * W), jj = (x / W) % W, j = x % W;
+    const int bb = pb0 + pp;
+    double v = 0.0;
+    if (bb < batch && jj < w && j <= jj)
+      v = __ldg(L.p + bb * L.stride + pm_off(L.i0 + c0 + jj, L.j0 + c0 + j, L.cn));
+    smem[(size_t)pp * RS + jj * (W + 1) + j] = v;
+  }
+  for (int x = t; x < P * W; x += T) {
+    const int pp = x / W, j = x % W;
+    const int bb = pb0 + pp;
+    double r = 0.0;
+    if (bb < batch && j < w) {
+      if (dinv)
+        r = __ldg(dinv + bb * sdinv + c0 + j);
+      else
+        r = 1.0 / __ldg(L.p + bb * L.stride + pm_off(L.i0 + c0 + j, L.j0 + c0 + j, L.cn));
+    }
+    smem[(size_t)pp * RS + W * (W + 1) + j] = r;
+  }
+
+  // (a)
+  double acc[W];
+  const double *brow = B.p + (active ? b : 0) * B.stride + pm_off(B.i0 + (active ? row : 0), B.j0, B.cn);
+  double *xrow = D.p + (active ? b : 0) * D.stride + pm_off(D.i0 + (active ? row : 0), D.j0, D.cn);
+#pragma unroll
+  for (int jj = 0; jj < W; jj++) acc[jj] = (active && jj < w) ? alpha * brow[(long long)(c0 + jj) * PS] : 0.0;
+
+  // (b) downdate with the columns already solved
+  double *stage = stage_base + (size_t)min(p, P - 1) * KC * SPITCH;
+  for (int l0 = 0; l0 < c0; l0 += KC) {
+    __syncthreads();
+    for (int x = t; x < P * 32 * KC; x += T) {
+      const int pp = x / (32 * KC);
+      const int y = x - pp * 32 * KC;
+      const int r4 = y % PS, ll = (y / PS) % KC, pnl = y / (PS * KC);
+      const int jj = pnl * PS + r4;
+      const int bb = pb0 + pp;
+      stage_base[(size_t)pp * KC * SPITCH + ll * SPITCH + jj] =
+          (bb < batch && jj < w) ? __ldg(L.p + bb * L.stride + pm_off(L.i0 + c0 + jj, L.j0 + l0 + ll, L.cn)) : 0.0;
+    }
+    __syncthreads();
+    if (active) {
+#pragma unroll 2
+      for (int ll = 0; ll < KC; ll++) {
+        const double x = xrow[(long long)(l0 + ll) * PS];
+#pragma unroll
+        for (int jj = 0; jj < W; jj += 2) {
+          const double2 lv = *(const double2 *)&stage[ll * SPITCH + jj];
+          acc[jj] = fma(-x, lv.x, acc[jj]);
+          if (jj + 1 < W) acc[jj + 1] = fma(-x, lv.y, acc[jj + 1]);
+        }
+      }
+    }
+  }
+  __syncthreads();
+
+  // (d) substitution against the diagonal block
+  if (active) {
+#pragma unroll
+    for (int j = 0; j < W; j++) {
+      acc[j] *= rinv[j];
+#pragma unroll
+      for (int jj = j + 1; jj < W; jj++) acc[jj] = fma(-acc[j], Ls[jj * (W + 1) + j], acc[jj]);
+    }
+    // (e)
+#pragma unroll
+    for (int jj = 0; jj < W; jj++)
+      if (jj < w) xrow[(long long)(c0 + jj) * PS] = acc[jj];
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(MAX_ROWS)
+k_trsm_rltn(int batch, int m, int n, double alpha, Op L, const double *dinv, long long sdinv, Op B,
+            OpW D, int P, int R, int chunks) {
+  extern __shared__ double smem[];
+  const int pb0 = (blockIdx.x / chunks) * P;
+  const int r0 = (blockIdx.x % chunks) * R;
+  for (int c0 = 0; c0 < n; c0 += 32) {
+    const int w8 = (min(32, n - c0) + 7) & ~7;
+    switch (w8) {
+      case 8: trsm_block<8>(smem, P, R, c0, m, n, alpha, pb0, batch, r0, L, dinv, sdinv, B, D); break;
+      case 16: trsm_block<16>(smem, P, R, c0, m, n, alpha, pb0, batch, r0, L, dinv, sdinv, B, D); break;
+      case 24: trsm_block<24>(smem, P, R, c0, m, n, alpha, pb0, batch, r0, L, dinv, sdinv, B, D); break;
+      default: trsm_block<32>(smem, P, R, c0, m, n, alpha, pb0, batch, r0, L, dinv, sdinv, B, D); break;
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_trsm_rltn(int batch, int m, int n, double alpha, Op L, const double *dinv,
+                             long long sdinv, Op B, OpW D, cudaStream_t s) {
+  int P = 1, R = m, chunks = 1;
+  if (m > MAX_ROWS) {
+    R = MAX_ROWS;
+    chunks = (m + MAX_ROWS - 1) / MAX_ROWS;
+  } else if (n <= 32) {
+    // a single column block: pack as many problems as fit in 256 rows
+    P = max(1, MAX_ROWS / m);
+  } else {
+    // blocked: up to 4 problems, enough to fill whole warps
+    while (P < 4 && 2 * P * m <= MAX_ROWS && (P * m) % 32 != 0) P *= 2;
+  }
+  const int W = n >= 32 ? 32 : ((n + 7) & ~7);
+  const size_t per_problem = ((size_t)ls_region(W) + (n > 32 ? (size_t)KC * SPITCH : 0)) * sizeof(double);
+  P = (int)min((size_t)P, (size_t)(96 * 1024) / per_problem);
+  P = max(1, min(P, batch));
+  const int threads = ((P * R + 31) / 32) * 32;
+  size_t smem = ((size_t)P * ls_region(W) + 1) * sizeof(double);
+  if (n > 32) smem += (size_t)P * KC * SPITCH * sizeof(double);
+  if (smem > 200 * 1024) return cudaErrorInvalidConfiguration;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_trsm_rltn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const long long blocks = (long long)((batch + P - 1) / P) * chunks;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  k_trsm_rltn<<<(unsigned)blocks, threads, smem, s>>>(batch, m, n, alpha, L, dinv, sdinv, B, D, P, R, chunks);
+  return cudaGetLastError();
+}
+
+}  // namespace bf

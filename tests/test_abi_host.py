@@ -1,0 +1,140 @@
+"""Host-side checks of the C ABI (no GPU needed).
+
+The library must load and export every entry point that include/bfgpu.h
+declares; the memory helpers must follow the descriptor rules; and invalid
+arguments must come back as the documented negative argument positions,
+which the host code decides before anything is launched.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1704_02457_gb300 import _abi
+from paper_1704_02457_gb300.build import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "bfgpu.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build()
+    return _abi.load()
+
+
+def _declared():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:[\w]+\s+\**)+(bf_\w+)\s*\(", txt, flags=re.M)))
+
+
+def test_header_declares_the_routines():
+    names = _declared()
+    for r in ["bf_dgemm_nt", "bf_dsyrk_ln", "bf_dpotrf_l", "bf_dtrsm_rltn", "bf_dsyrk_dpotrf_ln"]:
+        assert r in names and r + "_batched" in names
+    assert {"bf_memsize_dmat", "bf_create_dmat", "bf_pack_dmat_batched", "bf_unpack_dmat_batched"} <= set(names)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert names
+    for name in names:
+        assert hasattr(lib, name), name
+        assert name in _abi.SIGNATURES, name
+
+
+def test_struct_layout_matches_header():
+    # pointer, pointer, five ints, then size_t (8-byte aligned)
+    assert ctypes.sizeof(_abi.bf_dmat) == 8 + 8 + 5 * 4 + 4 + 8
+    assert _abi.bf_dmat.memsize.offset == 40
+
+
+def test_memsize_and_create(lib):
+    assert lib.bf_panel_height() == _abi.BF_PS == 4
+    for m, n in [(1, 1), (4, 4), (5, 3), (24, 24), (256, 256), (0, 7)]:
+        ms = lib.bf_memsize_dmat(m, n)
+        pm = -(-m // 4) * 4
+        assert ms % 256 == 0
+        assert ms >= (pm * n + min(m, n)) * 8
+        assert ms < (pm * n + min(m, n)) * 8 + 256
+    assert lib.bf_memsize_dmat(-1, 3) == 0
+    buf = ctypes.create_string_buffer(4096 + 256)
+    base = (ctypes.addressof(buf) + 255) // 256 * 256
+    d = _abi.bf_dmat()
+    assert lib.bf_create_dmat(5, 3, ctypes.byref(d), ctypes.c_void_p(base)) == 0
+    assert (d.m, d.n, d.pm, d.cn, d.ps) == (5, 3, 8, 3, 4)
+    assert d.pA == base and d.dA == base + 8 * 3 * 8
+    assert d.memsize == lib.bf_memsize_dmat(5, 3)
+    assert lib.bf_create_dmat(-1, 3, ctypes.byref(d), ctypes.c_void_p(base)) == -1
+    assert lib.bf_create_dmat(3, -1, ctypes.byref(d), ctypes.c_void_p(base)) == -2
+    assert lib.bf_create_dmat(3, 3, None, ctypes.c_void_p(base)) == -3
+    assert lib.bf_create_dmat(3, 3, ctypes.byref(d), ctypes.c_void_p(base + 8)) == -4
+
+
+def _desc(m, n, addr=0x10000):
+    d = _abi.bf_dmat()
+    d.pA, d.dA, d.m, d.n, d.pm, d.cn, d.ps, d.memsize = addr, 0, m, n, -(-m // 4) * 4, n, 4, 0
+    return d
+
+
+def test_argument_errors_are_reported_before_launch(lib):
+    # none of these calls reaches a kernel: validation fails first
+    A, B, C, D = (_desc(8, 8) for _ in range(4))
+    r = ctypes.byref
+    g = lib.bf_dgemm_nt_batched
+    assert g(-1, 8, 8, 8, 1.0, r(A), 0, 0, 0, r(B), 0, 0, 0, 1.0, r(C), 0, 0, 0, r(D), 0, 0, 0, None) == -1
+    assert g(1, -8, 8, 8, 1.0, r(A), 0, 0, 0, r(B), 0, 0, 0, 1.0, r(C), 0, 0, 0, r(D), 0, 0, 0, None) == -2
+    assert g(1, 8, 8, -1, 1.0, r(A), 0, 0, 0, r(B), 0, 0, 0, 1.0, r(C), 0, 0, 0, r(D), 0, 0, 0, None) == -4
+    assert g(1, 8, 8, 8, 1.0, None, 0, 0, 0, r(B), 0, 0, 0, 1.0, r(C), 0, 0, 0, r(D), 0, 0, 0, None) == -6
+    assert g(1, 8, 8, 8, 1.0, r(A), 1, 0, 0, r(B), 0, 0, 0, 1.0, r(C), 0, 0, 0, r(D), 0, 0, 0, None) == -7
+    assert g(1, 8, 8, 8, 1.0, r(A), 0, 1, 0, r(B), 0, 0, 0, 1.0, r(C), 0, 0, 0, r(D), 0, 0, 0, None) == -8
+    assert g(1, 8, 8, 8, 1.0, r(A), 0, 0, -1, r(B), 0, 0, 0, 1.0, r(C), 0, 0, 0, r(D), 0, 0, 0, None) == -9
+    # B has 8 rows, n = 9 rows do not fit below row offset bi: position of bi
+    assert g(1, 8, 9, 8, 1.0, r(A), 0, 0, 0, r(B), 0, 0, 0, 1.0, r(C), 0, 0, 0, r(D), 0, 0, 0, None) == -11
+    assert g(1, 8, 8, 8, 1.0, r(A), 0, 0, 0, r(B), 0, 0, 0, 1.0, None, 0, 0, 0, r(D), 0, 0, 0, None) == -15
+    # outputs of a batch must not overlap
+    assert g(2, 8, 8, 8, 1.0, r(A), 0, 0, 0, r(B), 0, 0, 0, 1.0, r(C), 0, 0, 0, r(D), 0, 0, 8, None) == -22
+    # single-problem form reports its own positions
+    assert lib.bf_dgemm_nt(8, 8, 8, 1.0, r(A), 0, 0, None, 0, 0, 1.0, r(C), 0, 0, r(D), 0, 0, None) == -8
+    bad = _desc(8, 8)
+    bad.ps = 8
+    assert lib.bf_dgemm_nt(8, 8, 8, 1.0, r(A), 0, 0, r(B), 0, 0, 1.0, r(C), 0, 0, r(bad), 0, 0, None) == -15
+    # syrk: positions shift by one (no n argument)
+    assert lib.bf_dsyrk_ln_batched(1, 8, 8, 1.0, r(A), 0, 0, 0, r(B), 0, 3, 0, 1.0, r(C), 0, 0, 0,
+                                   r(D), 0, 0, 0, None) == -11
+    assert lib.bf_dsyrk_ln(8, 8, 1.0, r(A), 0, 0, r(B), 0, 0, 1.0, r(C), 0, 0, r(D), 9, 0, None) == -15
+    # potrf / syrk_potrf / trsm
+    assert lib.bf_dpotrf_l_batched(1, 9, r(C), 0, 0, 0, r(D), 0, 0, 0, None, 0, None, None) == -4  # ci
+    assert lib.bf_dpotrf_l_batched(1, 8, r(C), 0, 0, 0, r(D), 0, 0, 0, ctypes.c_void_p(0x10001), 0, None, None) == -11
+    assert lib.bf_dpotrf_l(8, r(C), 0, 0, r(D), 0, 1, None, None) == -7
+    assert lib.bf_dsyrk_dpotrf_ln_batched(1, 8, 8, r(A), 0, 0, 0, None, 0, 0, 0, r(C), 0, 0, 0,
+                                          r(D), 0, 0, 0, None, 0, None, None) == -8
+    assert lib.bf_dsyrk_dpotrf_ln(8, 8, r(A), 0, 0, r(B), 0, 0, r(C), 0, 0, r(D), 0, 0,
+                                  ctypes.c_void_p(0x10002), None) == -15
+    assert lib.bf_dtrsm_rltn_batched(1, 8, 8, 1.0, r(A), 0, 0, 0, None, 0, r(B), 0, 0, 0, None, 0, 0, 0, None) == -15
+    assert lib.bf_dtrsm_rltn(8, 8, 1.0, r(A), 0, 0, r(B), 1, 0, r(D), 0, 0, None) == -8
+    # sizes beyond what the factorization kernels implement
+    big = _desc(600, 600)
+    assert lib.bf_dpotrf_l_batched(1, 600, r(big), 0, 0, 0, r(big), 0, 0, 0, None, 0, None, None) == _abi.BF_ERR_UNSUPPORTED
+
+
+def test_zero_sizes_return_without_work(lib):
+    r = ctypes.byref
+    A = _desc(8, 8)
+    # empty batch or empty matrices: success, nothing launched (descriptors not even read)
+    assert lib.bf_dgemm_nt_batched(0, 8, 8, 8, 1.0, None, 0, 0, 0, None, 0, 0, 0, 1.0, None, 0, 0, 0, None, 0, 0, 0, None) == 0
+    assert lib.bf_dgemm_nt_batched(3, 0, 8, 8, 1.0, None, 0, 0, 0, None, 0, 0, 0, 1.0, None, 0, 0, 0, None, 0, 0, 0, None) == 0
+    assert lib.bf_dpotrf_l_batched(5, 0, None, 0, 0, 0, None, 0, 0, 0, None, 0, None, None) == 0
+    assert lib.bf_dtrsm_rltn_batched(5, 0, 8, 1.0, None, 0, 0, 0, None, 0, None, 0, 0, 0, None, 0, 0, 0, None) == 0
+    assert lib.bf_pack_dmat_batched(0, 4, 4, None, 4, 16, r(A), 0, 0, 0, None) == 0
+
+
+def test_product_path_has_no_fallback():
+    # the binding refuses to run without the compiled library; there is no CPU path
+    import paper_1704_02457_gb300 as pkg
+    src = open(os.path.join(os.path.dirname(pkg.__file__), "__init__.py")).read()
+    src += open(os.path.join(os.path.dirname(pkg.__file__), "_abi.py")).read()
+    assert "oracle" not in src
+    assert "import numpy" not in src
