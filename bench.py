@@ -184,7 +184,11 @@ class Point:
             self.D = bf.DMatBatch(bt, n, n, tight=True)
             self.info = torch.zeros(bt, dtype=torch.int32, device=dev)
         elif routine == "dtrsm_rltn":
-            self.L = mk(inputs.chol_factor(bt, n, seed, dev))
+            # the factor of an SPD input, computed (untimed) by this library's potrf
+            S = mk(inputs.spd(bt, n, seed, dev))
+            self.L = bf.DMatBatch(bt, n, n, tight=True, fill=0.0)
+            bf.dpotrf_l(n, S, 0, 0, self.L, 0, 0, dinv=False)
+            del S
             self.B = mk(inputs.normal((bt, n, n), seed + 1, dev))
             self.D = bf.DMatBatch(bt, n, n, tight=True)
         elif routine == "dsyrk_dpotrf_ln":
@@ -453,7 +457,7 @@ def run_e2e(pts, args, dev, world):
                 pool["spd"] = h
             elif p.routine == "dtrsm_rltn":
                 h = torch.empty((bt, n, n), dtype=torch.float64, pin_memory=True)
-                h.copy_(inputs.chol_factor(bt, n, 7200 + n, dev).transpose(1, 2))
+                h.copy_(p.L.to_colmajor().transpose(1, 2))
                 pool["fac"] = h
             elif p.routine == "dsyrk_dpotrf_ln":
                 h = torch.zeros((bt, n, n), dtype=torch.float64, pin_memory=True)
@@ -466,11 +470,16 @@ def run_e2e(pts, args, dev, world):
         n, bt, pool = p.n, p.batch, pools[p.n]
         sz = bt * n * n
         norm = lambda i: pool["norm"][i * sz:(i + 1) * sz].view(bt, n, n)  # noqa: E731
-        ins = {"dgemm_nt": [("A", norm(0)), ("B", norm(1)), ("C", norm(2))],
-               "dsyrk_ln": [("A", norm(0)), ("C", norm(1))],
-               "dpotrf_l": [("C", pool.get("spd"))],
-               "dtrsm_rltn": [("L", pool.get("fac")), ("B", norm(0))],
-               "dsyrk_dpotrf_ln": [("A", norm(0)), ("C", pool.get("q"))]}[p.routine]
+        if p.routine == "dgemm_nt":
+            ins = [("A", norm(0)), ("B", norm(1)), ("C", norm(2))]
+        elif p.routine == "dsyrk_ln":
+            ins = [("A", norm(0)), ("C", norm(1))]
+        elif p.routine == "dpotrf_l":
+            ins = [("C", pool["spd"])]
+        elif p.routine == "dtrsm_rltn":
+            ins = [("L", pool["fac"]), ("B", norm(0))]
+        else:
+            ins = [("A", norm(0)), ("C", pool["q"])]
         h2d += sum(h.numel() * 8 for _, h in ins)
         d2h += sz * 8
         plan.append((p, ins))

@@ -47,6 +47,16 @@ __device__ __forceinline__ void tri_index(int t, int &tr, int &tc) {
   tc = t - r * (r + 1) / 2;
 }
 
+// 8-byte asynchronous global -> shared copy (cp.async, bypasses registers)
+__device__ __forceinline__ void cp_async8(double *dst, const double *src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
 // packed lower column-major: column l starts at cs(l); element (i, l) at cs(l) + i
 __device__ __forceinline__ int col_start(int l, int n) { return (l * (2 * n - l + 1)) / 2 - l; }
 
@@ -65,7 +75,10 @@ k_chol_small(int batch, int n, int k, Op A, Op B, Op C, OpW D, double *dinv, lon
   const int b = b0 + q;
   const bool valid = b < batch;
 
-  // ---- phase 1: lower triangle of C into shared memory (whole warp per problem)
+  // ---- phase 1: lower triangle of C into shared memory (whole warp per
+  // problem).  Asynchronous 8-byte copies: every lane issues all of its
+  // copies for all Q problems before waiting once, so the global latency is
+  // paid once per CTA instead of once per panel.
   for (int qq = 0; qq < Q; qq++) {
     const int bb = b0 + qq;
     if (bb >= batch) break;
@@ -76,16 +89,17 @@ k_chol_small(int batch, int n, int k, Op A, Op B, Op C, OpW D, double *dinv, lon
         const double *pp = pc + (long long)(C.i0 + p * PS) * C.cn + (long long)C.j0 * PS;
         for (int x = lane; x < ncol * PS; x += 32) {
           const int j = x / PS, i = p * PS + (x % PS);
-          if (i < n && i >= j) sm[(col_start(j, n) + i) * Q + qq] = pp[x];
+          if (i < n && i >= j) cp_async8(&sm[(col_start(j, n) + i) * Q + qq], pp + x);
         }
       }
     } else {
       for (int x = lane; x < n * n; x += 32) {
         const int j = x / n, i = x - j * n;
-        if (i >= j) sm[(col_start(j, n) + i) * Q + qq] = pc[pm_off(C.i0 + i, C.j0 + j, C.cn)];
+        if (i >= j) cp_async8(&sm[(col_start(j, n) + i) * Q + qq], pc + pm_off(C.i0 + i, C.j0 + j, C.cn));
       }
     }
   }
+  cp_async_wait_all();
   __syncwarp();
 
   // ---- syrk_potrf: add A*B^T in 4x4 register blocks of the lower block triangle

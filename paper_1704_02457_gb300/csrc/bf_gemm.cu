@@ -14,7 +14,8 @@
 // 32-byte panel column each (Sec. 4.3.3: 'NT' reads both A and B along their
 // panels), fetched with two 16-byte loads through L1; the 16 FMAs per column
 // pair hide them.  syrk_ln numbers only the blocks of the lower block
-// triangle, the diagonal blocks storing their lower half.
+// triangle, grouping the diagonal blocks in warps of their own that skip the
+// FMAs above the diagonal.
 #include "bf_internal.cuh"
 
 namespace bf {
@@ -29,21 +30,12 @@ __device__ __forceinline__ void tri_index(int t, int &tr, int &tc) {
   tc = t - r * (r + 1) / 2;
 }
 
-template <bool SYRK, bool ALIGNED>
-__global__ void __launch_bounds__(128)
-k_gemm_nt(int batch, int m, int n, int k, double alpha, Op A, Op B, double beta, Op C, OpW D,
-          int tiles_c, int tiles_pp) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (long long)batch * tiles_pp) return;
-  const int b = (int)(t / tiles_pp);
-  const int tt = (int)(t - (long long)b * tiles_pp);
-  int tr, tc;
-  if (SYRK) {
-    tri_index(tt, tr, tc);
-  } else {
-    tr = tt / tiles_c;
-    tc = tt - tr * tiles_c;
-  }
+// One 4x4 register block (rows i0.., columns j0..) of problem b.  DIAG: a
+// diagonal block of syrk, whose FMAs above the diagonal are skipped.
+template <bool SYRK, bool DIAG, bool ALIGNED>
+__device__ __forceinline__ void gemm_tile(int b, int tr, int tc, int m, int n, int k, double alpha,
+                                          const Op &A, const Op &B, double beta, const Op &C,
+                                          const OpW &D) {
   const int i0 = tr * 4, j0 = tc * 4;
   const double *pa = A.p + b * A.stride;
   const double *pb = B.p + b * B.stride;
@@ -103,7 +95,8 @@ k_gemm_nt(int batch, int m, int n, int k, double alpha, Op A, Op B, double beta,
 #pragma unroll
       for (int r = 0; r < 4; r++)
 #pragma unroll
-        for (int c = 0; c < 4; c++) acc[r][c] = fma(av[r], bv[c], acc[r][c]);
+        for (int c = 0; c < 4; c++)
+          if (!DIAG || c <= r) acc[r][c] = fma(av[r], bv[c], acc[r][c]);
     }
   } else {
     // generic variant (Sec. 4.4.2): sub-matrix rows not aligned to a panel top
@@ -125,7 +118,8 @@ k_gemm_nt(int batch, int m, int n, int k, double alpha, Op A, Op B, double beta,
 #pragma unroll
       for (int r = 0; r < 4; r++)
 #pragma unroll
-        for (int c = 0; c < 4; c++) acc[r][c] = fma(av[r], bv[c], acc[r][c]);
+        for (int c = 0; c < 4; c++)
+          if (!DIAG || c <= r) acc[r][c] = fma(av[r], bv[c], acc[r][c]);
     }
   }
 
@@ -174,12 +168,45 @@ k_gemm_nt(int batch, int m, int n, int k, double alpha, Op A, Op B, double beta,
   }
 }
 
+// gemm_nt: thread t -> (problem, block), blocks of a problem row-major.
+// syrk_ln: the strictly-lower blocks of all problems come first, then the
+// diagonal blocks of all problems, so that each warp does one kind of block
+// and the diagonal ones save their upper-half FMAs.
+template <bool SYRK, bool ALIGNED>
+__global__ void __launch_bounds__(128)
+k_gemm_nt(int batch, int m, int n, int k, double alpha, Op A, Op B, double beta, Op C, OpW D,
+          int tiles_c, int tiles_pp) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (!SYRK) {
+    if (t >= (long long)batch * tiles_pp) return;
+    const int b = (int)(t / tiles_pp);
+    const int tt = (int)(t - (long long)b * tiles_pp);
+    const int tr = tt / tiles_c;
+    gemm_tile<false, false, ALIGNED>(b, tr, tt - tr * tiles_c, m, n, k, alpha, A, B, beta, C, D);
+  } else {
+    const int TR = tiles_c;                 // block rows (= block columns)
+    const int OD = TR * (TR - 1) / 2;       // strictly-lower blocks per problem
+    const long long nod = (long long)batch * OD;
+    if (t < nod) {
+      const int b = (int)(t / OD);
+      int r, c;
+      tri_index((int)(t - (long long)b * OD), r, c);
+      gemm_tile<true, false, ALIGNED>(b, r + 1, c, m, n, k, alpha, A, B, beta, C, D);
+    } else if (t < nod + (long long)batch * TR) {
+      const long long u = t - nod;
+      const int b = (int)(u / TR);
+      const int d = (int)(u - (long long)b * TR);
+      gemm_tile<true, true, ALIGNED>(b, d, d, m, n, k, alpha, A, B, beta, C, D);
+    }
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_gemm_nt(bool syrk, int batch, int m, int n, int k, double alpha, Op A, Op B,
                            double beta, Op C, OpW D, bool aligned, cudaStream_t s) {
   const int tr = (m + 3) / 4, tcn = (n + 3) / 4;
-  const int tiles_pp = syrk ? tr * (tr + 1) / 2 : tr * tcn;
+  const int tiles_pp = syrk ? tr * (tr + 1) / 2 : tr * tcn;  // syrk: tcn == tr
   const long long total = (long long)batch * tiles_pp;
   const int threads = 128;
   const long long blocks = (total + threads - 1) / threads;

@@ -27,6 +27,21 @@ constexpr int MAX_ROWS = 256; // rows per CTA
 
 __host__ __device__ __forceinline__ int ls_region(int W) { return W * (W + 1) + W + 1; }
 
+// block width bucket: 4, 8, 16, 24 or 32 columns
+__host__ __device__ __forceinline__ int w_bucket(int w) { return w <= 4 ? 4 : (w + 7) & ~7; }
+
+// 1/d by Newton-Raphson iteration r <- r + r (1 - d r) from the hardware's
+// approximate reciprocal; two steps take the approximation to full double
+// precision.  Used once per column of L per CTA instead of an IEEE divide.
+__device__ __forceinline__ double recip_newton(double d) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+  double e = fma(-d, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-d, r, 1.0);
+  return fma(r, e, r);
+}
+
 template <int W>
 __device__ __forceinline__ void trsm_block(double *smem, int P, int R, int c0, int m, int n,
                                            double alpha, int pb0, int batch, int r0, Op L,
@@ -61,7 +76,7 @@ __device__ __forceinline__ void trsm_block(double *smem, int P, int R, int c0, i
       if (dinv)
         r = __ldg(dinv + bb * sdinv + c0 + j);
       else
-        r = 1.0 / __ldg(L.p + bb * L.stride + pm_off(L.i0 + c0 + j, L.j0 + c0 + j, L.cn));
+        r = recip_newton(__ldg(L.p + bb * L.stride + pm_off(L.i0 + c0 + j, L.j0 + c0 + j, L.cn)));
     }
     smem[(size_t)pp * RS + W * (W + 1) + j] = r;
   }
@@ -71,7 +86,11 @@ __device__ __forceinline__ void trsm_block(double *smem, int P, int R, int c0, i
   const double *brow = B.p + (active ? b : 0) * B.stride + pm_off(B.i0 + (active ? row : 0), B.j0, B.cn);
   double *xrow = D.p + (active ? b : 0) * D.stride + pm_off(D.i0 + (active ? row : 0), D.j0, D.cn);
 #pragma unroll
-  for (int jj = 0; jj < W; jj++) acc[jj] = (active && jj < w) ? alpha * brow[(long long)(c0 + jj) * PS] : 0.0;
+  for (int jj = 0; jj < W; jj++) acc[jj] = (active && jj < w) ? brow[(long long)(c0 + jj) * PS] : 0.0;
+  if (alpha != 1.0) {
+#pragma unroll
+    for (int jj = 0; jj < W; jj++) acc[jj] *= alpha;
+  }
 
   // (b) downdate with the columns already solved
   double *stage = stage_base + (size_t)min(p, P - 1) * KC * SPITCH;
@@ -125,8 +144,8 @@ k_trsm_rltn(int batch, int m, int n, double alpha, Op L, const double *dinv, lon
   const int pb0 = (blockIdx.x / chunks) * P;
   const int r0 = (blockIdx.x % chunks) * R;
   for (int c0 = 0; c0 < n; c0 += 32) {
-    const int w8 = (min(32, n - c0) + 7) & ~7;
-    switch (w8) {
+    switch (w_bucket(min(32, n - c0))) {
+      case 4: trsm_block<4>(smem, P, R, c0, m, n, alpha, pb0, batch, r0, L, dinv, sdinv, B, D); break;
       case 8: trsm_block<8>(smem, P, R, c0, m, n, alpha, pb0, batch, r0, L, dinv, sdinv, B, D); break;
       case 16: trsm_block<16>(smem, P, R, c0, m, n, alpha, pb0, batch, r0, L, dinv, sdinv, B, D); break;
       case 24: trsm_block<24>(smem, P, R, c0, m, n, alpha, pb0, batch, r0, L, dinv, sdinv, B, D); break;
@@ -150,7 +169,7 @@ cudaError_t launch_trsm_rltn(int batch, int m, int n, double alpha, Op L, const 
     // blocked: up to 4 problems, enough to fill whole warps
     while (P < 4 && 2 * P * m <= MAX_ROWS && (P * m) % 32 != 0) P *= 2;
   }
-  const int W = n >= 32 ? 32 : ((n + 7) & ~7);
+  const int W = w_bucket(min(n, 32));
   const size_t per_problem = ((size_t)ls_region(W) + (n > 32 ? (size_t)KC * SPITCH : 0)) * sizeof(double);
   P = (int)min((size_t)P, (size_t)(96 * 1024) / per_problem);
   P = max(1, min(P, batch));
