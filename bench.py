@@ -408,6 +408,8 @@ def run_gpu(args):
     }
     result["per_routine_gflops"] = {r: round(v[0] / (v[1] * 1e-3) / 1e9, 2) for r, v in per_routine.items()}
 
+    if not args.no_mixed:
+        result["mixed_vs_fp64"] = run_mixed(args, dev)
     if not args.no_e2e:
         result["e2e"] = run_e2e(pts, args, dev, world)
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -522,6 +524,77 @@ def run_e2e(pts, args, dev, world):
             "path": "pinned host column-major -> H2D -> bf_pack -> routine -> bf_unpack -> D2H"}
 
 
+def run_mixed(args, dev, bt=8192, n=128, nrhs=4):
+    """Mixed precision vs plain FP64 on SPD solves (FP32 factor + FP64
+    iterative refinement to a 1e-12 relative residual, against potrf + potrs
+    in FP64): 8192 systems of order 128 with cond(A) log-uniform in
+    [1e2, 1e6] and 4 right-hand sides each."""
+    import numpy as np
+    import torch
+
+    import paper_1704_02457_gb300 as bf
+    from paper_1704_02457_gb300 import inputs
+
+    A, cond = inputs.spd_cond(bt, n, 9000, dev)
+    B = inputs.normal((bt, n, nrhs), 9001, dev)
+    dA, dB = bf.DMatBatch.from_colmajor(A, tight=True), bf.DMatBatch.from_colmajor(B, tight=True)
+    dL = bf.DMatBatch(bt, n, n, tight=True, fill=0.0)
+    dX64, dXm = bf.DMatBatch(bt, n, nrhs, tight=True), bf.DMatBatch(bt, n, nrhs, tight=True)
+    info = torch.zeros(bt, dtype=torch.int32, device=dev)
+    iters = torch.zeros(bt, dtype=torch.int32, device=dev)
+    resid = torch.zeros(bt, dtype=torch.float64, device=dev)
+    work = None
+    stream = torch.cuda.current_stream()
+
+    def fp64():
+        bf.dpotrf_l(n, dA, 0, 0, dL, 0, 0, dinv=False, info=info, stream=stream)
+        bf.dpotrs_l(n, nrhs, dL, 0, 0, dB, 0, 0, dX64, 0, 0, stream=stream)
+
+    def mixed():
+        nonlocal work
+        work = bf.dposv_mixed(n, nrhs, dA, 0, 0, dB, 0, 0, dXm, 0, 0, tol=1e-12, max_iter=30,
+                              iters=iters, resid=resid, work=work, stream=stream)
+
+    def timeit(fn, reps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    reps = max(3, args.steps)
+    t64 = timeit(fp64, reps)
+    tmx = timeit(mixed, reps)
+    it = iters.cpu().numpy()
+    # relative residuals ||B - A X||_F / (||A||_F ||X||_F), recomputed in FP64 on the device by torch
+    Xm = dXm.to_colmajor()
+    X64 = dX64.to_colmajor()
+
+    def rel(X):
+        R = B - torch.bmm(A, X)
+        return (torch.linalg.matrix_norm(R) / (torch.linalg.matrix_norm(A) * torch.linalg.matrix_norm(X))).cpu().numpy()
+
+    rm, r64 = rel(Xm), rel(X64)
+    fl = bt * (n ** 3 / 3.0 + n ** 2 / 2.0 + n / 6.0 + 2.0 * n * n * nrhs)
+    hist = {int(k): int(v) for k, v in zip(*np.unique(it, return_counts=True))}
+    return {
+        "workload": "8192 SPD systems, n=128, cond log-uniform in [1e2,1e6] (Q diag(lam) Q^T), 4 RHS",
+        "fp64_path": "potrf_l + potrs_l (FP64)",
+        "mixed_path": "FP32 potrf (FFMA) + FP32 triangular solves + FP64 residuals, stop at 1e-12",
+        "fp64_ms": round(t64, 4), "mixed_ms": round(tmx, 4), "speedup": round(t64 / tmx, 3),
+        "fp64_gflops": round(fl / (t64 * 1e-3) / 1e9, 2),
+        "mixed_gflops_equiv": round(fl / (tmx * 1e-3) / 1e9, 2),
+        "max_rel_resid_fp64": float(r64.max()), "max_rel_resid_mixed": float(rm.max()),
+        "all_converged": bool((it >= 1).all()), "iters_hist": hist,
+        "mean_iters": round(float(it[it >= 1].mean()), 3) if (it >= 1).any() else None,
+    }
+
+
 # ---------------------------------------------------------- reference arm --
 
 def run_reference(args):
@@ -564,6 +637,7 @@ def main():
     ap.add_argument("--points", default="", help="comma list of routine@n, routine or n (debug subsets)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=0.3, help="seconds of oracle time per point")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -201,6 +201,44 @@ int bf_dsyrk_dpotrf_ln(int m, int k, const bf_dmat *sA, int ai, int aj,
                        const bf_dmat *sB, int bi, int bj, const bf_dmat *sC, int ci, int cj,
                        const bf_dmat *sD, int di, int dj, int *info, void *stream);
 
+/* ---- solves with the Cholesky factor -------------------------------------- */
+
+/* potrs: solves A X = B for X, given the lower Cholesky factor L of A
+ * (L L^T = A, as computed by bf_dpotrf_l_batched):  X = L^{-T} L^{-1} B.
+ * The two triangular solves are the right-hand-side forms of trsm (trsv_lnn
+ * and trsv_ltn of the paper's BLAS level-2 list, Appendix A.3).
+ * L is the n x n lower triangle of sL at (li, lj); B and X are n x nrhs and
+ * may coincide.  Supports n <= 160 and 1 <= nrhs <= 8. */
+int bf_dpotrs_l_batched(int batch, int n, int nrhs, const bf_dmat *sL, int li, int lj,
+                        long long strideL, const bf_dmat *sB, int bi, int bj, long long strideB,
+                        const bf_dmat *sX, int xi, int xj, long long strideX, void *stream);
+
+/* Bytes of device workspace bf_dposv_mixed_batched needs for `batch`
+ * systems of order n (the single-precision factors and their status). */
+size_t bf_dposv_mixed_worksize(int batch, int n);
+
+/* Mixed-precision SPD solve with FP64 iterative refinement (not in the
+ * paper, which has separate single- and double-precision routines,
+ * Appendix A.3): the lower Cholesky factor of fl32(A) is computed in FP32
+ * into `work`, then x = 0, r = b and, up to max_iter times,
+ *     d = (L32 L32^T)^{-1} r (FP32),  x += d,  r = b - A x (FP64),
+ * stopping once ||R||_F / (||A||_F ||X||_F) <= tol over the nrhs columns.
+ * A is n x n SPD (only its lower triangle is read); B and X are n x nrhs
+ * (they must not coincide).
+ * iters (device, may be NULL): per system, the number of corrections taken
+ *   when the tolerance was met; -1 if it was not met within max_iter (X
+ *   holds the last iterate); -2 if the FP32 factorization failed (X not
+ *   written).  Callers fall back to potrf + potrs for those systems.
+ * resid (device, may be NULL): the final relative residual per system.
+ * work: device memory of at least bf_dposv_mixed_worksize(batch, n) bytes,
+ *   256-byte aligned, owned by the caller; its contents are scratch.
+ * Supports n <= 160 and 1 <= nrhs <= 8. */
+int bf_dposv_mixed_batched(int batch, int n, int nrhs, const bf_dmat *sA, int ai, int aj,
+                           long long strideA, const bf_dmat *sB, int bi, int bj, long long strideB,
+                           const bf_dmat *sX, int xi, int xj, long long strideX, double tol,
+                           int max_iter, int *iters, double *resid, void *work, size_t work_bytes,
+                           void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -74,6 +74,8 @@ def _lib():
             lib.or_dpotrf_l_batch.argtypes = [_i, _i, _dp, _i, _l, _dp, _i, _l, _dp, _l, _ip]
             lib.or_dtrsm_rltn_batch.argtypes = [_i, _i, _i, _d, _dp, _i, _l, _dp, _i, _l,
                                                 _dp, _i, _l]
+            lib.or_dpotrs_l.argtypes = [_i, _i, _dp, _i, _dp, _i, _dp, _i]
+            lib.or_dpotrs_l_batch.argtypes = [_i, _i, _i, _dp, _i, _l, _dp, _i, _l, _dp, _i, _l]
             lib.or_dsyrk_dpotrf_ln_batch.argtypes = [_i, _i, _i, _dp, _i, _l, _dp, _i, _l,
                                                      _dp, _i, _l, _dp, _i, _l, _dp, _l, _ip]
             _LIB = lib
@@ -167,6 +169,19 @@ def dtrsm_rltn(alpha, L, B):
     _lib().or_dtrsm_rltn_batch(bt, m, n, alpha, _ptr(lbuf), n, n * n, _ptr(bbuf), m, m * n,
                                _ptr(d), m, m * n)
     out = _back(d)
+    return out[0] if single else out
+
+
+def dpotrs_l(L, B):
+    """X = A^{-1} B for A = L L^T (L lower), B n x nrhs."""
+    single = np.asarray(B).ndim == 2
+    L, B = _batched(L), _batched(B)
+    bt, n, nrhs = B.shape
+    lbuf, bbuf = _colmajor(L), _colmajor(B)
+    x = np.zeros((bt, nrhs, n))
+    _lib().or_dpotrs_l_batch(bt, n, nrhs, _ptr(lbuf), n, n * n, _ptr(bbuf), n, n * nrhs,
+                             _ptr(x), n, n * nrhs)
+    out = _back(x)
     return out[0] if single else out
 
 

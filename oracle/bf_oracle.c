@@ -128,6 +128,29 @@ int or_dsyrk_dpotrf_ln(int m, int k, const double *A, int lda, const double *B, 
   return info;
 }
 
+/* potrs (solve with the Cholesky factor; the two right-hand-side triangular
+ * solves trsv_lnn and trsv_ltn of the BLAS level-2 list, Appendix A.3):
+ * given lower L with L L^T = A, X = A^{-1} B by
+ *   forward substitution  L Y = B:    Y[i] = (B[i] - sum_{l<i} L[i][l] Y[l]) / L[i][i]
+ *   backward substitution L^T X = Y:  X[i] = (Y[i] - sum_{l>i} L[l][i] X[l]) / L[i][i]
+ * column by column of B (n x nrhs).  Y is kept in X; B and X may coincide. */
+void or_dpotrs_l(int n, int nrhs, const double *L, int ldl, const double *B, int ldb, double *X,
+                 int ldx) {
+  if (n <= 0 || nrhs <= 0) return;
+  for (int k = 0; k < nrhs; k++) {
+    for (int i = 0; i < n; i++) {
+      double s = EL(B, ldb, i, k);
+      for (int l = 0; l < i; l++) s -= EL(L, ldl, i, l) * EL(X, ldx, l, k);
+      EL(X, ldx, i, k) = s / EL(L, ldl, i, i);
+    }
+    for (int i = n - 1; i >= 0; i--) {
+      double s = EL(X, ldx, i, k);
+      for (int l = i + 1; l < n; l++) s -= EL(L, ldl, l, i) * EL(X, ldx, l, k);
+      EL(X, ldx, i, k) = s / EL(L, ldl, i, i);
+    }
+  }
+}
+
 /* Panel-major format (Sec. 4.3.3): rows are grouped in panels of ps rows
  * (ps a power of two); each panel is a column-major ps x cn block (lda = ps)
  * and panels follow one another, ps*cn doubles apart.  Element (r, c) of the
@@ -201,6 +224,13 @@ void or_dtrsm_rltn_batch(int batch, int m, int n, double alpha, const double *L,
   for (int b = 0; b < batch; b++)
     or_dtrsm_rltn(m, n, alpha, L + (size_t)b * sL, ldl, B + (size_t)b * sB, ldb,
                   D + (size_t)b * sD, ldd);
+}
+
+void or_dpotrs_l_batch(int batch, int n, int nrhs, const double *L, int ldl, long sL,
+                       const double *B, int ldb, long sB, double *X, int ldx, long sX) {
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int b = 0; b < batch; b++)
+    or_dpotrs_l(n, nrhs, L + (size_t)b * sL, ldl, B + (size_t)b * sB, ldb, X + (size_t)b * sX, ldx);
 }
 
 void or_dsyrk_dpotrf_ln_batch(int batch, int m, int k, const double *A, int lda, long sA,

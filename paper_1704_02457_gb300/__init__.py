@@ -19,6 +19,7 @@ from ._abi import BF_ALIGN, BF_ERR_UNSUPPORTED, BF_PS, bf_dmat, load
 __all__ = [
     "BF_PS", "BF_ALIGN", "BF_ERR_UNSUPPORTED", "BfError", "DMatBatch", "bf_dmat", "load",
     "dgemm_nt", "dsyrk_ln", "dpotrf_l", "dtrsm_rltn", "dsyrk_dpotrf_ln", "pack", "unpack",
+    "dpotrs_l", "dposv_mixed", "dposv_mixed_worksize",
 ]
 
 
@@ -190,3 +191,34 @@ def dtrsm_rltn(m, n, alpha, L, li, lj, B, bi, bj, D, di, dj, use_dinv=False, bat
     _check("bf_dtrsm_rltn_batched", load().bf_dtrsm_rltn_batched(
         batch, m, n, alpha, *_op(L, li, lj), dptr, L.stride if dptr else 0, *_op(B, bi, bj),
         *_op(D, di, dj), _stream(stream)))
+
+
+def dpotrs_l(n, nrhs, L, li, lj, B, bi, bj, X, xi, xj, batch=None, stream=None):
+    """X <- A^{-1} B with A = L L^T (bf_dpotrs_l_batched); B, X are n x nrhs."""
+    batch = X.batch if batch is None else batch
+    _check("bf_dpotrs_l_batched", load().bf_dpotrs_l_batched(
+        batch, n, nrhs, *_op(L, li, lj), *_op(B, bi, bj), *_op(X, xi, xj), _stream(stream)))
+
+
+def dposv_mixed_worksize(batch, n):
+    return load().bf_dposv_mixed_worksize(batch, n)
+
+
+def dposv_mixed(n, nrhs, A, ai, aj, B, bi, bj, X, xi, xj, tol=1e-12, max_iter=30, iters=None,
+                resid=None, work=None, batch=None, stream=None):
+    """Mixed-precision SPD solve with FP64 iterative refinement
+    (bf_dposv_mixed_batched).  work: a device tensor of at least
+    dposv_mixed_worksize(batch, n) bytes (allocated here if None, returned)."""
+    torch = _torch()
+    batch = X.batch if batch is None else batch
+    need = dposv_mixed_worksize(batch, n)
+    if work is None:
+        raw = torch.empty(need + BF_ALIGN, dtype=torch.uint8, device=X.storage.device)
+        off = (-raw.data_ptr()) % BF_ALIGN
+        work = raw[off:off + need]
+    _check("bf_dposv_mixed_batched", load().bf_dposv_mixed_batched(
+        batch, n, nrhs, *_op(A, ai, aj), *_op(B, bi, bj), *_op(X, xi, xj), float(tol), int(max_iter),
+        ctypes.c_void_p(iters.data_ptr()) if iters is not None else None,
+        ctypes.c_void_p(resid.data_ptr()) if resid is not None else None,
+        ctypes.c_void_p(work.data_ptr()), work.numel() * work.element_size(), _stream(stream)))
+    return work

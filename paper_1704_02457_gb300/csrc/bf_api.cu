@@ -292,4 +292,59 @@ int bf_dsyrk_dpotrf_ln(int m, int k, const bf_dmat *sA, int ai, int aj, const bf
   return -map[-r];
 }
 
+// ------------------------------------------------------------------ solves
+
+int bf_dpotrs_l_batched(int batch, int n, int nrhs, const bf_dmat *sL, int li, int lj,
+                        long long strideL, const bf_dmat *sB, int bi, int bj, long long strideB,
+                        const bf_dmat *sX, int xi, int xj, long long strideX, void *stream) {
+  if (batch < 0) return -1;
+  if (n < 0) return -2;
+  if (nrhs < 0) return -3;
+  if (batch == 0 || n == 0 || nrhs == 0) return 0;
+  if (n > POSV_MAX_N || nrhs > POSV_MAX_NRHS) return BF_ERR_UNSUPPORTED;
+  if (int w = check_op(sL, li, lj, n, n, strideL, batch, false)) return pos_err(w, 4);
+  if (int w = check_op(sB, bi, bj, n, nrhs, strideB, batch, false)) return pos_err(w, 8);
+  if (int w = check_op(sX, xi, xj, n, nrhs, strideX, batch, true)) return pos_err(w, 12);
+  return status(launch_potrs(batch, n, nrhs, make_op(sL, li, lj, strideL), make_op(sB, bi, bj, strideB),
+                             make_opw(sX, xi, xj, strideX), (cudaStream_t)stream));
+}
+
+size_t bf_dposv_mixed_worksize(int batch, int n) {
+  if (batch <= 0 || n <= 0) return 0;
+  const size_t pm = ((size_t)n + PS - 1) / PS * PS;
+  const size_t l32 = ((size_t)batch * pm * n * sizeof(float) + BF_ALIGN - 1) / BF_ALIGN * BF_ALIGN;
+  const size_t info = ((size_t)batch * sizeof(int) + BF_ALIGN - 1) / BF_ALIGN * BF_ALIGN;
+  return l32 + info;
+}
+
+int bf_dposv_mixed_batched(int batch, int n, int nrhs, const bf_dmat *sA, int ai, int aj,
+                           long long strideA, const bf_dmat *sB, int bi, int bj, long long strideB,
+                           const bf_dmat *sX, int xi, int xj, long long strideX, double tol,
+                           int max_iter, int *iters, double *resid, void *work, size_t work_bytes,
+                           void *stream) {
+  if (batch < 0) return -1;
+  if (n < 0) return -2;
+  if (nrhs < 0) return -3;
+  if (batch == 0 || n == 0 || nrhs == 0) return 0;
+  if (n > POSV_MAX_N || nrhs > POSV_MAX_NRHS) return BF_ERR_UNSUPPORTED;
+  if (int w = check_op(sA, ai, aj, n, n, strideA, batch, false)) return pos_err(w, 4);
+  if (int w = check_op(sB, bi, bj, n, nrhs, strideB, batch, false)) return pos_err(w, 8);
+  if (int w = check_op(sX, xi, xj, n, nrhs, strideX, batch, true)) return pos_err(w, 12);
+  if (sX->pA == sB->pA) return -12;
+  if (!(tol >= 0.0)) return -16;
+  if (max_iter < 1) return -17;
+  if (iters && !aligned_to(iters, 4)) return -18;
+  if (resid && !aligned_to(resid, 8)) return -19;
+  if (!work || !aligned_to(work, BF_ALIGN)) return -20;
+  if (work_bytes < bf_dposv_mixed_worksize(batch, n)) return -21;
+  const size_t pm = ((size_t)n + PS - 1) / PS * PS;
+  float *l32 = (float *)work;
+  int *info32 = (int *)((char *)work + ((size_t)batch * pm * n * sizeof(float) + BF_ALIGN - 1) / BF_ALIGN * BF_ALIGN);
+  const Op A = make_op(sA, ai, aj, strideA);
+  const bool fast = fast_path({&A});
+  return status(launch_posv_mixed(batch, n, nrhs, A, make_op(sB, bi, bj, strideB),
+                                  make_opw(sX, xi, xj, strideX), tol, max_iter, iters, resid, l32,
+                                  info32, fast, (cudaStream_t)stream));
+}
+
 }  // extern "C"

@@ -243,29 +243,41 @@ k_chol_small(int batch, int n, int k, Op A, Op B, Op C, OpW D, double *dinv, lon
 // ---------------------------------------------------------------------------
 constexpr int KC = 32;  // columns per staged chunk
 
+// Compute type of the row kernel: double for the library routines, float
+// for the single-precision factor of the mixed-precision solver.
+template <typename T> struct Vec2;
+template <> struct Vec2<double> { using type = double2; };
+template <> struct Vec2<float> { using type = float2; };
+__device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
+__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+
+template <typename T>
 struct RowsSmem {
-  double stage[KC][34];  // stage[ll][jj]: row c0+jj, column l0+ll of the shared operand
-                         // (even pitch: pairs (jj, jj+1) are read as one 16-byte load)
-  double Ls[32][33];     // diagonal block of L: Ls[jj][j]
-  double rinv[32];
+  T stage[KC][34];  // stage[ll][jj]: row c0+jj, column l0+ll of the shared operand
+                    // (even pitch: pairs (jj, jj+1) are read as one vector load)
+  T Ls[32][33];     // diagonal block of L: Ls[jj][j]
+  T rinv[32];
   int bad;
 };
 
-template <int W, bool FUSED, bool ALIGNED>
-__device__ __forceinline__ void rows_block(RowsSmem &S, int c0, int n, int k, const double *pa,
-                                           const double *pb, const double *pc, double *pd, Op A,
-                                           Op B, Op C, OpW D, double *dinv_b) {
+template <int W, bool FUSED, bool ALIGNED, typename T>
+__device__ __forceinline__ void rows_block(RowsSmem<T> &S, int c0, int n, int k, const double *pa,
+                                           const double *pb, const double *pc, T *pd, Op A,
+                                           Op B, Op C, OpWT<T> D, T *dinv_b) {
+  using T2 = typename Vec2<T>::type;
   const int i = threadIdx.x;
-  const int T = blockDim.x;
+  const int T_ = blockDim.x;
   const int w = min(32, n - c0);
   const bool active = (i < n) && (i >= c0);
-  double acc[W];
+  T acc[W];
 
   // (a) C[i][c0 + jj] for the lower part of the block column
 #pragma unroll
   for (int jj = 0; jj < W; jj++) {
     const int col = c0 + jj;
-    acc[jj] = (active && jj < w && i >= col) ? pc[pm_off(C.i0 + i, C.j0 + col, C.cn)] : 0.0;
+    acc[jj] = (active && jj < w && i >= col) ? (T)pc[pm_off(C.i0 + i, C.j0 + col, C.cn)] : (T)0;
   }
 
   // (a') syrk_potrf: += A[i][:] * B[c0..c0+w)[:]^T, B rows staged per chunk
@@ -274,20 +286,20 @@ __device__ __forceinline__ void rows_block(RowsSmem &S, int c0, int n, int k, co
     for (int l0 = 0; l0 < k; l0 += KC) {
       const int kc = min(KC, k - l0);
       __syncthreads();
-      for (int x = i; x < 32 * KC; x += T) {
+      for (int x = i; x < 32 * KC; x += T_) {
         const int r4 = x % PS, ll = (x / PS) % KC, pnl = x / (PS * KC);
         const int jj = pnl * PS + r4;
-        S.stage[ll][jj] = (jj < w && ll < kc) ? __ldg(pb + pm_off(B.i0 + c0 + jj, B.j0 + l0 + ll, B.cn)) : 0.0;
+        S.stage[ll][jj] = (jj < w && ll < kc) ? (T)__ldg(pb + pm_off(B.i0 + c0 + jj, B.j0 + l0 + ll, B.cn)) : (T)0;
       }
       __syncthreads();
       if (active) {
         for (int ll = 0; ll < kc; ll++) {
-          const double x = __ldg(arow + (long long)(l0 + ll) * PS);
+          const T x = (T)__ldg(arow + (long long)(l0 + ll) * PS);
 #pragma unroll
           for (int jj = 0; jj < W; jj += 2) {
-            const double2 bv = *(const double2 *)&S.stage[ll][jj];
-            acc[jj] = fma(x, bv.x, acc[jj]);
-            if (jj + 1 < W) acc[jj + 1] = fma(x, bv.y, acc[jj + 1]);
+            const T2 bv = *(const T2 *)&S.stage[ll][jj];
+            acc[jj] = fma_t(x, bv.x, acc[jj]);
+            if (jj + 1 < W) acc[jj + 1] = fma_t(x, bv.y, acc[jj + 1]);
           }
         }
       }
@@ -296,24 +308,24 @@ __device__ __forceinline__ void rows_block(RowsSmem &S, int c0, int n, int k, co
 
   // (b) downdate with the columns of L already computed: -= L[i][0:c0] L[c0..][0:c0]^T
   {
-    const double *lrow = pd + pm_off(D.i0 + min(i, n - 1), D.j0, D.cn);
+    const T *lrow = pd + pm_off(D.i0 + min(i, n - 1), D.j0, D.cn);
     for (int l0 = 0; l0 < c0; l0 += KC) {
       __syncthreads();
-      for (int x = i; x < 32 * KC; x += T) {
+      for (int x = i; x < 32 * KC; x += T_) {
         const int r4 = x % PS, ll = (x / PS) % KC, pnl = x / (PS * KC);
         const int jj = pnl * PS + r4;
-        S.stage[ll][jj] = (jj < w) ? pd[pm_off(D.i0 + c0 + jj, D.j0 + l0 + ll, D.cn)] : 0.0;
+        S.stage[ll][jj] = (jj < w) ? pd[pm_off(D.i0 + c0 + jj, D.j0 + l0 + ll, D.cn)] : (T)0;
       }
       __syncthreads();
       if (active) {
 #pragma unroll 2
         for (int ll = 0; ll < KC; ll++) {
-          const double x = lrow[(long long)(l0 + ll) * PS];
+          const T x = lrow[(long long)(l0 + ll) * PS];
 #pragma unroll
           for (int jj = 0; jj < W; jj += 2) {
-            const double2 lv = *(const double2 *)&S.stage[ll][jj];
-            acc[jj] = fma(-x, lv.x, acc[jj]);
-            if (jj + 1 < W) acc[jj + 1] = fma(-x, lv.y, acc[jj + 1]);
+            const T2 lv = *(const T2 *)&S.stage[ll][jj];
+            acc[jj] = fma_t(-x, lv.x, acc[jj]);
+            if (jj + 1 < W) acc[jj + 1] = fma_t(-x, lv.y, acc[jj + 1]);
           }
         }
       }
@@ -327,9 +339,9 @@ __device__ __forceinline__ void rows_block(RowsSmem &S, int c0, int n, int k, co
 #pragma unroll
     for (int j = 0; j < W; j++) {
       if (j < w) {
-        const double d = __shfl_sync(FULL, acc[j], j);
-        const double r = rsqrt(d);
-        if (!(d > 0.0) && bad == 0) bad = c0 + j + 1;
+        const T d = __shfl_sync(FULL, acc[j], j);
+        const T r = rsqrt_t(d);
+        if (!(d > (T)0) && bad == 0) bad = c0 + j + 1;
         if (lane == j) {
           acc[j] = d * r;
           S.rinv[j] = r;
@@ -338,8 +350,8 @@ __device__ __forceinline__ void rows_block(RowsSmem &S, int c0, int n, int k, co
         }
 #pragma unroll
         for (int jj = j + 1; jj < W; jj++) {
-          const double v = __shfl_sync(FULL, acc[j], jj);
-          acc[jj] = fma(-acc[j], v, acc[jj]);
+          const T v = __shfl_sync(FULL, acc[j], jj);
+          acc[jj] = fma_t(-acc[j], v, acc[jj]);
         }
       }
     }
@@ -355,13 +367,13 @@ __device__ __forceinline__ void rows_block(RowsSmem &S, int c0, int n, int k, co
     for (int j = 0; j < W; j++) {
       acc[j] *= S.rinv[j];
 #pragma unroll
-      for (int jj = j + 1; jj < W; jj++) acc[jj] = fma(-acc[j], S.Ls[jj][j], acc[jj]);
+      for (int jj = j + 1; jj < W; jj++) acc[jj] = fma_t(-acc[j], S.Ls[jj][j], acc[jj]);
     }
   }
 
   // (e) store the block column
   if (active) {
-    double *drow = pd + pm_off(D.i0 + i, D.j0, D.cn);
+    T *drow = pd + pm_off(D.i0 + i, D.j0, D.cn);
 #pragma unroll
     for (int jj = 0; jj < W; jj++) {
       const int col = c0 + jj;
@@ -372,25 +384,25 @@ __device__ __forceinline__ void rows_block(RowsSmem &S, int c0, int n, int k, co
   __syncthreads();
 }
 
-template <bool FUSED, bool ALIGNED>
+template <bool FUSED, bool ALIGNED, typename T>
 __global__ void __launch_bounds__(512)
-k_chol_rows(int n, int k, Op A, Op B, Op C, OpW D, double *dinv, long long sdinv, int *info) {
-  __shared__ RowsSmem S;
+k_chol_rows(int n, int k, Op A, Op B, Op C, OpWT<T> D, T *dinv, long long sdinv, int *info) {
+  __shared__ RowsSmem<T> S;
   const int b = blockIdx.x;
   const double *pa = FUSED ? A.p + b * A.stride : nullptr;
   const double *pb = FUSED ? B.p + b * B.stride : nullptr;
   const double *pc = C.p + b * C.stride;
-  double *pd = D.p + b * D.stride;
-  double *dinv_b = dinv ? dinv + b * sdinv : nullptr;
+  T *pd = D.p + b * D.stride;
+  T *dinv_b = dinv ? dinv + b * sdinv : nullptr;
   if (threadIdx.x == 0) S.bad = 0;
   __syncthreads();
   for (int c0 = 0; c0 < n; c0 += 32) {
     const int w8 = (min(32, n - c0) + 7) & ~7;
     switch (w8) {
-      case 8: rows_block<8, FUSED, ALIGNED>(S, c0, n, k, pa, pb, pc, pd, A, B, C, D, dinv_b); break;
-      case 16: rows_block<16, FUSED, ALIGNED>(S, c0, n, k, pa, pb, pc, pd, A, B, C, D, dinv_b); break;
-      case 24: rows_block<24, FUSED, ALIGNED>(S, c0, n, k, pa, pb, pc, pd, A, B, C, D, dinv_b); break;
-      default: rows_block<32, FUSED, ALIGNED>(S, c0, n, k, pa, pb, pc, pd, A, B, C, D, dinv_b); break;
+      case 8: rows_block<8, FUSED, ALIGNED, T>(S, c0, n, k, pa, pb, pc, pd, A, B, C, D, dinv_b); break;
+      case 16: rows_block<16, FUSED, ALIGNED, T>(S, c0, n, k, pa, pb, pc, pd, A, B, C, D, dinv_b); break;
+      case 24: rows_block<24, FUSED, ALIGNED, T>(S, c0, n, k, pa, pb, pc, pd, A, B, C, D, dinv_b); break;
+      default: rows_block<32, FUSED, ALIGNED, T>(S, c0, n, k, pa, pb, pc, pd, A, B, C, D, dinv_b); break;
     }
   }
   if (info && threadIdx.x == 0) info[b] = S.bad;
@@ -432,9 +444,9 @@ cudaError_t launch_chol_t(bool aligned, int batch, int n, int k, Op A, Op B, Op 
   }
   const int threads = (n + 31) & ~31;
   if (aligned)
-    k_chol_rows<FUSED, true><<<batch, threads, 0, s>>>(n, k, A, B, C, D, dinv, sdinv, info);
+    k_chol_rows<FUSED, true, double><<<batch, threads, 0, s>>>(n, k, A, B, C, D, dinv, sdinv, info);
   else
-    k_chol_rows<FUSED, false><<<batch, threads, 0, s>>>(n, k, A, B, C, D, dinv, sdinv, info);
+    k_chol_rows<FUSED, false, double><<<batch, threads, 0, s>>>(n, k, A, B, C, D, dinv, sdinv, info);
   return cudaGetLastError();
 }
 
@@ -444,6 +456,17 @@ cudaError_t launch_chol(bool fused, int batch, int n, int k, Op A, Op B, Op C, O
                         double *dinv, long long sdinv, int *info, bool aligned, cudaStream_t s) {
   return fused ? launch_chol_t<true>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s)
                : launch_chol_t<false>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
+}
+
+cudaError_t launch_chol_f32(int batch, int n, Op C, OpWT<float> D, int *info, bool aligned,
+                            cudaStream_t s) {
+  const int threads = (n + 31) & ~31;
+  const Op none{nullptr, 0, 0, 0, 0};
+  if (aligned)
+    k_chol_rows<false, true, float><<<batch, threads, 0, s>>>(n, 0, none, none, C, D, nullptr, 0, info);
+  else
+    k_chol_rows<false, false, float><<<batch, threads, 0, s>>>(n, 0, none, none, C, D, nullptr, 0, info);
+  return cudaGetLastError();
 }
 
 }  // namespace bf

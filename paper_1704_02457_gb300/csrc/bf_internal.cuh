@@ -24,13 +24,15 @@ struct Op {
   int i0, j0;
 };
 
-// A written operand.
-struct OpW {
-  double *p;
+// A written operand (of element type T; OpW for the FP64 routines).
+template <typename T>
+struct OpWT {
+  T *p;
   long long stride;
   int cn;
   int i0, j0;
 };
+using OpW = OpWT<double>;
 
 __host__ __device__ __forceinline__ long long pm_off(int r, int c, int cn) {
   return (long long)(r & ~(PS - 1)) * cn + (long long)c * PS + (r & (PS - 1));
@@ -45,8 +47,20 @@ cudaError_t launch_gemm_nt(bool syrk, int batch, int m, int n, int k, double alp
 cudaError_t launch_chol(bool fused, int batch, int n, int k, Op A, Op B, Op C, OpW D,
                         double *dinv, long long sdinv, int *info, bool aligned, cudaStream_t s);
 
+// FP32 lower Cholesky factor of an FP64 input (the mixed-precision solver's
+// working factor), written panel-major in single precision.
+cudaError_t launch_chol_f32(int batch, int n, Op C, OpWT<float> D, int *info, bool aligned,
+                            cudaStream_t s);
+
 cudaError_t launch_trsm_rltn(int batch, int m, int n, double alpha, Op L, const double *dinv,
                              long long sdinv, Op B, OpW D, cudaStream_t s);
+
+// A X = B with the FP64 factor L (potrs), and the mixed-precision solver
+// (FP32 factor in the workspace l32 / info32, FP64 iterative refinement).
+cudaError_t launch_potrs(int batch, int n, int nrhs, Op L, Op B, OpW X, cudaStream_t s);
+cudaError_t launch_posv_mixed(int batch, int n, int nrhs, Op A, Op B, OpW X, double tol,
+                              int max_iter, int *iters, double *resid, float *l32, int *info32,
+                              bool aligned, cudaStream_t s);
 
 cudaError_t launch_pack(int batch, int m, int n, const double *A, int lda, long long sA, OpW B,
                         cudaStream_t s);
@@ -56,5 +70,7 @@ cudaError_t launch_unpack(int batch, int m, int n, Op A, double *B, int ldb, lon
 // Largest order the factorization kernels accept.
 constexpr int CHOL_MAX_N = 512;
 constexpr int TRSM_MAX_N = 4096;
+constexpr int POSV_MAX_N = 160;
+constexpr int POSV_MAX_NRHS = 8;
 
 }  // namespace bf

@@ -1,0 +1,299 @@
+// Cholesky solves of SPD systems A X = B with a few right-hand sides:
+//
+//  potrs (FP64):  X = L^{-T} L^{-1} B with the factor from potrf_l.  The two
+//    triangular solves are the right-hand-side forms of trsm (the trsv_lnn /
+//    trsv_ltn routines of the paper's BLAS-2 list, Appendix A.3).
+//
+//  posv mixed:    the single-precision factor L32 of fl32(A) (k_chol_rows in
+//    FP32, written to the caller's workspace) is used for FP32 triangular
+//    solves inside an FP64 iterative refinement:
+//        x = 0, r = b
+//        repeat:  d = L32^{-T} L32^{-1} r   (FP32)
+//                 x = x + d                 (FP64)
+//                 r = b - A x               (FP64, A's lower triangle)
+//        until ||R||_F / (||A||_F ||X||_F) <= tol   (all right-hand sides)
+//    Each correction shrinks the residual by about cond(A) * 2^-24, so for
+//    cond(A) <= 1e6 a handful of FP64 residuals replaces the FP64
+//    factorization.
+//
+// One CTA per system.  The factor lives packed in shared memory (column l at
+// cs(l), element (i, l) at cs(l) + i), one warp solves one right-hand side
+// (column-oriented forward substitution, dot-product backward substitution),
+// and the FP64 residual gives every thread one row of A, read from L2 in
+// panel-major order, for all right-hand sides at once.
+#include <type_traits>
+
+#include "bf_internal.cuh"
+
+namespace bf {
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ int col_start(int l, int n) { return (l * (2 * n - l + 1)) / 2 - l; }
+
+template <typename T>
+__device__ __forceinline__ void cp_async(T *dst, const T *src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  if (sizeof(T) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+__device__ __forceinline__ double block_sum(double v, double *red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int i = 0; i < nw; i++) s += red[i];
+  return s;
+}
+
+// forward then backward substitution of one right-hand side v (length n) in
+// shared memory against the packed factor L, by one warp: v <- L^{-T} L^{-1} v
+template <typename T>
+__device__ __forceinline__ void warp_solve(const T *L, const T *dinv, T *v, int n) {
+  const int lane = threadIdx.x & 31;
+  // L y = v: column j finishes y_j, then updates the rows below it
+  for (int j = 0; j < n; j++) {
+    const T yj = v[j] * dinv[j];
+    __syncwarp();
+    const int cs = col_start(j, n);
+    for (int i = j + 1 + lane; i < n; i += 32) v[i] -= L[cs + i] * yj;
+    if (lane == 0) v[j] = yj;
+    __syncwarp();
+  }
+  // L^T x = y: x_j = (y_j - L(j+1:, j) . x(j+1:)) / L_jj, from the bottom up
+  for (int j = n - 1; j >= 0; j--) {
+    const int cs = col_start(j, n);
+    T part = (T)0;
+    for (int i = j + 1 + lane; i < n; i += 32) part += L[cs + i] * v[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(FULL, part, o);
+    if (lane == 0) v[j] = (v[j] - part) * dinv[j];
+    __syncwarp();
+  }
+}
+
+// Column l of packed element e: column l starts at l(2n - l + 1)/2, so l is
+// the smaller root of l^2 - (2n+1) l + 2e = 0, corrected for rounding.
+__device__ __forceinline__ int packed_col(int e, int n) {
+  const float q = 2.0f * n + 1.0f;
+  int l = (int)((q - sqrtf(q * q - 8.0f * e)) * 0.5f);
+  l = max(0, min(l, n - 1));
+  while (l > 0 && col_start(l, n) + l > e) l--;
+  while (l + 1 < n && col_start(l + 1, n) + l + 1 <= e) l++;
+  return l;
+}
+
+// Loads the packed lower triangle of the panel-major factor into shared memory.
+template <typename T>
+__device__ __forceinline__ void load_factor(T *L, const T *pl, int cn, int i0, int j0, int n) {
+  const int NE = n * (n + 1) / 2;
+  for (int e = threadIdx.x; e < NE; e += blockDim.x) {
+    const int l = packed_col(e, n);
+    const int i = e - col_start(l, n);
+    cp_async(&L[e], pl + pm_off(i0 + i, j0 + l, cn));
+  }
+}
+
+// r = b - A x for NR right-hand sides (A's lower triangle, symmetric);
+// accumulates ||r||^2 and ||x||^2 of this thread's rows.
+template <int NR>
+__device__ __forceinline__ void residual(int n, const double *pa, const Op &A, const double *pb,
+                                         const Op &B, const double *x64, double *r64, double &rs,
+                                         double &xs) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double acc[NR];
+#pragma unroll
+    for (int k = 0; k < NR; k++) acc[k] = 0.0;
+    const double *arow = pa + pm_off(A.i0 + i, A.j0, A.cn);
+    for (int j = 0; j <= i; j++) {
+      const double a = arow[(long long)j * PS];
+#pragma unroll
+      for (int k = 0; k < NR; k++) acc[k] = fma(a, x64[k * n + j], acc[k]);
+    }
+    for (int j = i + 1; j < n; j++) {
+      const double a = pa[pm_off(A.i0 + j, A.j0 + i, A.cn)];
+#pragma unroll
+      for (int k = 0; k < NR; k++) acc[k] = fma(a, x64[k * n + j], acc[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < NR; k++) {
+      const double r = pb[pm_off(B.i0 + i, B.j0 + k, B.cn)] - acc[k];
+      r64[k * n + i] = r;
+      rs += r * r;
+      xs += x64[k * n + i] * x64[k * n + i];
+    }
+  }
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(256, 1)
+k_posv(int n, int nrhs, Op A, const float *l32, long long sl32, const int *info32, Op Lf, Op B,
+       OpW X, double tol, int max_iter, int *iters, double *resid) {
+  using TL = typename std::conditional<MIXED, float, double>::type;
+  extern __shared__ double smem_d[];
+  const int b = blockIdx.x;
+  const int t = threadIdx.x, T = blockDim.x;
+  const int NE = n * (n + 1) / 2;
+  // shared memory: [x64 | r64 (MIXED)] [red] [L (TL)] [dinv (TL)] [v (TL)]
+  double *x64 = smem_d;
+  double *r64 = x64 + (MIXED ? nrhs * n : 0);
+  double *red = r64 + (MIXED ? nrhs * n : 0);
+  TL *L = (TL *)(red + 32);
+  TL *dinv = L + ((NE + 3) & ~3);
+  TL *v = dinv + ((n + 3) & ~3);
+
+  if (MIXED && info32 && info32[b] != 0) {
+    // the single-precision factorization failed: report and leave X untouched
+    if (t == 0) {
+      if (iters) iters[b] = -2;
+      if (resid) resid[b] = -1.0;
+    }
+    return;
+  }
+
+  // factor into shared memory, right-hand sides alongside
+  if (MIXED)
+    load_factor<float>((float *)L, l32 + b * sl32, n, 0, 0, n);
+  else
+    load_factor<double>((double *)L, Lf.p + b * Lf.stride, Lf.cn, Lf.i0, Lf.j0, n);
+  const double *pb = B.p + b * B.stride;
+  for (int e = t; e < nrhs * n; e += T) {
+    const int k = e / n, i = e - k * n;
+    const double bv = pb[pm_off(B.i0 + i, B.j0 + k, B.cn)];
+    if (MIXED) {
+      r64[e] = bv;
+      x64[e] = 0.0;
+    } else {
+      v[e] = (TL)bv;
+    }
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  for (int j = t; j < n; j += T) dinv[j] = (TL)1 / L[col_start(j, n) + j];
+  __syncthreads();
+
+  const int warp = t >> 5, nwarps = (T + 31) >> 5;
+  if (!MIXED) {
+    for (int k = warp; k < nrhs; k += nwarps) warp_solve<TL>(L, dinv, v + k * n, n);
+    __syncthreads();
+    double *px = X.p + b * X.stride;
+    for (int e = t; e < nrhs * n; e += T) {
+      const int k = e / n, i = e - k * n;
+      px[pm_off(X.i0 + i, X.j0 + k, X.cn)] = (double)v[e];
+    }
+    return;
+  }
+
+  // ||A||_F from the lower triangle (off-diagonal entries count twice)
+  const double *pa = A.p + b * A.stride;
+  double s = 0.0;
+  for (int e = t; e < NE; e += T) {
+    const int l = packed_col(e, n);
+    const int i = e - col_start(l, n);
+    const double a = pa[pm_off(A.i0 + i, A.j0 + l, A.cn)];
+    s += (i == l ? 1.0 : 2.0) * a * a;
+  }
+  const double anrm = sqrt(block_sum(s, red));
+
+  int it = 0;
+  double rel = 0.0;
+  bool done = false;
+  for (; it < max_iter && !done; it++) {
+    // d = A32^{-1} r in single precision
+    for (int e = t; e < nrhs * n; e += T) v[e] = (TL)r64[e];
+    __syncthreads();
+    for (int k = warp; k < nrhs; k += nwarps) warp_solve<TL>(L, dinv, v + k * n, n);
+    __syncthreads();
+    for (int e = t; e < nrhs * n; e += T) x64[e] += (double)v[e];
+    __syncthreads();
+    // r = b - A x in FP64; thread i owns row i for every right-hand side
+    double rs = 0.0, xs = 0.0;
+    switch (nrhs) {
+      case 1: residual<1>(n, pa, A, pb, B, x64, r64, rs, xs); break;
+      case 2: residual<2>(n, pa, A, pb, B, x64, r64, rs, xs); break;
+      case 3: residual<3>(n, pa, A, pb, B, x64, r64, rs, xs); break;
+      case 4: residual<4>(n, pa, A, pb, B, x64, r64, rs, xs); break;
+      case 5: residual<5>(n, pa, A, pb, B, x64, r64, rs, xs); break;
+      case 6: residual<6>(n, pa, A, pb, B, x64, r64, rs, xs); break;
+      case 7: residual<7>(n, pa, A, pb, B, x64, r64, rs, xs); break;
+      default: residual<8>(n, pa, A, pb, B, x64, r64, rs, xs); break;
+    }
+    const double rn = sqrt(block_sum(rs, red));
+    const double xn = sqrt(block_sum(xs, red));
+    rel = rn / (anrm * xn);
+    done = rel <= tol;  // the same value in every thread
+    __syncthreads();
+  }
+  double *px = X.p + b * X.stride;
+  for (int e = t; e < nrhs * n; e += T) {
+    const int k = e / n, i = e - k * n;
+    px[pm_off(X.i0 + i, X.j0 + k, X.cn)] = x64[e];
+  }
+  if (t == 0) {
+    if (iters) iters[b] = done ? it : -1;
+    if (resid) resid[b] = rel;
+  }
+}
+
+size_t posv_smem(bool mixed, int n, int nrhs) {
+  const size_t ne = (size_t)n * (n + 1) / 2;
+  const size_t tl = mixed ? 4 : 8;
+  size_t bytes = (mixed ? 2 * (size_t)nrhs * n * 8 : 0) + 32 * 8;
+  bytes += (((ne + 3) & ~(size_t)3) + (((size_t)n + 3) & ~(size_t)3) + (size_t)nrhs * n) * tl;
+  return bytes;
+}
+
+int posv_threads(int n, int nrhs) {
+  const int t = max(32 * nrhs, (n + 31) & ~31);
+  return min(256, max(32, t));
+}
+
+template <bool MIXED>
+cudaError_t set_posv_smem_attr() {
+  static bool done = false;
+  if (done) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k_posv<MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e == cudaSuccess) done = true;
+  return e;
+}
+
+}  // namespace
+
+cudaError_t launch_potrs(int batch, int n, int nrhs, Op L, Op B, OpW X, cudaStream_t s) {
+  const size_t smem = posv_smem(false, n, nrhs);
+  if (smem > 200 * 1024) return cudaErrorInvalidConfiguration;
+  cudaError_t e = set_posv_smem_attr<false>();
+  if (e != cudaSuccess) return e;
+  const Op none{nullptr, 0, 0, 0, 0};
+  k_posv<false><<<batch, posv_threads(n, nrhs), smem, s>>>(n, nrhs, none, nullptr, 0, nullptr, L, B, X,
+                                                           0.0, 0, nullptr, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_posv_mixed(int batch, int n, int nrhs, Op A, Op B, OpW X, double tol,
+                              int max_iter, int *iters, double *resid, float *l32, int *info32,
+                              bool aligned, cudaStream_t s) {
+  const int pm = (n + PS - 1) / PS * PS;
+  const OpWT<float> D{l32, (long long)pm * n, n, 0, 0};
+  cudaError_t e = launch_chol_f32(batch, n, A, D, info32, aligned, s);
+  if (e != cudaSuccess) return e;
+  const size_t smem = posv_smem(true, n, nrhs);
+  if (smem > 200 * 1024) return cudaErrorInvalidConfiguration;
+  e = set_posv_smem_attr<true>();
+  if (e != cudaSuccess) return e;
+  const Op none{nullptr, 0, 0, 0, 0};
+  k_posv<true><<<batch, posv_threads(n, nrhs), smem, s>>>(n, nrhs, A, l32, (long long)pm * n, info32, none,
+                                                          B, X, tol, max_iter, iters, resid);
+  return cudaGetLastError();
+}
+
+}  // namespace bf

@@ -46,6 +46,26 @@ def chol_factor(batch: int, n: int, seed: int, device="cpu") -> torch.Tensor:
     return torch.linalg.cholesky(spd(batch, n, seed, device))
 
 
+def spd_cond(batch: int, n: int, seed: int, device="cpu", log10_cond=(2.0, 6.0)):
+    """SPD matrices Q diag(lam) Q^T with cond(A) log-uniform in 10**log10_cond.
+
+    Q is a random orthogonal matrix (QR of an iid N(0,1) matrix, computed on
+    the host by torch.linalg.qr) and lam is log-spaced from 1 down to 1/cond.
+    Returns (A, cond) with A symmetrized as (A + A^T)/2."""
+    g = gen(seed, "cpu")
+    G = torch.randn(batch, n, n, generator=g, dtype=torch.float64)
+    Q, R = torch.linalg.qr(G)
+    Q = Q * torch.sign(torch.diagonal(R, dim1=1, dim2=2)).unsqueeze(1)
+    lo, hi = log10_cond
+    lc = lo + (hi - lo) * torch.rand(batch, generator=g, dtype=torch.float64)
+    t = torch.linspace(0.0, 1.0, n, dtype=torch.float64)
+    lam = torch.pow(10.0, -lc.unsqueeze(1) * t.unsqueeze(0))  # 1 ... 10**-lc
+    Q = Q.to(device)
+    A = torch.bmm(Q * lam.to(device).unsqueeze(1), Q.transpose(1, 2))
+    A = 0.5 * (A + A.transpose(1, 2))
+    return A, torch.pow(10.0, lc)
+
+
 def integers(shape, lo: int, hi: int, seed: int, device="cpu") -> torch.Tensor:
     """iid integers in [lo, hi] stored as float64."""
     x = torch.randint(lo, hi + 1, tuple(shape), generator=gen(seed, device), device=device)

@@ -33,6 +33,10 @@ MUTANTS = {
     "trsm_drops_alpha": ("double s = alpha * EL(B, ldb, i, j);", "double s = EL(B, ldb, i, j);"),
     "syrk_potrf_drops_C": ("or_dsyrk_ln(m, k, 1.0, A, lda, B, ldb, 1.0, C, ldc, T, m);",
                            "or_dsyrk_ln(m, k, 1.0, A, lda, B, ldb, 0.0, C, ldc, T, m);"),
+    "potrs_backward_uses_row": ("for (int l = i + 1; l < n; l++) s -= EL(L, ldl, l, i) * EL(X, ldx, l, k);",
+                                "for (int l = i + 1; l < n; l++) s -= EL(L, ldl, i, l) * EL(X, ldx, l, k);"),
+    "potrs_forward_drops_term": ("for (int l = 0; l < i; l++) s -= EL(L, ldl, i, l) * EL(X, ldx, l, k);",
+                                 "for (int l = 1; l < i; l++) s -= EL(L, ldl, i, l) * EL(X, ldx, l, k);"),
     "pack_row_in_panel": ("(size_t)c * (size_t)ps + (size_t)(r % ps)", "(size_t)c * (size_t)ps + (size_t)((r + 1) % ps)"),
 }
 
@@ -50,6 +54,7 @@ def _battery():
         lambda: pins.test_pack_is_the_3d_panel_view(8, 13, 17),
         lambda: pins.test_golden_cholesky_3x3(),
         lambda: pins.test_golden_trsm_3x3(),
+        lambda: pins.test_potrs_integer_solution_returns_exactly(8, 4),
     ]
     for c in checks:
         try:

@@ -236,6 +236,36 @@ def test_trsm_matches_scipy():
             <= 1e-15)
 
 
+# ---------------------------------------------------------------- potrs_l ---
+
+@pytest.mark.parametrize("n,nrhs", [(1, 1), (3, 2), (8, 4), (24, 4), (33, 7)])
+def test_potrs_integer_solution_returns_exactly(n, nrhs):
+    rng = np.random.default_rng(300 + n)
+    L = _int_lower_pow2(n, rng, off=2)
+    X = _ints((n, nrhs), -8, 8, rng)
+    B = L @ (L.T @ X)  # exact integers: A X with A = L L^T
+    assert np.abs(B).max() < 2 ** 50
+    assert np.array_equal(oracle.dpotrs_l(L.astype(float), B.astype(float)), X.astype(float))
+
+
+def test_potrs_identity_and_upper_not_read():
+    B = RNG.standard_normal((6, 3))
+    L = np.eye(6)
+    L[np.triu_indices(6, 1)] = np.nan
+    assert np.array_equal(oracle.dpotrs_l(L, B), B)
+
+
+def test_potrs_matches_lapack_solve():
+    n, nrhs = 64, 4
+    M = RNG.standard_normal((n, n))
+    A = M @ M.T + n * np.eye(n)
+    B = RNG.standard_normal((n, nrhs))
+    X = oracle.dpotrs_l(np.linalg.cholesky(A), B)
+    want = np.linalg.solve(A, B)  # LAPACK dgesv
+    assert np.linalg.norm(X - want) / np.linalg.norm(want) <= 1e-13
+    assert np.linalg.norm(A @ X - B) / (np.linalg.norm(A) * np.linalg.norm(X)) <= 1e-15
+
+
 # ---------------------------------------------------------- syrk_potrf_ln ---
 
 @pytest.mark.parametrize("n,k", [(1, 1), (4, 4), (8, 3), (24, 24), (33, 50)])
