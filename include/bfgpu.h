@@ -56,6 +56,13 @@ extern "C" {
 
 #define BF_ERR_UNSUPPORTED 100000
 
+/* Returned by bf_dposv_mixed_batched_noalloc when the problem needs more
+ * scratch than its fixed array holds. */
+#define BF_ERR_TOO_LARGE 100001
+
+/* Bytes of the fixed scratch array of bf_dposv_mixed_batched_noalloc. */
+#define BF_NOALLOC_WORK_BYTES (16 * 1024 * 1024)
+
 /* Matrix descriptor: the blasfeo_dmat structure of Appendix A.1.1 with the
  * members that the panel-major format needs (Sec. 4.3.3).
  *   pA      device pointer to the first element of the storage; 32-byte
@@ -238,6 +245,36 @@ int bf_dposv_mixed_batched(int batch, int n, int nrhs, const bf_dmat *sA, int ai
                            const bf_dmat *sX, int xi, int xj, long long strideX, double tol,
                            int max_iter, int *iters, double *resid, void *work, size_t work_bytes,
                            void *stream);
+
+/* The mixed-precision solver above, for callers that cannot allocate
+ * device memory.  The paper has no counterpart: its routines take external
+ * memory from the caller (Appendix A.1.2) but have no solver that needs
+ * scratch.
+ *
+ * Who needs it: a caller that has no way to hand over a workspace.  A
+ * controller running a fixed-period loop may forbid allocation there,
+ * because cudaMalloc can block the device and can fail at run time.  A
+ * plugin may run inside a host application that owns all device memory.
+ *
+ * Same arguments, checks, results and error codes as
+ * bf_dposv_mixed_batched, minus work / work_bytes.  The scratch is a fixed
+ * array of BF_NOALLOC_WORK_BYTES (16 MiB) inside this library's device
+ * memory; every GPU that loads the library holds it until the process exits.
+ *   - Problems need bf_dposv_mixed_worksize(batch, n) <= BF_NOALLOC_WORK_BYTES
+ *     (for n = 128, up to 255 systems).  Larger calls return
+ *     BF_ERR_TOO_LARGE and launch nothing.
+ *   - The first call on a device looks up the array's address
+ *     (cudaGetSymbolAddress) with that device current.  Make that first call
+ *     before any stream capture on the device.
+ *   - All calls share the array, and it keeps the last call's contents.
+ *     Nothing in it needs to start at zero.  Calls whose kernels overlap on
+ *     the GPU race on it; serialize them (one stream, one thread at a time).
+ *   - Nothing is allocated or freed. */
+int bf_dposv_mixed_batched_noalloc(int batch, int n, int nrhs, const bf_dmat *sA, int ai, int aj,
+                                   long long strideA, const bf_dmat *sB, int bi, int bj,
+                                   long long strideB, const bf_dmat *sX, int xi, int xj,
+                                   long long strideX, double tol, int max_iter, int *iters,
+                                   double *resid, void *stream);
 
 #ifdef __cplusplus
 }

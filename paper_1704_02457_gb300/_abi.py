@@ -17,6 +17,8 @@ _c_int, _c_ll, _c_d, _c_vp, _c_sz = ctypes.c_int, ctypes.c_longlong, ctypes.c_do
 BF_PS = 4
 BF_ALIGN = 256
 BF_ERR_UNSUPPORTED = 100000
+BF_ERR_TOO_LARGE = 100001
+BF_NOALLOC_WORK_BYTES = 16 * 1024 * 1024
 
 
 class bf_dmat(ctypes.Structure):
@@ -62,6 +64,8 @@ SIGNATURES = {
     "bf_dposv_mixed_worksize": (_c_sz, [_c_int, _c_int]),
     "bf_dposv_mixed_batched": (_c_int, [_c_int, _c_int, _c_int, *_M, *_M, *_M, _c_d, _c_int, _c_vp,
                                         _c_vp, _c_vp, _c_sz, _c_vp]),
+    "bf_dposv_mixed_batched_noalloc": (_c_int, [_c_int, _c_int, _c_int, *_M, *_M, *_M, _c_d, _c_int,
+                                                _c_vp, _c_vp, _c_vp]),
 }
 
 _LOCK = threading.Lock()
