@@ -410,6 +410,8 @@ def run_gpu(args):
 
     if not args.no_mixed:
         result["mixed_vs_fp64"] = run_mixed(args, dev)
+    if not args.no_riccati:
+        result["riccati"] = run_riccati(args, dev)
     if not args.no_e2e:
         result["e2e"] = run_e2e(pts, args, dev, world)
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -595,6 +597,62 @@ def run_mixed(args, dev, bt=8192, n=128, nrhs=4):
     }
 
 
+def run_riccati(args, dev, batch=4096, N=20):
+    """Uneven batched backward Riccati recursion (square-root form, Sec. 5.3):
+    4096 MPC instances, horizon 20, nx ~ U{8..64}, nu ~ U{2..16}, A and B iid
+    N(0, 1/nx), Q = R = I, P_N = I.  The bucket launches are captured in a
+    CUDA graph and replayed; CTA widths come from the autotuner."""
+    import numpy as np
+    import torch
+
+    from paper_1704_02457_gb300 import inputs
+    from paper_1704_02457_gb300.riccati import RiccatiBatch
+
+    rng = np.random.default_rng(20170508)
+    nx = rng.integers(8, 65, size=batch)
+    nu = rng.integers(2, 17, size=batch)
+    rb = RiccatiBatch(nx, nu, N, device=dev)
+    counter = [0]
+
+    def gen(a, b, count):
+        counter[0] += 1
+        A = inputs.normal((count, a, a), 11000 + 2 * counter[0], dev) / np.sqrt(a)
+        B = inputs.normal((count, a, b), 11001 + 2 * counter[0], dev) / np.sqrt(a)
+        return A, B
+
+    rb.set_inputs(gen, None)
+    tune = rb.autotune()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        rb.run()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        rb.run()
+    for _ in range(2):
+        graph.replay()
+    torch.cuda.synchronize()
+    reps = max(3, args.steps)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        graph.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    info = rb.infos()
+    gf = rb.flops / (ms * 1e-3) / 1e9
+    return {
+        "workload": "4096 MPC instances, N=20, nx~U{8..64}, nu~U{2..16}, A,B~N(0,1/nx), Q=R=I, P_N=I; "
+                    "square-root Riccati (trmm_rlnn + syrk_potrf_ln + trsm_rlnn per stage)",
+        "ms": round(ms, 4), "gflops": round(gf, 2), "frac_fp64_peak": round(gf / FP64_PEAK_GFLOPS, 4),
+        "flops": rb.flops, "launches_per_recursion": len(rb.buckets), "cuda_graph": True,
+        "autotune": tune, "all_info_zero": bool((info == 0).all()),
+    }
+
+
 # ---------------------------------------------------------- reference arm --
 
 def run_reference(args):
@@ -638,6 +696,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-riccati", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=0.3, help="seconds of oracle time per point")
     args = ap.parse_args()
     if args.impl == "reference":

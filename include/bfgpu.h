@@ -246,6 +246,55 @@ int bf_dposv_mixed_batched(int batch, int n, int nrhs, const bf_dmat *sA, int ai
                            int max_iter, int *iters, double *resid, void *work, size_t work_bytes,
                            void *stream);
 
+/* ---- backward Riccati recursion (Sec. 5.3) -------------------------------- */
+
+/* One MPC instance of bf_driccati_sqrt_batched, in device memory.  All
+ * matrices are panel-major (BF_PS rows per panel) with the given panel
+ * lengths (cn >= the matrix's column count):
+ *   BAt  (nu+nx) x nx: the stacked [B^T; A^T] of x+ = A x + B u
+ *   M0   (nu+nx) x (nu+nx): [[R, S^T], [S, Q]]; only its lower triangle is read
+ *   LN   nx x nx: lower Cholesky factor of the terminal cost P_N
+ *   L    outputs: N lower factors nx x nx, stage k at L + k*l_stride
+ *        (doubles); L_k L_k^T = P_k.  Only the lower triangles are written.
+ *   Kt   outputs: N gains transposed, nx x nu, stage k at Kt + k*kt_stride;
+ *        K_k = Kt_k^T is the feedback u = K_k x.
+ *   info outputs (may be NULL): N ints; 0, or 1 + the column of the first
+ *        non-positive pivot of stage k's factorization, or -1 if the
+ *        instance's sizes exceed the call's max_nx / max_nu. */
+typedef struct bf_riccati_prob {
+  int nx, nu;
+  const double *BAt;
+  int bat_cn;
+  const double *M0;
+  int m0_cn;
+  const double *LN;
+  int ln_cn;
+  double *L;
+  int l_cn;
+  long long l_stride;
+  double *Kt;
+  int kt_cn;
+  long long kt_stride;
+  int *info;
+} bf_riccati_prob;
+
+/* Backward Riccati recursion in the square-root form of Sec. 5.3, for
+ * `batch` independent instances of possibly different sizes.  For each
+ * instance and k = N-1, ..., 0, from Lc = L_{k+1} (L_N = LN):
+ *     C = [B^T; A^T] Lc                                   (trmm_rlnn)
+ *     [[Lam, 0], [Lo, L_k]] = chol(M0 + C C^T)            (syrk_potrf_ln)
+ *     Kt_k Lam = -Lo                                      (trsm_rlnn)
+ * probs: device array of the instances; order (device, may be NULL): the
+ * instances to process, as indices into probs (batch of them), best sorted
+ * by decreasing size so that the GPU starts the longest ones first;
+ * max_nx, max_nu: bounds on the sizes of those instances (they size the
+ * shared memory; instances beyond them are reported in info and skipped);
+ * threads: CTA width (a multiple of 32, 32..512) or 0 for 256.
+ * Returns BF_ERR_UNSUPPORTED if max_nx, max_nu need more than 200 KB of
+ * shared memory (e.g. beyond nx = 64, nu = 64). */
+int bf_driccati_sqrt_batched(int batch, int N, const bf_riccati_prob *probs, const int *order,
+                             int max_nx, int max_nu, int threads, void *stream);
+
 /* The mixed-precision solver above, for callers that cannot allocate
  * device memory.  The paper has no counterpart: its routines take external
  * memory from the caller (Appendix A.1.2) but have no solver that needs

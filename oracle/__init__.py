@@ -74,6 +74,8 @@ def _lib():
             lib.or_dpotrf_l_batch.argtypes = [_i, _i, _dp, _i, _l, _dp, _i, _l, _dp, _l, _ip]
             lib.or_dtrsm_rltn_batch.argtypes = [_i, _i, _i, _d, _dp, _i, _l, _dp, _i, _l,
                                                 _dp, _i, _l]
+            lib.or_dtrmm_rlnn.argtypes = [_i, _i, _d, _dp, _i, _dp, _i, _dp, _i]
+            lib.or_dtrsm_rlnn.argtypes = [_i, _i, _d, _dp, _i, _dp, _i, _dp, _i]
             lib.or_dpotrs_l.argtypes = [_i, _i, _dp, _i, _dp, _i, _dp, _i]
             lib.or_dpotrs_l_batch.argtypes = [_i, _i, _i, _dp, _i, _l, _dp, _i, _l, _dp, _i, _l]
             lib.or_dsyrk_dpotrf_ln_batch.argtypes = [_i, _i, _i, _dp, _i, _l, _dp, _i, _l,
@@ -218,3 +220,46 @@ def unpack(pA, m: int, n: int, ps: int, cn: int, ai: int = 0, aj: int = 0):
     a = np.zeros((n, m))
     _lib().or_unpack(m, n, ps, cn, _ptr(pA), ai, aj, _ptr(a), m)
     return _back(a)
+
+
+def dtrmm_rlnn(alpha, B, L):
+    """D = alpha * B * L, L lower (single problem)."""
+    B = np.asarray(B, dtype=np.float64)
+    m, n = B.shape
+    b, lb = _colmajor(B), _colmajor(L)
+    d = np.zeros((n, m))
+    _lib().or_dtrmm_rlnn(m, n, alpha, _ptr(b), m, _ptr(lb), n, _ptr(d), m)
+    return _back(d)
+
+
+def dtrsm_rlnn(alpha, L, B):
+    """X with X * L = alpha * B, L lower (single problem)."""
+    B = np.asarray(B, dtype=np.float64)
+    m, n = B.shape
+    b, lb = _colmajor(B), _colmajor(L)
+    d = np.zeros((n, m))
+    _lib().or_dtrsm_rlnn(m, n, alpha, _ptr(lb), n, _ptr(b), m, _ptr(d), m)
+    return _back(d)
+
+
+def riccati_sqrt(A, B, M0, LN, N):
+    """Backward Riccati recursion in the square-root form of Sec. 5.3, for one
+    instance with dynamics x+ = A x + B u (A nx x nx, B nx x nu):
+        C        = [B^T; A^T] * Lc            (trmm_rlnn; Lc = chol(P_{k+1}))
+        [[Lam, 0], [Lo, Lc']] = chol(M0 + C C^T)   (syrk_potrf_ln, M0 = [[R, S^T], [S, Q]])
+        Kt       : Kt * Lam = -Lo              (trsm_rlnn; Kt = K^T, the gain transposed)
+    starting from Lc = LN = chol(P_N).  Returns (Ls, Kts, infos) indexed by
+    stage k = 0..N-1 (stage N-1 computed first)."""
+    A, B = np.asarray(A, dtype=np.float64), np.asarray(B, dtype=np.float64)
+    nx, nu = B.shape
+    BAt = np.concatenate([B.T, A.T], axis=0)
+    Lc = np.tril(np.asarray(LN, dtype=np.float64))
+    Ls, Kts, infos = [None] * N, [None] * N, [0] * N
+    for k in range(N - 1, -1, -1):
+        C = dtrmm_rlnn(1.0, BAt, Lc)
+        F, _, info = dsyrk_dpotrf_ln(C, C, M0)
+        F = np.tril(F)
+        Lam, Lo, Lc = F[:nu, :nu], F[nu:, :nu], F[nu:, nu:]
+        Kts[k] = dtrsm_rlnn(-1.0, Lam, Lo)
+        Ls[k], infos[k] = Lc.copy(), info
+    return Ls, Kts, infos

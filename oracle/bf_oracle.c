@@ -151,6 +151,38 @@ void or_dpotrs_l(int n, int nrhs, const double *L, int ldl, const double *B, int
   }
 }
 
+/* trmm_rlnn (Sec. 5.2.2 "trmm_rlnn"; right, lower, not transposed,
+ * non-unit): D <- alpha * B * L with L n x n lower triangular (strictly upper
+ * part not read), B and D m x n:
+ *   D[i][j] = alpha * sum_{l >= j} B[i][l] L[l][j]. */
+void or_dtrmm_rlnn(int m, int n, double alpha, const double *B, int ldb, const double *L, int ldl,
+                   double *D, int ldd) {
+  if (m <= 0 || n <= 0) return;
+  for (int j = 0; j < n; j++) {
+    for (int i = 0; i < m; i++) {
+      double s = 0.0;
+      for (int l = j; l < n; l++) s += EL(B, ldb, i, l) * EL(L, ldl, l, j);
+      EL(D, ldd, i, j) = alpha * s;
+    }
+  }
+}
+
+/* trsm_rlnn (right, lower, not transposed, non-unit): D = X with
+ * X * L = alpha * B, L n x n lower, B and D m x n.  Column by column from
+ * the last:  X[i][j] = (alpha B[i][j] - sum_{l > j} X[i][l] L[l][j]) / L[j][j].
+ * B and D may coincide. */
+void or_dtrsm_rlnn(int m, int n, double alpha, const double *L, int ldl, const double *B, int ldb,
+                   double *D, int ldd) {
+  if (m <= 0 || n <= 0) return;
+  for (int j = n - 1; j >= 0; j--) {
+    for (int i = 0; i < m; i++) {
+      double s = alpha * EL(B, ldb, i, j);
+      for (int l = j + 1; l < n; l++) s -= EL(D, ldd, i, l) * EL(L, ldl, l, j);
+      EL(D, ldd, i, j) = s / EL(L, ldl, j, j);
+    }
+  }
+}
+
 /* Panel-major format (Sec. 4.3.3): rows are grouped in panels of ps rows
  * (ps a power of two); each panel is a column-major ps x cn block (lda = ps)
  * and panels follow one another, ps*cn doubles apart.  Element (r, c) of the

@@ -35,6 +35,19 @@ class bf_dmat(ctypes.Structure):
     ]
 
 
+class bf_riccati_prob(ctypes.Structure):
+    """Mirror of the C struct bf_riccati_prob (include/bfgpu.h)."""
+    _fields_ = [
+        ("nx", _c_int), ("nu", _c_int),
+        ("BAt", _c_vp), ("bat_cn", _c_int),
+        ("M0", _c_vp), ("m0_cn", _c_int),
+        ("LN", _c_vp), ("ln_cn", _c_int),
+        ("L", _c_vp), ("l_cn", _c_int), ("l_stride", _c_ll),
+        ("Kt", _c_vp), ("kt_cn", _c_int), ("kt_stride", _c_ll),
+        ("info", _c_vp),
+    ]
+
+
 _P = ctypes.POINTER(bf_dmat)
 
 # name -> (restype, argtypes); the same order as the declarations in bfgpu.h
@@ -64,6 +77,7 @@ SIGNATURES = {
     "bf_dposv_mixed_worksize": (_c_sz, [_c_int, _c_int]),
     "bf_dposv_mixed_batched": (_c_int, [_c_int, _c_int, _c_int, *_M, *_M, *_M, _c_d, _c_int, _c_vp,
                                         _c_vp, _c_vp, _c_sz, _c_vp]),
+    "bf_driccati_sqrt_batched": (_c_int, [_c_int, _c_int, _c_vp, _c_vp, _c_int, _c_int, _c_int, _c_vp]),
     "bf_dposv_mixed_batched_noalloc": (_c_int, [_c_int, _c_int, _c_int, *_M, *_M, *_M, _c_d, _c_int,
                                                 _c_vp, _c_vp, _c_vp]),
 }

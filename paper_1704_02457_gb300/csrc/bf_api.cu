@@ -347,4 +347,21 @@ int bf_dposv_mixed_batched(int batch, int n, int nrhs, const bf_dmat *sA, int ai
                                   info32, fast, (cudaStream_t)stream));
 }
 
+// ---------------------------------------------------------------- Riccati
+
+int bf_driccati_sqrt_batched(int batch, int N, const bf_riccati_prob *probs, const int *order,
+                             int max_nx, int max_nu, int threads, void *stream) {
+  if (batch < 0) return -1;
+  if (N < 0) return -2;
+  if (batch == 0 || N == 0) return 0;
+  if (!probs || !aligned_to(probs, 8)) return -3;
+  if (order && !aligned_to(order, 4)) return -4;
+  if (max_nx < 1) return -5;
+  if (max_nu < 1) return -6;
+  if (threads == 0) threads = 256;
+  if (threads < 32 || threads > 512 || threads % 32 != 0) return -7;
+  if (riccati_smem(max_nx, max_nu) > 200 * 1024) return BF_ERR_UNSUPPORTED;
+  return status(launch_riccati(batch, N, probs, order, max_nx, max_nu, threads, (cudaStream_t)stream));
+}
+
 }  // extern "C"

@@ -62,6 +62,11 @@ cudaError_t launch_posv_mixed(int batch, int n, int nrhs, Op A, Op B, OpW X, dou
                               int max_iter, int *iters, double *resid, float *l32, int *info32,
                               bool aligned, cudaStream_t s);
 
+// Backward Riccati recursion, square-root form (one CTA per instance).
+size_t riccati_smem(int max_nx, int max_nu);
+cudaError_t launch_riccati(int batch, int N, const bf_riccati_prob *probs, const int *order,
+                           int max_nx, int max_nu, int threads, cudaStream_t s);
+
 cudaError_t launch_pack(int batch, int m, int n, const double *A, int lda, long long sA, OpW B,
                         cudaStream_t s);
 cudaError_t launch_unpack(int batch, int m, int n, Op A, double *B, int ldb, long long sB,

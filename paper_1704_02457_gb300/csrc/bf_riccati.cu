@@ -1,0 +1,168 @@
+// Backward Riccati recursion of linear MPC (Sec. 5.3), square-root form,
+// batched over independent instances of different sizes.
+//
+// For dynamics x+ = A x + B u (A nx x nx, B nx x nu) and stage cost matrix
+// M0 = [[R, S^T], [S, Q]], each stage k = N-1, ..., 0 computes from the
+// factor Lc = chol(P_{k+1}) (P_N given by its factor LN):
+//     C                 = [B^T; A^T] * Lc            (trmm_rlnn)
+//     [[Lam, 0],
+//      [Lo,  Lc_k]]     = chol(M0 + C C^T)           (syrk_potrf_ln, fused)
+//     Kt_k * Lam        = -Lo                        (trsm_rlnn; Kt_k = K_k^T)
+// so that Lc_k Lc_k^T = P_k and K_k is the feedback gain u = K_k x.
+//
+// GB300 design.  Instances are independent and a stage of one instance needs
+// only the previous stage of the same instance, so one CTA carries one
+// instance through all N stages with Lc kept in shared memory: there is no
+// launch or grid-wide synchronization between stages, and only the outputs
+// (Lc_k, Kt_k) go to HBM.  The block scheduler hands out CTAs in blockIdx
+// order, so the caller passes the instances sorted by decreasing cost
+// (`order`) and the machine balances the uneven sizes as in longest-job-first
+// scheduling.  Instances are grouped in size buckets, each launch sizing its
+// shared memory and CTA width for its bucket.
+//
+// Within a CTA, the trmm and syrk put rows on lanes (all lanes of a warp run
+// dot products of the same length); the factorization is right-looking over
+// the packed lower triangle of M, with the thread that updates the next
+// pivot computing its rsqrt (one per column), and the gain is one thread per
+// row of Kt walking the columns of Lam backwards with the saved reciprocals.
+#include "bf_internal.cuh"
+
+namespace bf {
+namespace {
+
+__device__ __forceinline__ int col_start(int l, int n) { return (l * (2 * n - l + 1)) / 2 - l; }
+
+// column of packed lower element e in an s x s triangle (element (i, l) at col_start(l, s) + i)
+__device__ __forceinline__ int packed_col(int e, int s) {
+  const float q = 2.0f * s + 1.0f;
+  int l = (int)((q - sqrtf(fmaxf(q * q - 8.0f * e, 0.0f))) * 0.5f);
+  l = max(0, min(l, s - 1));
+  while (l > 0 && col_start(l, s) + l > e) l--;
+  while (l + 1 < s && col_start(l + 1, s) + l + 1 <= e) l++;
+  return l;
+}
+
+__global__ void __launch_bounds__(512)
+k_riccati(int batch, int N, const bf_riccati_prob *probs, const int *order, int max_nx, int max_nu) {
+  extern __shared__ double sm[];
+  const int t = threadIdx.x, T = blockDim.x;
+  if (blockIdx.x >= (unsigned)batch) return;
+  const int p = order ? order[blockIdx.x] : (int)blockIdx.x;
+  const bf_riccati_prob P = probs[p];
+  const int nx = P.nx, nu = P.nu, m = nx + nu;
+  if (nx < 1 || nu < 1 || nx > max_nx || nu > max_nu) {
+    // descriptor outside this launch's bucket: report, compute nothing
+    if (P.info)
+      for (int k = t; k < N; k += T) P.info[k] = -1;
+    return;
+  }
+  const int lp = nx + 1, cp = nx + 1;
+  double *Lc = sm;                          // nx x nx, row-major, pitch lp
+  double *C = Lc + nx * lp;                 // m x nx, row-major, pitch cp (reused for Kt)
+  double *M = C + m * cp;                   // packed lower m x m, column-major
+  double *rv = M + m * (m + 1) / 2;         // 1 / pivot of each column of M
+  __shared__ int s_bad;
+
+  for (int e = t; e < nx * nx; e += T) {
+    const int i = e / nx, j = e - i * nx;
+    Lc[i * lp + j] = (j <= i) ? P.LN[pm_off(i, j, P.ln_cn)] : 0.0;
+  }
+  __syncthreads();
+
+  for (int k = N - 1; k >= 0; k--) {
+    // (1) C = [B^T; A^T] * Lc: C(i, j) = sum_{l >= j} BAt(i, l) Lc(l, j)
+    for (int e = t; e < m * nx; e += T) {
+      const int j = e / m, i = e - j * m;
+      const double *brow = P.BAt + pm_off(i, 0, P.bat_cn);
+      double acc = 0.0;
+      for (int l = j; l < nx; l++) acc = fma(__ldg(brow + (long long)l * PS), Lc[l * lp + j], acc);
+      C[i * cp + j] = acc;
+    }
+    if (t == 0) s_bad = 0;
+    __syncthreads();
+
+    // (2) M = M0 + C C^T, lower triangle
+    const int NE = m * (m + 1) / 2;
+    for (int e = t; e < NE; e += T) {
+      const int j = packed_col(e, m), i = e - col_start(j, m);
+      double acc = __ldg(P.M0 + pm_off(i, j, P.m0_cn));
+      const double *ci = C + i * cp, *cj = C + j * cp;
+      for (int l = 0; l < nx; l++) acc = fma(ci[l], cj[l], acc);
+      M[e] = acc;
+    }
+    __syncthreads();
+    if (t == 0) {
+      const double d = M[0];
+      rv[0] = rsqrt(d);
+      if (!(d > 0.0)) s_bad = 1;
+    }
+    __syncthreads();
+
+    // (3) Cholesky of M, right-looking over the packed lower triangle
+    for (int j = 0; j < m; j++) {
+      const int cj = col_start(j, m);
+      const double r = rv[j];
+      for (int i = j + 1 + t; i < m; i += T) M[cj + i] *= r;
+      if (t == 0) M[cj + j] *= r;  // d * rsqrt(d)
+      __syncthreads();
+      const int s = m - j - 1;  // trailing triangle rows/cols j+1 .. m-1
+      const int TE = s * (s + 1) / 2;
+      for (int e = t; e < TE; e += T) {
+        const int kk = packed_col(e, s), ii = e - col_start(kk, s);
+        const int kc = j + 1 + kk, ic = j + 1 + ii;
+        const int idx = col_start(kc, m) + ic;
+        const double v = fma(-M[cj + ic], M[cj + kc], M[idx]);
+        M[idx] = v;
+        if (ii == kk && kk == 0) {  // next pivot
+          rv[kc] = rsqrt(v);
+          if (!(v > 0.0) && s_bad == 0) s_bad = kc + 1;
+        }
+      }
+      __syncthreads();
+    }
+
+    // (4) outputs: Kt * Lam = -Lo, then the new factor Lc = M[nu:, nu:]
+    double *X = C;  // nx x nu, pitch nu + 1
+    double *kt = P.Kt + (long long)k * P.kt_stride;
+    for (int i = t; i < nx; i += T) {
+      for (int j = nu - 1; j >= 0; j--) {
+        double s = -M[col_start(j, m) + nu + i];
+        for (int l = j + 1; l < nu; l++) s = fma(-X[i * (nu + 1) + l], M[col_start(j, m) + l], s);
+        s *= rv[j];
+        X[i * (nu + 1) + j] = s;
+        kt[pm_off(i, j, P.kt_cn)] = s;
+      }
+    }
+    double *lk = P.L + (long long)k * P.l_stride;
+    for (int e = t; e < nx * nx; e += T) {
+      const int i = e / nx, j = e - i * nx;
+      const double v = (j <= i) ? M[col_start(nu + j, m) + nu + i] : 0.0;
+      Lc[i * lp + j] = v;
+      if (j <= i) lk[pm_off(i, j, P.l_cn)] = v;
+    }
+    if (t == 0 && P.info) P.info[k] = s_bad;
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+size_t riccati_smem(int max_nx, int max_nu) {
+  const size_t nx = max_nx, m = (size_t)max_nx + max_nu;
+  return (nx * (nx + 1) + m * (nx + 1) + m * (m + 1) / 2 + m) * sizeof(double);
+}
+
+cudaError_t launch_riccati(int batch, int N, const bf_riccati_prob *probs, const int *order,
+                           int max_nx, int max_nu, int threads, cudaStream_t s) {
+  const size_t smem = riccati_smem(max_nx, max_nu);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_riccati, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_riccati<<<batch, threads, smem, s>>>(batch, N, probs, order, max_nx, max_nu);
+  return cudaGetLastError();
+}
+
+}  // namespace bf

@@ -138,3 +138,43 @@ def test_product_path_has_no_fallback():
     src += open(os.path.join(os.path.dirname(pkg.__file__), "_abi.py")).read()
     assert "oracle" not in src
     assert "import numpy" not in src
+
+
+def test_struct_offsets_match_the_c_header(tmp_path):
+    # compile a small C program against include/bfgpu.h and compare the layout
+    src = tmp_path / "layout.c"
+    src.write_text("""
+#include <stdio.h>
+#include <stddef.h>
+#include "bfgpu.h"
+int main(void) {
+  printf("%zu %zu %zu %zu\\n", sizeof(bf_dmat), offsetof(bf_dmat, memsize), sizeof(bf_riccati_prob),
+         offsetof(bf_riccati_prob, info));
+  printf("%zu %zu %zu %zu\\n", offsetof(bf_riccati_prob, l_stride), offsetof(bf_riccati_prob, Kt),
+         offsetof(bf_riccati_prob, kt_stride), offsetof(bf_riccati_prob, M0));
+  return 0;
+}
+""")
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    R = _abi.bf_riccati_prob
+    want = [ctypes.sizeof(_abi.bf_dmat), _abi.bf_dmat.memsize.offset, ctypes.sizeof(R), R.info.offset,
+            R.l_stride.offset, R.Kt.offset, R.kt_stride.offset, R.M0.offset]
+    assert [int(x) for x in out] == want
+
+
+def test_riccati_argument_checks(lib):
+    g = lib.bf_driccati_sqrt_batched
+    p = ctypes.c_void_p(0x10000)
+    assert g(-1, 4, p, None, 8, 2, 0, None) == -1
+    assert g(1, -1, p, None, 8, 2, 0, None) == -2
+    assert g(0, 4, None, None, 8, 2, 0, None) == 0
+    assert g(1, 4, None, None, 8, 2, 0, None) == -3
+    assert g(1, 4, p, ctypes.c_void_p(0x10002), 8, 2, 0, None) == -4
+    assert g(1, 4, p, None, 0, 2, 0, None) == -5
+    assert g(1, 4, p, None, 8, 0, 0, None) == -6
+    assert g(1, 4, p, None, 8, 2, 48, None) == -7
+    assert g(1, 4, p, None, 8, 2, 1024, None) == -7
+    assert g(1, 4, p, None, 200, 20, 0, None) == _abi.BF_ERR_UNSUPPORTED

@@ -30,13 +30,18 @@ MUTANTS = {
     "potrf_wrong_index": ("for (int l = 0; l < j; l++) s -= EL(D, ldd, i, l) * EL(D, ldd, j, l);\n      EL(D, ldd, i, j) = s / ljj;",
                           "for (int l = 0; l < j; l++) s -= EL(D, ldd, i, l) * EL(D, ldd, l, j);\n      EL(D, ldd, i, j) = s / ljj;"),
     "trsm_reads_upper": ("s -= EL(D, ldd, i, l) * EL(L, ldl, j, l);", "s -= EL(D, ldd, i, l) * EL(L, ldl, l, j);"),
-    "trsm_drops_alpha": ("double s = alpha * EL(B, ldb, i, j);", "double s = EL(B, ldb, i, j);"),
+    "trsm_drops_alpha": ("double s = alpha * EL(B, ldb, i, j);\n      for (int l = 0; l < j; l++)",
+                         "double s = EL(B, ldb, i, j);\n      for (int l = 0; l < j; l++)"),
     "syrk_potrf_drops_C": ("or_dsyrk_ln(m, k, 1.0, A, lda, B, ldb, 1.0, C, ldc, T, m);",
                            "or_dsyrk_ln(m, k, 1.0, A, lda, B, ldb, 0.0, C, ldc, T, m);"),
     "potrs_backward_uses_row": ("for (int l = i + 1; l < n; l++) s -= EL(L, ldl, l, i) * EL(X, ldx, l, k);",
                                 "for (int l = i + 1; l < n; l++) s -= EL(L, ldl, i, l) * EL(X, ldx, l, k);"),
     "potrs_forward_drops_term": ("for (int l = 0; l < i; l++) s -= EL(L, ldl, i, l) * EL(X, ldx, l, k);",
                                  "for (int l = 1; l < i; l++) s -= EL(L, ldl, i, l) * EL(X, ldx, l, k);"),
+    "trmm_full_triangle": ("for (int l = j; l < n; l++) s += EL(B, ldb, i, l) * EL(L, ldl, l, j);",
+                           "for (int l = 0; l < n; l++) s += EL(B, ldb, i, l) * EL(L, ldl, l, j);"),
+    "trsm_rlnn_transposed": ("for (int l = j + 1; l < n; l++) s -= EL(D, ldd, i, l) * EL(L, ldl, l, j);",
+                             "for (int l = j + 1; l < n; l++) s -= EL(D, ldd, i, l) * EL(L, ldl, j, l);"),
     "pack_row_in_panel": ("(size_t)c * (size_t)ps + (size_t)(r % ps)", "(size_t)c * (size_t)ps + (size_t)((r + 1) % ps)"),
 }
 
@@ -55,6 +60,8 @@ def _battery():
         lambda: pins.test_golden_cholesky_3x3(),
         lambda: pins.test_golden_trsm_3x3(),
         lambda: pins.test_potrs_integer_solution_returns_exactly(8, 4),
+        lambda: pins.test_trmm_rlnn_integer_exact(5, 3),
+        lambda: pins.test_trsm_rlnn_integer_exact(7, 4),
     ]
     for c in checks:
         try:

@@ -367,3 +367,49 @@ def test_golden_trsm_3x3():
     g = _read_golden("trsm_rltn_2x3.txt")
     got = oracle.dtrsm_rltn(g["alpha"][0, 0], g["L"], g["B"])
     assert np.array_equal(got, g["X"])
+
+
+# ------------------------------------------------ trmm_rlnn, trsm_rlnn, Riccati
+
+@pytest.mark.parametrize("m,n", [(1, 1), (5, 3), (24, 24), (40, 17)])
+def test_trmm_rlnn_integer_exact(m, n):
+    rng = np.random.default_rng(600 + m)
+    B = _ints((m, n), -8, 8, rng)
+    L = np.tril(_ints((n, n), -8, 8, rng))
+    Lnan = L.astype(float)
+    Lnan[np.triu_indices(n, 1)] = np.nan  # the upper part must not be read
+    assert np.array_equal(oracle.dtrmm_rlnn(2.0, B.astype(float), Lnan), (2 * (B @ L)).astype(float))
+
+
+@pytest.mark.parametrize("m,n", [(1, 1), (7, 4), (24, 24), (30, 16)])
+def test_trsm_rlnn_integer_exact(m, n):
+    rng = np.random.default_rng(700 + m)
+    L = _int_lower_pow2(n, rng)
+    X = _ints((m, n), -16, 16, rng)
+    B = X @ L
+    assert np.array_equal(oracle.dtrsm_rlnn(1.0, L.astype(float), B.astype(float)), X.astype(float))
+    assert np.array_equal(oracle.dtrsm_rlnn(-0.5, L.astype(float), B.astype(float)), -X / 2.0)
+
+
+@pytest.mark.parametrize("nx,nu", [(3, 1), (8, 2), (20, 5), (40, 16)])
+def test_riccati_sqrt_matches_classical_recursion(nx, nu):
+    # the factors of the square-root form must reproduce the explicit Riccati
+    # recursion P = Q + A^T P A - A^T P B (R + B^T P B)^{-1} B^T P A and its gain
+    rng = np.random.default_rng(800 + nx)
+    A = rng.standard_normal((nx, nx)) / np.sqrt(nx)
+    B = rng.standard_normal((nx, nu)) / np.sqrt(nx)
+    Rm = np.eye(nu) + 0.1 * np.diag(rng.random(nu))
+    Qm = np.eye(nx) + 0.1 * np.diag(rng.random(nx))
+    M0 = np.zeros((nu + nx, nu + nx))
+    M0[:nu, :nu], M0[nu:, nu:] = Rm, Qm
+    N = 6
+    Ls, Kts, infos = oracle.riccati_sqrt(A, B, M0, np.eye(nx), N)
+    P = np.eye(nx)
+    for k in range(N - 1, -1, -1):
+        G = Rm + B.T @ P @ B
+        K = -np.linalg.solve(G, B.T @ P @ A)
+        P = Qm + A.T @ P @ A + A.T @ P @ B @ K
+        P = 0.5 * (P + P.T)
+        assert infos[k] == 0
+        assert np.linalg.norm(Ls[k] @ Ls[k].T - P) / np.linalg.norm(P) <= 1e-13
+        assert np.linalg.norm(Kts[k].T - K) / np.linalg.norm(K) <= 1e-12
