@@ -412,6 +412,8 @@ def run_gpu(args):
         result["mixed_vs_fp64"] = run_mixed(args, dev)
     if not args.no_riccati:
         result["riccati"] = run_riccati(args, dev)
+    if not args.no_adjoint:
+        result["adjoint"] = run_adjoint(args, dev)
     if not args.no_e2e:
         result["e2e"] = run_e2e(pts, args, dev, world)
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -653,6 +655,67 @@ def run_riccati(args, dev, batch=4096, N=20):
     }
 
 
+def run_adjoint(args, dev, bt=2048, n=64, nrhs=1):
+    """Factor-and-solve x = A^{-1} b and its hand-written adjoint
+    (db = A^{-1} xbar, dA = -sym(db x^T)) on 2048 SPD systems
+    M M^T + 64 I of order 64 with one right-hand side.  The gradient is
+    cross-checked against torch.linalg.solve's autograd (symmetrized)."""
+    import torch
+
+    import paper_1704_02457_gb300 as bf
+    from paper_1704_02457_gb300 import inputs
+
+    S = inputs.spd(bt, n, 12000, dev)
+    B = inputs.normal((bt, n, nrhs), 12001, dev)
+    W = inputs.normal((bt, n, nrhs), 12002, dev)
+    dS, dB, dW = (bf.DMatBatch.from_colmajor(X, tight=True) for X in (S, B, W))
+    dL = bf.DMatBatch(bt, n, n, tight=True, fill=0.0)
+    dX = bf.DMatBatch(bt, n, nrhs, tight=True)
+    dBb, dAb = bf.DMatBatch(bt, n, nrhs, tight=True), bf.DMatBatch(bt, n, n, tight=True)
+    lib = bf.load()
+    stream = torch.cuda.current_stream()
+
+    def fwd():
+        bf.dpotrf_l(n, dS, 0, 0, dL, 0, 0, dinv=False, stream=stream)
+        bf.dpotrs_l(n, nrhs, dL, 0, 0, dB, 0, 0, dX, 0, 0, stream=stream)
+
+    def bwd():
+        bf._check("adjoint", lib.bf_dposv_adjoint_batched(bt, n, nrhs, *bf._op(dL), *bf._op(dX), *bf._op(dW),
+                                                          *bf._op(dBb), *bf._op(dAb), bf._stream(stream)))
+
+    def timeit(fn, reps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    reps = max(3, args.steps)
+    tf, tb = timeit(fwd, reps), timeit(bwd, reps)
+    # cross-check on a sample against torch's autograd of a general solve
+    k = 64
+    A_ = S[:k].clone().requires_grad_(True)
+    B_ = B[:k].clone().requires_grad_(True)
+    (torch.linalg.solve(A_, B_) * W[:k]).sum().backward()
+    gA_ref = 0.5 * (A_.grad + A_.grad.transpose(1, 2))
+    gA, gB = dAb.to_colmajor()[:k], dBb.to_colmajor()[:k]
+    relA = float(((gA - gA_ref).norm(dim=(1, 2)) / gA_ref.norm(dim=(1, 2))).max())
+    relB = float(((gB - B_.grad).norm(dim=(1, 2)) / B_.grad.norm(dim=(1, 2))).max())
+    fl_f = bt * (n ** 3 / 3.0 + n ** 2 / 2.0 + n / 6.0 + 2.0 * n * n * nrhs)
+    fl_b = bt * (2.0 * n * n * nrhs + 4.0 * n * n * nrhs)
+    return {
+        "workload": "2048 SPD systems M M^T + 64 I, n=64, 1 RHS; forward potrf+potrs, backward adjoint kernel",
+        "forward_ms": round(tf, 4), "backward_ms": round(tb, 4),
+        "forward_gflops": round(fl_f / (tf * 1e-3) / 1e9, 2), "backward_gflops": round(fl_b / (tb * 1e-3) / 1e9, 2),
+        "max_rel_err_dA_vs_torch": relA, "max_rel_err_db_vs_torch": relB,
+    }
+
+
 # ---------------------------------------------------------- reference arm --
 
 def run_reference(args):
@@ -697,6 +760,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-riccati", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=0.3, help="seconds of oracle time per point")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -220,6 +220,20 @@ int bf_dpotrs_l_batched(int batch, int n, int nrhs, const bf_dmat *sL, int li, i
                         long long strideL, const bf_dmat *sB, int bi, int bj, long long strideB,
                         const bf_dmat *sX, int xi, int xj, long long strideX, void *stream);
 
+/* Adjoint (reverse-mode derivative) of the factor-and-solve X = A^{-1} B
+ * (not in the paper): given the lower factor L of A (L L^T = A), the
+ * solution X and the cotangent Xbar = d loss / d X (all n x nrhs),
+ *     Bbar = A^{-1} Xbar                  (d loss / d B)
+ *     Abar = -(Bbar X^T + X Bbar^T) / 2   (d loss / d A for symmetric A)
+ * Bbar is n x nrhs, Abar n x n (written in full).  Outputs must not overlap
+ * the inputs.  Supports n <= 160 and 1 <= nrhs <= 8. */
+int bf_dposv_adjoint_batched(int batch, int n, int nrhs, const bf_dmat *sL, int li, int lj,
+                             long long strideL, const bf_dmat *sX, int xi, int xj, long long strideX,
+                             const bf_dmat *sXbar, int xbi, int xbj, long long strideXbar,
+                             const bf_dmat *sBbar, int bbi, int bbj, long long strideBbar,
+                             const bf_dmat *sAbar, int abi, int abj, long long strideAbar,
+                             void *stream);
+
 /* Bytes of device workspace bf_dposv_mixed_batched needs for `batch`
  * systems of order n (the single-precision factors and their status). */
 size_t bf_dposv_mixed_worksize(int batch, int n);

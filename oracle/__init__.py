@@ -74,6 +74,7 @@ def _lib():
             lib.or_dpotrf_l_batch.argtypes = [_i, _i, _dp, _i, _l, _dp, _i, _l, _dp, _l, _ip]
             lib.or_dtrsm_rltn_batch.argtypes = [_i, _i, _i, _d, _dp, _i, _l, _dp, _i, _l,
                                                 _dp, _i, _l]
+            lib.or_dposv_adjoint.argtypes = [_i, _i, _dp, _i, _dp, _i, _dp, _i, _dp, _i, _dp, _i]
             lib.or_dtrmm_rlnn.argtypes = [_i, _i, _d, _dp, _i, _dp, _i, _dp, _i]
             lib.or_dtrsm_rlnn.argtypes = [_i, _i, _d, _dp, _i, _dp, _i, _dp, _i]
             lib.or_dpotrs_l.argtypes = [_i, _i, _dp, _i, _dp, _i, _dp, _i]
@@ -263,3 +264,14 @@ def riccati_sqrt(A, B, M0, LN, N):
         Kts[k] = dtrsm_rlnn(-1.0, Lam, Lo)
         Ls[k], infos[k] = Lc.copy(), info
     return Ls, Kts, infos
+
+
+def dposv_adjoint(L, X, Xbar):
+    """(Bbar, Abar) of the solve X = A^{-1} B for A = L L^T (single system)."""
+    L, X, Xbar = (np.asarray(v, dtype=np.float64) for v in (L, X, Xbar))
+    n, nrhs = X.shape
+    lb, xb, xbb = _colmajor(L), _colmajor(X), _colmajor(Xbar)
+    bb = np.zeros((nrhs, n))
+    ab = np.zeros((n, n))
+    _lib().or_dposv_adjoint(n, nrhs, _ptr(lb), n, _ptr(xb), n, _ptr(xbb), n, _ptr(bb), n, _ptr(ab), n)
+    return _back(bb), _back(ab)

@@ -183,6 +183,25 @@ void or_dtrsm_rlnn(int m, int n, double alpha, const double *L, int ldl, const d
   }
 }
 
+/* Adjoint of the Cholesky factor-and-solve X = A^{-1} B (not in the paper):
+ * given the factor L of A, the solution X and the cotangent Xbar (n x nrhs),
+ *   Bbar = A^{-1} Xbar                          (potrs with L)
+ *   Abar = -(Bbar X^T + X Bbar^T) / 2           (the symmetric part of
+ *                                                -Bbar X^T; A is symmetric)
+ * Abar is written in full (n x n).  Bbar must not alias X or Xbar. */
+void or_dposv_adjoint(int n, int nrhs, const double *L, int ldl, const double *X, int ldx,
+                      const double *Xbar, int ldxb, double *Bbar, int ldbb, double *Abar, int lda) {
+  if (n <= 0 || nrhs <= 0) return;
+  or_dpotrs_l(n, nrhs, L, ldl, Xbar, ldxb, Bbar, ldbb);
+  for (int j = 0; j < n; j++)
+    for (int i = 0; i < n; i++) {
+      double s = 0.0;
+      for (int k = 0; k < nrhs; k++)
+        s += EL(Bbar, ldbb, i, k) * EL(X, ldx, j, k) + EL(X, ldx, i, k) * EL(Bbar, ldbb, j, k);
+      EL(Abar, lda, i, j) = -0.5 * s;
+    }
+}
+
 /* Panel-major format (Sec. 4.3.3): rows are grouped in panels of ps rows
  * (ps a power of two); each panel is a column-major ps x cn block (lda = ps)
  * and panels follow one another, ps*cn doubles apart.  Element (r, c) of the

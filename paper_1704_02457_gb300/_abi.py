@@ -74,6 +74,7 @@ SIGNATURES = {
     "bf_dsyrk_dpotrf_ln": (_c_int, [_c_int, _c_int, _P, _c_int, _c_int, _P, _c_int, _c_int,
                                     _P, _c_int, _c_int, _P, _c_int, _c_int, _c_vp, _c_vp]),
     "bf_dpotrs_l_batched": (_c_int, [_c_int, _c_int, _c_int, *_M, *_M, *_M, _c_vp]),
+    "bf_dposv_adjoint_batched": (_c_int, [_c_int, _c_int, _c_int, *_M, *_M, *_M, *_M, *_M, _c_vp]),
     "bf_dposv_mixed_worksize": (_c_sz, [_c_int, _c_int]),
     "bf_dposv_mixed_batched": (_c_int, [_c_int, _c_int, _c_int, *_M, *_M, *_M, _c_d, _c_int, _c_vp,
                                         _c_vp, _c_vp, _c_sz, _c_vp]),

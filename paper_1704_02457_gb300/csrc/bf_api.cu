@@ -309,6 +309,27 @@ int bf_dpotrs_l_batched(int batch, int n, int nrhs, const bf_dmat *sL, int li, i
                              make_opw(sX, xi, xj, strideX), (cudaStream_t)stream));
 }
 
+int bf_dposv_adjoint_batched(int batch, int n, int nrhs, const bf_dmat *sL, int li, int lj,
+                             long long strideL, const bf_dmat *sX, int xi, int xj, long long strideX,
+                             const bf_dmat *sXbar, int xbi, int xbj, long long strideXbar,
+                             const bf_dmat *sBbar, int bbi, int bbj, long long strideBbar,
+                             const bf_dmat *sAbar, int abi, int abj, long long strideAbar,
+                             void *stream) {
+  if (batch < 0) return -1;
+  if (n < 0) return -2;
+  if (nrhs < 0) return -3;
+  if (batch == 0 || n == 0 || nrhs == 0) return 0;
+  if (n > POSV_MAX_N || nrhs > POSV_MAX_NRHS) return BF_ERR_UNSUPPORTED;
+  if (int w = check_op(sL, li, lj, n, n, strideL, batch, false)) return pos_err(w, 4);
+  if (int w = check_op(sX, xi, xj, n, nrhs, strideX, batch, false)) return pos_err(w, 8);
+  if (int w = check_op(sXbar, xbi, xbj, n, nrhs, strideXbar, batch, false)) return pos_err(w, 12);
+  if (int w = check_op(sBbar, bbi, bbj, n, nrhs, strideBbar, batch, true)) return pos_err(w, 16);
+  if (int w = check_op(sAbar, abi, abj, n, n, strideAbar, batch, true)) return pos_err(w, 20);
+  return status(launch_posv_adjoint(batch, n, nrhs, make_op(sL, li, lj, strideL), make_op(sX, xi, xj, strideX),
+                                    make_op(sXbar, xbi, xbj, strideXbar), make_opw(sBbar, bbi, bbj, strideBbar),
+                                    make_opw(sAbar, abi, abj, strideAbar), (cudaStream_t)stream));
+}
+
 size_t bf_dposv_mixed_worksize(int batch, int n) {
   if (batch <= 0 || n <= 0) return 0;
   const size_t pm = ((size_t)n + PS - 1) / PS * PS;

@@ -58,6 +58,8 @@ cudaError_t launch_trsm_rltn(int batch, int m, int n, double alpha, Op L, const 
 // A X = B with the FP64 factor L (potrs), and the mixed-precision solver
 // (FP32 factor in the workspace l32 / info32, FP64 iterative refinement).
 cudaError_t launch_potrs(int batch, int n, int nrhs, Op L, Op B, OpW X, cudaStream_t s);
+cudaError_t launch_posv_adjoint(int batch, int n, int nrhs, Op L, Op X, Op Xbar, OpW Bbar, OpW Abar,
+                                cudaStream_t s);
 cudaError_t launch_posv_mixed(int batch, int n, int nrhs, Op A, Op B, OpW X, double tol,
                               int max_iter, int *iters, double *resid, float *l32, int *info32,
                               bool aligned, cudaStream_t s);

@@ -244,6 +244,50 @@ k_posv(int n, int nrhs, Op A, const float *l32, long long sl32, const int *info3
   }
 }
 
+// Adjoint of X = A^{-1} B given A's factor L: Bbar = A^{-1} Xbar (the solve
+// with the saved factor, one warp per right-hand side) and
+// Abar = -(Bbar X^T + X Bbar^T) / 2, written in full.
+__global__ void __launch_bounds__(256)
+k_posv_adjoint(int n, int nrhs, Op Lf, Op Xs, Op Xb, OpW Bb, OpW Ab) {
+  extern __shared__ double smem_d[];
+  const int b = blockIdx.x;
+  const int t = threadIdx.x, T = blockDim.x;
+  const int NE = n * (n + 1) / 2;
+  double *L = smem_d;
+  double *dinv = L + ((NE + 1) & ~1);
+  double *v = dinv + ((n + 1) & ~1);  // Xbar, then Bbar
+  double *x = v + nrhs * n;
+  load_factor<double>(L, Lf.p + b * Lf.stride, Lf.cn, Lf.i0, Lf.j0, n);
+  const double *px = Xs.p + b * Xs.stride, *pxb = Xb.p + b * Xb.stride;
+  for (int e = t; e < nrhs * n; e += T) {
+    const int k = e / n, i = e - k * n;
+    v[e] = pxb[pm_off(Xb.i0 + i, Xb.j0 + k, Xb.cn)];
+    x[e] = px[pm_off(Xs.i0 + i, Xs.j0 + k, Xs.cn)];
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  for (int j = t; j < n; j += T) dinv[j] = 1.0 / L[col_start(j, n) + j];
+  __syncthreads();
+  const int warp = t >> 5, nwarps = (T + 31) >> 5;
+  for (int k = warp; k < nrhs; k += nwarps) warp_solve<double>(L, dinv, v + k * n, n);
+  __syncthreads();
+  double *pbb = Bb.p + b * Bb.stride;
+  for (int e = t; e < nrhs * n; e += T) {
+    const int k = e / n, i = e - k * n;
+    pbb[pm_off(Bb.i0 + i, Bb.j0 + k, Bb.cn)] = v[e];
+  }
+  double *pab = Ab.p + b * Ab.stride;
+  for (int e = t; e < n * n; e += T) {
+    const int j = e / n, i = e - j * n;
+    // (bbar_i x_j + x_i bbar_j) with separately rounded products and sums,
+    // so that Abar(i, j) and Abar(j, i) are the same number bit for bit
+    double s = 0.0;
+    for (int k = 0; k < nrhs; k++)
+      s = __dadd_rn(s, __dadd_rn(__dmul_rn(v[k * n + i], x[k * n + j]), __dmul_rn(x[k * n + i], v[k * n + j])));
+    pab[pm_off(Ab.i0 + i, Ab.j0 + j, Ab.cn)] = -0.5 * s;
+  }
+}
+
 size_t posv_smem(bool mixed, int n, int nrhs) {
   const size_t ne = (size_t)n * (n + 1) / 2;
   const size_t tl = mixed ? 4 : 8;
@@ -276,6 +320,21 @@ cudaError_t launch_potrs(int batch, int n, int nrhs, Op L, Op B, OpW X, cudaStre
   const Op none{nullptr, 0, 0, 0, 0};
   k_posv<false><<<batch, posv_threads(n, nrhs), smem, s>>>(n, nrhs, none, nullptr, 0, nullptr, L, B, X,
                                                            0.0, 0, nullptr, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_posv_adjoint(int batch, int n, int nrhs, Op L, Op X, Op Xbar, OpW Bbar, OpW Abar,
+                                cudaStream_t s) {
+  const size_t ne = (size_t)n * (n + 1) / 2;
+  const size_t smem = (((ne + 1) & ~(size_t)1) + (((size_t)n + 1) & ~(size_t)1) + 2 * (size_t)nrhs * n) * 8;
+  if (smem > 200 * 1024) return cudaErrorInvalidConfiguration;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_posv_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_posv_adjoint<<<batch, posv_threads(n, nrhs), smem, s>>>(n, nrhs, L, X, Xbar, Bbar, Abar);
   return cudaGetLastError();
 }
 

@@ -413,3 +413,46 @@ def test_riccati_sqrt_matches_classical_recursion(nx, nu):
         assert infos[k] == 0
         assert np.linalg.norm(Ls[k] @ Ls[k].T - P) / np.linalg.norm(P) <= 1e-13
         assert np.linalg.norm(Kts[k].T - K) / np.linalg.norm(K) <= 1e-12
+
+
+# ------------------------------------------------------ adjoint of the solve
+
+def _solve(A, B):
+    L, _, info = oracle.dpotrf_l(A)
+    assert info == 0
+    return oracle.dpotrs_l(np.tril(L), B), np.tril(L)
+
+
+def test_adjoint_identity_closed_form():
+    # A = I: X = B, Bbar = Xbar, Abar = -(Xbar B^T + B Xbar^T)/2
+    n, nrhs = 5, 2
+    B, Xbar = RNG.standard_normal((n, nrhs)), RNG.standard_normal((n, nrhs))
+    X, L = _solve(np.eye(n), B)
+    Bbar, Abar = oracle.dposv_adjoint(L, X, Xbar)
+    assert np.array_equal(Bbar, Xbar)
+    np.testing.assert_allclose(Abar, -0.5 * (Xbar @ B.T + B @ Xbar.T), rtol=1e-15, atol=1e-15)
+
+
+@pytest.mark.parametrize("n,nrhs", [(3, 1), (8, 2), (16, 1)])
+def test_adjoint_matches_central_differences(n, nrhs):
+    # loss = <W, X(A, B)>; perturb A symmetrically (entry (i, j) and (j, i)) and B
+    rng = np.random.default_rng(900 + n)
+    M = rng.standard_normal((n, n))
+    A = M @ M.T + n * np.eye(n)
+    B, W = rng.standard_normal((n, nrhs)), rng.standard_normal((n, nrhs))
+    X, L = _solve(A, B)
+    Bbar, Abar = oracle.dposv_adjoint(L, X, W)
+    h = 1e-6
+    loss = lambda A_, B_: float(np.sum(W * _solve(A_, B_)[0]))  # noqa: E731
+    for (i, j) in [(0, 0), (n - 1, 0), (n // 2, n // 3), (n - 1, n - 1)]:
+        E = np.zeros((n, n))
+        E[i, j] = E[j, i] = 1.0
+        fd = (loss(A + h * E, B) - loss(A - h * E, B)) / (2 * h)
+        want = Abar[i, j] + (Abar[j, i] if i != j else 0.0)
+        assert abs(fd - want) <= 1e-7 * max(1.0, abs(want))
+    for (i, k) in [(0, 0), (n - 1, nrhs - 1)]:
+        E = np.zeros((n, nrhs))
+        E[i, k] = 1.0
+        fd = (loss(A, B + h * E) - loss(A, B - h * E)) / (2 * h)
+        assert abs(fd - Bbar[i, k]) <= 1e-7 * max(1.0, abs(Bbar[i, k]))
+    assert np.allclose(Abar, Abar.T, rtol=0, atol=1e-15)
