@@ -262,14 +262,18 @@ struct RowsSmem {
   int bad;
 };
 
-template <int W, bool FUSED, bool ALIGNED, typename T>
+// One block column [c0, c0 + BW) of the factorization.  W is the number of
+// accumulators (the block's width rounded up to a multiple of 8).  The
+// diagonal block's rows c0..c0+BW-1 are lanes base..base+BW-1 of one warp
+// (BW divides 32 and c0 is a multiple of BW).
+template <int W, int BW, bool FUSED, bool ALIGNED, typename T>
 __device__ __forceinline__ void rows_block(RowsSmem<T> &S, int c0, int n, int k, const double *pa,
                                            const double *pb, const double *pc, T *pd, Op A,
                                            Op B, Op C, OpWT<T> D, T *dinv_b) {
   using T2 = typename Vec2<T>::type;
   const int i = threadIdx.x;
   const int T_ = blockDim.x;
-  const int w = min(32, n - c0);
+  const int w = min(BW, n - c0);
   const bool active = (i < n) && (i >= c0);
   T acc[W];
 
@@ -286,7 +290,7 @@ __device__ __forceinline__ void rows_block(RowsSmem<T> &S, int c0, int n, int k,
     for (int l0 = 0; l0 < k; l0 += KC) {
       const int kc = min(KC, k - l0);
       __syncthreads();
-      for (int x = i; x < 32 * KC; x += T_) {
+      for (int x = i; x < BW * KC; x += T_) {
         const int r4 = x % PS, ll = (x / PS) % KC, pnl = x / (PS * KC);
         const int jj = pnl * PS + r4;
         S.stage[ll][jj] = (jj < w && ll < kc) ? (T)__ldg(pb + pm_off(B.i0 + c0 + jj, B.j0 + l0 + ll, B.cn)) : (T)0;
@@ -310,16 +314,17 @@ __device__ __forceinline__ void rows_block(RowsSmem<T> &S, int c0, int n, int k,
   {
     const T *lrow = pd + pm_off(D.i0 + min(i, n - 1), D.j0, D.cn);
     for (int l0 = 0; l0 < c0; l0 += KC) {
+      const int kc = min(KC, c0 - l0);
       __syncthreads();
-      for (int x = i; x < 32 * KC; x += T_) {
+      for (int x = i; x < BW * KC; x += T_) {
         const int r4 = x % PS, ll = (x / PS) % KC, pnl = x / (PS * KC);
         const int jj = pnl * PS + r4;
-        S.stage[ll][jj] = (jj < w) ? pd[pm_off(D.i0 + c0 + jj, D.j0 + l0 + ll, D.cn)] : (T)0;
+        S.stage[ll][jj] = (jj < w && ll < kc) ? pd[pm_off(D.i0 + c0 + jj, D.j0 + l0 + ll, D.cn)] : (T)0;
       }
       __syncthreads();
       if (active) {
 #pragma unroll 2
-        for (int ll = 0; ll < KC; ll++) {
+        for (int ll = 0; ll < kc; ll++) {
           const T x = lrow[(long long)(l0 + ll) * PS];
 #pragma unroll
           for (int jj = 0; jj < W; jj += 2) {
@@ -332,37 +337,41 @@ __device__ __forceinline__ void rows_block(RowsSmem<T> &S, int c0, int n, int k,
     }
   }
 
-  // (c) diagonal block: the warp holding rows c0..c0+31 factors it in registers
+  // (c) diagonal block: its rows are lanes base..base+BW-1 of one warp, which
+  // factor it in registers with shuffles among themselves
   const int lane = i & 31;
-  if ((i >> 5) == (c0 >> 5)) {
-    int bad = 0;  // every lane sees every pivot, so every lane tracks the first bad one
+  const int base = c0 & 31;
+  const int dl = lane - base;
+  if ((i >> 5) == (c0 >> 5) && dl >= 0 && dl < BW) {
+    const unsigned dmask = (BW == 32) ? FULL : (((1u << BW) - 1u) << base);
+    int bad = 0;  // every diagonal lane sees every pivot and tracks the first bad one
+    // all W columns: padding columns (j >= w) hold zeros and only feed other
+    // padding columns, which are never stored
 #pragma unroll
     for (int j = 0; j < W; j++) {
-      if (j < w) {
-        const T d = __shfl_sync(FULL, acc[j], j);
-        const T r = rsqrt_t(d);
-        if (!(d > (T)0) && bad == 0) bad = c0 + j + 1;
-        if (lane == j) {
-          acc[j] = d * r;
-          S.rinv[j] = r;
-        } else {
-          acc[j] *= r;
-        }
+      const T d = __shfl_sync(dmask, acc[j], base + j);
+      const T r = rsqrt_t(d);
+      if (j < w && !(d > (T)0) && bad == 0) bad = c0 + j + 1;
+      if (dl == j) {
+        acc[j] = d * r;
+        S.rinv[j] = r;
+      } else {
+        acc[j] *= r;
+      }
 #pragma unroll
-        for (int jj = j + 1; jj < W; jj++) {
-          const T v = __shfl_sync(FULL, acc[j], jj);
-          acc[jj] = fma_t(-acc[j], v, acc[jj]);
-        }
+      for (int jj = j + 1; jj < W; jj++) {
+        const T v = __shfl_sync(dmask, acc[j], base + jj);
+        acc[jj] = fma_t(-acc[j], v, acc[jj]);
       }
     }
 #pragma unroll
-    for (int jj = 0; jj < W; jj++) S.Ls[lane][jj] = acc[jj];
-    if (lane == 0 && bad != 0 && S.bad == 0) S.bad = bad;
+    for (int jj = 0; jj < W; jj++) S.Ls[dl][jj] = acc[jj];
+    if (dl == 0 && bad != 0 && S.bad == 0) S.bad = bad;
   }
   __syncthreads();
 
   // (d) rows below the diagonal block: substitution against it
-  if (active && i >= c0 + 32) {
+  if (active && i >= c0 + BW) {
 #pragma unroll
     for (int j = 0; j < W; j++) {
       acc[j] *= S.rinv[j];
@@ -384,7 +393,7 @@ __device__ __forceinline__ void rows_block(RowsSmem<T> &S, int c0, int n, int k,
   __syncthreads();
 }
 
-template <bool FUSED, bool ALIGNED, typename T>
+template <int BW, bool FUSED, bool ALIGNED, typename T>
 __global__ void __launch_bounds__(512)
 k_chol_rows(int n, int k, Op A, Op B, Op C, OpWT<T> D, T *dinv, long long sdinv, int *info) {
   __shared__ RowsSmem<T> S;
@@ -396,17 +405,28 @@ k_chol_rows(int n, int k, Op A, Op B, Op C, OpWT<T> D, T *dinv, long long sdinv,
   T *dinv_b = dinv ? dinv + b * sdinv : nullptr;
   if (threadIdx.x == 0) S.bad = 0;
   __syncthreads();
-  for (int c0 = 0; c0 < n; c0 += 32) {
-    const int w8 = (min(32, n - c0) + 7) & ~7;
-    switch (w8) {
-      case 8: rows_block<8, FUSED, ALIGNED, T>(S, c0, n, k, pa, pb, pc, pd, A, B, C, D, dinv_b); break;
-      case 16: rows_block<16, FUSED, ALIGNED, T>(S, c0, n, k, pa, pb, pc, pd, A, B, C, D, dinv_b); break;
-      case 24: rows_block<24, FUSED, ALIGNED, T>(S, c0, n, k, pa, pb, pc, pd, A, B, C, D, dinv_b); break;
-      default: rows_block<32, FUSED, ALIGNED, T>(S, c0, n, k, pa, pb, pc, pd, A, B, C, D, dinv_b); break;
+  for (int c0 = 0; c0 < n; c0 += BW) {
+    const int w8 = (min(BW, n - c0) + 7) & ~7;
+    if (BW == 16) {
+      if (w8 == 8)
+        rows_block<8, 16, FUSED, ALIGNED, T>(S, c0, n, k, pa, pb, pc, pd, A, B, C, D, dinv_b);
+      else
+        rows_block<16, 16, FUSED, ALIGNED, T>(S, c0, n, k, pa, pb, pc, pd, A, B, C, D, dinv_b);
+    } else {
+      switch (w8) {
+        case 8: rows_block<8, 32, FUSED, ALIGNED, T>(S, c0, n, k, pa, pb, pc, pd, A, B, C, D, dinv_b); break;
+        case 16: rows_block<16, 32, FUSED, ALIGNED, T>(S, c0, n, k, pa, pb, pc, pd, A, B, C, D, dinv_b); break;
+        case 24: rows_block<24, 32, FUSED, ALIGNED, T>(S, c0, n, k, pa, pb, pc, pd, A, B, C, D, dinv_b); break;
+        default: rows_block<32, 32, FUSED, ALIGNED, T>(S, c0, n, k, pa, pb, pc, pd, A, B, C, D, dinv_b); break;
+      }
     }
   }
   if (info && threadIdx.x == 0) info[b] = S.bad;
 }
+
+// Block width of k_chol_rows: 16-column blocks halve the work the diagonal
+// block's warp spends above the diagonal and the registers per thread.
+constexpr int ROWS_BW = 16;
 
 // smallest G whose shared-memory triangle for 32/G problems fits the budget
 int pick_small_g(int n) {
@@ -444,9 +464,9 @@ cudaError_t launch_chol_t(bool aligned, int batch, int n, int k, Op A, Op B, Op 
   }
   const int threads = (n + 31) & ~31;
   if (aligned)
-    k_chol_rows<FUSED, true, double><<<batch, threads, 0, s>>>(n, k, A, B, C, D, dinv, sdinv, info);
+    k_chol_rows<ROWS_BW, FUSED, true, double><<<batch, threads, 0, s>>>(n, k, A, B, C, D, dinv, sdinv, info);
   else
-    k_chol_rows<FUSED, false, double><<<batch, threads, 0, s>>>(n, k, A, B, C, D, dinv, sdinv, info);
+    k_chol_rows<ROWS_BW, FUSED, false, double><<<batch, threads, 0, s>>>(n, k, A, B, C, D, dinv, sdinv, info);
   return cudaGetLastError();
 }
 
@@ -463,9 +483,9 @@ cudaError_t launch_chol_f32(int batch, int n, Op C, OpWT<float> D, int *info, bo
   const int threads = (n + 31) & ~31;
   const Op none{nullptr, 0, 0, 0, 0};
   if (aligned)
-    k_chol_rows<false, true, float><<<batch, threads, 0, s>>>(n, 0, none, none, C, D, nullptr, 0, info);
+    k_chol_rows<ROWS_BW, false, true, float><<<batch, threads, 0, s>>>(n, 0, none, none, C, D, nullptr, 0, info);
   else
-    k_chol_rows<false, false, float><<<batch, threads, 0, s>>>(n, 0, none, none, C, D, nullptr, 0, info);
+    k_chol_rows<ROWS_BW, false, false, float><<<batch, threads, 0, s>>>(n, 0, none, none, C, D, nullptr, 0, info);
   return cudaGetLastError();
 }
 
