@@ -428,12 +428,17 @@ k_chol_rows(int n, int k, Op A, Op B, Op C, OpWT<T> D, T *dinv, long long sdinv,
 // block's warp spends above the diagonal and the registers per thread.
 constexpr int ROWS_BW = 16;
 
-// smallest G whose shared-memory triangle for 32/G problems fits the budget
+// Lanes per problem of k_chol_small: the smallest G (at most 16) whose
+// shared-memory triangles for the 32/G problems of a warp fit the budget, so
+// that enough single-warp CTAs are resident on each SM.  Measured on the
+// sweep: more resident warps pay for a larger G (the pivot's rsqrt shared by
+// fewer problems) up to G = 16; beyond that the rsqrt dominates.
+constexpr long long SMALL_SMEM_BUDGET = 20 * 1024;
 int pick_small_g(int n) {
   const long long ne = (long long)n * (n + 1) / 2;
-  for (int g = 1; g <= 32; g *= 2)
-    if (ne * (32 / g) * 8 <= 40 * 1024) return g;
-  return 0;
+  for (int g = 1; g <= 16; g *= 2)
+    if (ne * (32 / g) * 8 <= SMALL_SMEM_BUDGET) return g;
+  return (ne * 2 * 8 <= 48 * 1024) ? 16 : 0;
 }
 
 template <int G, bool FUSED>
