@@ -151,6 +151,25 @@ def config_dict(points):
     }
 
 
+# ------------------------------------------------------------- multi-rank --
+
+def max_over_ranks(x: float, world: int, device="cpu") -> float:
+    """The largest value of x over all ranks (the slowest rank's time)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(flops_per_rank: float, seconds: float, world: int) -> float:
+    """Whole-job GFLOP/s: every rank runs the same workload on its own GPU
+    (independent problems, weak scaling), timed by the slowest rank."""
+    return flops_per_rank * world / seconds / 1e9
+
+
 # ------------------------------------------------------------------ clocks --
 
 class ClockSampler:
@@ -265,65 +284,90 @@ class Point:
                                info=self.info, stream=stream)
 
 
-def cpu_sample_rates(points_spec, budget_s=0.25, max_threads=None):
-    """Oracle GFLOP/s per (routine, n) on a bounded sample; returns (rates, cores, desc)."""
-    import numpy as np
+class OracleSampler:
+    """The CPU oracle timed on a bounded sample of every sweep point.
 
-    import oracle
-    from paper_1704_02457_gb300 import inputs
+    Calibration picks, per point, a sample of problems that takes about
+    budget_s seconds (at most the point's full batch) and keeps its inputs;
+    each timed pass then runs the oracle on those cached inputs and returns
+    GFLOP/s per point.  The oracle runs its problems on every host core
+    (OpenMP)."""
 
-    oracle.build()
-    if max_threads:
-        oracle.set_num_threads(max_threads)
-    cores = oracle.num_threads()
-    rates, sizes = {}, {}
-    for routine, n in points_spec:
-        f = flops(routine, n)
-        # probe with a tiny batch, then size the sample to the budget
-        count = max(1, min(inputs.sweep_batch(routine, n), int(2e7 / max(f, 1.0))))
-        for attempt in range(3):
-            t = _oracle_run(routine, n, count)
-            if t >= 0.5 * budget_s or count >= inputs.sweep_batch(routine, n):
-                break
-            count = min(inputs.sweep_batch(routine, n), int(count * min(64.0, budget_s / max(t, 1e-6))) + 1)
-        rates[(routine, n)] = f * count / t / 1e9
-        sizes[(routine, n)] = count
-    desc = ("oracle (plain C loops, -O2 -ffp-contract=off, OpenMP over problems) on a bounded "
-            "sample per point (" + ", ".join(f"{r}@{n}:{sizes[(r, n)]}" for r, n in points_spec[:3])
-            + ", ...), about %.2f s each; step time = sum over points of full-batch flops / sample rate"
-            % budget_s)
-    return rates, cores, desc, sizes
+    def __init__(self, points_spec, budget_s=0.25):
+        import oracle
+        from paper_1704_02457_gb300 import inputs
+
+        oracle.build()
+        self.spec = list(points_spec)
+        self.cores = oracle.num_threads()
+        self.cache = {}
+        for routine, n in self.spec:
+            full = inputs.sweep_batch(routine, n)
+            # probe with ~20 MFLOP, then size the sample to the budget
+            count = max(1, min(full, int(2e7 / max(flops(routine, n), 1.0))))
+            data = _oracle_inputs(routine, n, count)
+            t = _oracle_time(routine, n, data)
+            if t < 0.5 * budget_s and count < full:
+                count = min(full, int(count * min(256.0, budget_s / max(t, 1e-6))) + 1)
+                data = _oracle_inputs(routine, n, count)
+            self.cache[(routine, n)] = (count, data)
+
+    def rates(self):
+        out = {}
+        for (routine, n), (count, data) in self.cache.items():
+            out[(routine, n)] = flops(routine, n) * count / _oracle_time(routine, n, data) / 1e9
+        return out
+
+    def describe(self):
+        first = ", ".join(f"{r}@{n}:{self.cache[(r, n)][0]}" for r, n in self.spec[:3])
+        return ("oracle (plain C loops, -O2 -ffp-contract=off, OpenMP over problems) on a bounded sample "
+                f"of problems per point ({first}, ...); step time = sum over points of full-batch "
+                "flops / sample rate")
 
 
-def _oracle_run(routine, n, count):
+def _oracle_inputs(routine, n, count):
+    """Sample inputs, already in the oracle's column-major layout, with output
+    buffers: the timed call runs the C routine only."""
     import numpy as np
 
     import oracle
     rng = np.random.default_rng(7 + n)
     A = rng.standard_normal((count, n, n))
-    if routine in ("dpotrf_l",):
-        S = A @ A.transpose(0, 2, 1) + n * np.eye(n)
-        t0 = time.perf_counter()
-        oracle.dpotrf_l(S)
-        return time.perf_counter() - t0
-    if routine == "dtrsm_rltn":
-        L = np.linalg.cholesky(A @ A.transpose(0, 2, 1) + n * np.eye(n))
-        B = rng.standard_normal((count, n, n))
-        t0 = time.perf_counter()
-        oracle.dtrsm_rltn(1.0, L, B)
-        return time.perf_counter() - t0
-    if routine == "dsyrk_dpotrf_ln":
-        Q = np.broadcast_to(n * np.eye(n), (count, n, n))
-        t0 = time.perf_counter()
-        oracle.dsyrk_dpotrf_ln(A, A, Q)
-        return time.perf_counter() - t0
-    B = rng.standard_normal((count, n, n))
-    C = rng.standard_normal((count, n, n))
-    t0 = time.perf_counter()
-    if routine == "dgemm_nt":
-        oracle.dgemm_nt(1.0, A, B, 1.0, C)
+    cm = oracle._colmajor
+    if routine == "dpotrf_l":
+        ins = (cm(A @ A.transpose(0, 2, 1) + n * np.eye(n)),)
+    elif routine == "dtrsm_rltn":
+        ins = (cm(np.linalg.cholesky(A @ A.transpose(0, 2, 1) + n * np.eye(n))), cm(rng.standard_normal((count, n, n))))
+    elif routine == "dsyrk_dpotrf_ln":
+        ins = (cm(A), cm(np.broadcast_to(n * np.eye(n), (count, n, n))))
     else:
-        oracle.dsyrk_ln(1.0, A, A, 1.0, C)
+        ins = (cm(A), cm(rng.standard_normal((count, n, n))), cm(rng.standard_normal((count, n, n))))
+    out = np.zeros((count, n, n))
+    return ins + (out, np.zeros((count, n)), np.zeros(count, dtype=np.int32), count)
+
+
+def _oracle_time(routine, n, data):
+    import ctypes
+
+    import oracle
+    lib, P = oracle._lib(), oracle._ptr
+    *ins, out, dinv, info, bt = data
+    nn = n * n
+    ip = info.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    t0 = time.perf_counter()
+    if routine == "dpotrf_l":
+        lib.or_dpotrf_l_batch(bt, n, P(ins[0]), n, nn, P(out), n, nn, P(dinv), n, ip)
+    elif routine == "dtrsm_rltn":
+        lib.or_dtrsm_rltn_batch(bt, n, n, 1.0, P(ins[0]), n, nn, P(ins[1]), n, nn, P(out), n, nn)
+    elif routine == "dsyrk_dpotrf_ln":
+        lib.or_dsyrk_dpotrf_ln_batch(bt, n, n, P(ins[0]), n, nn, P(ins[0]), n, nn, P(ins[1]), n, nn,
+                                     P(out), n, nn, P(dinv), n, ip)
+    elif routine == "dgemm_nt":
+        lib.or_dgemm_nt_batch(bt, n, n, n, 1.0, P(ins[0]), n, nn, P(ins[1]), n, nn, 1.0, P(ins[2]), n, nn,
+                              P(out), n, nn)
+    else:
+        lib.or_dsyrk_ln_batch(bt, n, n, 1.0, P(ins[0]), n, nn, P(ins[0]), n, nn, 1.0, P(ins[2]), n, nn,
+                              P(out), n, nn)
     return time.perf_counter() - t0
 
 
@@ -388,14 +432,10 @@ def run_gpu(args):
     clocks = sampler.stop()
     if world > 1:
         torch.distributed.barrier()
-    total_ms = t0.elapsed_time(t1)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(t0.elapsed_time(t1), world, dev)
     ms_per_step = total_ms / K
     step_flops = sum(p.flops for p in pts)
-    value = step_flops * world / (ms_per_step * 1e-3) / 1e9
+    value = job_rate(step_flops, ms_per_step * 1e-3, world)
 
     per_point = []
     per_routine = {}
@@ -472,10 +512,11 @@ def run_gpu(args):
     if not args.no_e2e:
         result["e2e"] = run_e2e(pts, args, dev, world)
     if rank == 0 and world == 1 and not args.no_cpu:
-        rates, cores, desc, _ = cpu_sample_rates(spec, budget_s=args.cpu_budget)
+        sampler = OracleSampler(spec, budget_s=args.cpu_budget)
+        rates = sampler.rates()
         t_cpu = sum(p.flops / (rates[(p.routine, p.n)] * 1e9) for p in pts)
         result["cpu_baseline"] = {"value": round(step_flops / t_cpu / 1e9, 3), "unit": "GFLOP/s",
-                                  "cores": cores, "kind": "oracle", "sample": desc}
+                                  "cores": sampler.cores, "kind": "oracle", "sample": sampler.describe()}
     if world > 1:
         torch.distributed.destroy_process_group()
     if rank == 0:
@@ -579,13 +620,9 @@ def run_e2e(pts, args, dev, world):
     for _ in range(steps):
         e2e_step()
     torch.cuda.synchronize()
-    dt = (time.perf_counter() - t0) / steps
-    if world > 1:
-        t = torch.tensor([dt], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        dt = float(t.item())
+    dt = max_over_ranks((time.perf_counter() - t0) / steps, world, dev)
     step_flops = sum(p.flops for p in pts)
-    return {"value": round(step_flops * world / dt / 1e9, 2), "unit": "GFLOP/s",
+    return {"value": round(job_rate(step_flops, dt, world), 2), "unit": "GFLOP/s",
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": steps,
             "ms_per_step": round(dt * 1e3, 2),
             "path": "pinned host column-major -> H2D -> bf_pack -> routine -> bf_unpack -> D2H, "
@@ -783,19 +820,21 @@ def run_adjoint(args, dev, bt=2048, n=64, nrhs=1):
 # ---------------------------------------------------------- reference arm --
 
 def run_reference(args):
+    """The reference arm: the CPU oracle, timed on the host cores on a bounded
+    sample of every sweep point (cached after one calibration), reported as
+    the same whole-step GFLOP/s metric."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if world > 1 and rank != 0:
         return
-    spec = [(r, n) for n in SWEEP_N for r in ROUTINES]
     from paper_1704_02457_gb300 import inputs
-    budget = args.cpu_budget
-    rates = None
+    spec = [(r, n) for n in SWEEP_N for r in ROUTINES]
+    sampler = OracleSampler(spec, budget_s=args.ref_budget)
     for _ in range(args.warmup):
-        rates, cores, desc, sizes = cpu_sample_rates(spec, budget_s=budget * 0.2)
+        sampler.rates()
     step_times = []
     for _ in range(args.steps):
-        rates, cores, desc, sizes = cpu_sample_rates(spec, budget_s=budget)
+        rates = sampler.rates()
         step_times.append(sum(flops(r, n) * inputs.sweep_batch(r, n) / (rates[(r, n)] * 1e9) for r, n in spec))
     step_flops = sum(flops(r, n) * inputs.sweep_batch(r, n) for r, n in spec)
     t = statistics.median(step_times)
@@ -807,8 +846,8 @@ def run_reference(args):
         "warmup": args.warmup, "ms_per_step": round(t * 1e3, 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded iid N(0,1), SPD M M^T + n I)", "config": config_dict(spec),
-        "cpu_baseline": {"value": round(value, 3), "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
-                         "sample": desc},
+        "cpu_baseline": {"value": round(value, 3), "unit": "GFLOP/s", "cores": sampler.cores, "kind": "oracle",
+                         "sample": sampler.describe()},
         "e2e": {"value": round(value, 3), "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -825,7 +864,9 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-riccati", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
-    ap.add_argument("--cpu-budget", type=float, default=0.3, help="seconds of oracle time per point")
+    ap.add_argument("--cpu-budget", type=float, default=0.15, help="seconds of oracle time per point")
+    ap.add_argument("--ref-budget", type=float, default=0.06,
+                    help="seconds of oracle time per point and step of the reference arm")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
