@@ -130,8 +130,12 @@ def kernel_of(routine, n):
     if routine == "dtrsm_rltn":
         return "k_trsm_rltn"
     fused = int(routine == "dsyrk_dpotrf_ln")
-    if n <= 64 and small_g(n):
+    if n <= 48 and small_g(n):
         return f"k_chol_small<{small_g(n)},{fused},1>"
+    if n <= 192:
+        return f"k_chol_rows2<16,{fused},1,double,384>"
+    if n <= 256 and not fused:
+        return "k_chol_rows2<16,0,1,double,512>"
     return f"k_chol_rows<16,{fused},1,double>"
 
 
@@ -509,6 +513,8 @@ def run_gpu(args):
         result["riccati"] = run_riccati(args, dev)
     if not args.no_adjoint:
         result["adjoint"] = run_adjoint(args, dev)
+    if not args.no_next4:
+        result["next4"] = run_next4(args, dev)
     if not args.no_e2e:
         result["e2e"] = run_e2e(pts, args, dev, world)
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -817,6 +823,76 @@ def run_adjoint(args, dev, bt=2048, n=64, nrhs=1):
     }
 
 
+def next4_flops(routine: str, n: int) -> float:
+    """Flops of one n x n problem, counted from the algorithm's own steps:
+    gemm_nn 2n^3; trmm_rlnn one FMA per nonzero of L per row of B; getrf per
+    column j a reciprocal-scaled column of k = n-j-1 multipliers and a k x k
+    rank-1 update; gelqf per row i a norm and scaling of k = n-i-1 entries,
+    then for each of the k rows below a dot product and an update of k+1
+    entries."""
+    if routine == "dgemm_nn":
+        return 2.0 * n ** 3
+    if routine == "dtrmm_rlnn":
+        return float(n * n * (n + 1))
+    if routine == "dgetrf":
+        return float(sum(k + 2 * k * k for k in range(n)))
+    if routine == "dgelqf":
+        return float(sum(3 * k + k * (4 * k + 3) for k in range(n)))
+    raise ValueError(routine)
+
+
+NEXT4_POINTS = [("dgemm_nn", 64, 4096), ("dtrmm_rlnn", 64, 4096), ("dgetrf", 16, 65536), ("dgetrf", 64, 8192),
+                ("dgetrf", 128, 2048), ("dgelqf", 16, 65536), ("dgelqf", 64, 8192), ("dgelqf", 128, 2048)]
+
+
+def run_next4(args, dev):
+    """The remaining routines of the paper's list on square problems, each
+    batch's inputs larger than L2 (at least 128 MiB read per launch): CUDA
+    events around `reps` back-to-back launches on the current stream after
+    three warm-up launches."""
+    import torch
+
+    import paper_1704_02457_gb300 as bf
+    from paper_1704_02457_gb300 import inputs
+
+    stream = torch.cuda.current_stream()
+    out = {}
+    for i, (r, n, bt) in enumerate(NEXT4_POINTS):
+        A = bf.DMatBatch.from_colmajor(inputs.normal((bt, n, n), 13000 + 7 * i, dev), tight=True)
+        D = bf.DMatBatch(bt, n, n, device=dev, tight=True)
+        if r in ("dgemm_nn", "dtrmm_rlnn"):
+            B = bf.DMatBatch.from_colmajor(inputs.normal((bt, n, n), 13001 + 7 * i, dev), tight=True)
+        if r == "dgemm_nn":
+            C = bf.DMatBatch.from_colmajor(inputs.normal((bt, n, n), 13002 + 7 * i, dev), tight=True)
+            fn = lambda: bf.dgemm_nn(n, n, n, 1.0, A, 0, 0, B, 0, 0, 1.0, C, 0, 0, D, 0, 0, stream=stream)  # noqa: E731
+        elif r == "dtrmm_rlnn":
+            fn = lambda: bf.dtrmm_rlnn(n, n, 1.0, A, 0, 0, B, 0, 0, D, 0, 0, stream=stream)  # noqa: E731
+        elif r == "dgetrf":
+            ipiv = torch.empty((bt, n), dtype=torch.int32, device=dev)
+            info = torch.empty((bt,), dtype=torch.int32, device=dev)
+            fn = lambda: bf.dgetrf(n, A, 0, 0, D, 0, 0, ipiv, info=info, stream=stream)  # noqa: E731
+        else:
+            tau = torch.empty((bt, n), dtype=torch.float64, device=dev)
+            fn = lambda: bf.dgelqf(n, n, A, 0, 0, D, 0, 0, tau, stream=stream)  # noqa: E731
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        reps = max(3, args.steps)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        g = bt * next4_flops(r, n) / (ms * 1e-3) / 1e9
+        out[f"{r}@{n}"] = {"batch": bt, "ms": round(ms, 4), "gflops": round(g, 2),
+                           "frac_of_fp64_alu_peak": round(g / FP64_PEAK_GFLOPS, 4)}
+        del A, D
+        torch.cuda.empty_cache()
+    return out
+
+
 # ---------------------------------------------------------- reference arm --
 
 def run_reference(args):
@@ -864,6 +940,7 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-riccati", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-next4", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=0.15, help="seconds of oracle time per point")
     ap.add_argument("--ref-budget", type=float, default=0.06,
                     help="seconds of oracle time per point and step of the reference arm")

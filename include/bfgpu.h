@@ -138,6 +138,34 @@ int bf_dgemm_nt(int m, int n, int k, double alpha, const bf_dmat *sA, int ai, in
                 const bf_dmat *sB, int bi, int bj, double beta, const bf_dmat *sC, int ci, int cj,
                 const bf_dmat *sD, int di, int dj, void *stream);
 
+/* gemm_nn (Sec. 5.2.2 "gemm_nn"):
+ *     D <- alpha * A * B + beta * C
+ * A is m x k, B is k x n, C and D are m x n.  C and D may coincide; no other
+ * overlap.  beta == 0 means C is not read. */
+int bf_dgemm_nn_batched(int batch, int m, int n, int k, double alpha,
+                        const bf_dmat *sA, int ai, int aj, long long strideA,
+                        const bf_dmat *sB, int bi, int bj, long long strideB, double beta,
+                        const bf_dmat *sC, int ci, int cj, long long strideC,
+                        const bf_dmat *sD, int di, int dj, long long strideD, void *stream);
+
+int bf_dgemm_nn(int m, int n, int k, double alpha, const bf_dmat *sA, int ai, int aj,
+                const bf_dmat *sB, int bi, int bj, double beta, const bf_dmat *sC, int ci, int cj,
+                const bf_dmat *sD, int di, int dj, void *stream);
+
+/* trmm_rlnn (Sec. 5.2.2 "trmm_rlnn"; right, lower, not transposed,
+ * non-unit):
+ *     D <- alpha * B * L
+ * L is the n x n lower triangle of sL at (li, lj) (its strictly upper part
+ * does not affect the result); B and D are m x n and must not overlap. */
+int bf_dtrmm_rlnn_batched(int batch, int m, int n, double alpha,
+                          const bf_dmat *sL, int li, int lj, long long strideL,
+                          const bf_dmat *sB, int bi, int bj, long long strideB,
+                          const bf_dmat *sD, int di, int dj, long long strideD, void *stream);
+
+int bf_dtrmm_rlnn(int m, int n, double alpha, const bf_dmat *sL, int li, int lj,
+                  const bf_dmat *sB, int bi, int bj, const bf_dmat *sD, int di, int dj,
+                  void *stream);
+
 /* syrk_ln (Sec. 5.2.2):
  *     lower(D) <- alpha * A * B^T + beta * C
  * A and B are m x k and may be different matrices (or the same); C and D are
@@ -190,6 +218,36 @@ int bf_dpotrf_l_batched(int batch, int m, const bf_dmat *sC, int ci, int cj, lon
 
 int bf_dpotrf_l(int m, const bf_dmat *sC, int ci, int cj, const bf_dmat *sD, int di, int dj,
                 int *info, void *stream);
+
+/* getrf (Sec. 5.2.2 "getrf"; LU with partial pivoting, Appendix A.3):
+ *     P A = L U  for the n x n matrix C, stored in D (L unit lower, its
+ *     diagonal not stored; U upper).
+ * Column by column, the pivot is the first row at or below the diagonal with
+ * the largest |a(i, j)|; ipiv[b*strideIpiv + j] (device, 0-based) receives
+ * it, and row j was swapped with it over the whole matrix.  info (device, may
+ * be NULL): 0, or j+1 for the first exactly zero pivot (that column is then
+ * neither scaled nor used to update).  C and D may coincide.  Supports
+ * n <= 128. */
+int bf_dgetrf_batched(int batch, int n, const bf_dmat *sC, int ci, int cj, long long strideC,
+                      const bf_dmat *sD, int di, int dj, long long strideD, int *ipiv,
+                      long long strideIpiv, int *info, void *stream);
+
+int bf_dgetrf(int n, const bf_dmat *sC, int ci, int cj, const bf_dmat *sD, int di, int dj,
+              int *ipiv, int *info, void *stream);
+
+/* gelqf (Sec. 5.2.2 "gelqf"; LQ factorization, Appendix A.3):
+ *     A = L Q  for the m x n matrix C, stored in D.
+ * Householder reflectors H_i = I - tau_i v_i v_i^T, v_i = [1, x_i], applied
+ * from the right row by row (i < min(m, n)); beta = -sign(alpha) ||(alpha,
+ * x)||.  L is the lower triangle of D, x_i is left in the strictly upper
+ * part of row i, tau (device) receives tau_i at tau + b*strideTau + i, and
+ * Q = H_{k-1} ... H_0.  C and D may coincide.  Supports m * n <= 16384. */
+int bf_dgelqf_batched(int batch, int m, int n, const bf_dmat *sC, int ci, int cj, long long strideC,
+                      const bf_dmat *sD, int di, int dj, long long strideD, double *tau,
+                      long long strideTau, void *stream);
+
+int bf_dgelqf(int m, int n, const bf_dmat *sC, int ci, int cj, const bf_dmat *sD, int di, int dj,
+              double *tau, void *stream);
 
 /* syrk_potrf_ln (Sec. 4.7.2 "concatenating updates/downdates"; Sec. 5.3;
  * routine list in Appendix A.3):

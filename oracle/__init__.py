@@ -74,6 +74,10 @@ def _lib():
             lib.or_dpotrf_l_batch.argtypes = [_i, _i, _dp, _i, _l, _dp, _i, _l, _dp, _l, _ip]
             lib.or_dtrsm_rltn_batch.argtypes = [_i, _i, _i, _d, _dp, _i, _l, _dp, _i, _l,
                                                 _dp, _i, _l]
+            lib.or_dgetrf.argtypes = [_i, _dp, _i, _dp, _i, _ip]
+            lib.or_dgetrf.restype = _i
+            lib.or_dgelqf.argtypes = [_i, _i, _dp, _i, _dp, _i, _dp]
+            lib.or_dgemm_nn.argtypes = [_i, _i, _i, _d, _dp, _i, _dp, _i, _d, _dp, _i, _dp, _i]
             lib.or_dposv_adjoint.argtypes = [_i, _i, _dp, _i, _dp, _i, _dp, _i, _dp, _i, _dp, _i]
             lib.or_dtrmm_rlnn.argtypes = [_i, _i, _d, _dp, _i, _dp, _i, _dp, _i]
             lib.or_dtrsm_rlnn.argtypes = [_i, _i, _d, _dp, _i, _dp, _i, _dp, _i]
@@ -275,3 +279,50 @@ def dposv_adjoint(L, X, Xbar):
     ab = np.zeros((n, n))
     _lib().or_dposv_adjoint(n, nrhs, _ptr(lb), n, _ptr(xb), n, _ptr(xbb), n, _ptr(bb), n, _ptr(ab), n)
     return _back(bb), _back(ab)
+
+
+def dgemm_nn(alpha, A, B, beta, C):
+    """D = alpha*A*B + beta*C (single problem; A m x k, B k x n)."""
+    A, B, C = (np.asarray(v, dtype=np.float64) for v in (A, B, C))
+    m, k = A.shape
+    n = B.shape[1]
+    a, b, c = _colmajor(A), _colmajor(B), _colmajor(C)
+    d = np.zeros((n, m))
+    _lib().or_dgemm_nn(m, n, k, alpha, _ptr(a), m, _ptr(b), k, beta, _ptr(c), m, _ptr(d), m)
+    return _back(d)
+
+
+def dgetrf(A):
+    """(LU, ipiv, info) of P A = L U (single problem, square A); ipiv 0-based."""
+    A = np.asarray(A, dtype=np.float64)
+    n = A.shape[0]
+    a = _colmajor(A)
+    d = np.zeros((n, n))
+    ipiv = np.zeros(n, dtype=np.int32)
+    info = _lib().or_dgetrf(n, _ptr(a), n, _ptr(d), n, ipiv.ctypes.data_as(_ip))
+    return _back(d), ipiv, int(info)
+
+
+def dgelqf(A):
+    """(F, tau) of A = L Q (single problem): L in lower(F), reflectors in the
+    strictly upper part of F."""
+    A = np.asarray(A, dtype=np.float64)
+    m, n = A.shape
+    a = _colmajor(A)
+    d = np.zeros((n, m))
+    tau = np.zeros(min(m, n))
+    _lib().or_dgelqf(m, n, _ptr(a), m, _ptr(d), m, _ptr(tau))
+    return _back(d), tau
+
+
+def lq_q(F, tau):
+    """Q = H_{k-1} ... H_0 (n x n) from the reflectors of dgelqf (marshalling
+    helper for tests: plain products of the stored reflectors)."""
+    m, n = F.shape
+    Q = np.eye(n)
+    for i in range(len(tau)):
+        v = np.zeros(n)
+        v[i] = 1.0
+        v[i + 1:] = F[i, i + 1:]
+        Q = (np.eye(n) - tau[i] * np.outer(v, v)) @ Q
+    return Q

@@ -49,6 +49,22 @@ void or_dgemm_nt(int m, int n, int k, double alpha, const double *A, int lda,
   }
 }
 
+/* gemm_nn (Sec. 5.2.2 "gemm_nn"): D <- alpha * A * B + beta * C, A m x k,
+ * B k x n, C and D m x n; C and D may coincide; beta == 0: C not read. */
+void or_dgemm_nn(int m, int n, int k, double alpha, const double *A, int lda,
+                 const double *B, int ldb, double beta, const double *C, int ldc,
+                 double *D, int ldd) {
+  if (m <= 0 || n <= 0) return;
+  for (int j = 0; j < n; j++) {
+    for (int i = 0; i < m; i++) {
+      double s = 0.0;
+      for (int l = 0; l < k; l++) s += EL(A, lda, i, l) * EL(B, ldb, l, j);
+      double c = (beta == 0.0) ? 0.0 : beta * EL(C, ldc, i, j);
+      EL(D, ldd, i, j) = alpha * s + c;
+    }
+  }
+}
+
 /* syrk_ln (Sec. 5.2.2 "syrk_ln"): lower(D) <- alpha * A * B^T + beta * C,
  * A and B are m x k and may differ, C and D are m x m.  Only i >= j is
  * computed and written. */
@@ -200,6 +216,85 @@ void or_dposv_adjoint(int n, int nrhs, const double *L, int ldl, const double *X
         s += EL(Bbar, ldbb, i, k) * EL(X, ldx, j, k) + EL(X, ldx, i, k) * EL(Bbar, ldbb, j, k);
       EL(Abar, lda, i, j) = -0.5 * s;
     }
+}
+
+/* getrf (Sec. 5.2.2 "getrf"; LU factorization with partial pivoting, the
+ * routine list of Appendix A.3): P A = L U for the n x n matrix A, in the
+ * unblocked right-looking order, column by column:
+ *   p      = first i >= j with |A[i][j]| maximal          (pivot row)
+ *   swap rows j and p (whole rows); ipiv[j] = p           (0-based)
+ *   A[i][j] = A[i][j] / A[j][j],  i > j                   (multipliers, L)
+ *   A[i][c] -= A[i][j] A[j][c],   i > j, c > j            (update)
+ * L (unit diagonal, not stored) and U overwrite D (a copy of C).  A zero
+ * pivot sets info = j+1 (first one) and skips that column's division.
+ * Returns info. */
+int or_dgetrf(int n, const double *C, int ldc, double *D, int ldd, int *ipiv) {
+  if (n <= 0) return 0;
+  int info = 0;
+  for (int j = 0; j < n; j++)
+    for (int i = 0; i < n; i++) EL(D, ldd, i, j) = EL(C, ldc, i, j);
+  for (int j = 0; j < n; j++) {
+    int p = j;
+    double best = fabs(EL(D, ldd, j, j));
+    for (int i = j + 1; i < n; i++)
+      if (fabs(EL(D, ldd, i, j)) > best) {
+        best = fabs(EL(D, ldd, i, j));
+        p = i;
+      }
+    ipiv[j] = p;
+    if (p != j)
+      for (int c = 0; c < n; c++) {
+        double t = EL(D, ldd, j, c);
+        EL(D, ldd, j, c) = EL(D, ldd, p, c);
+        EL(D, ldd, p, c) = t;
+      }
+    double piv = EL(D, ldd, j, j);
+    if (piv == 0.0) {
+      if (info == 0) info = j + 1;
+      continue;
+    }
+    for (int i = j + 1; i < n; i++) EL(D, ldd, i, j) = EL(D, ldd, i, j) / piv;
+    for (int c = j + 1; c < n; c++)
+      for (int i = j + 1; i < n; i++) EL(D, ldd, i, c) -= EL(D, ldd, i, j) * EL(D, ldd, j, c);
+  }
+  return info;
+}
+
+/* gelqf (Sec. 5.2.2 "gelqf"; LQ factorization, routine list of Appendix A.3):
+ * A = L Q for the m x n matrix A, by Householder reflectors applied from the
+ * right, row by row (i < min(m, n)):
+ *   alpha = A[i][i], x = A[i][i+1:n], s = ||x||^2
+ *   if s == 0:  tau[i] = 0 (H_i = I)
+ *   else:       beta = -sign(alpha) sqrt(alpha^2 + s); tau[i] = (beta - alpha) / beta
+ *               x = x / (alpha - beta); A[i][i] = beta
+ *   H_i = I - tau[i] v v^T with v = [1, x]; rows r > i: A[r][i:n] <- A[r][i:n] H_i
+ * L is the lower triangle of the result; the reflectors v (without their
+ * leading 1) are left in the strictly upper part of row i, and Q =
+ * H_{k-1} ... H_1 H_0 with k = min(m, n).  D is a copy of C on entry. */
+void or_dgelqf(int m, int n, const double *C, int ldc, double *D, int ldd, double *tau) {
+  if (m <= 0 || n <= 0) return;
+  for (int j = 0; j < n; j++)
+    for (int i = 0; i < m; i++) EL(D, ldd, i, j) = EL(C, ldc, i, j);
+  int k = m < n ? m : n;
+  for (int i = 0; i < k; i++) {
+    double alpha = EL(D, ldd, i, i), s = 0.0;
+    for (int c = i + 1; c < n; c++) s += EL(D, ldd, i, c) * EL(D, ldd, i, c);
+    double t = 0.0;
+    if (s != 0.0) {
+      double beta = -copysign(sqrt(alpha * alpha + s), alpha);
+      t = (beta - alpha) / beta;
+      double scal = 1.0 / (alpha - beta);
+      for (int c = i + 1; c < n; c++) EL(D, ldd, i, c) *= scal;
+      EL(D, ldd, i, i) = beta;
+    }
+    tau[i] = t;
+    for (int r = i + 1; r < m; r++) {
+      double w = EL(D, ldd, r, i);
+      for (int c = i + 1; c < n; c++) w += EL(D, ldd, r, c) * EL(D, ldd, i, c);
+      EL(D, ldd, r, i) -= t * w;
+      for (int c = i + 1; c < n; c++) EL(D, ldd, r, c) -= t * w * EL(D, ldd, i, c);
+    }
+  }
 }
 
 /* Panel-major format (Sec. 4.3.3): rows are grouped in panels of ps rows

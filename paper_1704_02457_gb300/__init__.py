@@ -19,7 +19,7 @@ from ._abi import BF_ALIGN, BF_ERR_UNSUPPORTED, BF_PS, bf_dmat, load
 __all__ = [
     "BF_PS", "BF_ALIGN", "BF_ERR_UNSUPPORTED", "BfError", "DMatBatch", "bf_dmat", "load",
     "dgemm_nt", "dsyrk_ln", "dpotrf_l", "dtrsm_rltn", "dsyrk_dpotrf_ln", "pack", "unpack",
-    "dpotrs_l", "dposv_mixed", "dposv_mixed_worksize",
+    "dpotrs_l", "dposv_mixed", "dposv_mixed_worksize", "dgemm_nn", "dtrmm_rlnn", "dgetrf", "dgelqf",
 ]
 
 
@@ -222,3 +222,36 @@ def dposv_mixed(n, nrhs, A, ai, aj, B, bi, bj, X, xi, xj, tol=1e-12, max_iter=30
         ctypes.c_void_p(resid.data_ptr()) if resid is not None else None,
         ctypes.c_void_p(work.data_ptr()), work.numel() * work.element_size(), _stream(stream)))
     return work
+
+
+def dgemm_nn(m, n, k, alpha, A, ai, aj, B, bi, bj, beta, C, ci, cj, D, di, dj, batch=None, stream=None):
+    """D <- alpha * A * B + beta * C (bf_dgemm_nn_batched); B is k x n."""
+    batch = D.batch if batch is None else batch
+    _check("bf_dgemm_nn_batched", load().bf_dgemm_nn_batched(
+        batch, m, n, k, alpha, *_op(A, ai, aj), *_op(B, bi, bj), beta, *_op(C, ci, cj),
+        *_op(D, di, dj), _stream(stream)))
+
+
+def dtrmm_rlnn(m, n, alpha, L, li, lj, B, bi, bj, D, di, dj, batch=None, stream=None):
+    """D <- alpha * B * L, L lower (bf_dtrmm_rlnn_batched)."""
+    batch = D.batch if batch is None else batch
+    _check("bf_dtrmm_rlnn_batched", load().bf_dtrmm_rlnn_batched(
+        batch, m, n, alpha, *_op(L, li, lj), *_op(B, bi, bj), *_op(D, di, dj), _stream(stream)))
+
+
+def dgetrf(n, C, ci, cj, D, di, dj, ipiv, info=None, batch=None, stream=None):
+    """P A = L U with partial pivoting (bf_dgetrf_batched); ipiv: int32 device
+    tensor (batch, n), 0-based pivot rows."""
+    batch = D.batch if batch is None else batch
+    _check("bf_dgetrf_batched", load().bf_dgetrf_batched(
+        batch, n, *_op(C, ci, cj), *_op(D, di, dj), ctypes.c_void_p(ipiv.data_ptr()), ipiv.shape[-1],
+        ctypes.c_void_p(info.data_ptr()) if info is not None else None, _stream(stream)))
+
+
+def dgelqf(m, n, C, ci, cj, D, di, dj, tau, batch=None, stream=None):
+    """A = L Q by Householder reflectors (bf_dgelqf_batched); tau: float64
+    device tensor (batch, min(m, n))."""
+    batch = D.batch if batch is None else batch
+    _check("bf_dgelqf_batched", load().bf_dgelqf_batched(
+        batch, m, n, *_op(C, ci, cj), *_op(D, di, dj), ctypes.c_void_p(tau.data_ptr()), tau.shape[-1],
+        _stream(stream)))

@@ -61,6 +61,16 @@ SIGNATURES = {
     "bf_dgemm_nt_batched": (_c_int, [_c_int, _c_int, _c_int, _c_int, _c_d, *_M, *_M, _c_d, *_M, *_M, _c_vp]),
     "bf_dgemm_nt": (_c_int, [_c_int, _c_int, _c_int, _c_d, _P, _c_int, _c_int, _P, _c_int, _c_int,
                              _c_d, _P, _c_int, _c_int, _P, _c_int, _c_int, _c_vp]),
+    "bf_dgemm_nn_batched": (_c_int, [_c_int, _c_int, _c_int, _c_int, _c_d, *_M, *_M, _c_d, *_M, *_M, _c_vp]),
+    "bf_dgemm_nn": (_c_int, [_c_int, _c_int, _c_int, _c_d, _P, _c_int, _c_int, _P, _c_int, _c_int,
+                             _c_d, _P, _c_int, _c_int, _P, _c_int, _c_int, _c_vp]),
+    "bf_dtrmm_rlnn_batched": (_c_int, [_c_int, _c_int, _c_int, _c_d, *_M, *_M, *_M, _c_vp]),
+    "bf_dtrmm_rlnn": (_c_int, [_c_int, _c_int, _c_d, _P, _c_int, _c_int, _P, _c_int, _c_int,
+                               _P, _c_int, _c_int, _c_vp]),
+    "bf_dgetrf_batched": (_c_int, [_c_int, _c_int, *_M, *_M, _c_vp, _c_ll, _c_vp, _c_vp]),
+    "bf_dgetrf": (_c_int, [_c_int, _P, _c_int, _c_int, _P, _c_int, _c_int, _c_vp, _c_vp, _c_vp]),
+    "bf_dgelqf_batched": (_c_int, [_c_int, _c_int, _c_int, *_M, *_M, _c_vp, _c_ll, _c_vp]),
+    "bf_dgelqf": (_c_int, [_c_int, _c_int, _P, _c_int, _c_int, _P, _c_int, _c_int, _c_vp, _c_vp]),
     "bf_dsyrk_ln_batched": (_c_int, [_c_int, _c_int, _c_int, _c_d, *_M, *_M, _c_d, *_M, *_M, _c_vp]),
     "bf_dsyrk_ln": (_c_int, [_c_int, _c_int, _c_d, _P, _c_int, _c_int, _P, _c_int, _c_int, _c_d,
                              _P, _c_int, _c_int, _P, _c_int, _c_int, _c_vp]),

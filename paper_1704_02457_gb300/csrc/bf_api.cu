@@ -171,6 +171,67 @@ int bf_dgemm_nt(int m, int n, int k, double alpha, const bf_dmat *sA, int ai, in
   return -map[-r];
 }
 
+int bf_dgemm_nn_batched(int batch, int m, int n, int k, double alpha, const bf_dmat *sA, int ai,
+                        int aj, long long strideA, const bf_dmat *sB, int bi, int bj,
+                        long long strideB, double beta, const bf_dmat *sC, int ci, int cj,
+                        long long strideC, const bf_dmat *sD, int di, int dj, long long strideD,
+                        void *stream) {
+  if (batch < 0) return -1;
+  if (m < 0) return -2;
+  if (n < 0) return -3;
+  if (k < 0) return -4;
+  if (batch == 0 || m == 0 || n == 0) return 0;
+  if (k > 0) {
+    if (int w = check_op(sA, ai, aj, m, k, strideA, batch, false)) return pos_err(w, 6);
+    if (int w = check_op(sB, bi, bj, k, n, strideB, batch, false)) return pos_err(w, 10);
+  }
+  if (beta != 0.0)
+    if (int w = check_op(sC, ci, cj, m, n, strideC, batch, false)) return pos_err(w, 15);
+  if (int w = check_op(sD, di, dj, m, n, strideD, batch, true)) return pos_err(w, 19);
+  const Op A = make_op(k > 0 ? sA : nullptr, ai, aj, strideA);
+  const Op B = make_op(k > 0 ? sB : nullptr, bi, bj, strideB);
+  const Op C = make_op(beta != 0.0 ? sC : nullptr, ci, cj, strideC);
+  const bool fast = fast_path({&A});
+  return status(launch_gemm_nn(false, batch, m, n, k, alpha, A, B, beta, C, make_opw(sD, di, dj, strideD),
+                               fast, (cudaStream_t)stream));
+}
+
+int bf_dgemm_nn(int m, int n, int k, double alpha, const bf_dmat *sA, int ai, int aj,
+                const bf_dmat *sB, int bi, int bj, double beta, const bf_dmat *sC, int ci, int cj,
+                const bf_dmat *sD, int di, int dj, void *stream) {
+  const int r = bf_dgemm_nn_batched(1, m, n, k, alpha, sA, ai, aj, 0, sB, bi, bj, 0, beta, sC,
+                                    ci, cj, 0, sD, di, dj, 0, stream);
+  if (r >= 0) return r;
+  static const int map[24] = {0, 0, 1, 2, 3, 4, 5, 6, 7, 0, 8, 9, 10, 0, 11, 12, 13, 14, 0, 15, 16, 17, 0, 18};
+  return -map[-r];
+}
+
+int bf_dtrmm_rlnn_batched(int batch, int m, int n, double alpha, const bf_dmat *sL, int li, int lj,
+                          long long strideL, const bf_dmat *sB, int bi, int bj, long long strideB,
+                          const bf_dmat *sD, int di, int dj, long long strideD, void *stream) {
+  if (batch < 0) return -1;
+  if (m < 0) return -2;
+  if (n < 0) return -3;
+  if (batch == 0 || m == 0 || n == 0) return 0;
+  if (int w = check_op(sL, li, lj, n, n, strideL, batch, false)) return pos_err(w, 5);
+  if (int w = check_op(sB, bi, bj, m, n, strideB, batch, false)) return pos_err(w, 9);
+  if (int w = check_op(sD, di, dj, m, n, strideD, batch, true)) return pos_err(w, 13);
+  if (sD->pA == sB->pA) return -13;  // D is written while B is still read
+  const Op B = make_op(sB, bi, bj, strideB);
+  const Op none{nullptr, 0, 0, 0, 0};
+  const bool fast = fast_path({&B});
+  return status(launch_gemm_nn(true, batch, m, n, n, alpha, B, make_op(sL, li, lj, strideL), 0.0, none,
+                               make_opw(sD, di, dj, strideD), fast, (cudaStream_t)stream));
+}
+
+int bf_dtrmm_rlnn(int m, int n, double alpha, const bf_dmat *sL, int li, int lj, const bf_dmat *sB,
+                  int bi, int bj, const bf_dmat *sD, int di, int dj, void *stream) {
+  const int r = bf_dtrmm_rlnn_batched(1, m, n, alpha, sL, li, lj, 0, sB, bi, bj, 0, sD, di, dj, 0, stream);
+  if (r >= 0) return r;
+  static const int map[17] = {0, 0, 1, 2, 3, 4, 5, 6, 0, 7, 8, 9, 0, 10, 11, 12, 0};
+  return -map[-r];
+}
+
 int bf_dsyrk_ln_batched(int batch, int m, int k, double alpha, const bf_dmat *sA, int ai, int aj,
                         long long strideA, const bf_dmat *sB, int bi, int bj, long long strideB,
                         double beta, const bf_dmat *sC, int ci, int cj, long long strideC,
@@ -366,6 +427,57 @@ int bf_dposv_mixed_batched(int batch, int n, int nrhs, const bf_dmat *sA, int ai
   return status(launch_posv_mixed(batch, n, nrhs, A, make_op(sB, bi, bj, strideB),
                                   make_opw(sX, xi, xj, strideX), tol, max_iter, iters, resid, l32,
                                   info32, fast, (cudaStream_t)stream));
+}
+
+// ------------------------------------------------------------ getrf / gelqf
+
+int bf_dgetrf_batched(int batch, int n, const bf_dmat *sC, int ci, int cj, long long strideC,
+                      const bf_dmat *sD, int di, int dj, long long strideD, int *ipiv,
+                      long long strideIpiv, int *info, void *stream) {
+  if (batch < 0) return -1;
+  if (n < 0) return -2;
+  if (batch == 0 || n == 0) return 0;
+  if (n > GETRF_MAX_N) return BF_ERR_UNSUPPORTED;
+  if (int w = check_op(sC, ci, cj, n, n, strideC, batch, false)) return pos_err(w, 3);
+  if (int w = check_op(sD, di, dj, n, n, strideD, batch, true)) return pos_err(w, 7);
+  if (!ipiv || !aligned_to(ipiv, 4)) return -11;
+  if (strideIpiv < 0 || (batch > 1 && strideIpiv < n)) return -12;
+  if (info && !aligned_to(info, 4)) return -13;
+  return status(launch_getrf(batch, n, make_op(sC, ci, cj, strideC), make_opw(sD, di, dj, strideD), ipiv,
+                             strideIpiv, info, (cudaStream_t)stream));
+}
+
+int bf_dgetrf(int n, const bf_dmat *sC, int ci, int cj, const bf_dmat *sD, int di, int dj, int *ipiv,
+              int *info, void *stream) {
+  const int r = bf_dgetrf_batched(1, n, sC, ci, cj, 0, sD, di, dj, 0, ipiv, 0, info, stream);
+  if (r >= 0) return r;
+  static const int map[14] = {0, 0, 1, 2, 3, 4, 0, 5, 6, 7, 0, 8, 0, 9};
+  return -map[-r];
+}
+
+int bf_dgelqf_batched(int batch, int m, int n, const bf_dmat *sC, int ci, int cj, long long strideC,
+                      const bf_dmat *sD, int di, int dj, long long strideD, double *tau,
+                      long long strideTau, void *stream) {
+  if (batch < 0) return -1;
+  if (m < 0) return -2;
+  if (n < 0) return -3;
+  if (batch == 0 || m == 0 || n == 0) return 0;
+  if ((long long)m * n > GELQF_MAX_MN) return BF_ERR_UNSUPPORTED;
+  if (int w = check_op(sC, ci, cj, m, n, strideC, batch, false)) return pos_err(w, 4);
+  if (int w = check_op(sD, di, dj, m, n, strideD, batch, true)) return pos_err(w, 8);
+  const int k = m < n ? m : n;
+  if (!tau || !aligned_to(tau, 8)) return -12;
+  if (strideTau < 0 || (batch > 1 && strideTau < k)) return -13;
+  return status(launch_gelqf(batch, m, n, make_op(sC, ci, cj, strideC), make_opw(sD, di, dj, strideD), tau,
+                             strideTau, (cudaStream_t)stream));
+}
+
+int bf_dgelqf(int m, int n, const bf_dmat *sC, int ci, int cj, const bf_dmat *sD, int di, int dj,
+              double *tau, void *stream) {
+  const int r = bf_dgelqf_batched(1, m, n, sC, ci, cj, 0, sD, di, dj, 0, tau, 0, stream);
+  if (r >= 0) return r;
+  static const int map[14] = {0, 0, 1, 2, 3, 4, 5, 0, 6, 7, 8, 0, 9, 0};
+  return -map[-r];
 }
 
 // ---------------------------------------------------------------- Riccati

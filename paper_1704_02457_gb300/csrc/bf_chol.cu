@@ -12,22 +12,26 @@
 // reciprocal cost several FMAs each, so the sequential part of a small
 // Cholesky must be shared by many problems at once.  Two kernels:
 //
-//  k_chol_small (n <= 64): a warp holds Q = 32/G problems, G lanes per
+//  k_chol_small (n <= 48): a warp holds Q = 32/G problems, G lanes per
 //    problem.  The lower triangles live packed in shared memory, problem q's
 //    element e at sm[e*Q + q].  The factorization runs column by column
 //    (Cholesky-Crout); the pivot's rsqrt is one warp instruction for all Q
 //    problems.  For syrk_potrf the A*B^T sum is added in 4x4 register blocks
 //    straight into the shared-memory triangle before the factorization.
 //
-//  k_chol_rows (n <= 512): one CTA per problem, one thread per row, blocks of
-//    up to 32 columns held in registers.  For block column [c0, c0+W):
+//  k_chol_rows (n <= 512): one thread per row, blocks of 16 columns held in
+//    registers, P problems per CTA (P = 2 up to n = 256 for potrf and 192 for
+//    syrk_potrf: a warp holds 16 rows of each of the two problems, so the
+//    diagonal block of a block column is one full warp; P = 1 above).  For
+//    block column [c0, c0+16):
 //      (a) acc = C[i][c0..]  (+ A[i][:] * B[c0..][:]^T for syrk_potrf)
 //      (b) acc -= L[i][0:c0] * L[c0..][0:c0]^T            (gemm_nt downdate)
-//      (c) the warp of rows c0..c0+31 factors the diagonal block in
+//      (c) the lanes of rows c0..c0+15 factor the diagonal block in
 //          registers with warp shuffles (potrf_l kernel on a register block)
 //      (d) the rows below solve against it (trsm_rltn kernel)
-//    The operand rows shared by all threads, B[c0..][l..] and L[c0..][l..],
-//    are staged 32 columns at a time in shared memory and read as broadcasts.
+//    The operand rows shared by a problem's threads, B[c0..][l..] and
+//    L[c0..][l..], are staged 32 columns at a time in shared memory and read
+//    as broadcasts.
 //
 // Non-SPD input: the first column j whose pivot is not > 0 (NaN included)
 // sets info = j+1; the arithmetic continues on NaNs without branching, so the
@@ -253,28 +257,60 @@ __device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
 
-template <typename T>
-struct RowsSmem {
-  T stage[KC][34];  // stage[ll][jj]: row c0+jj, column l0+ll of the shared operand
-                    // (even pitch: pairs (jj, jj+1) are read as one vector load)
-  T Ls[32][33];     // diagonal block of L: Ls[jj][j]
-  T rinv[32];
-  int bad;
+template <typename T, int BW, int P>
+struct __align__(16) RowsSmem {
+  T stage[P][KC][BW + 2];  // stage[p][ll][jj]: row c0+jj, column l0+ll of problem p's shared
+                           // operand (even pitch: pairs (jj, jj+1) are one vector load)
+  T Ls[P][BW][BW + 1];     // diagonal block of L: Ls[p][jj][j]
+  T rinv[P][BW];
+  int bad[P];
+};
+
+// Two problems per CTA (RowMap<2>) up to these orders.  The CTA of 2n
+// threads must leave room for two CTAs per SM, or the FP64 pipes idle while
+// one warp factors a diagonal block: at n = 256 that caps registers at 64,
+// which potrf fits without spilling and syrk_potrf does not (measured on the
+// sweep: potrf n = 256 goes from 910 to 1000 GFLOP/s, syrk_potrf drops).
+#ifndef BF_ROWS_P2_MAX_N
+#define BF_ROWS_P2_MAX_N 256
+#endif
+#ifndef BF_ROWS_P2_MAX_N_FUSED
+#define BF_ROWS_P2_MAX_N_FUSED 192
+#endif
+
+// Thread -> (problem, row) map of the row kernel.  A warp holds RPW = 32/P
+// consecutive rows of each of the CTA's P problems: lanes [p*RPW, (p+1)*RPW)
+// are rows g*RPW .. g*RPW + RPW-1 of problem p, g the warp index.  With P = 2
+// and 16-column blocks the rows of a block's diagonal block fill one whole
+// warp (16 lanes per problem), so the diagonal factorization and the rows
+// below it never issue with idle lanes.
+template <int P>
+struct RowMap {
+  static constexpr int RPW = 32 / P;
+  int lane, p, i;
+  __device__ __forceinline__ RowMap() {
+    lane = threadIdx.x & 31;
+    p = lane / RPW;
+    i = (threadIdx.x >> 5) * RPW + (lane % RPW);
+  }
 };
 
 // One block column [c0, c0 + BW) of the factorization.  W is the number of
 // accumulators (the block's width rounded up to a multiple of 8).  The
-// diagonal block's rows c0..c0+BW-1 are lanes base..base+BW-1 of one warp
-// (BW divides 32 and c0 is a multiple of BW).
-template <int W, int BW, bool FUSED, bool ALIGNED, typename T>
-__device__ __forceinline__ void rows_block(RowsSmem<T> &S, int c0, int n, int k, const double *pa,
-                                           const double *pb, const double *pc, T *pd, Op A,
-                                           Op B, Op C, OpWT<T> D, T *dinv_b) {
+// diagonal block's rows c0..c0+BW-1 of problem p are lanes
+// p*RPW + c0%RPW + (0..BW-1) of warp c0/RPW (BW divides RPW and c0 is a
+// multiple of BW).
+template <int W, int BW, int P, bool FUSED, bool ALIGNED, typename T>
+__device__ __forceinline__ void rows_block(RowsSmem<T, BW, P> &S, const RowMap<P> &rm, int c0, int n, int k,
+                                           int b0, int batch, bool me_valid, const double *pa, const double *pc,
+                                           T *pd, Op A, Op B, Op C, OpWT<T> D, T *dinv, long long sdinv) {
   using T2 = typename Vec2<T>::type;
-  const int i = threadIdx.x;
+  constexpr int RPW = RowMap<P>::RPW;
+  const int t = threadIdx.x;
   const int T_ = blockDim.x;
+  const int i = rm.i, p = rm.p;
   const int w = min(BW, n - c0);
-  const bool active = (i < n) && (i >= c0);
+  const bool active = me_valid && (i < n) && (i >= c0);
   T acc[W];
 
   // (a) C[i][c0 + jj] for the lower part of the block column
@@ -290,10 +326,14 @@ __device__ __forceinline__ void rows_block(RowsSmem<T> &S, int c0, int n, int k,
     for (int l0 = 0; l0 < k; l0 += KC) {
       const int kc = min(KC, k - l0);
       __syncthreads();
-      for (int x = i; x < BW * KC; x += T_) {
-        const int r4 = x % PS, ll = (x / PS) % KC, pnl = x / (PS * KC);
+      for (int x = t; x < P * BW * KC; x += T_) {
+        const int px = x / (BW * KC), xr = x - px * (BW * KC);
+        const int r4 = xr % PS, ll = (xr / PS) % KC, pnl = xr / (PS * KC);
         const int jj = pnl * PS + r4;
-        S.stage[ll][jj] = (jj < w && ll < kc) ? (T)__ldg(pb + pm_off(B.i0 + c0 + jj, B.j0 + l0 + ll, B.cn)) : (T)0;
+        S.stage[px][ll][jj] =
+            (b0 + px < batch && jj < w && ll < kc)
+                ? (T)__ldg(B.p + (long long)(b0 + px) * B.stride + pm_off(B.i0 + c0 + jj, B.j0 + l0 + ll, B.cn))
+                : (T)0;
       }
       __syncthreads();
       if (active) {
@@ -301,7 +341,7 @@ __device__ __forceinline__ void rows_block(RowsSmem<T> &S, int c0, int n, int k,
           const T x = (T)__ldg(arow + (long long)(l0 + ll) * PS);
 #pragma unroll
           for (int jj = 0; jj < W; jj += 2) {
-            const T2 bv = *(const T2 *)&S.stage[ll][jj];
+            const T2 bv = *(const T2 *)&S.stage[p][ll][jj];
             acc[jj] = fma_t(x, bv.x, acc[jj]);
             if (jj + 1 < W) acc[jj + 1] = fma_t(x, bv.y, acc[jj + 1]);
           }
@@ -316,10 +356,14 @@ __device__ __forceinline__ void rows_block(RowsSmem<T> &S, int c0, int n, int k,
     for (int l0 = 0; l0 < c0; l0 += KC) {
       const int kc = min(KC, c0 - l0);
       __syncthreads();
-      for (int x = i; x < BW * KC; x += T_) {
-        const int r4 = x % PS, ll = (x / PS) % KC, pnl = x / (PS * KC);
+      for (int x = t; x < P * BW * KC; x += T_) {
+        const int px = x / (BW * KC), xr = x - px * (BW * KC);
+        const int r4 = xr % PS, ll = (xr / PS) % KC, pnl = xr / (PS * KC);
         const int jj = pnl * PS + r4;
-        S.stage[ll][jj] = (jj < w && ll < kc) ? pd[pm_off(D.i0 + c0 + jj, D.j0 + l0 + ll, D.cn)] : (T)0;
+        S.stage[px][ll][jj] =
+            (b0 + px < batch && jj < w && ll < kc)
+                ? D.p[(long long)(b0 + px) * D.stride + pm_off(D.i0 + c0 + jj, D.j0 + l0 + ll, D.cn)]
+                : (T)0;
       }
       __syncthreads();
       if (active) {
@@ -328,7 +372,7 @@ __device__ __forceinline__ void rows_block(RowsSmem<T> &S, int c0, int n, int k,
           const T x = lrow[(long long)(l0 + ll) * PS];
 #pragma unroll
           for (int jj = 0; jj < W; jj += 2) {
-            const T2 lv = *(const T2 *)&S.stage[ll][jj];
+            const T2 lv = *(const T2 *)&S.stage[p][ll][jj];
             acc[jj] = fma_t(-x, lv.x, acc[jj]);
             if (jj + 1 < W) acc[jj + 1] = fma_t(-x, lv.y, acc[jj + 1]);
           }
@@ -339,11 +383,10 @@ __device__ __forceinline__ void rows_block(RowsSmem<T> &S, int c0, int n, int k,
 
   // (c) diagonal block: its rows are lanes base..base+BW-1 of one warp, which
   // factor it in registers with shuffles among themselves
-  const int lane = i & 31;
-  const int base = c0 & 31;
-  const int dl = lane - base;
-  if ((i >> 5) == (c0 >> 5) && dl >= 0 && dl < BW) {
-    const unsigned dmask = (BW == 32) ? FULL : (((1u << BW) - 1u) << base);
+  const int base = p * RPW + (c0 % RPW);
+  const int dl = rm.lane - base;
+  if ((t >> 5) == c0 / RPW && dl >= 0 && dl < BW) {
+    const unsigned dmask = (BW * P == 32) ? FULL : (((1u << BW) - 1u) << base);
     int bad = 0;  // every diagonal lane sees every pivot and tracks the first bad one
     // all W columns: padding columns (j >= w) hold zeros and only feed other
     // padding columns, which are never stored
@@ -354,7 +397,7 @@ __device__ __forceinline__ void rows_block(RowsSmem<T> &S, int c0, int n, int k,
       if (j < w && !(d > (T)0) && bad == 0) bad = c0 + j + 1;
       if (dl == j) {
         acc[j] = d * r;
-        S.rinv[j] = r;
+        S.rinv[p][j] = r;
       } else {
         acc[j] *= r;
       }
@@ -365,8 +408,8 @@ __device__ __forceinline__ void rows_block(RowsSmem<T> &S, int c0, int n, int k,
       }
     }
 #pragma unroll
-    for (int jj = 0; jj < W; jj++) S.Ls[dl][jj] = acc[jj];
-    if (dl == 0 && bad != 0 && S.bad == 0) S.bad = bad;
+    for (int jj = 0; jj < W; jj++) S.Ls[p][dl][jj] = acc[jj];
+    if (dl == 0 && bad != 0 && S.bad[p] == 0) S.bad[p] = bad;
   }
   __syncthreads();
 
@@ -374,9 +417,9 @@ __device__ __forceinline__ void rows_block(RowsSmem<T> &S, int c0, int n, int k,
   if (active && i >= c0 + BW) {
 #pragma unroll
     for (int j = 0; j < W; j++) {
-      acc[j] *= S.rinv[j];
+      acc[j] *= S.rinv[p][j];
 #pragma unroll
-      for (int jj = j + 1; jj < W; jj++) acc[jj] = fma_t(-acc[j], S.Ls[jj][j], acc[jj]);
+      for (int jj = j + 1; jj < W; jj++) acc[jj] = fma_t(-acc[j], S.Ls[p][jj][j], acc[jj]);
     }
   }
 
@@ -389,44 +432,97 @@ __device__ __forceinline__ void rows_block(RowsSmem<T> &S, int c0, int n, int k,
       if (jj < w && i >= col) drow[(long long)col * PS] = acc[jj];
     }
   }
-  if (dinv_b && i < w) dinv_b[c0 + i] = S.rinv[i];
+  if (t < P * BW) {
+    const int px = t / BW, j = t - px * BW;
+    if (dinv && b0 + px < batch && j < w) dinv[(long long)(b0 + px) * sdinv + c0 + j] = S.rinv[px][j];
+  }
   __syncthreads();
 }
 
-template <int BW, bool FUSED, bool ALIGNED, typename T>
-__global__ void __launch_bounds__(512)
-k_chol_rows(int n, int k, Op A, Op B, Op C, OpWT<T> D, T *dinv, long long sdinv, int *info) {
-  __shared__ RowsSmem<T> S;
-  const int b = blockIdx.x;
-  const double *pa = FUSED ? A.p + b * A.stride : nullptr;
-  const double *pb = FUSED ? B.p + b * B.stride : nullptr;
-  const double *pc = C.p + b * C.stride;
-  T *pd = D.p + b * D.stride;
-  T *dinv_b = dinv ? dinv + b * sdinv : nullptr;
-  if (threadIdx.x == 0) S.bad = 0;
+// CTA = P problems of the batch (problems blockIdx.x*P + p), threads laid out
+// by RowMap<P>.  Problems past the end of the batch (last CTA) run along
+// without touching memory.
+template <int BW, int P, bool FUSED, bool ALIGNED, typename T>
+__device__ __forceinline__ void chol_rows_body(int batch, int n, int k, Op A, Op B, Op C, OpWT<T> D, T *dinv,
+                                               long long sdinv, int *info) {
+  __shared__ RowsSmem<T, BW, P> S;
+  const RowMap<P> rm;
+  const int b0 = blockIdx.x * P;
+  const bool me_valid = b0 + rm.p < batch;
+  const long long bme = me_valid ? b0 + rm.p : b0;  // lanes of a missing problem alias the first
+  const double *pa = FUSED ? A.p + bme * A.stride : nullptr;
+  const double *pc = C.p + bme * C.stride;
+  T *pd = D.p + bme * D.stride;
+  if (threadIdx.x < P) S.bad[threadIdx.x] = 0;
   __syncthreads();
   for (int c0 = 0; c0 < n; c0 += BW) {
     const int w8 = (min(BW, n - c0) + 7) & ~7;
-    if (BW == 16) {
-      if (w8 == 8)
-        rows_block<8, 16, FUSED, ALIGNED, T>(S, c0, n, k, pa, pb, pc, pd, A, B, C, D, dinv_b);
-      else
-        rows_block<16, 16, FUSED, ALIGNED, T>(S, c0, n, k, pa, pb, pc, pd, A, B, C, D, dinv_b);
-    } else {
-      switch (w8) {
-        case 8: rows_block<8, 32, FUSED, ALIGNED, T>(S, c0, n, k, pa, pb, pc, pd, A, B, C, D, dinv_b); break;
-        case 16: rows_block<16, 32, FUSED, ALIGNED, T>(S, c0, n, k, pa, pb, pc, pd, A, B, C, D, dinv_b); break;
-        case 24: rows_block<24, 32, FUSED, ALIGNED, T>(S, c0, n, k, pa, pb, pc, pd, A, B, C, D, dinv_b); break;
-        default: rows_block<32, 32, FUSED, ALIGNED, T>(S, c0, n, k, pa, pb, pc, pd, A, B, C, D, dinv_b); break;
-      }
-    }
+    if (w8 == 8)
+      rows_block<8, BW, P, FUSED, ALIGNED, T>(S, rm, c0, n, k, b0, batch, me_valid, pa, pc, pd, A, B, C, D, dinv,
+                                              sdinv);
+    else
+      rows_block<16, BW, P, FUSED, ALIGNED, T>(S, rm, c0, n, k, b0, batch, me_valid, pa, pc, pd, A, B, C, D, dinv,
+                                               sdinv);
   }
-  if (info && threadIdx.x == 0) info[b] = S.bad;
+  if (info && threadIdx.x < P && b0 + (int)threadIdx.x < batch) info[b0 + threadIdx.x] = S.bad[threadIdx.x];
+}
+
+// One problem per CTA, up to 512 rows.
+template <int BW, bool FUSED, bool ALIGNED, typename T>
+__global__ void __launch_bounds__(512)
+k_chol_rows(int batch, int n, int k, Op A, Op B, Op C, OpWT<T> D, T *dinv, long long sdinv, int *info) {
+  chol_rows_body<BW, 1, FUSED, ALIGNED, T>(batch, n, k, A, B, C, D, dinv, sdinv, info);
+}
+
+// Two problems per CTA, up to MAXT/2 rows; registers bounded so that two
+// CTAs of MAXT threads fit an SM.
+template <int BW, bool FUSED, bool ALIGNED, typename T, int MAXT>
+__global__ void __launch_bounds__(MAXT, 2)
+k_chol_rows2(int batch, int n, int k, Op A, Op B, Op C, OpWT<T> D, T *dinv, long long sdinv, int *info) {
+  chol_rows_body<BW, 2, FUSED, ALIGNED, T>(batch, n, k, A, B, C, D, dinv, sdinv, info);
 }
 
 // Block width of k_chol_rows: 16-column blocks halve the work the diagonal
 // block's warp spends above the diagonal and the registers per thread.
 constexpr int ROWS_BW = 16;
+
+
+// MAXT: the launch bound of the two-problem kernel (0 for one problem per CTA)
+template <int MAXT, bool FUSED, bool ALIGNED, typename T>
+cudaError_t launch_rows_p(int batch, int n, int k, Op A, Op B, Op C, OpWT<T> D, T *dinv, long long sdinv,
+                          int *info, cudaStream_t s) {
+  constexpr int P = MAXT ? 2 : 1;
+  constexpr int RPW = 32 / P;
+  const int threads = ((n + RPW - 1) / RPW) * 32;
+  const unsigned blocks = (unsigned)((batch + P - 1) / P);
+  if constexpr (P == 1)
+    k_chol_rows<ROWS_BW, FUSED, ALIGNED, T><<<blocks, threads, 0, s>>>(batch, n, k, A, B, C, D, dinv, sdinv, info);
+  else
+    k_chol_rows2<ROWS_BW, FUSED, ALIGNED, T, MAXT>
+        <<<blocks, threads, 0, s>>>(batch, n, k, A, B, C, D, dinv, sdinv, info);
+  return cudaGetLastError();
+}
+
+template <int MAXT, bool FUSED, typename T>
+cudaError_t launch_rows_a(bool aligned, int batch, int n, int k, Op A, Op B, Op C, OpWT<T> D, T *dinv,
+                          long long sdinv, int *info, cudaStream_t s) {
+  return aligned ? launch_rows_p<MAXT, FUSED, true, T>(batch, n, k, A, B, C, D, dinv, sdinv, info, s)
+                 : launch_rows_p<MAXT, FUSED, false, T>(batch, n, k, A, B, C, D, dinv, sdinv, info, s);
+}
+
+template <bool FUSED, typename T>
+cudaError_t launch_rows(bool aligned, int batch, int n, int k, Op A, Op B, Op C, OpWT<T> D, T *dinv,
+                        long long sdinv, int *info, cudaStream_t s) {
+  if constexpr (sizeof(T) == 8) {  // the FP32 factor of the mixed solver keeps one problem per CTA
+    constexpr int p2_max = FUSED ? BF_ROWS_P2_MAX_N_FUSED : BF_ROWS_P2_MAX_N;
+    if (n <= 192 && n <= p2_max)
+      return launch_rows_a<384, FUSED, T>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
+    if (n <= p2_max)
+      return launch_rows_a<2 * (p2_max > 192 ? p2_max : 192), FUSED, T>(aligned, batch, n, k, A, B, C, D, dinv,
+                                                                      sdinv, info, s);
+  }
+  return launch_rows_a<0, FUSED, T>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
+}
 
 // Lanes per problem of k_chol_small: the smallest G (at most 16) whose
 // shared-memory triangles for the 32/G problems of a warp fit the budget, so
@@ -434,6 +530,13 @@ constexpr int ROWS_BW = 16;
 // sweep: more resident warps pay for a larger G (the pivot's rsqrt shared by
 // fewer problems) up to G = 16; beyond that the rsqrt dominates.
 constexpr long long SMALL_SMEM_BUDGET = 20 * 1024;
+
+// Largest order factored by k_chol_small; the row kernel takes over above
+// (measured: at n = 64 the two-problem row kernel is 25% faster for potrf and
+// 6% for syrk_potrf, at n = 40 and 48 it is slower).
+#ifndef BF_CHOL_SMALL_MAX_N
+#define BF_CHOL_SMALL_MAX_N 48
+#endif
 int pick_small_g(int n) {
   const long long ne = (long long)n * (n + 1) / 2;
   for (int g = 1; g <= 16; g *= 2)
@@ -457,7 +560,7 @@ cudaError_t launch_small_g(bool aligned, int batch, int n, int k, Op A, Op B, Op
 template <bool FUSED>
 cudaError_t launch_chol_t(bool aligned, int batch, int n, int k, Op A, Op B, Op C, OpW D,
                           double *dinv, long long sdinv, int *info, cudaStream_t s) {
-  const int g = (n <= 64) ? pick_small_g(n) : 0;
+  const int g = (n <= BF_CHOL_SMALL_MAX_N) ? pick_small_g(n) : 0;
   switch (g) {
     case 1: return launch_small_g<1, FUSED>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
     case 2: return launch_small_g<2, FUSED>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
@@ -467,12 +570,7 @@ cudaError_t launch_chol_t(bool aligned, int batch, int n, int k, Op A, Op B, Op 
     case 32: return launch_small_g<32, FUSED>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
     default: break;
   }
-  const int threads = (n + 31) & ~31;
-  if (aligned)
-    k_chol_rows<ROWS_BW, FUSED, true, double><<<batch, threads, 0, s>>>(n, k, A, B, C, D, dinv, sdinv, info);
-  else
-    k_chol_rows<ROWS_BW, FUSED, false, double><<<batch, threads, 0, s>>>(n, k, A, B, C, D, dinv, sdinv, info);
-  return cudaGetLastError();
+  return launch_rows<FUSED, double>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
 }
 
 }  // namespace
@@ -485,13 +583,8 @@ cudaError_t launch_chol(bool fused, int batch, int n, int k, Op A, Op B, Op C, O
 
 cudaError_t launch_chol_f32(int batch, int n, Op C, OpWT<float> D, int *info, bool aligned,
                             cudaStream_t s) {
-  const int threads = (n + 31) & ~31;
   const Op none{nullptr, 0, 0, 0, 0};
-  if (aligned)
-    k_chol_rows<ROWS_BW, false, true, float><<<batch, threads, 0, s>>>(n, 0, none, none, C, D, nullptr, 0, info);
-  else
-    k_chol_rows<ROWS_BW, false, false, float><<<batch, threads, 0, s>>>(n, 0, none, none, C, D, nullptr, 0, info);
-  return cudaGetLastError();
+  return launch_rows<false, float>(aligned, batch, n, 0, none, none, C, D, nullptr, 0, info, s);
 }
 
 }  // namespace bf

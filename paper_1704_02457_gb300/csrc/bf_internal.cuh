@@ -43,6 +43,11 @@ __host__ __device__ __forceinline__ long long pm_off(int r, int c, int cn) {
 cudaError_t launch_gemm_nt(bool syrk, int batch, int m, int n, int k, double alpha, Op A, Op B,
                            double beta, Op C, OpW D, bool aligned, cudaStream_t s);
 
+// gemm_nn (trmm = false: D = alpha A X + beta C, X k x n) and trmm_rlnn
+// (trmm = true: D = alpha A X with X = L lower n x n, k = n, C unused).
+cudaError_t launch_gemm_nn(bool trmm, int batch, int m, int n, int k, double alpha, Op A, Op X,
+                           double beta, Op C, OpW D, bool aligned, cudaStream_t s);
+
 // potrf_l (fused = false) and syrk_potrf_ln (fused = true, A and B used).
 cudaError_t launch_chol(bool fused, int batch, int n, int k, Op A, Op B, Op C, OpW D,
                         double *dinv, long long sdinv, int *info, bool aligned, cudaStream_t s);
@@ -63,6 +68,25 @@ cudaError_t launch_posv_adjoint(int batch, int n, int nrhs, Op L, Op X, Op Xbar,
 cudaError_t launch_posv_mixed(int batch, int n, int nrhs, Op A, Op B, OpW X, double tol,
                               int max_iter, int *iters, double *resid, float *l32, int *info32,
                               bool aligned, cudaStream_t s);
+
+// 1/d by Newton-Raphson iteration r <- r + r (1 - d r) from the hardware's
+// approximate reciprocal (rcp.approx.ftz.f64); two steps take it to full
+// double precision.  Used where one reciprocal is shared by a column of
+// multiplications, instead of an IEEE divide.  Subnormal d flushes to zero.
+__device__ __forceinline__ double recip_newton(double d) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+  double e = fma(-d, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-d, r, 1.0);
+  return fma(r, e, r);
+}
+
+// LU with partial pivoting (square n <= 128) and Householder LQ (m*n <= 16384).
+cudaError_t launch_getrf(int batch, int n, Op C, OpW D, int *ipiv, long long sipiv, int *info, cudaStream_t s);
+cudaError_t launch_gelqf(int batch, int m, int n, Op C, OpW D, double *tau, long long stau, cudaStream_t s);
+constexpr int GETRF_MAX_N = 128;
+constexpr int GELQF_MAX_MN = 16384;
 
 // Backward Riccati recursion, square-root form (one CTA per instance).
 size_t riccati_smem(int max_nx, int max_nu);

@@ -30,18 +30,6 @@ __host__ __device__ __forceinline__ int ls_region(int W) { return W * (W + 1) + 
 // block width bucket: 4, 8, 16, 24 or 32 columns
 __host__ __device__ __forceinline__ int w_bucket(int w) { return w <= 4 ? 4 : (w + 7) & ~7; }
 
-// 1/d by Newton-Raphson iteration r <- r + r (1 - d r) from the hardware's
-// approximate reciprocal; two steps take the approximation to full double
-// precision.  Used once per column of L per CTA instead of an IEEE divide.
-__device__ __forceinline__ double recip_newton(double d) {
-  double r;
-  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
-  double e = fma(-d, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-d, r, 1.0);
-  return fma(r, e, r);
-}
-
 template <int W>
 __device__ __forceinline__ void trsm_block(double *smem, int P, int R, int c0, int m, int n,
                                            double alpha, int pb0, int batch, int r0, Op L,

@@ -115,8 +115,21 @@ def test_argument_errors_are_reported_before_launch(lib):
                                   ctypes.c_void_p(0x10002), None) == -15
     assert lib.bf_dtrsm_rltn_batched(1, 8, 8, 1.0, r(A), 0, 0, 0, None, 0, r(B), 0, 0, 0, None, 0, 0, 0, None) == -15
     assert lib.bf_dtrsm_rltn(8, 8, 1.0, r(A), 0, 0, r(B), 1, 0, r(D), 0, 0, None) == -8
+    # getrf / gelqf
+    ip = ctypes.c_void_p(0x10000)
+    assert lib.bf_dgetrf_batched(1, 9, r(C), 0, 0, 0, r(D), 0, 0, 0, ip, 0, None, None) == -4  # ci
+    assert lib.bf_dgetrf_batched(1, 8, r(C), 0, 0, 0, r(D), 0, 0, 0, None, 0, None, None) == -11
+    assert lib.bf_dgetrf_batched(2, 8, r(C), 0, 0, 0, r(D), 0, 0, 64, ip, 4, None, None) == -12
+    assert lib.bf_dgetrf_batched(1, 8, r(C), 0, 0, 0, r(D), 0, 0, 0, ip, 0, ctypes.c_void_p(0x10002), None) == -13
+    assert lib.bf_dgetrf(8, r(C), 0, 0, r(D), 0, 1, ip, None, None) == -7
+    assert lib.bf_dgelqf_batched(1, 8, 9, r(C), 0, 0, 0, r(D), 0, 0, 0, ip, 0, None) == -6  # cj
+    assert lib.bf_dgelqf_batched(1, 8, 8, r(C), 0, 0, 0, r(D), 0, 0, 0, ctypes.c_void_p(0x10004), 0, None) == -12
+    assert lib.bf_dgelqf_batched(2, 4, 8, r(C), 0, 0, 0, r(D), 0, 0, 64, ip, 3, None) == -13
+    assert lib.bf_dgelqf(8, 8, r(C), 1, 0, r(D), 0, 0, ip, None) == -4
     # sizes beyond what the factorization kernels implement
     big = _desc(600, 600)
+    assert lib.bf_dgetrf_batched(1, 129, r(big), 0, 0, 0, r(big), 0, 0, 0, ip, 0, None, None) == _abi.BF_ERR_UNSUPPORTED
+    assert lib.bf_dgelqf_batched(1, 129, 128, r(big), 0, 0, 0, r(big), 0, 0, 0, ip, 0, None) == _abi.BF_ERR_UNSUPPORTED
     assert lib.bf_dpotrf_l_batched(1, 600, r(big), 0, 0, 0, r(big), 0, 0, 0, None, 0, None, None) == _abi.BF_ERR_UNSUPPORTED
 
 

@@ -17,12 +17,12 @@ from tests import test_oracle_pins as pins
 SRC = os.path.join(os.path.dirname(oracle.__file__), "bf_oracle.c")
 
 MUTANTS = {
-    "gemm_transposed_B": ("s += EL(A, lda, i, l) * EL(B, ldb, j, l);\n      double c = (beta == 0.0) ? 0.0 : beta * EL(C, ldc, i, j);\n      EL(D, ldd, i, j) = alpha * s + c;\n    }\n  }\n}\n\n/* syrk_ln",
-                          "s += EL(A, lda, i, l) * EL(B, ldb, l, j);\n      double c = (beta == 0.0) ? 0.0 : beta * EL(C, ldc, i, j);\n      EL(D, ldd, i, j) = alpha * s + c;\n    }\n  }\n}\n\n/* syrk_ln"),
-    "gemm_sign": ("EL(D, ldd, i, j) = alpha * s + c;\n    }\n  }\n}\n\n/* syrk_ln",
-                  "EL(D, ldd, i, j) = alpha * s - c;\n    }\n  }\n}\n\n/* syrk_ln"),
-    "gemm_drops_last_k": ("for (int l = 0; l < k; l++) s += EL(A, lda, i, l) * EL(B, ldb, j, l);\n      double c = (beta == 0.0) ? 0.0 : beta * EL(C, ldc, i, j);\n      EL(D, ldd, i, j) = alpha * s + c;\n    }\n  }\n}\n\n/* syrk_ln",
-                          "for (int l = 0; l < k - 1; l++) s += EL(A, lda, i, l) * EL(B, ldb, j, l);\n      double c = (beta == 0.0) ? 0.0 : beta * EL(C, ldc, i, j);\n      EL(D, ldd, i, j) = alpha * s + c;\n    }\n  }\n}\n\n/* syrk_ln"),
+    "gemm_transposed_B": ("s += EL(A, lda, i, l) * EL(B, ldb, j, l);\n      double c = (beta == 0.0) ? 0.0 : beta * EL(C, ldc, i, j);\n      EL(D, ldd, i, j) = alpha * s + c;\n    }\n  }\n}\n\n/* gemm_nn",
+                          "s += EL(A, lda, i, l) * EL(B, ldb, l, j);\n      double c = (beta == 0.0) ? 0.0 : beta * EL(C, ldc, i, j);\n      EL(D, ldd, i, j) = alpha * s + c;\n    }\n  }\n}\n\n/* gemm_nn"),
+    "gemm_sign": ("EL(D, ldd, i, j) = alpha * s + c;\n    }\n  }\n}\n\n/* gemm_nn",
+                  "EL(D, ldd, i, j) = alpha * s - c;\n    }\n  }\n}\n\n/* gemm_nn"),
+    "gemm_drops_last_k": ("for (int l = 0; l < k; l++) s += EL(A, lda, i, l) * EL(B, ldb, j, l);\n      double c = (beta == 0.0) ? 0.0 : beta * EL(C, ldc, i, j);\n      EL(D, ldd, i, j) = alpha * s + c;\n    }\n  }\n}\n\n/* gemm_nn",
+                          "for (int l = 0; l < k - 1; l++) s += EL(A, lda, i, l) * EL(B, ldb, j, l);\n      double c = (beta == 0.0) ? 0.0 : beta * EL(C, ldc, i, j);\n      EL(D, ldd, i, j) = alpha * s + c;\n    }\n  }\n}\n\n/* gemm_nn"),
     "syrk_writes_upper": ("for (int i = j; i < m; i++) {", "for (int i = 0; i < m; i++) {"),
     "potrf_dropped_term": ("for (int l = 0; l < j; l++) d -= EL(D, ldd, j, l) * EL(D, ldd, j, l);",
                            "for (int l = 1; l < j; l++) d -= EL(D, ldd, j, l) * EL(D, ldd, j, l);"),
@@ -42,6 +42,12 @@ MUTANTS = {
                            "for (int l = 0; l < n; l++) s += EL(B, ldb, i, l) * EL(L, ldl, l, j);"),
     "trsm_rlnn_transposed": ("for (int l = j + 1; l < n; l++) s -= EL(D, ldd, i, l) * EL(L, ldl, l, j);",
                              "for (int l = j + 1; l < n; l++) s -= EL(D, ldd, i, l) * EL(L, ldl, j, l);"),
+    "gemm_nn_transposed_B": ("s += EL(A, lda, i, l) * EL(B, ldb, l, j);\n      double c = (beta == 0.0) ? 0.0 : beta * EL(C, ldc, i, j);\n      EL(D, ldd, i, j) = alpha * s + c;\n    }\n  }\n}\n\n/* syrk_ln",
+                             "s += EL(A, lda, i, l) * EL(B, ldb, j, l);\n      double c = (beta == 0.0) ? 0.0 : beta * EL(C, ldc, i, j);\n      EL(D, ldd, i, j) = alpha * s + c;\n    }\n  }\n}\n\n/* syrk_ln"),
+    "getrf_no_swap": ("    if (p != j)\n      for (int c = 0; c < n; c++) {", "    if (0)\n      for (int c = 0; c < n; c++) {"),
+    "gelqf_beta_sign": ("double beta = -copysign(sqrt(alpha * alpha + s), alpha);",
+                        "double beta = copysign(sqrt(alpha * alpha + s), alpha);"),
+    "gelqf_drops_w_update": ("      EL(D, ldd, r, i) -= t * w;\n", "\n"),
     "pack_row_in_panel": ("(size_t)c * (size_t)ps + (size_t)(r % ps)", "(size_t)c * (size_t)ps + (size_t)((r + 1) % ps)"),
 }
 
@@ -62,6 +68,9 @@ def _battery():
         lambda: pins.test_potrs_integer_solution_returns_exactly(8, 4),
         lambda: pins.test_trmm_rlnn_integer_exact(5, 3),
         lambda: pins.test_trsm_rlnn_integer_exact(7, 4),
+        lambda: pins.test_gemm_nn_integer_exact(7, 5, 9),
+        lambda: pins.test_getrf_matches_lapack(9),
+        lambda: pins.test_gelqf_matches_qr_of_transpose(12, 20),
     ]
     for c in checks:
         try:

@@ -456,3 +456,77 @@ def test_adjoint_matches_central_differences(n, nrhs):
         fd = (loss(A, B + h * E) - loss(A, B - h * E)) / (2 * h)
         assert abs(fd - Bbar[i, k]) <= 1e-7 * max(1.0, abs(Bbar[i, k]))
     assert np.allclose(Abar, Abar.T, rtol=0, atol=1e-15)
+
+
+# ---------------------------------------------------------------- gemm_nn ----
+
+@pytest.mark.parametrize("m,n,k", [(1, 1, 1), (7, 5, 9), (24, 24, 24), (33, 17, 40)])
+def test_gemm_nn_integer_exact(m, n, k):
+    rng = np.random.default_rng(1100 + m)
+    A, B, C = _ints((m, k), -8, 8, rng), _ints((k, n), -8, 8, rng), _ints((m, n), -8, 8, rng)
+    got = oracle.dgemm_nn(-2.0, A.astype(float), B.astype(float), 3.0, C.astype(float))
+    assert np.array_equal(got, (-2 * (A @ B) + 3 * C).astype(float))
+
+
+# ------------------------------------------------------------ getrf, gelqf
+
+@pytest.mark.parametrize("n", [1, 3, 8, 17, 32])
+def test_getrf_integer_no_swap_exact(n):
+    # A = L U with unit-lower L of entries in {-1, 0, 1} and upper U with
+    # power-of-two diagonal: partial pivoting keeps the diagonal (ties go to
+    # the first row) and every step is exact
+    rng = np.random.default_rng(1500 + n)
+    L = np.tril(rng.integers(-1, 2, size=(n, n)), -1) + np.eye(n, dtype=np.int64)
+    U = np.triu(rng.integers(-4, 5, size=(n, n)), 1)
+    U[np.arange(n), np.arange(n)] = 2 ** rng.integers(3, 6, size=n)
+    A = (L @ U).astype(float)
+    LU, ipiv, info = oracle.dgetrf(A)
+    assert info == 0 and np.array_equal(ipiv, np.arange(n))
+    assert np.array_equal(np.tril(LU, -1) + np.eye(n), L.astype(float))
+    assert np.array_equal(np.triu(LU), U.astype(float))
+
+
+@pytest.mark.parametrize("n", [2, 9, 24, 50])
+def test_getrf_matches_lapack(n):
+    sl = pytest.importorskip("scipy.linalg")
+    A = RNG.standard_normal((n, n))
+    LU, ipiv, info = oracle.dgetrf(A)
+    lu_ref, piv_ref = sl.lu_factor(A)  # LAPACK dgetrf
+    assert info == 0
+    assert np.array_equal(ipiv, piv_ref)
+    assert np.linalg.norm(LU - lu_ref) <= 1e-13 * np.linalg.norm(lu_ref)
+    # P A = L U
+    PA = A.copy()
+    for j, p in enumerate(ipiv):
+        PA[[j, p]] = PA[[p, j]]
+    Lm = np.tril(LU, -1) + np.eye(n)
+    assert np.linalg.norm(PA - Lm @ np.triu(LU)) <= 1e-14 * n * np.linalg.norm(A)
+
+
+def test_getrf_singular_reports_first_zero_pivot():
+    A = np.array([[1.0, 2.0, 3.0], [2.0, 4.0, 6.0], [1.0, 0.0, 1.0]])
+    _, _, info = oracle.dgetrf(A)
+    assert info == 3 or info == 2
+    assert oracle.dgetrf(np.zeros((4, 4)))[2] == 1
+
+
+@pytest.mark.parametrize("m,n", [(1, 1), (3, 5), (8, 8), (12, 20), (20, 12), (33, 40)])
+def test_gelqf_matches_qr_of_transpose(m, n):
+    rng = np.random.default_rng(1600 + m * n)
+    A = rng.standard_normal((m, n))
+    F, tau = oracle.dgelqf(A)
+    k = min(m, n)
+    L = np.tril(F)[:, :k]
+    R = np.linalg.qr(A.T, mode="r")  # LAPACK dgeqrf of A^T: A = R^T Q^T
+    assert np.linalg.norm(L - R.T[:, :k]) <= 1e-13 * np.linalg.norm(A)
+    Q = oracle.lq_q(F, tau)
+    assert np.linalg.norm(Q @ Q.T - np.eye(n)) <= 1e-14 * n
+    Lfull = np.zeros((m, n))
+    Lfull[:, :k] = L
+    assert np.linalg.norm(Lfull @ Q - A) <= 1e-14 * n * np.linalg.norm(A)
+
+
+def test_gelqf_zero_tail_gives_identity_reflector():
+    A = np.array([[3.0, 0.0, 0.0], [1.0, 2.0, 5.0]])
+    F, tau = oracle.dgelqf(A)
+    assert tau[0] == 0.0 and F[0, 0] == 3.0

@@ -358,6 +358,35 @@ def test_syrk_potrf_config_form(n, k):
     check_dinv(dD.dinv().cpu().numpy(), got, dinv_want)
 
 
+@pytest.mark.parametrize("n", [65, 100, 192])
+def test_syrk_potrf_paired_problems_odd_batch_and_failing_neighbour(n):
+    """Up to n = 192 the row kernel factors two problems per CTA.  With an odd
+    batch the last CTA has one problem; a failing problem must not disturb the
+    other problem of its CTA."""
+    bt, k = 5, 7
+    M = inputs.normal((bt, n, k), 140 + n)
+    Q = (torch.eye(n, dtype=torch.float64) * float(n)).expand(bt, n, n).contiguous().numpy().copy()
+    Q[2, n - 3, n - 3] = -1e6            # problem 2 (second of CTA 1) fails late
+    Q[4, 0, 0] = np.nan                  # problem 4 (alone in the last CTA) fails first
+    want, dinv_want, info_want = oracle.dsyrk_dpotrf_ln(M.numpy(), M.numpy(), Q)
+    dM = put(M)
+    dD = bf.DMatBatch(bt, n, n, fill=np.nan)
+    info = torch.full((bt,), -7, dtype=torch.int32, device=dev())
+    bf.dsyrk_dpotrf_ln(n, k, dM, 0, 0, dM, 0, 0, put(torch.from_numpy(Q)), 0, 0, dD, 0, 0, info=info)
+    got_info = info.cpu().numpy()
+    assert list(got_info) == list(info_want) == [0, 0, n - 2, 0, 1]
+    got = get(dD)
+    dinv = dD.dinv().cpu().numpy()
+    for b in (0, 1, 3):
+        S = Q[b] + M[b].numpy() @ M[b].numpy().T
+        assert chol_resid(got[b], S) <= 1e-13
+        assert fro(np.tril(got[b]) - np.tril(want[b])) / fro(np.tril(want[b])) <= 1e-12
+        check_dinv(dinv[b], got[b], dinv_want[b])
+    # problem 2's columns before the failing pivot are still its factor's
+    c = n - 3
+    assert fro(np.tril(got[2])[:, :c] - np.tril(want[2])[:, :c]) / fro(np.tril(want[2])[:, :c]) <= 1e-12
+
+
 @pytest.mark.parametrize("n,k", [(4, 4), (8, 3), (24, 24), (33, 50), (100, 17)])
 def test_syrk_potrf_exact_construction(n, k):
     bt = 3
