@@ -93,10 +93,23 @@ def roofline_gflops(routine, n, hbm_gbs):
 # kernel's source file when the counters were taken: the bench reports the
 # traffic only while that file is unchanged.
 TRAFFIC = {
+    ("k_gemm_nt<0,1>", "dgemm_nt", 256): {
+        "bytes": 1076209152 + 335009536,
+        "src": "paper_1704_02457_gb300/csrc/bf_gemm.cu",
+        "blob": "c0d0da9ac044265b21ee9186324dc9a9dd8ea1af",
+        "profile": "profiles/k_gemm_nt_n256.md",
+    },
     ("k_chol_rows<16,1,1,double>", "dsyrk_dpotrf_ln", 256): {
-        "bytes": 5571173632 + 256111360,
+        "bytes": 5531728896 + 255543552,
         "src": "paper_1704_02457_gb300/csrc/bf_chol.cu",
-        "blob": "c8b618ef253dd4587ed0cc171cef42e32aa4f269",
+        "blob": "f52e70d447b1e7338e38615ac643413b70da9f90",
+        "profile": "profiles/k_chol_rows_syrk_potrf_n256.md",
+    },
+    ("k_chol_rows2<16,1,1,double,384>", "dsyrk_dpotrf_ln", 128): {
+        "bytes": 1521071872 + 252816896,
+        "src": "paper_1704_02457_gb300/csrc/bf_chol.cu",
+        "blob": "f52e70d447b1e7338e38615ac643413b70da9f90",
+        "profile": "profiles/k_chol_rows2_syrk_potrf_n128.md",
     },
 }
 
@@ -482,8 +495,8 @@ def run_gpu(args):
         "kernel_time_share": round(sum(t for t, _ in by_kernel[dom]) / step_ms, 4),
         "peak_source": "FP64 ALU peak from unit counts and clock (152 SMs x 2 FMA/clk x 2 flop x "
                        "2.07 GHz); HBM roof of the per-point fractions uses %s %.0f GB/s" % (hbm_src, hbm),
-        "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of this launch "
-                          "(profiles/k_chol_rows_syrk_potrf_n256.md)" if traffic else None,
+        "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of this launch (%s)" % tr["profile"])
+                          if traffic else None,
     }
 
     result = {
