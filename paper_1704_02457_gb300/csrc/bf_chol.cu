@@ -278,6 +278,11 @@ struct __align__(16) RowsSmem {
 #define BF_ROWS_P2_MAX_N_FUSED 192
 #endif
 
+#ifndef BF_ROWS_KUNROLL
+#define BF_ROWS_KUNROLL 4
+#endif
+constexpr int ROWS_KUNROLL = BF_ROWS_KUNROLL;  // unroll of the syrk k-loop
+
 // Thread -> (problem, row) map of the row kernel.  A warp holds RPW = 32/P
 // consecutive rows of each of the CTA's P problems: lanes [p*RPW, (p+1)*RPW)
 // are rows g*RPW .. g*RPW + RPW-1 of problem p, g the warp index.  With P = 2
@@ -337,6 +342,7 @@ __device__ __forceinline__ void rows_block(RowsSmem<T, BW, P> &S, const RowMap<P
       }
       __syncthreads();
       if (active) {
+#pragma unroll ROWS_KUNROLL
         for (int ll = 0; ll < kc; ll++) {
           const T x = (T)__ldg(arow + (long long)(l0 + ll) * PS);
 #pragma unroll
