@@ -7,6 +7,8 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "bfgpu.h"
 
 namespace bf {
@@ -68,6 +70,20 @@ cudaError_t launch_posv_adjoint(int batch, int n, int nrhs, Op L, Op X, Op Xbar,
 cudaError_t launch_posv_mixed(int batch, int n, int nrhs, Op A, Op B, OpW X, double tol,
                               int max_iter, int *iters, double *resid, float *l32, int *info32,
                               bool aligned, cudaStream_t s);
+
+// Raise a kernel's dynamic shared-memory limit to `bytes`, once per device
+// (the attribute is per device; `done` is the call site's bit mask of the
+// devices already set, devices >= 64 are set on every call).
+inline cudaError_t smem_attr_once(const void *fn, int bytes, std::atomic<unsigned long long> &done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_release);
+  return e;
+}
 
 // 1/d by Newton-Raphson iteration r <- r + r (1 - d r) from the hardware's
 // approximate reciprocal (rcp.approx.ftz.f64); two steps take it to full

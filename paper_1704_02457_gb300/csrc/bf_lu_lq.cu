@@ -34,6 +34,15 @@ __device__ __forceinline__ void cp_async8(double *dst, const double *src) {
 
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// Pivot key of x: the bits of |x| as a signed integer (for non-negative
+// doubles the IEEE order is the integer order), -1 for NaN, so that the
+// pivot search compares on the integer pipes instead of issuing FP64
+// compares, and NaN never wins.
+__device__ __forceinline__ long long pivot_key(double x) {
+  const long long a = __double_as_longlong(x) & 0x7fffffffffffffffLL;
+  return a > 0x7ff0000000000000LL ? -1LL : a;
+}
+
 // whole m x n matrices of the warp's problems in and out of shared memory
 template <int Q>
 __device__ __forceinline__ void load_all(double *sm, int b0, int batch, int m, int n, const Op &C) {
@@ -79,11 +88,11 @@ k_getrf(int batch, int n, Op C, OpW D, int *ipiv, long long sipiv, int *info) {
   int first_zero = 0;
   for (int j = 0; j < n; j++) {
     // pivot: largest |a(i, j)|, i >= j, first such row
-    const bool diag_nan = isnan(A_(j, j));  // read before any lane can swap
-    double best = -1.0;
+    const bool diag_nan = pivot_key(A_(j, j)) < 0;  // read before any lane can swap
+    long long best = -1;
     int bi = j;  // stays the diagonal if nothing compares larger (e.g. NaN)
     for (int i = j + s; i < n; i += G) {
-      const double v = fabs(A_(i, j));
+      const long long v = pivot_key(A_(i, j));
       if (v > best) {
         best = v;
         bi = i;
@@ -91,7 +100,7 @@ k_getrf(int batch, int n, Op C, OpW D, int *ipiv, long long sipiv, int *info) {
     }
 #pragma unroll
     for (int o = 1; o < G; o <<= 1) {
-      const double ov = __shfl_xor_sync(FULL, best, o);
+      const long long ov = __shfl_xor_sync(FULL, best, o);
       const int oi = __shfl_xor_sync(FULL, bi, o);
       if (ov > best || (ov == best && oi < bi)) {
         best = ov;
@@ -173,48 +182,6 @@ k_gelqf(int batch, int m, int n, Op C, OpW D, double *tau, long long stau) {
 // row (swaps, the reflector's row) touches distinct banks.
 // ---------------------------------------------------------------------------
 
-// (value, row) arg-max over the CTA; ties go to the smaller row.  red holds
-// one slot per warp; every thread returns the same row.
-__device__ __forceinline__ int cta_argmax(double v, int idx, double *red_v, int *red_i) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const double ov = __shfl_xor_sync(FULL, v, o);
-    const int oi = __shfl_xor_sync(FULL, idx, o);
-    if (ov > v || (ov == v && oi < idx)) {
-      v = ov;
-      idx = oi;
-    }
-  }
-  if (lane == 0) {
-    red_v[wid] = v;
-    red_i[wid] = idx;
-  }
-  __syncthreads();
-  double bv = red_v[0];
-  int bi = red_i[0];
-  for (int w = 1; w < nw; w++) {
-    const double ov = red_v[w];
-    const int oi = red_i[w];
-    if (ov > bv || (ov == bv && oi < bi)) {
-      bv = ov;
-      bi = oi;
-    }
-  }
-  return bi;
-}
-
-__device__ __forceinline__ double cta_sum(double v, double *red_v) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-  if (lane == 0) red_v[wid] = v;
-  __syncthreads();
-  double s = 0.0;
-  for (int w = 0; w < nw; w++) s += red_v[w];
-  return s;
-}
-
 // panel-major <-> shared memory (column-major, leading dimension ld), walked
 // in panel-major order so that consecutive threads touch consecutive words
 __device__ __forceinline__ void rows_load(double *sm, int ld, int m, int n, const double *pc, const Op &C) {
@@ -236,36 +203,105 @@ __device__ __forceinline__ void rows_store(const double *sm, int ld, int m, int 
   }
 }
 
-__global__ void __launch_bounds__(128)
+// Pivot arg-max over the CTA on integer keys (pivot_key), carrying the
+// winner's signed value; ties go to the smaller row.  Every thread returns
+// the same row.
+__device__ __forceinline__ int cta_argmax_v(long long key, int idx, double v, double *out_v, long long *red_k,
+                                            int *red_i, double *red_s) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long ok = __shfl_xor_sync(FULL, key, o);
+    const int oi = __shfl_xor_sync(FULL, idx, o);
+    const double ov = __shfl_xor_sync(FULL, v, o);
+    if (ok > key || (ok == key && oi < idx)) {
+      key = ok;
+      idx = oi;
+      v = ov;
+    }
+  }
+  if (lane == 0) {
+    red_k[wid] = key;
+    red_i[wid] = idx;
+    red_s[wid] = v;
+  }
+  __syncthreads();
+  long long bk = red_k[0];
+  double bv = red_s[0];
+  int bi = red_i[0];
+  for (int w = 1; w < nw; w++) {
+    const long long ok = red_k[w];
+    const int oi = red_i[w];
+    if (ok > bk || (ok == bk && oi < bi)) {
+      bk = ok;
+      bi = oi;
+      bv = red_s[w];
+    }
+  }
+  *out_v = bv;
+  return bi;
+}
+
+// getrf, one CTA per problem.  Per column j, three barriers:
+//  (1) arg-max of |a(i, j)|, i >= j (NaN entries never win, a NaN diagonal
+//      keeps its row); every thread learns the pivot row p and value;
+//  (2) thread t swaps rows j and p in column t (t != j); warp 0 scales
+//      column j below the diagonal by the pivot's reciprocal (row p takes
+//      the old diagonal, read before barrier (1)).  An FP64 instruction costs
+//      the same for 1 or 32 lanes, so the per-column scalar work stays on one
+//      warp;
+//  (3) the trailing update a(i, c) -= l(i) u(c), i, c > j, spread over all
+//      threads element by element (column-major order), so the work does
+//      not shrink onto fewer warps as the factorization proceeds.
+__global__ void __launch_bounds__(256)
 k_getrf_rows(int n, int ld, Op C, OpW D, int *ipiv, long long sipiv, int *info) {
   extern __shared__ double sm[];
-  __shared__ double red_v[4];
-  __shared__ int red_i[4];
-  const int b = blockIdx.x, t = threadIdx.x;
+  __shared__ long long red_k[8];
+  __shared__ double red_s[8];
+  __shared__ int red_i[8];
+  const int b = blockIdx.x, t = threadIdx.x, T_ = blockDim.x;
   rows_load(sm, ld, n, n, C.p + b * C.stride, C);
   int first_zero = 0;
   for (int j = 0; j < n; j++) {
-    // NaN entries never win; a NaN diagonal keeps its row.  Both reads come
-    // before the barrier inside cta_argmax, so before any swap.
     const double x = (t >= j && t < n) ? sm[j * ld + t] : CUDART_NAN;
-    const bool diag_nan = isnan(sm[j * ld + j]);
-    const bool cand = !isnan(x);
-    const int p = cta_argmax(cand ? fabs(x) : -1.0, cand ? t : n, red_v, red_i);
-    const int pr = (p < n && !diag_nan) ? p : j;
-    if (pr != j && t < n) {
-      const double x = sm[t * ld + j];
-      sm[t * ld + j] = sm[t * ld + pr];
-      sm[t * ld + pr] = x;
-    }
+    const double djj = sm[j * ld + j];  // read before barrier (1): rewritten in phase (2)
+    const long long key = pivot_key(x);
+    double pv;
+    const int p = cta_argmax_v(key, key >= 0 ? t : n, x, &pv, red_k, red_i, red_s);
+    const bool keep = (p >= n) || pivot_key(djj) < 0;
+    const int pr = keep ? j : p;
+    const double piv = keep ? djj : pv;
     if (t == 0) ipiv[b * sipiv + j] = pr;
-    __syncthreads();
-    const double piv = sm[j * ld + j];
     if (piv == 0.0) {
       if (first_zero == 0) first_zero = j + 1;
-    } else if (t > j && t < n) {
-      const double l = sm[j * ld + t] * recip_newton(piv);
-      sm[j * ld + t] = l;
-      for (int c = j + 1; c < n; c++) sm[c * ld + t] = fma(-l, sm[c * ld + j], sm[c * ld + t]);
+      // column j is zero at and below the diagonal: no swap, no update
+      __syncthreads();
+      continue;
+    }
+    if (pr != j && t < n && t != j) {
+      const double y = sm[t * ld + j];
+      sm[t * ld + j] = sm[t * ld + pr];
+      sm[t * ld + pr] = y;
+    }
+    if (t < 32) {  // one warp forms the reciprocal and the multipliers (FP64 work is issued per warp)
+      const double r = recip_newton(piv);
+      for (int i = j + 1 + t; i < n; i += 32) sm[j * ld + i] = ((i == pr) ? djj : sm[j * ld + i]) * r;
+      if (t == 0) sm[j * ld + j] = piv;
+    }
+    __syncthreads();
+    const int R = n - j - 1;
+    if (R > 0) {
+      int c = j + 1 + t / R, i = j + 1 + t % R;
+      const int dc = T_ / R, di = T_ % R;
+      while (c < n) {
+        sm[c * ld + i] = fma(-sm[j * ld + i], sm[c * ld + j], sm[c * ld + i]);
+        c += dc;
+        i += di;
+        if (i >= n) {
+          i -= R;
+          c++;
+        }
+      }
     }
     __syncthreads();
   }
@@ -273,34 +309,90 @@ k_getrf_rows(int n, int ld, Op C, OpW D, int *ipiv, long long sipiv, int *info) 
   if (info && t == 0) info[b] = first_zero;
 }
 
-__global__ void __launch_bounds__(128)
+// gelqf, one CTA per problem.  Per row i, two barriers:
+//  (1) warp 0 forms beta, tau and 1/(alpha - beta) from alpha and the norm
+//      of a(i, i+1:n) (computed ahead, see (2)), scales the row into the
+//      reflector x and writes beta and tau.  An FP64 instruction costs the
+//      same for 1 or 32 lanes, so the per-row scalar work stays on one warp;
+//  (2) the rows below, each by a group of S lanes (S a power of two with
+//      rows * S filling the CTA, so the lanes stay busy as the rows run out):
+//      w = a(r, i) + a(r, i+1:n) . x by a strided partial sum and a shuffle
+//      reduction within the group, then a(r, i:n) -= tau w [1, x].  The group
+//      of row i+1 then sums the squares of its new a(i+1, i+2:n): the next
+//      step's norm.
+__device__ __forceinline__ double warp_row_norm2(const double *sm, int ld, int r, int c0, int n) {
+  const int lane = threadIdx.x & 31;
+  double part = 0.0;
+  for (int c = c0 + lane; c < n; c += 32) part = fma(sm[c * ld + r], sm[c * ld + r], part);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(FULL, part, o);
+  return part;
+}
+
+__global__ void __launch_bounds__(256)
 k_gelqf_rows(int m, int n, int ld, Op C, OpW D, double *tau, long long stau) {
   extern __shared__ double sm[];
-  __shared__ double red_v[4];
+  __shared__ double sc[2];  // tau, norm of the next row
   const int b = blockIdx.x, t = threadIdx.x, T_ = blockDim.x;
   rows_load(sm, ld, m, n, C.p + b * C.stride, C);
   const int k = min(m, n);
+  if (t < 32) {
+    const double ss0 = warp_row_norm2(sm, ld, 0, 1, n);
+    if (t == 0) sc[1] = ss0;
+  }
+  __syncthreads();
   for (int i = 0; i < k; i++) {
-    double part = 0.0;
-    for (int c = i + 1 + t; c < n; c += T_) part = fma(sm[c * ld + i], sm[c * ld + i], part);
-    const double alpha = sm[i * ld + i];  // read before the barrier in cta_sum: thread 0 overwrites it
-    const double ss = cta_sum(part, red_v);
-    double tv = 0.0;
-    if (ss != 0.0) {
-      const double beta = -copysign(sqrt(fma(alpha, alpha, ss)), alpha);
-      tv = (beta - alpha) / beta;
-      const double scal = 1.0 / (alpha - beta);
-      for (int c = i + 1 + t; c < n; c += T_) sm[c * ld + i] *= scal;
-      if (t == 0) sm[i * ld + i] = beta;
+    if (t < 32) {
+      const double ss = sc[1];
+      const double alpha = sm[i * ld + i];
+      double tv = 0.0;
+      __syncwarp();
+      if (ss != 0.0) {
+        const double beta = -copysign(sqrt(fma(alpha, alpha, ss)), alpha);
+        tv = (beta - alpha) / beta;
+        const double scal = 1.0 / (alpha - beta);
+        for (int c = i + 1 + t; c < n; c += 32) sm[c * ld + i] *= scal;
+        if (t == 0) sm[i * ld + i] = beta;
+      }
+      if (t == 0) {
+        tau[b * stau + i] = tv;
+        sc[0] = tv;
+      }
     }
-    if (t == 0) tau[b * stau + i] = tv;
     __syncthreads();
-    for (int r = i + 1 + t; r < m; r += T_) {
-      double w = sm[i * ld + r];
-      for (int c = i + 1; c < n; c++) w = fma(sm[c * ld + r], sm[c * ld + i], w);
-      const double tw = tv * w;
-      sm[i * ld + r] -= tw;
-      for (int c = i + 1; c < n; c++) sm[c * ld + r] = fma(-tw, sm[c * ld + i], sm[c * ld + r]);
+    const double tv = sc[0];
+    const int R = m - i - 1;
+    if (tv != 0.0 && R > 0) {
+      int S = 1;
+      while (S < 32 && 2 * S * R <= T_) S *= 2;
+      const int sub = t & (S - 1), groups = T_ / S;
+      const int iters = (R + groups - 1) / groups;  // same trip count on every lane
+      for (int it = 0; it < iters; it++) {
+        const int r = i + 1 + t / S + it * groups;
+        const bool ok = r < m;
+        double w = (ok && sub == 0) ? sm[i * ld + r] : 0.0;
+        if (ok)
+          for (int c = i + 1 + sub; c < n; c += S) w = fma(sm[c * ld + r], sm[c * ld + i], w);
+        for (int o = 1; o < S; o <<= 1) w += __shfl_xor_sync(FULL, w, o);
+        double nx = 0.0;
+        if (ok) {
+          const double tw = tv * w;
+          if (sub == 0) sm[i * ld + r] -= tw;
+          for (int c = i + 1 + sub; c < n; c += S) {
+            const double y = fma(-tw, sm[c * ld + i], sm[c * ld + r]);
+            sm[c * ld + r] = y;
+            if (c >= i + 2) nx = fma(y, y, nx);
+          }
+        }
+        if (r == i + 1) {  // the first group only; its S lanes share r
+          const unsigned gmask = (S == 32) ? FULL : (((1u << S) - 1u) << ((t & 31) & ~(S - 1)));
+          for (int o = 1; o < S; o <<= 1) nx += __shfl_xor_sync(gmask, nx, o);
+          if (sub == 0) sc[1] = nx;
+        }
+      }
+    } else if (R > 0 && t < 32) {  // H_i = I: the next row is unchanged
+      const double ss1 = warp_row_norm2(sm, ld, i + 1, i + 2, n);
+      if (t == 0) sc[1] = ss1;
     }
     __syncthreads();
   }
@@ -316,8 +408,14 @@ int pick_g(size_t bytes_per_problem) {
   return 32;
 }
 
+// Rows from which the one-CTA-per-problem kernels are used (measured on
+// square sweeps: the one-warp kernels win up to n = 32 for getrf, where the
+// row kernel's per-column barriers dominate, and up to n = 64 for gelqf).
 #ifndef BF_LU_ROWS_MIN
-#define BF_LU_ROWS_MIN 32  // rows from which the one-CTA-per-problem kernels are used
+#define BF_LU_ROWS_MIN 48
+#endif
+#ifndef BF_LQ_ROWS_MIN
+#define BF_LQ_ROWS_MIN 65
 #endif
 
 cudaError_t set_smem(const void *fn, size_t smem) {
@@ -353,7 +451,7 @@ cudaError_t launch_getrf(int batch, int n, Op C, OpW D, int *ipiv, long long sip
     const size_t smem = (size_t)ld * n * sizeof(double);
     cudaError_t e = set_smem((const void *)k_getrf_rows, smem);
     if (e != cudaSuccess) return e;
-    k_getrf_rows<<<batch, ((n + 31) / 32) * 32, smem, s>>>(n, ld, C, D, ipiv, sipiv, info);
+    k_getrf_rows<<<batch, n > 64 ? 256 : 128, smem, s>>>(n, ld, C, D, ipiv, sipiv, info);
     return cudaGetLastError();
   }
   switch (pick_g((size_t)n * n * 8)) {
@@ -367,12 +465,12 @@ cudaError_t launch_getrf(int batch, int n, Op C, OpW D, int *ipiv, long long sip
 }
 
 cudaError_t launch_gelqf(int batch, int m, int n, Op C, OpW D, double *tau, long long stau, cudaStream_t s) {
-  if (m >= BF_LU_ROWS_MIN) {
+  if (m >= BF_LQ_ROWS_MIN) {
     const int ld = m | 1;
     const size_t smem = (size_t)ld * n * sizeof(double);
     cudaError_t e = set_smem((const void *)k_gelqf_rows, smem);
     if (e != cudaSuccess) return e;
-    k_gelqf_rows<<<batch, min(128, ((m + 31) / 32) * 32), smem, s>>>(m, n, ld, C, D, tau, stau);
+    k_gelqf_rows<<<batch, (size_t)m * n > 4096 ? 256 : 128, smem, s>>>(m, n, ld, C, D, tau, stau);
     return cudaGetLastError();
   }
   switch (pick_g((size_t)m * n * 8)) {

@@ -303,11 +303,8 @@ int posv_threads(int n, int nrhs) {
 
 template <bool MIXED>
 cudaError_t set_posv_smem_attr() {
-  static bool done = false;
-  if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k_posv<MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  if (e == cudaSuccess) done = true;
-  return e;
+  static std::atomic<unsigned long long> done{0};
+  return smem_attr_once((const void *)k_posv<MIXED>, 200 * 1024, done);
 }
 
 }  // namespace
@@ -328,12 +325,9 @@ cudaError_t launch_posv_adjoint(int batch, int n, int nrhs, Op L, Op X, Op Xbar,
   const size_t ne = (size_t)n * (n + 1) / 2;
   const size_t smem = (((ne + 1) & ~(size_t)1) + (((size_t)n + 1) & ~(size_t)1) + 2 * (size_t)nrhs * n) * 8;
   if (smem > 200 * 1024) return cudaErrorInvalidConfiguration;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_posv_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static std::atomic<unsigned long long> attr{0};
+  cudaError_t e = smem_attr_once((const void *)k_posv_adjoint, 200 * 1024, attr);
+  if (e != cudaSuccess) return e;
   k_posv_adjoint<<<batch, posv_threads(n, nrhs), smem, s>>>(n, nrhs, L, X, Xbar, Bbar, Abar);
   return cudaGetLastError();
 }

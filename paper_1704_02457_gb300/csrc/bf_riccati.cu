@@ -155,12 +155,9 @@ size_t riccati_smem(int max_nx, int max_nu) {
 cudaError_t launch_riccati(int batch, int N, const bf_riccati_prob *probs, const int *order,
                            int max_nx, int max_nu, int threads, cudaStream_t s) {
   const size_t smem = riccati_smem(max_nx, max_nu);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_riccati, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static std::atomic<unsigned long long> attr{0};
+  cudaError_t e = smem_attr_once((const void *)k_riccati, 200 * 1024, attr);
+  if (e != cudaSuccess) return e;
   k_riccati<<<batch, threads, smem, s>>>(batch, N, probs, order, max_nx, max_nu);
   return cudaGetLastError();
 }

@@ -165,12 +165,9 @@ cudaError_t launch_trsm_rltn(int batch, int m, int n, double alpha, Op L, const 
   size_t smem = ((size_t)P * ls_region(W) + 1) * sizeof(double);
   if (n > 32) smem += (size_t)P * KC * SPITCH * sizeof(double);
   if (smem > 200 * 1024) return cudaErrorInvalidConfiguration;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_trsm_rltn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  static std::atomic<unsigned long long> attr{0};
+  cudaError_t e = smem_attr_once((const void *)k_trsm_rltn, 200 * 1024, attr);
+  if (e != cudaSuccess) return e;
   const long long blocks = (long long)((batch + P - 1) / P) * chunks;
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
   k_trsm_rltn<<<(unsigned)blocks, threads, smem, s>>>(batch, m, n, alpha, L, dinv, sdinv, B, D, P, R, chunks);
