@@ -253,12 +253,12 @@ __device__ __forceinline__ int cta_argmax_v(long long key, int idx, double v, do
 //  (3) the trailing update a(i, c) -= l(i) u(c), i, c > j, spread over all
 //      threads element by element (column-major order), so the work does
 //      not shrink onto fewer warps as the factorization proceeds.
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(512)
 k_getrf_rows(int n, int ld, Op C, OpW D, int *ipiv, long long sipiv, int *info) {
   extern __shared__ double sm[];
-  __shared__ long long red_k[8];
-  __shared__ double red_s[8];
-  __shared__ int red_i[8];
+  __shared__ long long red_k[16];
+  __shared__ double red_s[16];
+  __shared__ int red_i[16];
   const int b = blockIdx.x, t = threadIdx.x, T_ = blockDim.x;
   rows_load(sm, ld, n, n, C.p + b * C.stride, C);
   int first_zero = 0;
@@ -329,7 +329,7 @@ __device__ __forceinline__ double warp_row_norm2(const double *sm, int ld, int r
   return part;
 }
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(512)
 k_gelqf_rows(int m, int n, int ld, Op C, OpW D, double *tau, long long stau) {
   extern __shared__ double sm[];
   __shared__ double sc[2];  // tau, norm of the next row
@@ -417,6 +417,12 @@ int pick_g(size_t bytes_per_problem) {
 #ifndef BF_LQ_ROWS_MIN
 #define BF_LQ_ROWS_MIN 65
 #endif
+// Threads of the row kernels for the largest matrices (one CTA per SM fits
+// by shared memory there, so the CTA itself must bring the warps).
+#ifndef BF_LU_BIG_THREADS
+#define BF_LU_BIG_THREADS 256
+#endif
+constexpr int LU_BIG_THREADS = BF_LU_BIG_THREADS;
 
 cudaError_t set_smem(const void *fn, size_t smem) {
   if (smem <= 48 * 1024) return cudaSuccess;
@@ -451,7 +457,7 @@ cudaError_t launch_getrf(int batch, int n, Op C, OpW D, int *ipiv, long long sip
     const size_t smem = (size_t)ld * n * sizeof(double);
     cudaError_t e = set_smem((const void *)k_getrf_rows, smem);
     if (e != cudaSuccess) return e;
-    k_getrf_rows<<<batch, n > 64 ? 256 : 128, smem, s>>>(n, ld, C, D, ipiv, sipiv, info);
+    k_getrf_rows<<<batch, n > 96 ? LU_BIG_THREADS : (n > 64 ? 256 : 128), smem, s>>>(n, ld, C, D, ipiv, sipiv, info);
     return cudaGetLastError();
   }
   switch (pick_g((size_t)n * n * 8)) {
@@ -470,7 +476,8 @@ cudaError_t launch_gelqf(int batch, int m, int n, Op C, OpW D, double *tau, long
     const size_t smem = (size_t)ld * n * sizeof(double);
     cudaError_t e = set_smem((const void *)k_gelqf_rows, smem);
     if (e != cudaSuccess) return e;
-    k_gelqf_rows<<<batch, (size_t)m * n > 4096 ? 256 : 128, smem, s>>>(m, n, ld, C, D, tau, stau);
+    k_gelqf_rows<<<batch, (size_t)m * n > 9216 ? LU_BIG_THREADS : ((size_t)m * n > 4096 ? 256 : 128), smem, s>>>(
+        m, n, ld, C, D, tau, stau);
     return cudaGetLastError();
   }
   switch (pick_g((size_t)m * n * 8)) {
