@@ -388,6 +388,188 @@ def _oracle_time(routine, n, data):
     return time.perf_counter() - t0
 
 
+# Error bounds of the check below: the gemm/syrk bound of the routines'
+# acceptance (max |D - D_oracle| <= 1e-15 k ||A||_F ||B||_F), the
+# factorization residual ||L L^T - S||_F / ||S||_F <= 1e-13 and, for trsm,
+# ||X L^T - B||_F / (||X||_F ||L||_F) <= 1e-13; the factors are also compared
+# with the oracle's (relative Frobenius distance <= 1e-12; 1e-11 for trsm).
+ORACLE_BOUNDS = {"dgemm_nt": 1e-15, "dsyrk_ln": 1e-15, "dpotrf_l": 1e-13, "dtrsm_rltn": 1e-13,
+                 "dsyrk_dpotrf_ln": 1e-13}
+
+
+def oracle_check(pts, samples=4, seed=11):
+    """Errors of the GPU results against the FP64 oracle on sampled problems
+    of every point (the first, the last and seeded random ones), read back
+    from the outputs the timed steps wrote.  Runs in the cpu_baseline leg."""
+    import numpy as np
+
+    import oracle
+
+    def fro(x):
+        return float(np.sqrt(np.sum(x * x)))
+
+    rng = np.random.default_rng(seed)
+    out, worst = [], {}
+    for p in pts:
+        bt, n = p.batch, p.n
+        idx = sorted({0, bt - 1, *[int(i) for i in rng.integers(0, bt, size=max(0, samples - 2))]})
+
+        def g(X):
+            return X.to_colmajor()[idx].cpu().numpy()
+
+        D = g(p.D)
+        names = {"dgemm_nt": ("A", "B", "C"), "dsyrk_ln": ("A", "C"), "dpotrf_l": ("C",),
+                 "dtrsm_rltn": ("L", "B"), "dsyrk_dpotrf_ln": ("A", "C")}[p.routine]
+        X = {k: g(getattr(p, k)) for k in names}
+        err = oerr = 0.0
+        for s in range(len(idx)):
+            if p.routine == "dgemm_nt":
+                A, B, C = X["A"][s], X["B"][s], X["C"][s]
+                e = np.abs(D[s] - oracle.dgemm_nt(1.0, A, B, 1.0, C)).max() / (n * fro(A) * fro(B))
+                err, oerr = max(err, e), max(oerr, e)
+            elif p.routine == "dsyrk_ln":
+                A, C = X["A"][s], X["C"][s]
+                Do = oracle.dsyrk_ln(1.0, A, A, 1.0, C, D0=np.zeros((n, n)))
+                e = np.abs(np.tril(D[s] - Do)).max() / (n * fro(A) ** 2)
+                err, oerr = max(err, e), max(oerr, e)
+            elif p.routine in ("dpotrf_l", "dsyrk_dpotrf_ln"):
+                if p.routine == "dpotrf_l":
+                    S = X["C"][s]
+                    Lo = oracle.dpotrf_l(S)[0]
+                else:
+                    A, C = X["A"][s], X["C"][s]
+                    S = C + A @ A.T
+                    Lo = oracle.dsyrk_dpotrf_ln(A, A, C)[0]
+                L = np.tril(D[s])
+                err = max(err, fro(L @ L.T - S) / fro(S))
+                oerr = max(oerr, fro(L - np.tril(Lo)) / fro(np.tril(Lo)))
+            else:
+                Lf, B = np.tril(X["L"][s]), X["B"][s]
+                err = max(err, fro(D[s] @ Lf.T - B) / (fro(D[s]) * fro(Lf)))
+                Xo = oracle.dtrsm_rltn(1.0, Lf, B)
+                oerr = max(oerr, fro(D[s] - Xo) / fro(Xo))
+        out.append({"routine": p.routine, "n": n, "problems": len(idx), "err": float(f"{err:.3e}"),
+                    "rel_to_oracle": float(f"{oerr:.3e}")})
+        w = worst.setdefault(p.routine, [0.0, 0.0])
+        w[0], w[1] = max(w[0], err), max(w[1], oerr)
+    ok = all(o["err"] <= ORACLE_BOUNDS[o["routine"]] and
+             o["rel_to_oracle"] <= (1e-11 if o["routine"] == "dtrsm_rltn" else 1e-12) for o in out)
+    return {"all_within_bounds": ok,
+            "max_by_routine": {r: {"err": float(f"{w[0]:.3e}"), "bound": ORACLE_BOUNDS[r],
+                                   "rel_to_oracle": float(f"{w[1]:.3e}")} for r, w in worst.items()},
+            "sample": f"{samples} problems per point (first, last, seeded random), outputs of the timed steps",
+            "per_point": out}
+
+
+def oracle_single_core(points=(("dgemm_nt", 24), ("dsyrk_dpotrf_ln", 24), ("dgemm_nt", 128),
+                               ("dsyrk_dpotrf_ln", 128)), budget_s=0.2):
+    """The oracle on one host core, for comparison with the paper's
+    single-core figures (context only: the oracle is plain loops)."""
+    import oracle
+    oracle.build()
+    cores = oracle.num_threads()
+    oracle.set_num_threads(1)
+    try:
+        out = {}
+        for routine, n in points:
+            count = max(1, int(2e6 / flops(routine, n)))
+            data = _oracle_inputs(routine, n, count)
+            t = _oracle_time(routine, n, data)
+            if t < budget_s:
+                count = max(1, int(count * budget_s / max(t, 1e-6)))
+                data = _oracle_inputs(routine, n, count)
+                t = _oracle_time(routine, n, data)
+            out[f"{routine}@{n}"] = round(flops(routine, n) * count / t / 1e9, 3)
+    finally:
+        oracle.set_num_threads(cores)
+    return out
+
+
+def host_cpu():
+    """One-line description of the host CPU (model name where the kernel
+    reports one, else the implementer/part codes of an Arm core)."""
+    import platform
+    info = {}
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    info.setdefault(k.strip(), v.strip())
+    except OSError:
+        pass
+    name = info.get("model name") or (
+        f"Arm implementer {info.get('CPU implementer', '?')} part {info.get('CPU part', '?')}"
+        if "CPU part" in info else platform.processor())
+    return f"{name}, {os.cpu_count()} logical cores, {platform.machine()}"
+
+
+def run_config1(args, dev, bt=128, n=24, graph_launches=100):
+    """The small parity configuration as a latency workload: 128 problems of
+    order 24 (gemm_nt with alpha = beta = 1; syrk_potrf of M, M with Q = 24 I;
+    trsm against that factor).  Per routine: the median of >= 20 single
+    launches after 5 warm-up launches (CUDA events, one stream), and the
+    per-launch time inside one captured CUDA graph of 100 launches."""
+    import statistics
+
+    import torch
+
+    import paper_1704_02457_gb300 as bf
+    from paper_1704_02457_gb300 import inputs
+
+    mk = lambda X: bf.DMatBatch.from_colmajor(X, tight=True)  # noqa: E731
+    A = mk(inputs.normal((bt, n, n), 20170508, dev))
+    B = mk(inputs.normal((bt, n, n), 20170509, dev))
+    C = mk(inputs.normal((bt, n, n), 20170510, dev))
+    Q = torch.zeros(bt, n, n, dtype=torch.float64, device=dev)
+    Q.diagonal(dim1=1, dim2=2).fill_(float(n))
+    Qd = mk(Q)
+    D = bf.DMatBatch(bt, n, n, device=dev, tight=True)
+    L = bf.DMatBatch(bt, n, n, device=dev, fill=0.0)
+    X = bf.DMatBatch(bt, n, n, device=dev, tight=True)
+    info = torch.zeros(bt, dtype=torch.int32, device=dev)
+    stream = torch.cuda.Stream()
+    calls = {
+        "dgemm_nt": lambda: bf.dgemm_nt(n, n, n, 1.0, A, 0, 0, B, 0, 0, 1.0, C, 0, 0, D, 0, 0, stream=stream),
+        "dsyrk_dpotrf_ln": lambda: bf.dsyrk_dpotrf_ln(n, n, A, 0, 0, A, 0, 0, Qd, 0, 0, L, 0, 0, info=info,
+                                                      stream=stream),
+        "dtrsm_rltn": lambda: bf.dtrsm_rltn(n, n, 1.0, L, 0, 0, B, 0, 0, X, 0, 0, use_dinv=True, stream=stream),
+    }
+    out = {}
+    with torch.cuda.stream(stream):
+        calls["dsyrk_dpotrf_ln"]()  # the factor trsm uses
+        for name, fn in calls.items():
+            for _ in range(5):
+                fn()
+            stream.synchronize()
+            ts = []
+            for _ in range(max(20, args.steps)):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=stream):
+                for _ in range(graph_launches):
+                    fn()
+            g.replay()
+            stream.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g.replay()
+            e1.record(stream)
+            e1.synchronize()
+            med = statistics.median(ts)
+            per = e0.elapsed_time(e1) / graph_launches
+            fl = flops(name, n) * bt
+            out[name] = {"launch_us": round(med * 1e3, 2), "graph_us_per_launch": round(per * 1e3, 2),
+                         "gflops_single": round(fl / (med * 1e-3) / 1e9, 2),
+                         "gflops_graph": round(fl / (per * 1e-3) / 1e9, 2)}
+    return {"workload": "128 problems, n = k = 24 (A, B, C iid N(0,1); Q = 24 I)", "routines": out}
+
+
 def run_gpu(args):
     import torch
 
@@ -528,6 +710,8 @@ def run_gpu(args):
         result["adjoint"] = run_adjoint(args, dev)
     if not args.no_next4:
         result["next4"] = run_next4(args, dev)
+    if not args.no_config1:
+        result["config1"] = run_config1(args, dev)
     if not args.no_e2e:
         result["e2e"] = run_e2e(pts, args, dev, world)
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -535,7 +719,9 @@ def run_gpu(args):
         rates = sampler.rates()
         t_cpu = sum(p.flops / (rates[(p.routine, p.n)] * 1e9) for p in pts)
         result["cpu_baseline"] = {"value": round(step_flops / t_cpu / 1e9, 3), "unit": "GFLOP/s",
-                                  "cores": sampler.cores, "kind": "oracle", "sample": sampler.describe()}
+                                  "cores": sampler.cores, "kind": "oracle", "sample": sampler.describe(),
+                                  "host_cpu": host_cpu(), "single_core_gflops": oracle_single_core()}
+        result["oracle_check"] = oracle_check(pts)
     if world > 1:
         torch.distributed.destroy_process_group()
     if rank == 0:
@@ -965,6 +1151,7 @@ def main():
     ap.add_argument("--no-riccati", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-next4", action="store_true")
+    ap.add_argument("--no-config1", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=0.15, help="seconds of oracle time per point")
     ap.add_argument("--ref-budget", type=float, default=0.06,
                     help="seconds of oracle time per point and step of the reference arm")

@@ -566,7 +566,13 @@ cudaError_t launch_small_g(bool aligned, int batch, int n, int k, Op A, Op B, Op
 template <bool FUSED>
 cudaError_t launch_chol_t(bool aligned, int batch, int n, int k, Op A, Op B, Op C, OpW D,
                           double *dinv, long long sdinv, int *info, cudaStream_t s) {
-  const int g = (n <= BF_CHOL_SMALL_MAX_N) ? pick_small_g(n) : 0;
+  int g = (n <= BF_CHOL_SMALL_MAX_N) ? pick_small_g(n) : 0;
+  // Small batches: more lanes per problem until the launch has a warp for
+  // every SM sub-partition (4 per SM), up to one problem per warp.  The
+  // budget's G is chosen for throughput; with few problems it would leave
+  // most of the GPU idle and each warp a long serial chain of FP64 work.
+  if (g)
+    while (g < 32 && (long long)batch * g < 32LL * 4 * device_sm_count()) g *= 2;
   switch (g) {
     case 1: return launch_small_g<1, FUSED>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
     case 2: return launch_small_g<2, FUSED>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);

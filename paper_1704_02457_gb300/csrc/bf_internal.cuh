@@ -85,6 +85,21 @@ inline cudaError_t smem_attr_once(const void *fn, int bytes, std::atomic<unsigne
   return e;
 }
 
+// Number of SMs of the current device (cached per device).
+inline int device_sm_count() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 152;
+  if (dev < 64) {
+    const int c = cache[dev].load(std::memory_order_relaxed);
+    if (c > 0) return c;
+  }
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
+  if (dev < 64) cache[dev].store(sms, std::memory_order_relaxed);
+  return sms;
+}
+
 // 1/d by Newton-Raphson iteration r <- r + r (1 - d r) from the hardware's
 // approximate reciprocal (rcp.approx.ftz.f64); two steps take it to full
 // double precision.  Used where one reciprocal is shared by a column of

@@ -161,6 +161,9 @@ cudaError_t launch_trsm_rltn(int batch, int m, int n, double alpha, Op L, const 
   const size_t per_problem = ((size_t)ls_region(W) + (n > 32 ? (size_t)KC * SPITCH : 0)) * sizeof(double);
   P = (int)min((size_t)P, (size_t)(96 * 1024) / per_problem);
   P = max(1, min(P, batch));
+  // Small batches: if the CTAs would not cover the SMs, keep each CTA within
+  // 4 warps so that no SM sub-partition serializes two warps' substitutions.
+  if ((batch + P - 1) / P < device_sm_count() && P * R > 128) P = max(1, 128 / R);
   const int threads = ((P * R + 31) / 32) * 32;
   size_t smem = ((size_t)P * ls_region(W) + 1) * sizeof(double);
   if (n > 32) smem += (size_t)P * KC * SPITCH * sizeof(double);

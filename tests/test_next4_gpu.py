@@ -197,3 +197,30 @@ def test_gelqf_matches_oracle(m, n):
         Lfull = np.zeros((m, n))
         Lfull[:, :k] = np.tril(F[b])[:, :k]
         assert np.linalg.norm(Lfull @ Q - A[b].numpy()) <= 1e-13 * n * np.linalg.norm(A[b].numpy())
+
+
+@pytest.mark.parametrize("n", [12, 64])
+def test_getrf_gelqf_in_place_with_offsets(n):
+    """C and D may coincide: factor in place at a sub-matrix offset, the
+    rest of the matrix untouched."""
+    bt = 3
+    A = inputs.normal((bt, n, n), 1800 + n)
+    dA = put(A, 2, 1, fill=3.0)
+    ipiv = torch.zeros((bt, n), dtype=torch.int32, device="cuda")
+    bf.dgetrf(n, dA, 2, 1, dA, 2, 1, ipiv)
+    whole = get(dA)
+    for b in range(bt):
+        LUo, pivo, _ = oracle.dgetrf(A[b].numpy())
+        assert np.linalg.norm(whole[b, 2:, 1:] - LUo) <= 1e-12 * np.linalg.norm(LUo)
+        assert np.array_equal(ipiv[b].cpu().numpy(), pivo)
+    assert np.all(whole[:, :2, :] == 3.0) and np.all(whole[:, :, :1] == 3.0)
+    m = n - 3
+    dQ = put(A[:, :m, :], 1, 0, fill=-1.0)
+    tau = torch.zeros((bt, m), dtype=torch.float64, device="cuda")
+    bf.dgelqf(m, n, dQ, 1, 0, dQ, 1, 0, tau)
+    whole = get(dQ)
+    for b in range(bt):
+        Fo, to = oracle.dgelqf(A[b, :m, :].numpy())
+        assert np.linalg.norm(whole[b, 1:, :] - Fo) <= 1e-12 * np.linalg.norm(Fo)
+        assert np.allclose(tau[b].cpu().numpy(), to, rtol=1e-12, atol=1e-15)
+    assert np.all(whole[:, :1, :] == -1.0)
