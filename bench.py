@@ -93,7 +93,7 @@ def roofline_gflops(routine, n, hbm_gbs):
 # kernel's source file when the counters were taken: the bench reports the
 # traffic only while that file is unchanged.
 TRAFFIC = {
-    ("k_gemm_nt<0,1>", "dgemm_nt", 256): {
+    ("k_gemm_nt<0,1,1>", "dgemm_nt", 256): {
         "bytes": 1076209152 + 335009536,
         "src": "paper_1704_02457_gb300/csrc/bf_gemm.cu",
         "blob": "c0d0da9ac044265b21ee9186324dc9a9dd8ea1af",
@@ -137,9 +137,9 @@ def small_g(n):
 def kernel_of(routine, n):
     """Name of the kernel the library launches for (routine, n) at this sweep."""
     if routine == "dgemm_nt":
-        return "k_gemm_nt<0,1>"
+        return "k_gemm_nt<0,1,1>"
     if routine == "dsyrk_ln":
-        return "k_gemm_nt<1,1>"
+        return "k_gemm_nt<1,1,1>"
     if routine == "dtrsm_rltn":
         return "k_trsm_rltn"
     fused = int(routine == "dsyrk_dpotrf_ln")

@@ -31,9 +31,12 @@ __device__ __forceinline__ void tri_index(int t, int &tr, int &tc) {
 }
 
 // One 4x4 register block (rows i0.., columns j0..) of problem b.  DIAG: a
-// diagonal block of syrk, whose FMAs above the diagonal are skipped.
-template <bool SYRK, bool DIAG, bool ALIGNED>
-__device__ __forceinline__ void gemm_tile(int b, int tr, int tc, int m, int n, int k, double alpha,
+// diagonal block of syrk, whose FMAs above the diagonal are skipped.  KS > 1
+// (small batches): the block is shared by KS adjacent lanes, lane ks taking
+// the columns l = ks, ks + KS, ...; the partial blocks are summed with
+// shuffles and lane 0 of the group writes D.
+template <bool SYRK, bool DIAG, bool ALIGNED, int KS>
+__device__ __forceinline__ void gemm_tile(int b, int tr, int tc, int ks, int m, int n, int k, double alpha,
                                           const Op &A, const Op &B, double beta, const Op &C,
                                           const OpW &D) {
   const int i0 = tr * 4, j0 = tc * 4;
@@ -47,7 +50,7 @@ __device__ __forceinline__ void gemm_tile(int b, int tr, int tc, int m, int n, i
   double acc[4][4];
 
   // alpha == 1: start from beta*C so that the epilogue costs no FP64 work.
-  if (a1 && beta != 0.0) {
+  if (a1 && beta != 0.0 && ks == 0) {
     if (ALIGNED && full) {
       const double *cp = pc + (long long)(C.i0 + i0) * C.cn + (long long)(C.j0 + j0) * PS;
 #pragma unroll
@@ -85,7 +88,7 @@ __device__ __forceinline__ void gemm_tile(int b, int tr, int tc, int m, int n, i
     const double *ap = pa + (long long)(A.i0 + i0) * A.cn + (long long)A.j0 * PS;
     const double *bp = pb + (long long)(B.i0 + j0) * B.cn + (long long)B.j0 * PS;
 #pragma unroll 4
-    for (int l = 0; l < k; l++) {
+    for (int l = ks; l < k; l += KS) {
       const double2 a01 = __ldg((const double2 *)(ap + l * PS));
       const double2 a23 = __ldg((const double2 *)(ap + l * PS + 2));
       const double2 b01 = __ldg((const double2 *)(bp + l * PS));
@@ -108,7 +111,7 @@ __device__ __forceinline__ void gemm_tile(int b, int tr, int tc, int m, int n, i
       br[r] = pb + pm_off(B.i0 + jj, B.j0, B.cn);
     }
 #pragma unroll 2
-    for (int l = 0; l < k; l++) {
+    for (int l = ks; l < k; l += KS) {
       double av[4], bv[4];
 #pragma unroll
       for (int r = 0; r < 4; r++) {
@@ -121,6 +124,19 @@ __device__ __forceinline__ void gemm_tile(int b, int tr, int tc, int m, int n, i
         for (int c = 0; c < 4; c++)
           if (!DIAG || c <= r) acc[r][c] = fma(av[r], bv[c], acc[r][c]);
     }
+  }
+
+  if (KS > 1) {
+    const int lane = threadIdx.x & 31;
+    const unsigned gmask = ((1u << KS) - 1u) << (lane & ~(KS - 1));
+#pragma unroll
+    for (int o = 1; o < KS; o <<= 1)
+#pragma unroll
+      for (int r = 0; r < 4; r++)
+#pragma unroll
+        for (int c = 0; c < 4; c++)
+          if (!DIAG || c <= r) acc[r][c] += __shfl_xor_sync(gmask, acc[r][c], o);
+    if (ks != 0) return;
   }
 
   // epilogue
@@ -172,17 +188,18 @@ __device__ __forceinline__ void gemm_tile(int b, int tr, int tc, int m, int n, i
 // syrk_ln: the strictly-lower blocks of all problems come first, then the
 // diagonal blocks of all problems, so that each warp does one kind of block
 // and the diagonal ones save their upper-half FMAs.
-template <bool SYRK, bool ALIGNED>
+template <bool SYRK, bool ALIGNED, int KS>
 __global__ void __launch_bounds__(128)
 k_gemm_nt(int batch, int m, int n, int k, double alpha, Op A, Op B, double beta, Op C, OpW D,
           int tiles_c, int tiles_pp) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / KS;
+  const int ks = (int)(threadIdx.x % KS);  // the KS lanes of a block are adjacent
   if (!SYRK) {
     if (t >= (long long)batch * tiles_pp) return;
     const int b = (int)(t / tiles_pp);
     const int tt = (int)(t - (long long)b * tiles_pp);
     const int tr = tt / tiles_c;
-    gemm_tile<false, false, ALIGNED>(b, tr, tt - tr * tiles_c, m, n, k, alpha, A, B, beta, C, D);
+    gemm_tile<false, false, ALIGNED, KS>(b, tr, tt - tr * tiles_c, ks, m, n, k, alpha, A, B, beta, C, D);
   } else {
     const int TR = tiles_c;                 // block rows (= block columns)
     const int OD = TR * (TR - 1) / 2;       // strictly-lower blocks per problem
@@ -191,14 +208,35 @@ k_gemm_nt(int batch, int m, int n, int k, double alpha, Op A, Op B, double beta,
       const int b = (int)(t / OD);
       int r, c;
       tri_index((int)(t - (long long)b * OD), r, c);
-      gemm_tile<true, false, ALIGNED>(b, r + 1, c, m, n, k, alpha, A, B, beta, C, D);
+      gemm_tile<true, false, ALIGNED, KS>(b, r + 1, c, ks, m, n, k, alpha, A, B, beta, C, D);
     } else if (t < nod + (long long)batch * TR) {
       const long long u = t - nod;
       const int b = (int)(u / TR);
       const int d = (int)(u - (long long)b * TR);
-      gemm_tile<true, true, ALIGNED>(b, d, d, m, n, k, alpha, A, B, beta, C, D);
+      gemm_tile<true, true, ALIGNED, KS>(b, d, d, ks, m, n, k, alpha, A, B, beta, C, D);
     }
   }
+}
+
+template <int KS>
+cudaError_t launch_gemm_ks(bool syrk, bool aligned, long long total, int batch, int m, int n, int k, double alpha,
+                           Op A, Op B, double beta, Op C, OpW D, int tcn, int tiles_pp, cudaStream_t s) {
+  const int threads = 128;
+  const long long blocks = (total * KS + threads - 1) / threads;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  const unsigned g = (unsigned)blocks;
+  if (syrk) {
+    if (aligned)
+      k_gemm_nt<true, true, KS><<<g, threads, 0, s>>>(batch, m, n, k, alpha, A, B, beta, C, D, tcn, tiles_pp);
+    else
+      k_gemm_nt<true, false, KS><<<g, threads, 0, s>>>(batch, m, n, k, alpha, A, B, beta, C, D, tcn, tiles_pp);
+  } else {
+    if (aligned)
+      k_gemm_nt<false, true, KS><<<g, threads, 0, s>>>(batch, m, n, k, alpha, A, B, beta, C, D, tcn, tiles_pp);
+    else
+      k_gemm_nt<false, false, KS><<<g, threads, 0, s>>>(batch, m, n, k, alpha, A, B, beta, C, D, tcn, tiles_pp);
+  }
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -208,21 +246,14 @@ cudaError_t launch_gemm_nt(bool syrk, int batch, int m, int n, int k, double alp
   const int tr = (m + 3) / 4, tcn = (n + 3) / 4;
   const int tiles_pp = syrk ? tr * (tr + 1) / 2 : tr * tcn;  // syrk: tcn == tr
   const long long total = (long long)batch * tiles_pp;
-  const int threads = 128;
-  const long long blocks = (total + threads - 1) / threads;
-  if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-  if (syrk) {
-    if (aligned)
-      k_gemm_nt<true, true><<<(unsigned)blocks, threads, 0, s>>>(batch, m, n, k, alpha, A, B, beta, C, D, tcn, tiles_pp);
-    else
-      k_gemm_nt<true, false><<<(unsigned)blocks, threads, 0, s>>>(batch, m, n, k, alpha, A, B, beta, C, D, tcn, tiles_pp);
-  } else {
-    if (aligned)
-      k_gemm_nt<false, true><<<(unsigned)blocks, threads, 0, s>>>(batch, m, n, k, alpha, A, B, beta, C, D, tcn, tiles_pp);
-    else
-      k_gemm_nt<false, false><<<(unsigned)blocks, threads, 0, s>>>(batch, m, n, k, alpha, A, B, beta, C, D, tcn, tiles_pp);
-  }
-  return cudaGetLastError();
+  // Small batches (fewer than two blocks per lane of every SM sub-partition's
+  // warp slot): split k over 2 or 4 lanes per block, so the launch spreads
+  // over the SMs instead of leaving each warp a long serial k-loop.
+  int ks = 1;
+  if (total < 2LL * 4 * 32 * device_sm_count()) ks = (k >= 16) ? 4 : (k >= 8 ? 2 : 1);
+  if (ks == 4) return launch_gemm_ks<4>(syrk, aligned, total, batch, m, n, k, alpha, A, B, beta, C, D, tcn, tiles_pp, s);
+  if (ks == 2) return launch_gemm_ks<2>(syrk, aligned, total, batch, m, n, k, alpha, A, B, beta, C, D, tcn, tiles_pp, s);
+  return launch_gemm_ks<1>(syrk, aligned, total, batch, m, n, k, alpha, A, B, beta, C, D, tcn, tiles_pp, s);
 }
 
 }  // namespace bf
