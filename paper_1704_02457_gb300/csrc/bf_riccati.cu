@@ -22,8 +22,8 @@
 //
 // Within a CTA, the trmm and syrk put rows on lanes (all lanes of a warp run
 // dot products of the same length); the factorization is right-looking over
-// the packed lower triangle of M, with the thread that updates the next
-// pivot computing its rsqrt (one per column), and the gain is one thread per
+// the packed lower triangle of M in panels of 4 columns (warp 0 factors a
+// panel, all threads apply its rank-4 update), and the gain is one thread per
 // row of Kt walking the columns of Lam backwards with the saved reciprocals.
 #include "bf_internal.cuh"
 
@@ -31,6 +31,11 @@ namespace bf {
 namespace {
 
 __device__ __forceinline__ int col_start(int l, int n) { return (l * (2 * n - l + 1)) / 2 - l; }
+
+#ifndef BF_RICCATI_RB
+#define BF_RICCATI_RB 4
+#endif
+constexpr int RB = BF_RICCATI_RB;  // panel width of the factorization
 
 // column of packed lower element e in an s x s triangle (element (i, l) at col_start(l, s) + i)
 __device__ __forceinline__ int packed_col(int e, int s) {
@@ -56,16 +61,16 @@ k_riccati(int batch, int N, const bf_riccati_prob *probs, const int *order, int 
       for (int k = t; k < N; k += T) P.info[k] = -1;
     return;
   }
-  const int lp = nx + 1, cp = nx + 1;
-  double *Lc = sm;                          // nx x nx, row-major, pitch lp
-  double *C = Lc + nx * lp;                 // m x nx, row-major, pitch cp (reused for Kt)
+  const int cp = nx + 1;
+  double *C = sm;                           // m x nx, row-major, pitch cp (reused for Kt)
   double *M = C + m * cp;                   // packed lower m x m, column-major
   double *rv = M + m * (m + 1) / 2;         // 1 / pivot of each column of M
   __shared__ int s_bad;
-
+  // The factor Lc of the next stage's P is the trailing nx x nx block of M's
+  // factor, so it is read in place: Lc(l, j) = M[col_start(nu + j) + nu + l].
   for (int e = t; e < nx * nx; e += T) {
-    const int i = e / nx, j = e - i * nx;
-    Lc[i * lp + j] = (j <= i) ? P.LN[pm_off(i, j, P.ln_cn)] : 0.0;
+    const int j = e / nx, i = e - j * nx;
+    if (i >= j) M[col_start(nu + j, m) + nu + i] = P.LN[pm_off(i, j, P.ln_cn)];
   }
   __syncthreads();
 
@@ -74,12 +79,13 @@ k_riccati(int batch, int N, const bf_riccati_prob *probs, const int *order, int 
     for (int e = t; e < m * nx; e += T) {
       const int j = e / m, i = e - j * m;
       const double *brow = P.BAt + pm_off(i, 0, P.bat_cn);
+      const double *lcol = M + col_start(nu + j, m) + nu;  // column j of Lc, rows l >= j at lcol[l]
       double acc = 0.0;
-      for (int l = j; l < nx; l++) acc = fma(__ldg(brow + (long long)l * PS), Lc[l * lp + j], acc);
+      for (int l = j; l < nx; l++) acc = fma(__ldg(brow + (long long)l * PS), lcol[l], acc);
       C[i * cp + j] = acc;
     }
     if (t == 0) s_bad = 0;
-    __syncthreads();
+    __syncthreads();  // M (holding Lc) is overwritten next
 
     // (2) M = M0 + C C^T, lower triangle
     const int NE = m * (m + 1) / 2;
@@ -91,32 +97,47 @@ k_riccati(int batch, int N, const bf_riccati_prob *probs, const int *order, int 
       M[e] = acc;
     }
     __syncthreads();
-    if (t == 0) {
-      const double d = M[0];
-      rv[0] = rsqrt(d);
-      if (!(d > 0.0)) s_bad = 1;
-    }
-    __syncthreads();
 
-    // (3) Cholesky of M, right-looking over the packed lower triangle
-    for (int j = 0; j < m; j++) {
-      const int cj = col_start(j, m);
-      const double r = rv[j];
-      for (int i = j + 1 + t; i < m; i += T) M[cj + i] *= r;
-      if (t == 0) M[cj + j] *= r;  // d * rsqrt(d)
+    // (3) Cholesky of M, right-looking in panels of RB columns: warp 0
+    // factors the panel (rows j0..m-1) with warp-level syncs only, then all
+    // threads apply its rank-RB update to the trailing triangle.  Two CTA
+    // barriers per panel instead of two per column.
+    for (int j0 = 0; j0 < m; j0 += RB) {
+      const int jb = min(RB, m - j0);
+      if (t < 32) {
+        for (int jj = 0; jj < jb; jj++) {
+          const int j = j0 + jj, cj = col_start(j, m);
+          const double d = M[cj + j];
+          const double r = rsqrt(d);
+          __syncwarp();
+          if (t == 0) {
+            rv[j] = r;
+            M[cj + j] = d * r;
+            if (!(d > 0.0) && s_bad == 0) s_bad = j + 1;
+          }
+          for (int i = j + 1 + t; i < m; i += 32) M[cj + i] *= r;
+          __syncwarp();
+          for (int c = j + 1; c < j0 + jb; c++) {  // the rest of the panel
+            const double lc = M[cj + c];
+            const int cc = col_start(c, m);
+            for (int i = c + t; i < m; i += 32) M[cc + i] = fma(-M[cj + i], lc, M[cc + i]);
+          }
+          __syncwarp();
+        }
+      }
       __syncthreads();
-      const int s = m - j - 1;  // trailing triangle rows/cols j+1 .. m-1
+      const int s = m - j0 - jb;  // trailing triangle rows/cols j0+jb .. m-1
       const int TE = s * (s + 1) / 2;
       for (int e = t; e < TE; e += T) {
         const int kk = packed_col(e, s), ii = e - col_start(kk, s);
-        const int kc = j + 1 + kk, ic = j + 1 + ii;
+        const int kc = j0 + jb + kk, ic = j0 + jb + ii;
         const int idx = col_start(kc, m) + ic;
-        const double v = fma(-M[cj + ic], M[cj + kc], M[idx]);
-        M[idx] = v;
-        if (ii == kk && kk == 0) {  // next pivot
-          rv[kc] = rsqrt(v);
-          if (!(v > 0.0) && s_bad == 0) s_bad = kc + 1;
+        double v = M[idx];
+        for (int jj = 0; jj < jb; jj++) {
+          const int cj = col_start(j0 + jj, m);
+          v = fma(-M[cj + ic], M[cj + kc], v);
         }
+        M[idx] = v;
       }
       __syncthreads();
     }
@@ -136,9 +157,7 @@ k_riccati(int batch, int N, const bf_riccati_prob *probs, const int *order, int 
     double *lk = P.L + (long long)k * P.l_stride;
     for (int e = t; e < nx * nx; e += T) {
       const int i = e / nx, j = e - i * nx;
-      const double v = (j <= i) ? M[col_start(nu + j, m) + nu + i] : 0.0;
-      Lc[i * lp + j] = v;
-      if (j <= i) lk[pm_off(i, j, P.l_cn)] = v;
+      if (j <= i) lk[pm_off(i, j, P.l_cn)] = M[col_start(nu + j, m) + nu + i];
     }
     if (t == 0 && P.info) P.info[k] = s_bad;
     __syncthreads();
@@ -149,7 +168,7 @@ k_riccati(int batch, int N, const bf_riccati_prob *probs, const int *order, int 
 
 size_t riccati_smem(int max_nx, int max_nu) {
   const size_t nx = max_nx, m = (size_t)max_nx + max_nu;
-  return (nx * (nx + 1) + m * (nx + 1) + m * (m + 1) / 2 + m) * sizeof(double);
+  return (m * (nx + 1) + m * (m + 1) / 2 + m) * sizeof(double);
 }
 
 cudaError_t launch_riccati(int batch, int N, const bf_riccati_prob *probs, const int *order,
