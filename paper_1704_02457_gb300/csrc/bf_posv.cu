@@ -18,7 +18,7 @@
 //
 // One CTA per system.  The factor lives packed in shared memory (column l at
 // cs(l), element (i, l) at cs(l) + i), one warp solves one right-hand side
-// (column-oriented forward substitution, dot-product backward substitution),
+// (column-oriented forward and backward substitution),
 // and the FP64 residual gives every thread one row of A, read from L2 in
 // panel-major order, for all right-hand sides at once.
 #include <type_traits>
@@ -69,14 +69,15 @@ __device__ __forceinline__ void warp_solve(const T *L, const T *dinv, T *v, int 
     if (lane == 0) v[j] = yj;
     __syncwarp();
   }
-  // L^T x = y: x_j = (y_j - L(j+1:, j) . x(j+1:)) / L_jj, from the bottom up
+  // L^T x = y, column-oriented from the bottom up: x_j finishes, then the
+  // rows above it take -L(j, i) x_j (L(j, i) = L^T(i, j) sits in packed
+  // column i).  No reductions: a dot-product form would spend five shuffle
+  // adds per column, each a full FP64 warp instruction.
   for (int j = n - 1; j >= 0; j--) {
-    const int cs = col_start(j, n);
-    T part = (T)0;
-    for (int i = j + 1 + lane; i < n; i += 32) part += L[cs + i] * v[i];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(FULL, part, o);
-    if (lane == 0) v[j] = (v[j] - part) * dinv[j];
+    const T xj = v[j] * dinv[j];
+    __syncwarp();
+    for (int i = lane; i < j; i += 32) v[i] -= L[col_start(i, n) + j] * xj;
+    if (lane == 0) v[j] = xj;
     __syncwarp();
   }
 }
