@@ -397,6 +397,65 @@ int bf_dposv_mixed_batched_noalloc(int batch, int n, int nrhs, const bf_dmat *sA
                                    long long strideX, double tol, int max_iter, int *iters,
                                    double *resid, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Descriptor-array batched forms: uneven sizes in one launch.
+ *
+ * The strided forms need every problem of a call to share sizes and layout.
+ * These take, for problem b, its sizes size[b] and, for every operand, a
+ * descriptor with the sub-matrix offsets that the paper's routines take
+ * next to it (Sec. 3.2 and Appendix A.2: "(sA, ai, aj)"), all in DEVICE
+ * arrays of length batch.  The calls are the paper's per-matrix routines
+ * with one launch for the whole array.  max_m (and max_n) bound the sizes
+ * and shape the launch.
+ *
+ * Arguments of the call itself are checked on the host (-i for argument i).
+ * Each problem's record is checked on the device, with the same rules as the
+ * strided forms.  A problem that fails is skipped (its output is untouched).
+ * status[b] (device, may be NULL) receives 0, or -1 for bad sizes (negative,
+ * or above max_m / max_n), or -(1 + p) for the p-th operand of the call
+ * (counting from 1 in the order of the signature).  Calls are asynchronous.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  bf_dmat mat; /* descriptor of the matrix */
+  int i, j;    /* sub-matrix offsets (row, column) */
+} bf_dsub;
+
+typedef struct {
+  int m, n, k; /* sizes of one problem; unused members are ignored */
+} bf_dsize;
+
+/* gemm_nt per problem: D <- alpha A B^T + beta C with sizes (m, n, k); C is
+ * not read (nor checked) when beta == 0.  Operands: A, B, C, D. */
+int bf_dgemm_nt_vbatched(int batch, const bf_dsize *size, double alpha, const bf_dsub *A,
+                         const bf_dsub *B, double beta, const bf_dsub *C, const bf_dsub *D,
+                         int max_m, int max_n, int *status, void *stream);
+
+/* syrk_ln per problem: sizes (m, -, k).  Operands: A, B, C, D. */
+int bf_dsyrk_ln_vbatched(int batch, const bf_dsize *size, double alpha, const bf_dsub *A,
+                         const bf_dsub *B, double beta, const bf_dsub *C, const bf_dsub *D,
+                         int max_m, int *status, void *stream);
+
+/* potrf_l per problem: size (m); m <= 512.  With want_dinv, 1/L_jj goes to
+ * D[b].mat.dA[D[b].j + j] when that descriptor has an inverse-diagonal
+ * array that reaches that far (D[b].j + m <= min(mat.m, mat.n)); otherwise
+ * it is not written.  info[b] (device, may be NULL) as for the strided
+ * form.  Operands: C, D. */
+int bf_dpotrf_l_vbatched(int batch, const bf_dsize *size, const bf_dsub *C, const bf_dsub *D,
+                         int want_dinv, int *info, int max_m, int *status, void *stream);
+
+/* trsm_rltn per problem: sizes (m, n); n <= 4096.  With use_dinv the
+ * reciprocals come from L[b].mat.dA[L[b].j + j] where that array reaches
+ * (L[b].j + n <= min(mat.m, mat.n)); else they are formed from L.
+ * Operands: L, B, D. */
+int bf_dtrsm_rltn_vbatched(int batch, const bf_dsize *size, double alpha, const bf_dsub *L,
+                           int use_dinv, const bf_dsub *B, const bf_dsub *D, int max_m, int max_n,
+                           int *status, void *stream);
+
+/* syrk_potrf_ln per problem: sizes (m, -, k); m <= 512.  Operands: A, B, C, D. */
+int bf_dsyrk_dpotrf_ln_vbatched(int batch, const bf_dsize *size, const bf_dsub *A, const bf_dsub *B,
+                                const bf_dsub *C, const bf_dsub *D, int want_dinv, int *info,
+                                int max_m, int *status, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -20,6 +20,8 @@ __all__ = [
     "BF_PS", "BF_ALIGN", "BF_ERR_UNSUPPORTED", "BfError", "DMatBatch", "bf_dmat", "load",
     "dgemm_nt", "dsyrk_ln", "dpotrf_l", "dtrsm_rltn", "dsyrk_dpotrf_ln", "pack", "unpack",
     "dpotrs_l", "dposv_mixed", "dposv_mixed_worksize", "dgemm_nn", "dtrmm_rlnn", "dgetrf", "dgelqf",
+    "dsub_records", "dsize_records", "dgemm_nt_vbatched", "dsyrk_ln_vbatched", "dpotrf_l_vbatched",
+    "dtrsm_rltn_vbatched", "dsyrk_dpotrf_ln_vbatched",
 ]
 
 
@@ -106,6 +108,15 @@ class DMatBatch:
         cm = X.to(device=out.storage.device, dtype=torch.float64).transpose(1, 2).contiguous()
         pack(cm, out, stream=stream)
         return out
+
+    def problem_desc(self, b: int) -> bf_dmat:
+        """Descriptor of problem b alone (for the descriptor-array forms)."""
+        d = bf_dmat()
+        ctypes.pointer(d)[0] = self.desc
+        off = int(b) * self.stride * 8
+        d.pA = self.desc.pA + off
+        d.dA = (self.desc.dA + off) if self.desc.dA else None
+        return d
 
     def to_colmajor(self, stream=None):
         """Unpack into a new (batch, m, n) float64 device tensor."""
@@ -254,4 +265,66 @@ def dgelqf(m, n, C, ci, cj, D, di, dj, tau, batch=None, stream=None):
     batch = D.batch if batch is None else batch
     _check("bf_dgelqf_batched", load().bf_dgelqf_batched(
         batch, m, n, *_op(C, ci, cj), *_op(D, di, dj), ctypes.c_void_p(tau.data_ptr()), tau.shape[-1],
+        _stream(stream)))
+
+
+# ---------------------------------------------------- descriptor-array forms
+
+def dsub_records(items, device=None):
+    """Device array of bf_dsub records from (DMatBatch, problem, i, j) tuples:
+    problem b of the batch, at sub-matrix offsets (i, j)."""
+    torch = _torch()
+    arr = (_abi.bf_dsub * max(1, len(items)))()
+    for r, (M, b, i, j) in zip(arr, items):
+        r.mat = M.problem_desc(b)
+        r.i, r.j = int(i), int(j)
+    raw = torch.frombuffer(bytearray(bytes(arr)), dtype=torch.uint8)
+    dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+    return raw.to(dev)
+
+
+def dsize_records(sizes, device=None):
+    """Device array of bf_dsize records from (m, n, k) tuples."""
+    torch = _torch()
+    t = torch.tensor([list(x) for x in sizes] or [[0, 0, 0]], dtype=torch.int32)
+    dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+    return t.to(dev).contiguous()
+
+
+def _vp(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def dgemm_nt_vbatched(batch, size, alpha, A, B, beta, C, D, max_m, max_n, status=None, stream=None):
+    """Per problem b: D_b <- alpha A_b B_b^T + beta C_b (bf_dgemm_nt_vbatched);
+    size, A, B, C, D from dsize_records / dsub_records."""
+    _check("bf_dgemm_nt_vbatched", load().bf_dgemm_nt_vbatched(
+        batch, _vp(size), alpha, _vp(A), _vp(B), beta, _vp(C), _vp(D), max_m, max_n, _vp(status),
+        _stream(stream)))
+
+
+def dsyrk_ln_vbatched(batch, size, alpha, A, B, beta, C, D, max_m, status=None, stream=None):
+    """Per problem b: lower(D_b) <- alpha A_b B_b^T + beta C_b (bf_dsyrk_ln_vbatched)."""
+    _check("bf_dsyrk_ln_vbatched", load().bf_dsyrk_ln_vbatched(
+        batch, _vp(size), alpha, _vp(A), _vp(B), beta, _vp(C), _vp(D), max_m, _vp(status), _stream(stream)))
+
+
+def dpotrf_l_vbatched(batch, size, C, D, max_m, want_dinv=False, info=None, status=None, stream=None):
+    """Per problem b: lower(D_b) <- chol(C_b) (bf_dpotrf_l_vbatched)."""
+    _check("bf_dpotrf_l_vbatched", load().bf_dpotrf_l_vbatched(
+        batch, _vp(size), _vp(C), _vp(D), int(want_dinv), _vp(info), max_m, _vp(status), _stream(stream)))
+
+
+def dtrsm_rltn_vbatched(batch, size, alpha, L, B, D, max_m, max_n, use_dinv=False, status=None, stream=None):
+    """Per problem b: D_b <- alpha B_b L_b^{-T} (bf_dtrsm_rltn_vbatched)."""
+    _check("bf_dtrsm_rltn_vbatched", load().bf_dtrsm_rltn_vbatched(
+        batch, _vp(size), alpha, _vp(L), int(use_dinv), _vp(B), _vp(D), max_m, max_n, _vp(status),
+        _stream(stream)))
+
+
+def dsyrk_dpotrf_ln_vbatched(batch, size, A, B, C, D, max_m, want_dinv=False, info=None, status=None,
+                             stream=None):
+    """Per problem b: lower(D_b) <- chol(C_b + A_b B_b^T) (bf_dsyrk_dpotrf_ln_vbatched)."""
+    _check("bf_dsyrk_dpotrf_ln_vbatched", load().bf_dsyrk_dpotrf_ln_vbatched(
+        batch, _vp(size), _vp(A), _vp(B), _vp(C), _vp(D), int(want_dinv), _vp(info), max_m, _vp(status),
         _stream(stream)))

@@ -35,6 +35,16 @@ class bf_dmat(ctypes.Structure):
     ]
 
 
+class bf_dsub(ctypes.Structure):
+    """Mirror of bf_dsub: one operand record of the descriptor-array forms."""
+    _fields_ = [("mat", bf_dmat), ("i", _c_int), ("j", _c_int)]
+
+
+class bf_dsize(ctypes.Structure):
+    """Mirror of bf_dsize: the sizes of one problem."""
+    _fields_ = [("m", _c_int), ("n", _c_int), ("k", _c_int)]
+
+
 class bf_riccati_prob(ctypes.Structure):
     """Mirror of the C struct bf_riccati_prob (include/bfgpu.h)."""
     _fields_ = [
@@ -67,6 +77,15 @@ SIGNATURES = {
     "bf_dtrmm_rlnn_batched": (_c_int, [_c_int, _c_int, _c_int, _c_d, *_M, *_M, *_M, _c_vp]),
     "bf_dtrmm_rlnn": (_c_int, [_c_int, _c_int, _c_d, _P, _c_int, _c_int, _P, _c_int, _c_int,
                                _P, _c_int, _c_int, _c_vp]),
+    "bf_dgemm_nt_vbatched": (_c_int, [_c_int, _c_vp, _c_d, _c_vp, _c_vp, _c_d, _c_vp, _c_vp, _c_int, _c_int,
+                                      _c_vp, _c_vp]),
+    "bf_dsyrk_ln_vbatched": (_c_int, [_c_int, _c_vp, _c_d, _c_vp, _c_vp, _c_d, _c_vp, _c_vp, _c_int, _c_vp,
+                                      _c_vp]),
+    "bf_dpotrf_l_vbatched": (_c_int, [_c_int, _c_vp, _c_vp, _c_vp, _c_int, _c_vp, _c_int, _c_vp, _c_vp]),
+    "bf_dtrsm_rltn_vbatched": (_c_int, [_c_int, _c_vp, _c_d, _c_vp, _c_int, _c_vp, _c_vp, _c_int, _c_int, _c_vp,
+                                        _c_vp]),
+    "bf_dsyrk_dpotrf_ln_vbatched": (_c_int, [_c_int, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_int, _c_vp, _c_int,
+                                             _c_vp, _c_vp]),
     "bf_dgetrf_batched": (_c_int, [_c_int, _c_int, *_M, *_M, _c_vp, _c_ll, _c_vp, _c_vp]),
     "bf_dgetrf": (_c_int, [_c_int, _P, _c_int, _c_int, _P, _c_int, _c_int, _c_vp, _c_vp, _c_vp]),
     "bf_dgelqf_batched": (_c_int, [_c_int, _c_int, _c_int, *_M, *_M, _c_vp, _c_ll, _c_vp]),

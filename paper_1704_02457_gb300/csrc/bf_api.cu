@@ -480,6 +480,86 @@ int bf_dgelqf(int m, int n, const bf_dmat *sC, int ci, int cj, const bf_dmat *sD
   return -map[-r];
 }
 
+// ----------------------------------------------- descriptor-array batched forms
+// Host checks cover the call's own arguments; each problem's record is
+// checked on the device (status array).
+
+int bf_dgemm_nt_vbatched(int batch, const bf_dsize *size, double alpha, const bf_dsub *A, const bf_dsub *B,
+                         double beta, const bf_dsub *C, const bf_dsub *D, int max_m, int max_n, int *st,
+                         void *stream) {
+  if (batch < 0) return -1;
+  if (batch > 0 && !size) return -2;
+  if (batch > 0 && !A) return -4;
+  if (batch > 0 && !B) return -5;
+  if (batch > 0 && beta != 0.0 && !C) return -7;
+  if (batch > 0 && !D) return -8;
+  if (max_m < 0) return -9;
+  if (max_n < 0) return -10;
+  if (batch == 0 || max_m == 0 || max_n == 0) return 0;
+  return status(launch_gemm_nt_v(false, batch, size, alpha, A, B, beta, C, D, max_m, max_n, st,
+                                 (cudaStream_t)stream));
+}
+
+int bf_dsyrk_ln_vbatched(int batch, const bf_dsize *size, double alpha, const bf_dsub *A, const bf_dsub *B,
+                         double beta, const bf_dsub *C, const bf_dsub *D, int max_m, int *st, void *stream) {
+  if (batch < 0) return -1;
+  if (batch > 0 && !size) return -2;
+  if (batch > 0 && !A) return -4;
+  if (batch > 0 && !B) return -5;
+  if (batch > 0 && beta != 0.0 && !C) return -7;
+  if (batch > 0 && !D) return -8;
+  if (max_m < 0) return -9;
+  if (batch == 0 || max_m == 0) return 0;
+  return status(launch_gemm_nt_v(true, batch, size, alpha, A, B, beta, C, D, max_m, max_m, st,
+                                 (cudaStream_t)stream));
+}
+
+int bf_dpotrf_l_vbatched(int batch, const bf_dsize *size, const bf_dsub *C, const bf_dsub *D, int want_dinv,
+                         int *info, int max_m, int *st, void *stream) {
+  if (batch < 0) return -1;
+  if (batch > 0 && !size) return -2;
+  if (batch > 0 && !C) return -3;
+  if (batch > 0 && !D) return -4;
+  if (info && !aligned_to(info, 4)) return -6;
+  if (max_m < 0) return -7;
+  if (max_m > CHOL_MAX_N) return BF_ERR_UNSUPPORTED;
+  if (batch == 0 || max_m == 0) return 0;
+  return status(launch_chol_v(false, batch, size, nullptr, nullptr, C, D, want_dinv != 0, info, max_m, st,
+                              (cudaStream_t)stream));
+}
+
+int bf_dtrsm_rltn_vbatched(int batch, const bf_dsize *size, double alpha, const bf_dsub *L, int use_dinv,
+                           const bf_dsub *B, const bf_dsub *D, int max_m, int max_n, int *st, void *stream) {
+  if (batch < 0) return -1;
+  if (batch > 0 && !size) return -2;
+  if (batch > 0 && !L) return -4;
+  if (batch > 0 && !B) return -6;
+  if (batch > 0 && !D) return -7;
+  if (max_m < 0) return -8;
+  if (max_n < 0) return -9;
+  if (max_n > TRSM_MAX_N) return BF_ERR_UNSUPPORTED;
+  if (batch == 0 || max_m == 0 || max_n == 0) return 0;
+  return status(launch_trsm_rltn_v(batch, size, alpha, L, use_dinv != 0, B, D, max_m, max_n, st,
+                                   (cudaStream_t)stream));
+}
+
+int bf_dsyrk_dpotrf_ln_vbatched(int batch, const bf_dsize *size, const bf_dsub *A, const bf_dsub *B,
+                                const bf_dsub *C, const bf_dsub *D, int want_dinv, int *info, int max_m,
+                                int *st, void *stream) {
+  if (batch < 0) return -1;
+  if (batch > 0 && !size) return -2;
+  if (batch > 0 && !A) return -3;
+  if (batch > 0 && !B) return -4;
+  if (batch > 0 && !C) return -5;
+  if (batch > 0 && !D) return -6;
+  if (info && !aligned_to(info, 4)) return -8;
+  if (max_m < 0) return -9;
+  if (max_m > CHOL_MAX_N) return BF_ERR_UNSUPPORTED;
+  if (batch == 0 || max_m == 0) return 0;
+  return status(launch_chol_v(true, batch, size, A, B, C, D, want_dinv != 0, info, max_m, st,
+                              (cudaStream_t)stream));
+}
+
 // ---------------------------------------------------------------- Riccati
 
 int bf_driccati_sqrt_batched(int batch, int N, const bf_riccati_prob *probs, const int *order,

@@ -449,11 +449,10 @@ __device__ __forceinline__ void rows_block(RowsSmem<T, BW, P> &S, const RowMap<P
 // by RowMap<P>.  Problems past the end of the batch (last CTA) run along
 // without touching memory.
 template <int BW, int P, bool FUSED, bool ALIGNED, typename T>
-__device__ __forceinline__ void chol_rows_body(int batch, int n, int k, Op A, Op B, Op C, OpWT<T> D, T *dinv,
-                                               long long sdinv, int *info) {
+__device__ __forceinline__ void chol_rows_body(int b0, int batch, int n, int k, Op A, Op B, Op C, OpWT<T> D,
+                                               T *dinv, long long sdinv, int *info) {
   __shared__ RowsSmem<T, BW, P> S;
   const RowMap<P> rm;
-  const int b0 = blockIdx.x * P;
   const bool me_valid = b0 + rm.p < batch;
   const long long bme = me_valid ? b0 + rm.p : b0;  // lanes of a missing problem alias the first
   const double *pa = FUSED ? A.p + bme * A.stride : nullptr;
@@ -477,7 +476,7 @@ __device__ __forceinline__ void chol_rows_body(int batch, int n, int k, Op A, Op
 template <int BW, bool FUSED, bool ALIGNED, typename T>
 __global__ void __launch_bounds__(512)
 k_chol_rows(int batch, int n, int k, Op A, Op B, Op C, OpWT<T> D, T *dinv, long long sdinv, int *info) {
-  chol_rows_body<BW, 1, FUSED, ALIGNED, T>(batch, n, k, A, B, C, D, dinv, sdinv, info);
+  chol_rows_body<BW, 1, FUSED, ALIGNED, T>(blockIdx.x, batch, n, k, A, B, C, D, dinv, sdinv, info);
 }
 
 // Two problems per CTA, up to MAXT/2 rows; registers bounded so that two
@@ -485,7 +484,45 @@ k_chol_rows(int batch, int n, int k, Op A, Op B, Op C, OpWT<T> D, T *dinv, long 
 template <int BW, bool FUSED, bool ALIGNED, typename T, int MAXT>
 __global__ void __launch_bounds__(MAXT, 2)
 k_chol_rows2(int batch, int n, int k, Op A, Op B, Op C, OpWT<T> D, T *dinv, long long sdinv, int *info) {
-  chol_rows_body<BW, 2, FUSED, ALIGNED, T>(batch, n, k, A, B, C, D, dinv, sdinv, info);
+  chol_rows_body<BW, 2, FUSED, ALIGNED, T>(blockIdx.x * 2, batch, n, k, A, B, C, D, dinv, sdinv, info);
+}
+
+// Descriptor-array form: CTA b factors problem b of its own order (rows past
+// it idle), after checking the problem's record.
+template <int BW, bool FUSED>
+__global__ void __launch_bounds__(512)
+k_chol_rows_v(int batch, const bf_dsize *size, const bf_dsub *A, const bf_dsub *B, const bf_dsub *C,
+              const bf_dsub *D, int want_dinv, int *info, int max_m, int *status) {
+  const int b = blockIdx.x;
+  if (b >= batch) return;
+  const int m = size[b].m, k = FUSED ? size[b].k : 0;
+  int err = 0;
+  if (m < 0 || k < 0 || m > max_m)
+    err = -1;
+  else if (m > 0) {
+    if (FUSED && k > 0 && !dsub_ok(A[b], m, k))
+      err = -2;
+    else if (FUSED && k > 0 && !dsub_ok(B[b], m, k))
+      err = -3;
+    else if (!dsub_ok(C[b], m, m))
+      err = FUSED ? -4 : -2;
+    else if (!dsub_ok(D[b], m, m))
+      err = FUSED ? -5 : -3;
+  }
+  if (threadIdx.x == 0 && status) status[b] = err;
+  if (err != 0) return;
+  if (m == 0) {
+    if (threadIdx.x == 0 && info) info[b] = 0;
+    return;
+  }
+  const Op c = dsub_op(C[b]);
+  const Op a = (FUSED && k > 0) ? dsub_op(A[b]) : c;  // k == 0: A and B are never read
+  const Op bb = (FUSED && k > 0) ? dsub_op(B[b]) : c;
+  const OpW d = dsub_opw(D[b]);
+  // the inverse-diagonal array holds min(m, n) entries of its matrix
+  const bf_dmat &dm = D[b].mat;
+  double *dv = (want_dinv && dm.dA && D[b].j + m <= min(dm.m, dm.n)) ? dm.dA + D[b].j : nullptr;
+  chol_rows_body<BW, 1, FUSED, false, double>(0, 1, m, k, a, bb, c, d, dv, 0, info ? info + b : nullptr);
 }
 
 // Block width of k_chol_rows: 16-column blocks halve the work the diagonal
@@ -591,6 +628,18 @@ cudaError_t launch_chol(bool fused, int batch, int n, int k, Op A, Op B, Op C, O
                         double *dinv, long long sdinv, int *info, bool aligned, cudaStream_t s) {
   return fused ? launch_chol_t<true>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s)
                : launch_chol_t<false>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
+}
+
+cudaError_t launch_chol_v(bool fused, int batch, const bf_dsize *size, const bf_dsub *A, const bf_dsub *B,
+                          const bf_dsub *C, const bf_dsub *D, bool want_dinv, int *info, int max_m, int *status,
+                          cudaStream_t s) {
+  const int threads = ((max_m + 31) / 32) * 32;
+  if (threads > 512 || threads == 0) return cudaErrorInvalidConfiguration;
+  if (fused)
+    k_chol_rows_v<ROWS_BW, true><<<batch, threads, 0, s>>>(batch, size, A, B, C, D, want_dinv, info, max_m, status);
+  else
+    k_chol_rows_v<ROWS_BW, false><<<batch, threads, 0, s>>>(batch, size, A, B, C, D, want_dinv, info, max_m, status);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_chol_f32(int batch, int n, Op C, OpWT<float> D, int *info, bool aligned,

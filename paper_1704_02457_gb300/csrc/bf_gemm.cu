@@ -218,6 +218,64 @@ k_gemm_nt(int batch, int m, int n, int k, double alpha, Op A, Op B, double beta,
   }
 }
 
+// Descriptor-array form: CTA = (problem, chunk of 128 register blocks).  The
+// problem's record is checked first; all threads of the CTA see the same
+// result, so an invalid or finished problem leaves the CTA as a whole.
+template <bool SYRK>
+__global__ void __launch_bounds__(128)
+k_gemm_nt_v(int batch, const bf_dsize *size, double alpha, const bf_dsub *A, const bf_dsub *B, double beta,
+            const bf_dsub *C, const bf_dsub *D, int chunks, int max_m, int max_n, int *status) {
+  const int b = blockIdx.x / chunks, chunk = blockIdx.x - b * chunks;
+  if (b >= batch) return;
+  const bf_dsize sz = size[b];
+  const int m = sz.m, n = SYRK ? sz.m : sz.n, k = sz.k;
+  int err = 0;
+  if (m < 0 || n < 0 || k < 0 || m > max_m || n > max_n)
+    err = -1;
+  else if (m > 0 && n > 0) {
+    if (k > 0 && !dsub_ok(A[b], m, k))
+      err = -2;
+    else if (k > 0 && !dsub_ok(B[b], n, k))
+      err = -3;
+    else if (beta != 0.0 && !dsub_ok(C[b], m, n))
+      err = -4;
+    else if (!dsub_ok(D[b], m, n))
+      err = -5;
+  }
+  if (chunk == 0 && threadIdx.x == 0 && status) status[b] = err;
+  if (err != 0 || m == 0 || n == 0) return;
+  const int tr = (m + 3) / 4, tcn = (n + 3) / 4;
+  const int tiles = SYRK ? tr * (tr + 1) / 2 : tr * tcn;
+  const int tile = chunk * blockDim.x + threadIdx.x;
+  if (tile >= tiles) return;
+  const OpW d = dsub_opw(D[b]);
+  const Op dr{d.p, 0, d.cn, d.i0, d.j0};
+  const Op a = k > 0 ? dsub_op(A[b]) : dr;  // k == 0: A and B are never read
+  const Op bb = k > 0 ? dsub_op(B[b]) : dr;
+  const Op c = beta != 0.0 ? dsub_op(C[b]) : Op{nullptr, 0, 0, 0, 0};
+  const bool aligned = (a.i0 % PS) == 0 && (bb.i0 % PS) == 0 && (!c.p || (c.i0 % PS) == 0) && (d.i0 % PS) == 0 &&
+                       !((unsigned long long)a.p & 15ull) && !((unsigned long long)bb.p & 15ull) &&
+                       (!c.p || !((unsigned long long)c.p & 15ull)) && !((unsigned long long)d.p & 15ull);
+  int r, cc;
+  if (SYRK) {
+    tri_index(tile, r, cc);
+  } else {
+    r = tile / tcn;
+    cc = tile - r * tcn;
+  }
+  if (SYRK && r == cc) {
+    if (aligned)
+      gemm_tile<true, true, true, 1>(0, r, cc, 0, m, n, k, alpha, a, bb, beta, c, d);
+    else
+      gemm_tile<true, true, false, 1>(0, r, cc, 0, m, n, k, alpha, a, bb, beta, c, d);
+  } else {
+    if (aligned)
+      gemm_tile<SYRK, false, true, 1>(0, r, cc, 0, m, n, k, alpha, a, bb, beta, c, d);
+    else
+      gemm_tile<SYRK, false, false, 1>(0, r, cc, 0, m, n, k, alpha, a, bb, beta, c, d);
+  }
+}
+
 template <int KS>
 cudaError_t launch_gemm_ks(bool syrk, bool aligned, long long total, int batch, int m, int n, int k, double alpha,
                            Op A, Op B, double beta, Op C, OpW D, int tcn, int tiles_pp, cudaStream_t s) {
@@ -240,6 +298,23 @@ cudaError_t launch_gemm_ks(bool syrk, bool aligned, long long total, int batch, 
 }
 
 }  // namespace
+
+cudaError_t launch_gemm_nt_v(bool syrk, int batch, const bf_dsize *size, double alpha, const bf_dsub *A,
+                             const bf_dsub *B, double beta, const bf_dsub *C, const bf_dsub *D, int max_m,
+                             int max_n, int *status, cudaStream_t s) {
+  const int tr = (max_m + 3) / 4, tcn = ((syrk ? max_m : max_n) + 3) / 4;
+  const long long tiles = syrk ? (long long)tr * (tr + 1) / 2 : (long long)tr * tcn;
+  const int chunks = (int)max(1LL, (tiles + 127) / 128);
+  const long long blocks = (long long)batch * chunks;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  if (syrk)
+    k_gemm_nt_v<true><<<(unsigned)blocks, 128, 0, s>>>(batch, size, alpha, A, B, beta, C, D, chunks, max_m,
+                                                       max_m, status);
+  else
+    k_gemm_nt_v<false><<<(unsigned)blocks, 128, 0, s>>>(batch, size, alpha, A, B, beta, C, D, chunks, max_m,
+                                                        max_n, status);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_gemm_nt(bool syrk, int batch, int m, int n, int k, double alpha, Op A, Op B,
                            double beta, Op C, OpW D, bool aligned, cudaStream_t s) {

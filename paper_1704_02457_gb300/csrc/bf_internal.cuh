@@ -100,6 +100,30 @@ inline int device_sm_count() {
   return sms;
 }
 
+// Device-side check of one operand record of the descriptor-array forms:
+// the same rules as the host's check of a strided operand.
+__device__ __forceinline__ bool dsub_ok(const bf_dsub &s, int rows, int cols) {
+  const bf_dmat &d = s.mat;
+  if (!d.pA || d.ps != PS || ((unsigned long long)d.pA & 7ull) || d.m < 0 || d.n < 0 || d.pm < d.m ||
+      d.pm % PS != 0 || d.cn < d.n)
+    return false;
+  return s.i >= 0 && s.i + rows <= d.m && s.j >= 0 && s.j + cols <= d.n;
+}
+
+__device__ __forceinline__ Op dsub_op(const bf_dsub &s) { return Op{s.mat.pA, 0, s.mat.cn, s.i, s.j}; }
+__device__ __forceinline__ OpW dsub_opw(const bf_dsub &s) { return OpW{s.mat.pA, 0, s.mat.cn, s.i, s.j}; }
+
+// Launchers of the descriptor-array forms (problems checked on the device).
+cudaError_t launch_gemm_nt_v(bool syrk, int batch, const bf_dsize *size, double alpha, const bf_dsub *A,
+                             const bf_dsub *B, double beta, const bf_dsub *C, const bf_dsub *D, int max_m,
+                             int max_n, int *status, cudaStream_t s);
+cudaError_t launch_chol_v(bool fused, int batch, const bf_dsize *size, const bf_dsub *A, const bf_dsub *B,
+                          const bf_dsub *C, const bf_dsub *D, bool want_dinv, int *info, int max_m, int *status,
+                          cudaStream_t s);
+cudaError_t launch_trsm_rltn_v(int batch, const bf_dsize *size, double alpha, const bf_dsub *L, bool use_dinv,
+                               const bf_dsub *B, const bf_dsub *D, int max_m, int max_n, int *status,
+                               cudaStream_t s);
+
 // 1/d by Newton-Raphson iteration r <- r + r (1 - d r) from the hardware's
 // approximate reciprocal (rcp.approx.ftz.f64); two steps take it to full
 // double precision.  Used where one reciprocal is shared by a column of

@@ -142,7 +142,65 @@ k_trsm_rltn(int batch, int m, int n, double alpha, Op L, const double *dinv, lon
   }
 }
 
+// Descriptor-array form: CTA = (problem, chunk of MAX_ROWS rows of X), one
+// problem per CTA, after checking the problem's record.
+__global__ void __launch_bounds__(MAX_ROWS)
+k_trsm_rltn_v(int batch, const bf_dsize *size, double alpha, const bf_dsub *Ls, int use_dinv, const bf_dsub *Bs,
+              const bf_dsub *Ds, int chunks, int max_m, int max_n, int *status) {
+  extern __shared__ double smem[];
+  const int b = blockIdx.x / chunks, chunk = blockIdx.x - b * chunks;
+  if (b >= batch) return;
+  const int m = size[b].m, n = size[b].n;
+  int err = 0;
+  if (m < 0 || n < 0 || m > max_m || n > max_n)
+    err = -1;
+  else if (m > 0 && n > 0) {
+    if (!dsub_ok(Ls[b], n, n))
+      err = -2;
+    else if (!dsub_ok(Bs[b], m, n))
+      err = -3;
+    else if (!dsub_ok(Ds[b], m, n))
+      err = -4;
+  }
+  if (chunk == 0 && threadIdx.x == 0 && status) status[b] = err;
+  const int R = blockDim.x, r0 = chunk * R;
+  if (err != 0 || m == 0 || n == 0 || r0 >= m) return;
+  const Op L = dsub_op(Ls[b]), B = dsub_op(Bs[b]);
+  const OpW D = dsub_opw(Ds[b]);
+  // the inverse-diagonal array holds min(m, n) entries of its matrix; outside
+  // it the reciprocals are formed here
+  const bf_dmat &lm = Ls[b].mat;
+  const double *dinv = (use_dinv && lm.dA && Ls[b].j + n <= min(lm.m, lm.n)) ? lm.dA + Ls[b].j : nullptr;
+  for (int c0 = 0; c0 < n; c0 += 32) {
+    switch (w_bucket(min(32, n - c0))) {
+      case 4: trsm_block<4>(smem, 1, R, c0, m, n, alpha, 0, 1, r0, L, dinv, 0, B, D); break;
+      case 8: trsm_block<8>(smem, 1, R, c0, m, n, alpha, 0, 1, r0, L, dinv, 0, B, D); break;
+      case 16: trsm_block<16>(smem, 1, R, c0, m, n, alpha, 0, 1, r0, L, dinv, 0, B, D); break;
+      case 24: trsm_block<24>(smem, 1, R, c0, m, n, alpha, 0, 1, r0, L, dinv, 0, B, D); break;
+      default: trsm_block<32>(smem, 1, R, c0, m, n, alpha, 0, 1, r0, L, dinv, 0, B, D); break;
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_trsm_rltn_v(int batch, const bf_dsize *size, double alpha, const bf_dsub *L, bool use_dinv,
+                               const bf_dsub *B, const bf_dsub *D, int max_m, int max_n, int *status,
+                               cudaStream_t s) {
+  const int R = min(MAX_ROWS, ((max_m + 31) / 32) * 32);
+  const int chunks = max(1, (max_m + R - 1) / R);
+  const int W = w_bucket(min(max(max_n, 1), 32));
+  size_t smem = ((size_t)ls_region(W) + 1) * sizeof(double);
+  if (max_n > 32) smem += (size_t)KC * SPITCH * sizeof(double);
+  static std::atomic<unsigned long long> attr{0};
+  cudaError_t e = smem_attr_once((const void *)k_trsm_rltn_v, 200 * 1024, attr);
+  if (e != cudaSuccess) return e;
+  const long long blocks = (long long)batch * chunks;
+  if (blocks > 0x7fffffffLL || R == 0) return cudaErrorInvalidConfiguration;
+  k_trsm_rltn_v<<<(unsigned)blocks, R, smem, s>>>(batch, size, alpha, L, use_dinv ? 1 : 0, B, D, chunks, max_m,
+                                                  max_n, status);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_trsm_rltn(int batch, int m, int n, double alpha, Op L, const double *dinv,
                              long long sdinv, Op B, OpW D, cudaStream_t s) {

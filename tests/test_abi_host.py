@@ -165,6 +165,8 @@ int main(void) {
          offsetof(bf_riccati_prob, info));
   printf("%zu %zu %zu %zu\\n", offsetof(bf_riccati_prob, l_stride), offsetof(bf_riccati_prob, Kt),
          offsetof(bf_riccati_prob, kt_stride), offsetof(bf_riccati_prob, M0));
+  printf("%zu %zu %zu %zu %zu\\n", sizeof(bf_dsub), offsetof(bf_dsub, i), offsetof(bf_dsub, j), sizeof(bf_dsize),
+         offsetof(bf_dsize, k));
   return 0;
 }
 """)
@@ -174,8 +176,27 @@ int main(void) {
     out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
     R = _abi.bf_riccati_prob
     want = [ctypes.sizeof(_abi.bf_dmat), _abi.bf_dmat.memsize.offset, ctypes.sizeof(R), R.info.offset,
-            R.l_stride.offset, R.Kt.offset, R.kt_stride.offset, R.M0.offset]
+            R.l_stride.offset, R.Kt.offset, R.kt_stride.offset, R.M0.offset,
+            ctypes.sizeof(_abi.bf_dsub), _abi.bf_dsub.i.offset, _abi.bf_dsub.j.offset, ctypes.sizeof(_abi.bf_dsize),
+            _abi.bf_dsize.k.offset]
     assert [int(x) for x in out] == want
+
+
+def test_descriptor_array_forms_check_their_own_arguments(lib):
+    # host-side checks only (the records live on the device and are checked there)
+    v = ctypes.c_void_p(0x10000)
+    assert lib.bf_dgemm_nt_vbatched(-1, v, 1.0, v, v, 1.0, v, v, 8, 8, None, None) == -1
+    assert lib.bf_dgemm_nt_vbatched(3, None, 1.0, v, v, 1.0, v, v, 8, 8, None, None) == -2
+    assert lib.bf_dgemm_nt_vbatched(3, v, 1.0, v, v, 1.0, None, v, 8, 8, None, None) == -7
+    assert lib.bf_dgemm_nt_vbatched(3, v, 1.0, v, v, 1.0, v, v, -1, 8, None, None) == -9
+    assert lib.bf_dgemm_nt_vbatched(0, None, 1.0, None, None, 0.0, None, None, 8, 8, None, None) == 0
+    assert lib.bf_dsyrk_ln_vbatched(3, v, 1.0, v, None, 1.0, v, v, 8, None, None) == -5
+    assert lib.bf_dpotrf_l_vbatched(3, v, v, None, 1, None, 8, None, None) == -4
+    assert lib.bf_dpotrf_l_vbatched(3, v, v, v, 1, ctypes.c_void_p(0x10002), 8, None, None) == -6
+    assert lib.bf_dpotrf_l_vbatched(3, v, v, v, 1, None, 513, None, None) == _abi.BF_ERR_UNSUPPORTED
+    assert lib.bf_dtrsm_rltn_vbatched(3, v, 1.0, v, 0, v, v, 8, -2, None, None) == -9
+    assert lib.bf_dtrsm_rltn_vbatched(3, v, 1.0, v, 0, v, v, 8, 5000, None, None) == _abi.BF_ERR_UNSUPPORTED
+    assert lib.bf_dsyrk_dpotrf_ln_vbatched(3, v, v, v, None, v, 0, None, 8, None, None) == -5
 
 
 def test_riccati_argument_checks(lib):

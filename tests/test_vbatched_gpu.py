@@ -1,0 +1,201 @@
+"""The descriptor-array batched forms: uneven sizes and offsets per problem
+in one launch, each problem against the oracle, and per-problem records that
+fail the device-side checks are skipped and reported."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1704_02457_gb300 as bf
+from paper_1704_02457_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1704_02457_gb300.build import build
+    build()
+    bf.load()
+
+
+def put(X, ai=0, aj=0, fill=0.0, tight=False):
+    """One-problem batch holding X (numpy m x n) at offsets (ai, aj) of a
+    matrix two rows and columns larger than needed."""
+    m, n = X.shape
+    D = bf.DMatBatch(1, m + ai + 2, n + aj + 2, fill=fill, tight=tight)
+    if m and n:
+        bf.pack(torch.from_numpy(np.ascontiguousarray(X.T))[None].cuda().contiguous(), D, ai, aj)
+    return D
+
+
+def blank(m, n, ai=0, aj=0, fill=0.0, tight=False):
+    """One-problem output batch, every element `fill`."""
+    return bf.DMatBatch(1, m + ai + 2, n + aj + 2, fill=fill, tight=tight)
+
+
+def get(D):
+    torch.cuda.synchronize()
+    return D.to_colmajor()[0].cpu().numpy()
+
+
+def ints(rng, shape, lo=-8, hi=8):
+    return rng.integers(lo, hi + 1, size=shape).astype(float)
+
+
+def test_gemm_nt_uneven_sizes_offsets_and_bad_records():
+    rng = np.random.default_rng(1)
+    nb = 24
+    sizes, A, B, C, D, offs, want = [], [], [], [], [], [], []
+    for b in range(nb):
+        m, n, k = (int(x) for x in rng.integers(0, 41, size=3))
+        if b == 3:
+            m = 0
+        if b == 5:
+            k = 0
+        if b == 7:
+            m, n, k = 10, 12, 9
+        o = [int(x) for x in rng.integers(0, 6, size=8)]
+        Ab, Bb, Cb = ints(rng, (m, k)), ints(rng, (n, k)), ints(rng, (m, n))
+        sizes.append((m, n, k))
+        A.append(put(Ab, o[0], o[1]))
+        B.append(put(Bb, o[2], o[3]))
+        C.append(put(Cb, o[4], o[5]))
+        D.append(blank(m, n, o[6], o[7], fill=7.0))
+        offs.append(o)
+        want.append(oracle.dgemm_nt(-2.0, Ab, Bb, 3.0, Cb) if m and n else None)
+    # problem 7: A's row offset runs past the matrix; problem 9: m above max_m
+    bad_a = list(offs[7])
+    bad_a[0] = A[7].m - sizes[7][0] + 1
+    sizes[9] = (50, sizes[9][1], sizes[9][2])
+    recs = lambda L, k: bf.dsub_records([(M, 0, o[k], o[k + 1]) for M, o in zip(L, offs)])  # noqa: E731
+    Arec = bf.dsub_records([(M, 0, (bad_a if b == 7 else o)[0], o[1]) for b, (M, o) in enumerate(zip(A, offs))])
+    status = torch.full((nb,), 99, dtype=torch.int32, device="cuda")
+    bf.dgemm_nt_vbatched(nb, bf.dsize_records(sizes), -2.0, Arec, recs(B, 2), 3.0, recs(C, 4), recs(D, 6),
+                         40, 40, status=status)
+    st = status.cpu().numpy()
+    assert st[7] == -2 and st[9] == -1
+    assert np.all(np.delete(st, [7, 9]) == 0)
+    for b in range(nb):
+        got = get(D[b])
+        m, n, _ = sizes[b]
+        i, j = offs[b][6], offs[b][7]
+        if b in (7, 9):
+            assert np.all(got == 7.0)
+            continue
+        if m and n:
+            assert np.array_equal(got[i:i + m, j:j + n], want[b])
+        mask = np.ones(got.shape, dtype=bool)
+        mask[i:i + m, j:j + n] = False
+        assert np.all(got[mask] == 7.0)
+
+
+def test_syrk_ln_uneven_lower_only():
+    rng = np.random.default_rng(2)
+    nb = 17
+    sizes, A, C, D, want = [], [], [], [], []
+    for b in range(nb):
+        m, k = int(rng.integers(1, 50)), int(rng.integers(0, 30))
+        Ab, Cb = ints(rng, (m, k)), ints(rng, (m, m))
+        sizes.append((m, 0, k))
+        A.append(put(Ab, b % 4, 1))
+        C.append(put(Cb, 0, b % 3))
+        D.append(blank(m, m, b % 5, 0, fill=np.nan))
+        want.append(oracle.dsyrk_ln(1.0, Ab, Ab, 1.0, Cb, D0=np.full((m, m), np.nan)))
+    Ar = bf.dsub_records([(M, 0, b % 4, 1) for b, M in enumerate(A)])
+    Cr = bf.dsub_records([(M, 0, 0, b % 3) for b, M in enumerate(C)])
+    Dr = bf.dsub_records([(M, 0, b % 5, 0) for b, M in enumerate(D)])
+    status = torch.full((nb,), 99, dtype=torch.int32, device="cuda")
+    bf.dsyrk_ln_vbatched(nb, bf.dsize_records(sizes), 1.0, Ar, Ar, 1.0, Cr, Dr, 49, status=status)
+    assert np.all(status.cpu().numpy() == 0)
+    for b in range(nb):
+        m = sizes[b][0]
+        got = get(D[b])[b % 5:b % 5 + m, :m]
+        low = np.tril(np.ones((m, m), dtype=bool))
+        assert np.array_equal(got[low], want[b][low])
+        assert np.all(np.isnan(got[~low]))
+
+
+def test_potrf_uneven_with_inverse_diagonal_and_info():
+    rng = np.random.default_rng(3)
+    nb = 13
+    sizes, C, D, Ls = [], [], [], []
+    for b in range(nb):
+        m = int(rng.integers(1, 101))
+        L = inputs.int_lower_pow2(1, m, 60 + b)[0].numpy()
+        S = L @ L.T
+        if b == 4:
+            S[m // 2, m // 2] = -1.0   # not positive definite at column m//2 (or earlier)
+        sizes.append((m, 0, 0))
+        C.append(put(S, 1, 2))
+        D.append(blank(m, m, 0, 0, fill=0.0))   # inverse-diagonal room: not tight
+        Ls.append(L)
+    info = torch.full((nb,), -7, dtype=torch.int32, device="cuda")
+    status = torch.full((nb,), 99, dtype=torch.int32, device="cuda")
+    bf.dpotrf_l_vbatched(nb, bf.dsize_records(sizes), bf.dsub_records([(M, 0, 1, 2) for M in C]),
+                         bf.dsub_records([(M, 0, 0, 0) for M in D]), 100, want_dinv=True, info=info,
+                         status=status)
+    assert np.all(status.cpu().numpy() == 0)
+    inf = info.cpu().numpy()
+    for b in range(nb):
+        m = sizes[b][0]
+        _, _, info_o = oracle.dpotrf_l(C[b].to_colmajor()[0].cpu().numpy()[1:1 + m, 2:2 + m])
+        assert inf[b] == info_o
+        if b == 4:
+            assert inf[b] >= 1
+            continue
+        got = np.tril(get(D[b])[:m, :m])
+        assert np.array_equal(got, Ls[b])
+        dinv = D[b].dinv()[0, :m].cpu().numpy()
+        assert np.allclose(dinv * np.diag(Ls[b]), 1.0, rtol=0, atol=8 * np.finfo(float).eps)
+
+
+def test_trsm_uneven_rows_beyond_one_cta():
+    rng = np.random.default_rng(4)
+    nb = 9
+    sizes, L, B, D, X = [], [], [], [], []
+    for b in range(nb):
+        m, n = int(rng.integers(1, 400)), int(rng.integers(1, 70))
+        Lb = inputs.int_lower_pow2(1, n, 80 + b)[0].numpy()
+        Xb = ints(rng, (m, n))
+        sizes.append((m, n, 0))
+        L.append(put(Lb, 0, 0))
+        B.append(put(Xb @ Lb.T, 2, 1))
+        D.append(blank(m, n, 3, 0, fill=5.0))
+        X.append(Xb)
+    status = torch.full((nb,), 99, dtype=torch.int32, device="cuda")
+    bf.dtrsm_rltn_vbatched(nb, bf.dsize_records(sizes), 1.0, bf.dsub_records([(M, 0, 0, 0) for M in L]),
+                           bf.dsub_records([(M, 0, 2, 1) for M in B]), bf.dsub_records([(M, 0, 3, 0) for M in D]),
+                           399, 69, status=status)
+    assert np.all(status.cpu().numpy() == 0)
+    for b in range(nb):
+        m, n, _ = sizes[b]
+        got = get(D[b])
+        assert np.array_equal(got[3:3 + m, :n], X[b])
+        assert np.all(got[:3] == 5.0)
+
+
+def test_syrk_potrf_uneven_matches_oracle():
+    rng = np.random.default_rng(5)
+    nb = 11
+    sizes, A, C, D, want = [], [], [], [], []
+    for b in range(nb):
+        m, k = int(rng.integers(1, 90)), int(rng.integers(1, 40))
+        M = rng.standard_normal((m, k))
+        Q = m * np.eye(m)
+        sizes.append((m, 0, k))
+        A.append(put(M, b % 4, 0))
+        C.append(put(Q, 0, 0))
+        D.append(blank(m, m, 0, b % 3, fill=np.nan))
+        want.append(oracle.dsyrk_dpotrf_ln(M, M, Q)[0])
+    Ar = bf.dsub_records([(X, 0, b % 4, 0) for b, X in enumerate(A)])
+    info = torch.full((nb,), -7, dtype=torch.int32, device="cuda")
+    bf.dsyrk_dpotrf_ln_vbatched(nb, bf.dsize_records(sizes), Ar, Ar, bf.dsub_records([(X, 0, 0, 0) for X in C]),
+                                bf.dsub_records([(X, 0, 0, b % 3) for b, X in enumerate(D)]), 89, info=info)
+    assert np.all(info.cpu().numpy() == 0)
+    for b in range(nb):
+        m = sizes[b][0]
+        got = np.tril(get(D[b])[:m, b % 3:b % 3 + m])
+        assert np.linalg.norm(got - np.tril(want[b])) <= 1e-12 * np.linalg.norm(want[b])
