@@ -712,6 +712,8 @@ def run_gpu(args):
         result["next4"] = run_next4(args, dev)
     if not args.no_config1:
         result["config1"] = run_config1(args, dev)
+    if not args.no_vbatched:
+        result["vbatched"] = run_vbatched(args, dev)
     if not args.no_e2e:
         result["e2e"] = run_e2e(pts, args, dev, world)
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -1103,6 +1105,60 @@ def run_next4(args, dev):
     return out
 
 
+def run_vbatched(args, dev, batch=4096, nmin=8, nmax=128):
+    """The descriptor-array forms on uneven sizes: 4096 problems of order
+    n ~ U{8..128} (k = n), each in the top-left corner of a 128 x 128 slot,
+    through gemm_nt and syrk_potrf (SPD: M M^T + n I).  CUDA events around
+    `reps` launches after three warm-up launches."""
+    import numpy as np
+    import torch
+
+    import paper_1704_02457_gb300 as bf
+    from paper_1704_02457_gb300 import inputs
+
+    rng = np.random.default_rng(14000)
+    ns = rng.integers(nmin, nmax + 1, size=batch)
+    sizes = bf.dsize_records([(int(n), int(n), int(n)) for n in ns], device=dev)
+    mk = lambda seed: bf.DMatBatch.from_colmajor(inputs.normal((batch, nmax, nmax), seed, dev), tight=True)  # noqa: E731
+    A, B, C = mk(14001), mk(14002), mk(14003)
+    Q = torch.zeros(batch, nmax, nmax, dtype=torch.float64, device=dev)
+    Q.diagonal(dim1=1, dim2=2).copy_(torch.from_numpy(np.repeat(ns[:, None], nmax, 1)).to(dev).double())
+    Qd = bf.DMatBatch.from_colmajor(Q, tight=True)
+    del Q
+    D = bf.DMatBatch(batch, nmax, nmax, device=dev, tight=True)
+    rec = lambda M: bf.dsub_records([(M, b, 0, 0) for b in range(batch)], device=dev)  # noqa: E731
+    rA, rB, rC, rQ, rD = rec(A), rec(B), rec(C), rec(Qd), rec(D)
+    info = torch.zeros(batch, dtype=torch.int32, device=dev)
+    status = torch.zeros(batch, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+    calls = {
+        "dgemm_nt": (lambda: bf.dgemm_nt_vbatched(batch, sizes, 1.0, rA, rB, 1.0, rC, rD, nmax, nmax, status=status,
+                                                  stream=stream), float(sum(flops("dgemm_nt", int(n)) for n in ns))),
+        "dsyrk_dpotrf_ln": (lambda: bf.dsyrk_dpotrf_ln_vbatched(batch, sizes, rA, rA, rQ, rD, nmax, info=info,
+                                                                status=status, stream=stream),
+                            float(sum(flops("dsyrk_dpotrf_ln", int(n)) for n in ns))),
+    }
+    out = {}
+    for name, (fn, fl) in calls.items():
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        reps = max(3, args.steps)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        g = fl / (ms * 1e-3) / 1e9
+        out[name] = {"ms": round(ms, 4), "gflops": round(g, 2), "frac_of_fp64_alu_peak": round(g / FP64_PEAK_GFLOPS, 4)}
+    out["status_all_zero"] = bool((status == 0).all())
+    out["info_all_zero"] = bool((info == 0).all())
+    out["workload"] = "4096 problems, n ~ U{8..128}, k = n, descriptor-array forms (one launch per routine)"
+    return out
+
+
 # ---------------------------------------------------------- reference arm --
 
 def run_reference(args):
@@ -1152,6 +1208,7 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-next4", action="store_true")
     ap.add_argument("--no-config1", action="store_true")
+    ap.add_argument("--no-vbatched", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=0.15, help="seconds of oracle time per point")
     ap.add_argument("--ref-budget", type=float, default=0.06,
                     help="seconds of oracle time per point and step of the reference arm")
