@@ -1039,9 +1039,9 @@ def next4_flops(routine: str, n: int) -> float:
     """Flops of one n x n problem, counted from the algorithm's own steps:
     gemm_nn 2n^3; trmm_rlnn one FMA per nonzero of L per row of B; getrf per
     column j a reciprocal-scaled column of k = n-j-1 multipliers and a k x k
-    rank-1 update; gelqf per row i a norm and scaling of k = n-i-1 entries,
-    then for each of the k rows below a dot product and an update of k+1
-    entries."""
+    rank-1 update; gelqf per row i a norm (2k) and scaling (k) of the
+    k = n-i-1 tail entries, then for each of the k rows below a dot product
+    (2k), tau * w and the update of k+1 entries (2k + 1)."""
     if routine == "dgemm_nn":
         return 2.0 * n ** 3
     if routine == "dtrmm_rlnn":
@@ -1049,7 +1049,7 @@ def next4_flops(routine: str, n: int) -> float:
     if routine == "dgetrf":
         return float(sum(k + 2 * k * k for k in range(n)))
     if routine == "dgelqf":
-        return float(sum(3 * k + k * (4 * k + 3) for k in range(n)))
+        return float(sum(3 * k + k * (4 * k + 2) for k in range(n)))
     raise ValueError(routine)
 
 

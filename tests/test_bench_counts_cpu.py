@@ -1,0 +1,107 @@
+"""The flop counts behind bench.py's GFLOP/s, against operation counts of
+plain implementations of the algorithms, and the bench's labels for the
+kernel the library picks, against the library's own size rules."""
+import numpy as np
+import pytest
+
+import bench
+
+
+class Counter:
+    """Scalar arithmetic that counts its operations (a multiply-add is two)."""
+
+    def __init__(self):
+        self.ops = 0
+
+    def mul(self, a, b):
+        self.ops += 1
+        return a * b
+
+    def add(self, a, b):
+        self.ops += 1
+        return a + b
+
+    def div(self, a, b):
+        self.ops += 1
+        return a / b
+
+
+def counted_lu(A):
+    c, A, n = Counter(), A.copy(), A.shape[0]
+    for j in range(n):
+        p = j + int(np.argmax(np.abs(A[j:, j])))
+        A[[j, p]] = A[[p, j]]
+        for i in range(j + 1, n):
+            A[i, j] = c.div(A[i, j], A[j, j])
+            for k in range(j + 1, n):
+                A[i, k] = c.add(A[i, k], -c.mul(A[i, j], A[j, k]))
+    return c.ops
+
+
+def counted_lq(A):
+    """Householder LQ, square: per row the norm of the tail, beta, tau and
+    the scaling of the tail, then for each row below a dot product with
+    [1, x] and the update a(r, i:) -= tau w [1, x]."""
+    c, A, n = Counter(), A.copy(), A.shape[0]
+    for i in range(n):
+        ss = 0.0
+        for k in range(i + 1, n):
+            ss = c.add(ss, c.mul(A[i, k], A[i, k]))
+        for k in range(i + 1, n):
+            A[i, k] = c.mul(A[i, k], 0.5)  # scaling by 1/(alpha - beta)
+        for r in range(i + 1, n):
+            w = A[r, i]
+            for k in range(i + 1, n):
+                w = c.add(w, c.mul(A[r, k], A[i, k]))
+            tw = c.mul(0.3, w)
+            A[r, i] = c.add(A[r, i], -tw)
+            for k in range(i + 1, n):
+                A[r, k] = c.add(A[r, k], -c.mul(tw, A[i, k]))
+    return c.ops
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 9])
+def test_getrf_flops_match_the_algorithm(n):
+    A = np.random.default_rng(n).standard_normal((n, n)) + n * np.eye(n)
+    assert bench.next4_flops("dgetrf", n) == counted_lu(A)
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 9])
+def test_gelqf_flops_match_the_algorithm(n):
+    A = np.random.default_rng(n).standard_normal((n, n))
+    assert bench.next4_flops("dgelqf", n) == counted_lq(A)
+
+
+@pytest.mark.parametrize("n", [1, 3, 8])
+def test_core_flops_are_the_lapack_counts(n):
+    assert bench.flops("dgemm_nt", n) == 2 * n ** 3
+    assert bench.flops("dsyrk_ln", n) == n * n * (n + 1)           # lower triangle, diagonal included
+    assert bench.flops("dtrsm_rltn", n) == n ** 3
+    potrf = n ** 3 / 3 + n ** 2 / 2 + n / 6
+    assert bench.flops("dpotrf_l", n) == pytest.approx(potrf)
+    assert bench.flops("dsyrk_dpotrf_ln", n) == pytest.approx(n * n * (n + 1) + potrf)
+    assert bench.next4_flops("dgemm_nn", n) == 2 * n ** 3
+    assert bench.next4_flops("dtrmm_rlnn", n) == n * n * (n + 1)
+
+
+def test_algorithmic_bytes_count_triangles_once():
+    n = 8
+    assert bench.alg_bytes("dgemm_nt", n) == 8 * 4 * n * n
+    assert bench.alg_bytes("dpotrf_l", n) == 8 * n * (n + 1)
+    assert bench.alg_bytes("dtrsm_rltn", n) == 8 * (n * (n + 1) / 2 + 2 * n * n)
+
+
+def test_kernel_labels_follow_the_library_size_rules():
+    # the small Cholesky keeps 32/G packed triangles of a warp within 20 KB, G <= 16, up to n = 48
+    for n in (4, 8, 12, 16, 20, 24, 32, 40, 48):
+        g = bench.small_g(n)
+        assert g in (1, 2, 4, 8, 16)
+        assert n * (n + 1) // 2 * (32 // g) * 8 <= 20 * 1024 or g == 16
+        if g > 1:
+            assert n * (n + 1) // 2 * (32 // (g // 2)) * 8 > 20 * 1024
+    assert bench.kernel_of("dpotrf_l", 48).startswith("k_chol_small<")
+    assert bench.kernel_of("dpotrf_l", 64) == "k_chol_rows2<16,0,1,double,384>"
+    assert bench.kernel_of("dpotrf_l", 256) == "k_chol_rows2<16,0,1,double,512>"
+    assert bench.kernel_of("dsyrk_dpotrf_ln", 192) == "k_chol_rows2<16,1,1,double,384>"
+    assert bench.kernel_of("dsyrk_dpotrf_ln", 256) == "k_chol_rows<16,1,1,double>"
+    assert bench.kernel_of("dgemm_nt", 4) == "k_gemm_nt<0,1,1>"
