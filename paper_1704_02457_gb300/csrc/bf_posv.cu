@@ -114,14 +114,12 @@ __device__ __forceinline__ void residual(int n, const double *pa, const Op &A, c
     double acc[NR];
 #pragma unroll
     for (int k = 0; k < NR; k++) acc[k] = 0.0;
+    // one loop over j for every lane (A(i, j) from row i below the diagonal,
+    // A(j, i) from column i above it): two loops of lane-dependent lengths
+    // would run n + 31 masked FP64 iterations per warp instead of n
     const double *arow = pa + pm_off(A.i0 + i, A.j0, A.cn);
-    for (int j = 0; j <= i; j++) {
-      const double a = arow[(long long)j * PS];
-#pragma unroll
-      for (int k = 0; k < NR; k++) acc[k] = fma(a, x64[k * n + j], acc[k]);
-    }
-    for (int j = i + 1; j < n; j++) {
-      const double a = pa[pm_off(A.i0 + j, A.j0 + i, A.cn)];
+    for (int j = 0; j < n; j++) {
+      const double a = (j <= i) ? arow[(long long)j * PS] : pa[pm_off(A.i0 + j, A.j0 + i, A.cn)];
 #pragma unroll
       for (int k = 0; k < NR; k++) acc[k] = fma(a, x64[k * n + j], acc[k]);
     }
@@ -196,14 +194,17 @@ k_posv(int n, int nrhs, Op A, const float *l32, long long sl32, const int *info3
 
   // ||A||_F from the lower triangle (off-diagonal entries count twice)
   const double *pa = A.p + b * A.stride;
-  double s = 0.0;
+  double sd = 0.0, so = 0.0;  // diagonal and off-diagonal sums of squares: one FMA per entry
   for (int e = t; e < NE; e += T) {
     const int l = packed_col(e, n);
     const int i = e - col_start(l, n);
     const double a = pa[pm_off(A.i0 + i, A.j0 + l, A.cn)];
-    s += (i == l ? 1.0 : 2.0) * a * a;
+    if (i == l)
+      sd = fma(a, a, sd);
+    else
+      so = fma(a, a, so);
   }
-  const double anrm = sqrt(block_sum(s, red));
+  const double anrm = sqrt(block_sum(fma(2.0, so, sd), red));
 
   int it = 0;
   double rel = 0.0;
