@@ -274,6 +274,9 @@ struct __align__(16) RowsSmem {
 #ifndef BF_ROWS_P2_MAX_N
 #define BF_ROWS_P2_MAX_N 256
 #endif
+#ifndef BF_ROWS_P2_FP32
+#define BF_ROWS_P2_FP32 0
+#endif
 #ifndef BF_ROWS_P2_MAX_N_FUSED
 #define BF_ROWS_P2_MAX_N_FUSED 192
 #endif
@@ -556,7 +559,7 @@ cudaError_t launch_rows_a(bool aligned, int batch, int n, int k, Op A, Op B, Op 
 template <bool FUSED, typename T>
 cudaError_t launch_rows(bool aligned, int batch, int n, int k, Op A, Op B, Op C, OpWT<T> D, T *dinv,
                         long long sdinv, int *info, cudaStream_t s) {
-  if constexpr (sizeof(T) == 8) {  // the FP32 factor of the mixed solver keeps one problem per CTA
+  if constexpr (sizeof(T) == 8 || BF_ROWS_P2_FP32) {  // by default the FP32 factor keeps one problem per CTA
     constexpr int p2_max = FUSED ? BF_ROWS_P2_MAX_N_FUSED : BF_ROWS_P2_MAX_N;
     if (n <= 192 && n <= p2_max)
       return launch_rows_a<384, FUSED, T>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
