@@ -141,6 +141,8 @@ def kernel_of(routine, n):
     if routine == "dsyrk_ln":
         return "k_gemm_nt<1,1,1>"
     if routine == "dtrsm_rltn":
+        if n <= 32:
+            return f"k_trsm_rltn_w<{4 if n <= 4 else (n + 7) // 8 * 8}>"
         return "k_trsm_rltn"
     fused = int(routine == "dsyrk_dpotrf_ln")
     if n <= 48 and small_g(n):

@@ -142,6 +142,30 @@ k_trsm_rltn(int batch, int m, int n, double alpha, Op L, const double *dinv, lon
   }
 }
 
+// n <= 32: a single column block of width bucket W, in a kernel of its own so
+// that its register count is that of W (the blocked kernel carries the
+// W = 32 path, whose register count would cap the small widths' occupancy).
+template <int W>
+__global__ void __launch_bounds__(MAX_ROWS)
+k_trsm_rltn_w(int batch, int m, int n, double alpha, Op L, const double *dinv, long long sdinv, Op B,
+              OpW D, int P, int R, int chunks) {
+  extern __shared__ double smem[];
+  const int pb0 = (blockIdx.x / chunks) * P;
+  const int r0 = (blockIdx.x % chunks) * R;
+  trsm_block<W>(smem, P, R, 0, m, n, alpha, pb0, batch, r0, L, dinv, sdinv, B, D);
+}
+
+template <int W>
+cudaError_t launch_trsm_w(unsigned g, int threads, size_t smem, cudaStream_t s, int batch, int m, int n,
+                          double alpha, Op L, const double *dinv, long long sdinv, Op B, OpW D, int P, int R,
+                          int chunks) {
+  static std::atomic<unsigned long long> attr{0};
+  cudaError_t e = smem_attr_once((const void *)k_trsm_rltn_w<W>, 200 * 1024, attr);
+  if (e != cudaSuccess) return e;
+  k_trsm_rltn_w<W><<<g, threads, smem, s>>>(batch, m, n, alpha, L, dinv, sdinv, B, D, P, R, chunks);
+  return cudaGetLastError();
+}
+
 // Descriptor-array form: CTA = (problem, chunk of MAX_ROWS rows of X), one
 // problem per CTA, after checking the problem's record.
 __global__ void __launch_bounds__(MAX_ROWS)
@@ -231,7 +255,17 @@ cudaError_t launch_trsm_rltn(int batch, int m, int n, double alpha, Op L, const 
   if (e != cudaSuccess) return e;
   const long long blocks = (long long)((batch + P - 1) / P) * chunks;
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-  k_trsm_rltn<<<(unsigned)blocks, threads, smem, s>>>(batch, m, n, alpha, L, dinv, sdinv, B, D, P, R, chunks);
+  const unsigned g = (unsigned)blocks;
+  if (n <= 32) {
+    switch (W) {
+      case 4: return launch_trsm_w<4>(g, threads, smem, s, batch, m, n, alpha, L, dinv, sdinv, B, D, P, R, chunks);
+      case 8: return launch_trsm_w<8>(g, threads, smem, s, batch, m, n, alpha, L, dinv, sdinv, B, D, P, R, chunks);
+      case 16: return launch_trsm_w<16>(g, threads, smem, s, batch, m, n, alpha, L, dinv, sdinv, B, D, P, R, chunks);
+      case 24: return launch_trsm_w<24>(g, threads, smem, s, batch, m, n, alpha, L, dinv, sdinv, B, D, P, R, chunks);
+      default: return launch_trsm_w<32>(g, threads, smem, s, batch, m, n, alpha, L, dinv, sdinv, B, D, P, R, chunks);
+    }
+  }
+  k_trsm_rltn<<<g, threads, smem, s>>>(batch, m, n, alpha, L, dinv, sdinv, B, D, P, R, chunks);
   return cudaGetLastError();
 }
 
