@@ -99,16 +99,16 @@ TRAFFIC = {
         "blob": "2cc3b29e43bfc36765f132c96806ac9719670d40",
         "profile": "profiles/k_gemm_nt_n256.md",
     },
-    ("k_chol_rows<16,1,1,double>", "dsyrk_dpotrf_ln", 256): {
-        "bytes": 5531602688 + 255609344,
+    ("k_chol_rows2<16,1,1,double,512>", "dsyrk_dpotrf_ln", 256): {
+        "bytes": 5684378880 + 266692352,
         "src": "paper_1704_02457_gb300/csrc/bf_chol.cu",
-        "blob": "d3e153f4d96ed7a2bddbdd9a250ecdf563948a7f",
-        "profile": "profiles/k_chol_rows_syrk_potrf_n256.md",
+        "blob": "14e8434c67321ab73502d2863abf62a38e0bbc76",
+        "profile": "profiles/k_chol_rows2_syrk_potrf_n256.md",
     },
     ("k_chol_rows2<16,1,1,double,384>", "dsyrk_dpotrf_ln", 128): {
-        "bytes": 1538729728 + 253031936,
+        "bytes": 1884979200 + 281203200,
         "src": "paper_1704_02457_gb300/csrc/bf_chol.cu",
-        "blob": "d3e153f4d96ed7a2bddbdd9a250ecdf563948a7f",
+        "blob": "14e8434c67321ab73502d2863abf62a38e0bbc76",
         "profile": "profiles/k_chol_rows2_syrk_potrf_n128.md",
     },
 }
@@ -145,12 +145,12 @@ def kernel_of(routine, n):
             return f"k_trsm_rltn_w<{4 if n <= 4 else (n + 7) // 8 * 8}>"
         return "k_trsm_rltn"
     fused = int(routine == "dsyrk_dpotrf_ln")
-    if n <= 48 and small_g(n):
+    if n <= 40 and small_g(n):
         return f"k_chol_small<{small_g(n)},{fused},1>"
     if n <= 192:
         return f"k_chol_rows2<16,{fused},1,double,384>"
-    if n <= 256 and not fused:
-        return "k_chol_rows2<16,0,1,double,512>"
+    if n <= 256:
+        return f"k_chol_rows2<16,{fused},1,double,512>"
     return f"k_chol_rows<16,{fused},1,double>"
 
 

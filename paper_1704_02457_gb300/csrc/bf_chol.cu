@@ -12,7 +12,7 @@
 // reciprocal cost several FMAs each, so the sequential part of a small
 // Cholesky must be shared by many problems at once.  Two kernels:
 //
-//  k_chol_small (n <= 48): a warp holds Q = 32/G problems, G lanes per
+//  k_chol_small (n <= 40): a warp holds Q = 32/G problems, G lanes per
 //    problem.  The lower triangles live packed in shared memory, problem q's
 //    element e at sm[e*Q + q].  The factorization runs column by column
 //    (Cholesky-Crout); the pivot's rsqrt is one warp instruction for all Q
@@ -20,10 +20,10 @@
 //    straight into the shared-memory triangle before the factorization.
 //
 //  k_chol_rows (n <= 512): one thread per row, blocks of 16 columns held in
-//    registers, P problems per CTA (P = 2 up to n = 256 for potrf and 192 for
-//    syrk_potrf: a warp holds 16 rows of each of the two problems, so the
-//    diagonal block of a block column is one full warp; P = 1 above).  For
-//    block column [c0, c0+16):
+//    registers, P problems per CTA (P = 2 up to n = 256: a warp holds 16 rows
+//    of each of the two problems, so the diagonal block of a block column is
+//    one full warp, which computes only the block's lower triangle, spread
+//    evenly over its lanes; P = 1 above).  For block column [c0, c0+16):
 //      (a) acc = C[i][c0..]  (+ A[i][:] * B[c0..][:]^T for syrk_potrf)
 //      (b) acc -= L[i][0:c0] * L[c0..][0:c0]^T            (gemm_nt downdate)
 //      (c) the lanes of rows c0..c0+15 factor the diagonal block in
@@ -268,17 +268,20 @@ struct __align__(16) RowsSmem {
 
 // Two problems per CTA (RowMap<2>) up to these orders.  The CTA of 2n
 // threads must leave room for two CTAs per SM, or the FP64 pipes idle while
-// one warp factors a diagonal block: at n = 256 that caps registers at 64,
-// which potrf fits without spilling and syrk_potrf does not (measured on the
-// sweep: potrf n = 256 goes from 910 to 1000 GFLOP/s, syrk_potrf drops).
+// one warp factors a diagonal block: at n = 256 that caps registers at 64.
+// Measured at n = 256: potrf 910 -> 1000 GFLOP/s; syrk_potrf 969 -> 938
+// before the diagonal warp's triangle split, 968 -> 988 with it.
 #ifndef BF_ROWS_P2_MAX_N
 #define BF_ROWS_P2_MAX_N 256
+#endif
+#ifndef BF_ROWS_SPLIT
+#define BF_ROWS_SPLIT 1  // balanced triangle split of the diagonal warp's k-loops
 #endif
 #ifndef BF_ROWS_P2_FP32
 #define BF_ROWS_P2_FP32 0
 #endif
 #ifndef BF_ROWS_P2_MAX_N_FUSED
-#define BF_ROWS_P2_MAX_N_FUSED 192
+#define BF_ROWS_P2_MAX_N_FUSED 256
 #endif
 
 #ifndef BF_ROWS_KUNROLL
@@ -303,6 +306,22 @@ struct RowMap {
   }
 };
 
+// Balanced split of a 16 x 16 lower triangle (136 entries) over 16 lanes:
+// lane s takes row s up to column min(s, 8), and lanes s <= 6 also take row
+// 15 - s from column 9 on.  Slot m (0..8) of lane s is entry (row, col);
+// lanes 0..7 use slots 0..7, lanes 8..15 slots 0..8.
+__device__ __forceinline__ void split_slot(int s, int m, int &row, int &col, bool &valid) {
+  if (s >= 8 || m <= s) {
+    row = s;
+    col = m;
+    valid = m <= s;
+  } else {
+    row = 15 - s;
+    col = 8 + m - s;
+    valid = m <= 7;
+  }
+}
+
 // One block column [c0, c0 + BW) of the factorization.  W is the number of
 // accumulators (the block's width rounded up to a multiple of 8).  The
 // diagonal block's rows c0..c0+BW-1 of problem p are lanes
@@ -320,12 +339,21 @@ __device__ __forceinline__ void rows_block(RowsSmem<T, BW, P> &S, const RowMap<P
   const int w = min(BW, n - c0);
   const bool active = me_valid && (i < n) && (i >= c0);
   T acc[W];
+  // Two problems per CTA, full 16-column block: the warp of the diagonal
+  // block (16 rows of each problem) computes only the block's lower triangle
+  // in (a') and (b), spread over its lanes by split_slot: at most 9 FMAs per
+  // step a lane instead of 16.  Its rows are gathered back before (c).
+  constexpr bool SPLIT = BF_ROWS_SPLIT && (P == 2 && BW == 16 && W == 16);
+  const bool dwarp = SPLIT && ((t >> 5) == c0 / RPW);  // warp-uniform
+  const int s16 = rm.lane & 15;                         // row within the diagonal block
 
-  // (a) C[i][c0 + jj] for the lower part of the block column
+  // (a) C[i][c0 + jj] for the lower part of the block column.  The diagonal
+  // warp keeps its 9 triangle slots in acc[0..8] until it gathers its rows,
+  // and adds C then.
 #pragma unroll
   for (int jj = 0; jj < W; jj++) {
     const int col = c0 + jj;
-    acc[jj] = (active && jj < w && i >= col) ? (T)pc[pm_off(C.i0 + i, C.j0 + col, C.cn)] : (T)0;
+    acc[jj] = (!dwarp && active && jj < w && i >= col) ? (T)pc[pm_off(C.i0 + i, C.j0 + col, C.cn)] : (T)0;
   }
 
   // (a') syrk_potrf: += A[i][:] * B[c0..c0+w)[:]^T, B rows staged per chunk
@@ -344,7 +372,22 @@ __device__ __forceinline__ void rows_block(RowsSmem<T, BW, P> &S, const RowMap<P
                 : (T)0;
       }
       __syncthreads();
-      if (active) {
+      if (dwarp) {
+        const int ro = 15 - s16, smax = s16 >= 8 ? 8 : s16;  // slots m <= smax are on the lane's own row
+        const bool own_ok = me_valid && s16 < w, oth_ok = me_valid && s16 <= 6 && ro < w;
+        const double *arow_o = pa + pm_off(A.i0 + min(c0 + ro, n - 1), A.j0, A.cn);
+        const int obase = max(0, 8 - s16);  // other-row slot m reads column 8 + m - s16
+        for (int ll = 0; ll < kc; ll++) {
+          const T xo = own_ok ? (T)__ldg(arow + (long long)(l0 + ll) * PS) : (T)0;
+          const T xt = oth_ok ? (T)__ldg(arow_o + (long long)(l0 + ll) * PS) : (T)0;
+          const T *st = S.stage[p][ll];
+#pragma unroll
+          for (int m = 0; m < 9; m++) {
+            const bool own = m <= smax;
+            acc[m] = fma_t(own ? xo : xt, own ? st[m] : st[min(obase + m, 15)], acc[m]);
+          }
+        }
+      } else if (active) {
 #pragma unroll ROWS_KUNROLL
         for (int ll = 0; ll < kc; ll++) {
           const T x = (T)__ldg(arow + (long long)(l0 + ll) * PS);
@@ -375,7 +418,18 @@ __device__ __forceinline__ void rows_block(RowsSmem<T, BW, P> &S, const RowMap<P
                 : (T)0;
       }
       __syncthreads();
-      if (active) {
+      if (dwarp) {
+        const int smax = s16 >= 8 ? 8 : s16, obase = max(0, 8 - s16);
+        for (int ll = 0; ll < kc; ll++) {
+          const T *st = S.stage[p][ll];
+          const T xo = st[s16], xt = st[15 - s16];
+#pragma unroll
+          for (int m = 0; m < 9; m++) {
+            const bool own = m <= smax;
+            acc[m] = fma_t(-(own ? xo : xt), own ? st[m] : st[min(obase + m, 15)], acc[m]);
+          }
+        }
+      } else if (active) {
 #pragma unroll 2
         for (int ll = 0; ll < kc; ll++) {
           const T x = lrow[(long long)(l0 + ll) * PS];
@@ -388,6 +442,25 @@ __device__ __forceinline__ void rows_block(RowsSmem<T, BW, P> &S, const RowMap<P
         }
       }
     }
+  }
+
+  // the diagonal warp: slots to shared memory, then each lane its row, plus C
+  if (dwarp) {
+#pragma unroll
+    for (int m = 0; m < 9; m++) {
+      int row, col;
+      bool ok;
+      split_slot(s16, m, row, col, ok);
+      if (ok) S.Ls[p][row][col] = acc[m];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int jj = 0; jj < W; jj++) {
+      const bool lower = jj <= s16;
+      const T cv = (me_valid && s16 < w && jj < w && lower) ? (T)pc[pm_off(C.i0 + i, C.j0 + c0 + jj, C.cn)] : (T)0;
+      acc[jj] = cv + (lower ? S.Ls[p][s16][jj] : (T)0);
+    }
+    __syncwarp();
   }
 
   // (c) diagonal block: its rows are lanes base..base+BW-1 of one warp, which
@@ -578,10 +651,10 @@ cudaError_t launch_rows(bool aligned, int batch, int n, int k, Op A, Op B, Op C,
 constexpr long long SMALL_SMEM_BUDGET = 20 * 1024;
 
 // Largest order factored by k_chol_small; the row kernel takes over above
-// (measured: at n = 64 the two-problem row kernel is 25% faster for potrf and
-// 6% for syrk_potrf, at n = 40 and 48 it is slower).
+// (measured with the triangle split: at n = 48 the two-problem row kernel is
+// 12% faster for potrf and 9% for syrk_potrf, at n = 40 it is slower).
 #ifndef BF_CHOL_SMALL_MAX_N
-#define BF_CHOL_SMALL_MAX_N 48
+#define BF_CHOL_SMALL_MAX_N 40
 #endif
 int pick_small_g(int n) {
   const long long ne = (long long)n * (n + 1) / 2;

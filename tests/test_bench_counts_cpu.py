@@ -92,16 +92,18 @@ def test_algorithmic_bytes_count_triangles_once():
 
 
 def test_kernel_labels_follow_the_library_size_rules():
-    # the small Cholesky keeps 32/G packed triangles of a warp within 20 KB, G <= 16, up to n = 48
-    for n in (4, 8, 12, 16, 20, 24, 32, 40, 48):
+    # the small Cholesky keeps 32/G packed triangles of a warp within 20 KB, G <= 16, up to n = 40
+    for n in (4, 8, 12, 16, 20, 24, 32, 40):
         g = bench.small_g(n)
         assert g in (1, 2, 4, 8, 16)
         assert n * (n + 1) // 2 * (32 // g) * 8 <= 20 * 1024 or g == 16
         if g > 1:
             assert n * (n + 1) // 2 * (32 // (g // 2)) * 8 > 20 * 1024
-    assert bench.kernel_of("dpotrf_l", 48).startswith("k_chol_small<")
+    assert bench.kernel_of("dpotrf_l", 40).startswith("k_chol_small<")
+    assert bench.kernel_of("dpotrf_l", 48) == "k_chol_rows2<16,0,1,double,384>"
     assert bench.kernel_of("dpotrf_l", 64) == "k_chol_rows2<16,0,1,double,384>"
     assert bench.kernel_of("dpotrf_l", 256) == "k_chol_rows2<16,0,1,double,512>"
     assert bench.kernel_of("dsyrk_dpotrf_ln", 192) == "k_chol_rows2<16,1,1,double,384>"
-    assert bench.kernel_of("dsyrk_dpotrf_ln", 256) == "k_chol_rows<16,1,1,double>"
+    assert bench.kernel_of("dsyrk_dpotrf_ln", 256) == "k_chol_rows2<16,1,1,double,512>"
+    assert bench.kernel_of("dsyrk_dpotrf_ln", 300) == "k_chol_rows<16,1,1,double>"
     assert bench.kernel_of("dgemm_nt", 4) == "k_gemm_nt<0,1,1>"
