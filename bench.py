@@ -128,7 +128,7 @@ def small_g(n):
     ne = n * (n + 1) // 2
     g = 1
     while g <= 16:
-        if ne * (32 // g) * 8 <= 20 * 1024:
+        if ne * (32 // g) * 8 <= 26 * 1024:
             return g
         g *= 2
     return 16 if ne * 2 * 8 <= 48 * 1024 else 0
@@ -145,6 +145,8 @@ def kernel_of(routine, n):
             return f"k_trsm_rltn_w<{4 if n <= 4 else (n + 7) // 8 * 8}>"
         return "k_trsm_rltn"
     fused = int(routine == "dsyrk_dpotrf_ln")
+    if n <= 8:  # the sweep's batches give one lane per problem
+        return f"k_chol_tiny<{n},{fused},1>"
     if n <= 40 and small_g(n):
         return f"k_chol_small<{small_g(n)},{fused},1>"
     if n <= 192:
@@ -152,6 +154,19 @@ def kernel_of(routine, n):
     if n <= 256:
         return f"k_chol_rows2<16,{fused},1,double,512>"
     return f"k_chol_rows<16,{fused},1,double>"
+
+
+def launches_of(routine, n, batch, sms=152):
+    """Kernel launches of one call at this sweep.  The Cholesky of orders
+    193..256 splits a batch whose last wave of two-problem CTAs (two per SM)
+    holds more pairs than SMs but at most 80% of its slots: the pairs of the
+    full waves, then the rest one problem per CTA."""
+    if routine in ("dpotrf_l", "dsyrk_dpotrf_ln") and 192 < n <= 256:
+        slots, pairs = 2 * sms, (batch + 1) // 2
+        rest = pairs % slots
+        if pairs > slots and sms < rest and rest * 100 <= slots * 80:
+            return 2
+    return 1
 
 
 WORKLOAD = ("FP64 routine sweep: dgemm_nt, dsyrk_ln, dpotrf_l, dtrsm_rltn, dsyrk_dpotrf_ln "
@@ -598,6 +613,7 @@ def run_gpu(args):
         keep = set(args.points.split(","))
         spec = [(r, n) for r, n in spec if f"{r}@{n}" in keep or r in keep or str(n) in keep]
     hbm, hbm_src = measured_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
     pts = []
     for i, (r, n) in enumerate(spec):
         pts.append(Point(r, n, dev, seed=5000 + 97 * i))
@@ -697,7 +713,7 @@ def run_gpu(args):
         "dtype": "f64",
         "data": "synthetic (seeded iid N(0,1), SPD M M^T + n I)",
         "config": config_dict(spec),
-        "gpu_launches": len(pts) * K,
+        "gpu_launches": sum(launches_of(p.routine, p.n, p.batch, sms) for p in pts) * K,
         "clocks": clocks,
         "roofline": roof_obj,
         "per_point": per_point,

@@ -10,11 +10,18 @@
 // changes on GB300 is where the lanes go.  A warp-wide FP64 instruction costs
 // the same with 1 or 32 active lanes, and the per-column square root and
 // reciprocal cost several FMAs each, so the sequential part of a small
-// Cholesky must be shared by many problems at once.  Two kernels:
+// Cholesky must be shared by many problems at once.  Three kernels:
+//
+//  k_chol_tiny (n <= 8, when the batch gives one lane per problem at least
+//    one warp per SM sub-partition): one lane per problem, the whole
+//    triangle in registers, factored right-looking with compile-time indices.
 //
 //  k_chol_small (n <= 40): a warp holds Q = 32/G problems, G lanes per
 //    problem.  The lower triangles live packed in shared memory, problem q's
-//    element e at sm[e*Q + q].  The factorization runs column by column
+//    element e at sm[e*Q' + q], Q' = Q + 1 for Q >= 16: the odd pitch puts
+//    the elements that the load and store phases copy for one problem (lanes
+//    along e) in distinct banks, as it does the G rows read at once in the
+//    factorization.  The factorization runs column by column
 //    (Cholesky-Crout); the pivot's rsqrt is one warp instruction for all Q
 //    problems.  For syrk_potrf the A*B^T sum is added in 4x4 register blocks
 //    straight into the shared-memory triangle before the factorization.
@@ -67,11 +74,24 @@ __device__ __forceinline__ int col_start(int l, int n) { return (l * (2 * n - l 
 // ---------------------------------------------------------------------------
 // k_chol_small
 // ---------------------------------------------------------------------------
+#ifndef BF_SMALL_PAD
+#define BF_SMALL_PAD 1
+#endif
+// The pad applies from 16 problems per warp (G <= 2), where the copies'
+// conflicts were worst (potrf n = 16: 523 -> 579 GFLOP/s); with 8 or 4
+// problems per warp the extra shared memory cost more resident warps than
+// the conflicts (n = 24: 649 -> 631 padded).
+#ifndef BF_SMALL_PAD_MINQ
+#define BF_SMALL_PAD_MINQ 16
+#endif
+// problem pitch of the shared-memory triangles of k_chol_small
+__host__ __device__ constexpr int small_pitch(int q) { return q + ((q >= BF_SMALL_PAD_MINQ) ? BF_SMALL_PAD : 0); }
 template <int G, bool FUSED, bool ALIGNED>
 __global__ void __launch_bounds__(32)
 k_chol_small(int batch, int n, int k, Op A, Op B, Op C, OpW D, double *dinv, long long sdinv,
              int *info) {
   constexpr int Q = 32 / G;
+  constexpr int QP = small_pitch(Q);
   extern __shared__ double sm[];
   const int lane = threadIdx.x;
   const int q = lane / G, s = lane % G;
@@ -93,13 +113,13 @@ k_chol_small(int batch, int n, int k, Op A, Op B, Op C, OpW D, double *dinv, lon
         const double *pp = pc + (long long)(C.i0 + p * PS) * C.cn + (long long)C.j0 * PS;
         for (int x = lane; x < ncol * PS; x += 32) {
           const int j = x / PS, i = p * PS + (x % PS);
-          if (i < n && i >= j) cp_async8(&sm[(col_start(j, n) + i) * Q + qq], pp + x);
+          if (i < n && i >= j) cp_async8(&sm[(col_start(j, n) + i) * QP + qq], pp + x);
         }
       }
     } else {
       for (int x = lane; x < n * n; x += 32) {
         const int j = x / n, i = x - j * n;
-        if (i >= j) cp_async8(&sm[(col_start(j, n) + i) * Q + qq], pc + pm_off(C.i0 + i, C.j0 + j, C.cn));
+        if (i >= j) cp_async8(&sm[(col_start(j, n) + i) * QP + qq], pc + pm_off(C.i0 + i, C.j0 + j, C.cn));
       }
     }
   }
@@ -162,7 +182,7 @@ k_chol_small(int batch, int n, int k, Op A, Op B, Op C, OpW D, double *dinv, lon
 #pragma unroll
         for (int c = 0; c < 4; c++) {
           const int i = i0 + r, j = j0 + c;
-          if (i < n && i >= j) sm[(col_start(j, n) + i) * Q + q] += acc[r][c];
+          if (i < n && i >= j) sm[(col_start(j, n) + i) * QP + q] += acc[r][c];
         }
     }
   }
@@ -177,32 +197,32 @@ k_chol_small(int batch, int n, int k, Op A, Op B, Op C, OpW D, double *dinv, lon
     int i = istart;
     // four rows at a time share the loads of row j
     for (; i + 3 * G < n; i += 4 * G) {
-      double a0 = sm[(cj + i) * Q + q], a1 = sm[(cj + i + G) * Q + q];
-      double a2 = sm[(cj + i + 2 * G) * Q + q], a3 = sm[(cj + i + 3 * G) * Q + q];
+      double a0 = sm[(cj + i) * QP + q], a1 = sm[(cj + i + G) * QP + q];
+      double a2 = sm[(cj + i + 2 * G) * QP + q], a3 = sm[(cj + i + 3 * G) * QP + q];
       int cl = 0;
       for (int l = 0; l < j; l++) {
-        const double ljl = sm[(cl + j) * Q + q];
-        a0 = fma(-sm[(cl + i) * Q + q], ljl, a0);
-        a1 = fma(-sm[(cl + i + G) * Q + q], ljl, a1);
-        a2 = fma(-sm[(cl + i + 2 * G) * Q + q], ljl, a2);
-        a3 = fma(-sm[(cl + i + 3 * G) * Q + q], ljl, a3);
+        const double ljl = sm[(cl + j) * QP + q];
+        a0 = fma(-sm[(cl + i) * QP + q], ljl, a0);
+        a1 = fma(-sm[(cl + i + G) * QP + q], ljl, a1);
+        a2 = fma(-sm[(cl + i + 2 * G) * QP + q], ljl, a2);
+        a3 = fma(-sm[(cl + i + 3 * G) * QP + q], ljl, a3);
         cl += n - l - 1;
       }
       if (i == j) dval = a0;
-      sm[(cj + i) * Q + q] = a0;
-      sm[(cj + i + G) * Q + q] = a1;
-      sm[(cj + i + 2 * G) * Q + q] = a2;
-      sm[(cj + i + 3 * G) * Q + q] = a3;
+      sm[(cj + i) * QP + q] = a0;
+      sm[(cj + i + G) * QP + q] = a1;
+      sm[(cj + i + 2 * G) * QP + q] = a2;
+      sm[(cj + i + 3 * G) * QP + q] = a3;
     }
     for (; i < n; i += G) {
-      double a0 = sm[(cj + i) * Q + q];
+      double a0 = sm[(cj + i) * QP + q];
       int cl = 0;
       for (int l = 0; l < j; l++) {
-        a0 = fma(-sm[(cl + i) * Q + q], sm[(cl + j) * Q + q], a0);
+        a0 = fma(-sm[(cl + i) * QP + q], sm[(cl + j) * QP + q], a0);
         cl += n - l - 1;
       }
       if (i == j) dval = a0;
-      sm[(cj + i) * Q + q] = a0;
+      sm[(cj + i) * QP + q] = a0;
     }
     // pivot of problem q comes from its sub-lane that owns row j
     const double d = (G == 1) ? dval : __shfl_sync(FULL, dval, q * G + (j % G));
@@ -210,9 +230,9 @@ k_chol_small(int batch, int n, int k, Op A, Op B, Op C, OpW D, double *dinv, lon
     if (!(d > 0.0) && first_bad == 0) first_bad = j + 1;
     for (int ii = istart; ii < n; ii += G) {
       if (ii == j)
-        sm[(cj + ii) * Q + q] = d * r;
+        sm[(cj + ii) * QP + q] = d * r;
       else
-        sm[(cj + ii) * Q + q] *= r;
+        sm[(cj + ii) * QP + q] *= r;
     }
     if (dinv && valid && s == (j % G)) dinv[b * sdinv + j] = r;
     __syncwarp();
@@ -229,17 +249,135 @@ k_chol_small(int batch, int n, int k, Op A, Op B, Op C, OpW D, double *dinv, lon
         double *pp = pd + (long long)(D.i0 + p * PS) * D.cn + (long long)D.j0 * PS;
         for (int x = lane; x < ncol * PS; x += 32) {
           const int j = x / PS, i = p * PS + (x % PS);
-          if (i < n && i >= j) pp[x] = sm[(col_start(j, n) + i) * Q + qq];
+          if (i < n && i >= j) pp[x] = sm[(col_start(j, n) + i) * QP + qq];
         }
       }
     } else {
       for (int x = lane; x < n * n; x += 32) {
         const int j = x / n, i = x - j * n;
-        if (i >= j) pd[pm_off(D.i0 + i, D.j0 + j, D.cn)] = sm[(col_start(j, n) + i) * Q + qq];
+        if (i >= j) pd[pm_off(D.i0 + i, D.j0 + j, D.cn)] = sm[(col_start(j, n) + i) * QP + qq];
       }
     }
   }
   if (info && valid && s == 0) info[b] = first_bad;
+}
+
+// ---------------------------------------------------------------------------
+// k_chol_tiny (n <= 8): one lane per problem, the whole triangle in registers
+// ---------------------------------------------------------------------------
+// With 32 problems per warp every FP64 instruction does useful work for 32
+// problems, the pivot's rsqrt included, and there is no shared memory to
+// stage through: each lane reads its own problem's lower triangle (pairs of
+// rows of a column are one 16-byte load when the operands are aligned),
+// factors it right-looking with compile-time indices, and writes the lower
+// triangle back.
+
+// element (i, j) of an operand whose top row is a panel top (i0 % PS == 0)
+__device__ __forceinline__ long long tiny_off(int i, int j, int cn) {
+  return (long long)(i & ~(PS - 1)) * cn + (long long)j * PS + (i & (PS - 1));
+}
+
+template <int N, bool ALIGNED>
+__device__ __forceinline__ void tiny_load_lower(double (&c)[N][N], const double *p, const Op &o) {
+  if (ALIGNED) {
+    const double *base = p + (long long)o.i0 * o.cn + (long long)o.j0 * PS;
+#pragma unroll
+    for (int j = 0; j < N; j++)
+#pragma unroll
+      for (int i = j; i < N; i++) {
+        if ((i & 1) == 0 && i + 1 < N) {
+          const double2 v = __ldg((const double2 *)(base + tiny_off(i, j, o.cn)));
+          c[i][j] = v.x;
+          c[i + 1][j] = v.y;
+        } else if (!((i & 1) == 1 && i - 1 >= j)) {
+          c[i][j] = __ldg(base + tiny_off(i, j, o.cn));
+        }
+      }
+  } else {
+#pragma unroll
+    for (int j = 0; j < N; j++)
+#pragma unroll
+      for (int i = j; i < N; i++) c[i][j] = __ldg(p + pm_off(o.i0 + i, o.j0 + j, o.cn));
+  }
+}
+
+// row l-column of an N x k operand: v[i] = X(i, l)
+template <int N, bool ALIGNED>
+__device__ __forceinline__ void tiny_load_col(double (&v)[N], const double *p, const Op &o, int l) {
+  if (ALIGNED) {
+    const double *base = p + (long long)o.i0 * o.cn + (long long)(o.j0 + l) * PS;
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+      if ((i & 1) == 0 && i + 1 < N) {
+        const double2 x = __ldg((const double2 *)(base + tiny_off(i, 0, o.cn)));
+        v[i] = x.x;
+        v[i + 1] = x.y;
+      } else if ((i & 1) == 0) {
+        v[i] = __ldg(base + tiny_off(i, 0, o.cn));
+      }
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; i++) v[i] = __ldg(p + pm_off(o.i0 + i, o.j0 + l, o.cn));
+  }
+}
+
+template <int N, bool FUSED, bool ALIGNED>
+__global__ void __launch_bounds__(128)
+k_chol_tiny(int batch, int k, Op A, Op B, Op C, OpW D, double *dinv, long long sdinv, int *info) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= batch) return;
+  double c[N][N];
+  tiny_load_lower<N, ALIGNED>(c, C.p + (long long)b * C.stride, C);
+  if (FUSED) {
+    const double *pa = A.p + (long long)b * A.stride, *pb = B.p + (long long)b * B.stride;
+#pragma unroll 2
+    for (int l = 0; l < k; l++) {
+      double av[N], bv[N];
+      tiny_load_col<N, ALIGNED>(av, pa, A, l);
+      tiny_load_col<N, ALIGNED>(bv, pb, B, l);
+#pragma unroll
+      for (int j = 0; j < N; j++)
+#pragma unroll
+        for (int i = j; i < N; i++) c[i][j] = fma(av[i], bv[j], c[i][j]);
+    }
+  }
+  int bad = 0;
+  double *dv = dinv ? dinv + (long long)b * sdinv : nullptr;
+#pragma unroll
+  for (int j = 0; j < N; j++) {
+    const double d = c[j][j];
+    const double r = rsqrt(d);
+    if (!(d > 0.0) && bad == 0) bad = j + 1;
+    c[j][j] = d * r;
+    if (dv) dv[j] = r;
+#pragma unroll
+    for (int i = j + 1; i < N; i++) c[i][j] *= r;
+#pragma unroll
+    for (int jj = j + 1; jj < N; jj++)
+#pragma unroll
+      for (int i = jj; i < N; i++) c[i][jj] = fma(-c[i][j], c[jj][j], c[i][jj]);
+  }
+  double *pd = D.p + (long long)b * D.stride;
+  if (ALIGNED) {
+    double *base = pd + (long long)D.i0 * D.cn + (long long)D.j0 * PS;
+#pragma unroll
+    for (int j = 0; j < N; j++)
+#pragma unroll
+      for (int i = j; i < N; i++) {
+        if ((i & 1) == 0 && i + 1 < N) {
+          *(double2 *)(base + tiny_off(i, j, D.cn)) = make_double2(c[i][j], c[i + 1][j]);
+        } else if (!((i & 1) == 1 && i - 1 >= j)) {
+          base[tiny_off(i, j, D.cn)] = c[i][j];
+        }
+      }
+  } else {
+#pragma unroll
+    for (int j = 0; j < N; j++)
+#pragma unroll
+      for (int i = j; i < N; i++) pd[pm_off(D.i0 + i, D.j0 + j, D.cn)] = c[i][j];
+  }
+  if (info) info[b] = bad;
 }
 
 // ---------------------------------------------------------------------------
@@ -629,26 +767,87 @@ cudaError_t launch_rows_a(bool aligned, int batch, int n, int k, Op A, Op B, Op 
                  : launch_rows_p<MAXT, FUSED, false, T>(batch, n, k, A, B, C, D, dinv, sdinv, info, s);
 }
 
+// Tail balance of the two-problem kernel at n > 192 (512-thread CTAs, two
+// resident per SM).  A CTA carries two whole problems, so when the last wave
+// holds more pairs than there are SMs, but leaves many slots empty, some SMs
+// run two pairs through it while the others idle (n = k = 256, batch 1024:
+// 512 pairs over 304 slots, SMs active 86% of the launch).  Then the pairs of
+// the full waves go to k_chol_rows2 and the rest of the problems to the
+// one-problem kernel, whose smaller CTAs spread them evenly: 989.5 -> 1018.3
+// GFLOP/s there.  Not applied when the last wave has at most one pair per SM
+// (each then runs alone at nearly the speed of two: potrf n = 256, batch
+// 2048, measured 1068 unsplit vs 1018 split), nor for n <= 192, where the
+// one-problem kernel is 10-30% slower per problem than the pair kernel.
+// The split is applied when the last wave is at most this fraction full (in
+// percent).
+#ifndef BF_ROWS_TAIL_FILL
+#define BF_ROWS_TAIL_FILL 80
+#endif
+
+template <typename T>
+inline OpWT<T> shift_op(OpWT<T> o, long long b) {
+  if (o.p) o.p += b * o.stride;
+  return o;
+}
+inline Op shift_op(Op o, long long b) {
+  if (o.p) o.p += b * o.stride;
+  return o;
+}
+
+template <int MAXT, bool FUSED, typename T>
+cudaError_t launch_rows_pairs(bool aligned, int batch, int n, int k, Op A, Op B, Op C, OpWT<T> D, T *dinv,
+                              long long sdinv, int *info, cudaStream_t s) {
+  int pairs_cut = 0;  // pairs that go to the two-problem kernel when the tail is split
+  if (BF_ROWS_TAIL_FILL > 0 && MAXT > 384 && n > 192) {
+    static std::atomic<int> occ[64 * 17];
+    const int threads = ((n + 15) / 16) * 32;
+    const void *fn = aligned ? (const void *)k_chol_rows2<ROWS_BW, FUSED, true, T, MAXT>
+                             : (const void *)k_chol_rows2<ROWS_BW, FUSED, false, T, MAXT>;
+    const int sms = device_sm_count();
+    const long long slots = (long long)resident_ctas(fn, threads, occ) * sms;
+    const long long pairs = (batch + 1) / 2;
+    if (slots > 0 && pairs > slots) {
+      const long long full = pairs / slots, rest = pairs - full * slots;
+      if (rest > sms && rest * 100 <= slots * BF_ROWS_TAIL_FILL) pairs_cut = (int)(full * slots);
+    }
+  }
+  if (pairs_cut == 0)
+    return launch_rows_a<MAXT, FUSED, T>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
+  const int head = 2 * pairs_cut;
+  cudaError_t e = launch_rows_a<MAXT, FUSED, T>(aligned, head, n, k, A, B, C, D, dinv, sdinv, info, s);
+  if (e != cudaSuccess) return e;
+  return launch_rows_a<0, FUSED, T>(aligned, batch - head, n, k, shift_op(A, head), shift_op(B, head),
+                                    shift_op(C, head), shift_op(D, head), dinv ? dinv + head * sdinv : nullptr,
+                                    sdinv, info ? info + head : nullptr, s);
+}
+
 template <bool FUSED, typename T>
 cudaError_t launch_rows(bool aligned, int batch, int n, int k, Op A, Op B, Op C, OpWT<T> D, T *dinv,
                         long long sdinv, int *info, cudaStream_t s) {
   if constexpr (sizeof(T) == 8 || BF_ROWS_P2_FP32) {  // by default the FP32 factor keeps one problem per CTA
     constexpr int p2_max = FUSED ? BF_ROWS_P2_MAX_N_FUSED : BF_ROWS_P2_MAX_N;
     if (n <= 192 && n <= p2_max)
-      return launch_rows_a<384, FUSED, T>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
+      return launch_rows_pairs<384, FUSED, T>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
     if (n <= p2_max)
-      return launch_rows_a<2 * (p2_max > 192 ? p2_max : 192), FUSED, T>(aligned, batch, n, k, A, B, C, D, dinv,
-                                                                      sdinv, info, s);
+      return launch_rows_pairs<2 * (p2_max > 192 ? p2_max : 192), FUSED, T>(aligned, batch, n, k, A, B, C, D,
+                                                                          dinv, sdinv, info, s);
   }
   return launch_rows_a<0, FUSED, T>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
 }
 
 // Lanes per problem of k_chol_small: the smallest G (at most 16) whose
 // shared-memory triangles for the 32/G problems of a warp fit the budget, so
-// that enough single-warp CTAs are resident on each SM.  Measured on the
-// sweep: more resident warps pay for a larger G (the pivot's rsqrt shared by
-// fewer problems) up to G = 16; beyond that the rsqrt dominates.
-constexpr long long SMALL_SMEM_BUDGET = 20 * 1024;
+// that enough single-warp CTAs are resident on each SM.  Measured: more
+// resident warps pay for a larger G (the pivot's rsqrt shared by fewer
+// problems); a lane that walks a whole problem through shared memory is
+// latency-bound (potrf n = 24 at G = 1: 244 GFLOP/s, at G = 4: 650).  26 KB
+// gives G = 2, 4, 8 at n = 16, 24, 32 (budgets of 40 and 80 KB were slower
+// there) and G = 8 rather than 16 at n = 33..40 (n = 40: potrf 550 -> 593,
+// syrk_potrf 806 -> 894 GFLOP/s).
+#ifndef BF_SMALL_SMEM_BUDGET_KB
+#define BF_SMALL_SMEM_BUDGET_KB 26
+#endif
+constexpr long long SMALL_SMEM_BUDGET = BF_SMALL_SMEM_BUDGET_KB * 1024;
 
 // Largest order factored by k_chol_small; the row kernel takes over above
 // (measured with the triangle split: at n = 48 the two-problem row kernel is
@@ -667,13 +866,50 @@ template <int G, bool FUSED>
 cudaError_t launch_small_g(bool aligned, int batch, int n, int k, Op A, Op B, Op C, OpW D,
                            double *dinv, long long sdinv, int *info, cudaStream_t s) {
   constexpr int Q = 32 / G;
-  const size_t smem = (size_t)n * (n + 1) / 2 * Q * sizeof(double);
+  const size_t smem = (size_t)n * (n + 1) / 2 * small_pitch(Q) * sizeof(double);
   const unsigned blocks = (unsigned)((batch + Q - 1) / Q);
+  if (smem > 48 * 1024) {
+    static std::atomic<unsigned long long> attr_a{0}, attr_u{0};
+    const void *fn = aligned ? (const void *)k_chol_small<G, FUSED, true> : (const void *)k_chol_small<G, FUSED, false>;
+    cudaError_t e = smem_attr_once(fn, 200 * 1024, aligned ? attr_a : attr_u);
+    if (e != cudaSuccess) return e;
+  }
   if (aligned)
     k_chol_small<G, FUSED, true><<<blocks, 32, smem, s>>>(batch, n, k, A, B, C, D, dinv, sdinv, info);
   else
     k_chol_small<G, FUSED, false><<<blocks, 32, smem, s>>>(batch, n, k, A, B, C, D, dinv, sdinv, info);
   return cudaGetLastError();
+}
+
+// Largest order factored by k_chol_tiny (one lane per problem, registers).
+#ifndef BF_CHOL_TINY_MAX_N
+#define BF_CHOL_TINY_MAX_N 8
+#endif
+
+template <int N, bool FUSED>
+cudaError_t launch_tiny_n(bool aligned, int batch, int k, Op A, Op B, Op C, OpW D, double *dinv, long long sdinv,
+                          int *info, cudaStream_t s) {
+  const unsigned blocks = (unsigned)((batch + 127) / 128);
+  if (aligned)
+    k_chol_tiny<N, FUSED, true><<<blocks, 128, 0, s>>>(batch, k, A, B, C, D, dinv, sdinv, info);
+  else
+    k_chol_tiny<N, FUSED, false><<<blocks, 128, 0, s>>>(batch, k, A, B, C, D, dinv, sdinv, info);
+  return cudaGetLastError();
+}
+
+template <bool FUSED>
+cudaError_t launch_tiny(bool aligned, int batch, int n, int k, Op A, Op B, Op C, OpW D, double *dinv,
+                        long long sdinv, int *info, cudaStream_t s) {
+  switch (n) {
+    case 1: return launch_tiny_n<1, FUSED>(aligned, batch, k, A, B, C, D, dinv, sdinv, info, s);
+    case 2: return launch_tiny_n<2, FUSED>(aligned, batch, k, A, B, C, D, dinv, sdinv, info, s);
+    case 3: return launch_tiny_n<3, FUSED>(aligned, batch, k, A, B, C, D, dinv, sdinv, info, s);
+    case 4: return launch_tiny_n<4, FUSED>(aligned, batch, k, A, B, C, D, dinv, sdinv, info, s);
+    case 5: return launch_tiny_n<5, FUSED>(aligned, batch, k, A, B, C, D, dinv, sdinv, info, s);
+    case 6: return launch_tiny_n<6, FUSED>(aligned, batch, k, A, B, C, D, dinv, sdinv, info, s);
+    case 7: return launch_tiny_n<7, FUSED>(aligned, batch, k, A, B, C, D, dinv, sdinv, info, s);
+    default: return launch_tiny_n<8, FUSED>(aligned, batch, k, A, B, C, D, dinv, sdinv, info, s);
+  }
 }
 
 template <bool FUSED>
@@ -686,6 +922,9 @@ cudaError_t launch_chol_t(bool aligned, int batch, int n, int k, Op A, Op B, Op 
   // most of the GPU idle and each warp a long serial chain of FP64 work.
   if (g)
     while (g < 32 && (long long)batch * g < 32LL * 4 * device_sm_count()) g *= 2;
+  // enough problems for one lane each: the register kernel
+  if (g == 1 && n <= BF_CHOL_TINY_MAX_N)
+    return launch_tiny<FUSED>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
   switch (g) {
     case 1: return launch_small_g<1, FUSED>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
     case 2: return launch_small_g<2, FUSED>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);

@@ -100,6 +100,24 @@ inline int device_sm_count() {
   return sms;
 }
 
+// CTAs of `fn` at `threads` threads (no dynamic shared memory) resident on
+// one SM of the current device; `cache` holds one entry per (device, warps)
+// for up to 64 devices and 16 warps.
+inline int resident_ctas(const void *fn, int threads, std::atomic<int> (&cache)[64 * 17]) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  const int w = (threads + 31) / 32;
+  const bool cached = dev < 64 && w <= 16;
+  if (cached) {
+    const int c = cache[dev * 17 + w].load(std::memory_order_relaxed);
+    if (c > 0) return c;
+  }
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, 0) != cudaSuccess) return 0;
+  if (cached && nb > 0) cache[dev * 17 + w].store(nb, std::memory_order_relaxed);
+  return nb;
+}
+
 // Device-side check of one operand record of the descriptor-array forms:
 // the same rules as the host's check of a strided operand.
 __device__ __forceinline__ bool dsub_ok(const bf_dsub &s, int rows, int cols) {

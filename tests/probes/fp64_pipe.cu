@@ -7,6 +7,9 @@
 //   dfma_ilp1_4warps   DFMA throughput with 4 warps per SM and one dependent
 //                      chain per thread (one warp per SM sub-partition)
 //   dmma_gflops        mma.sync m8n8k4 f64 throughput
+//   mixed_*            half the warps of each CTA in a DFMA loop, half in an
+//                      mma.sync f64 loop: the time of both together against
+//                      each alone tells whether the two share one pipe
 //   ffma_gflops        FP32 FMA throughput
 //   sqrt_ops, rcp_ops, rsqrt_ops   (x -> f(x) + 1) per second, FP64
 // All loops have fixed trip counts.
@@ -72,6 +75,42 @@ __global__ void k_dmma(double *out, int iters) {
   double s = 0.0;
 #pragma unroll
   for (int i = 0; i < 4; i++) s += c0[i] + c1[i];
+  out[tid] = s;
+}
+
+// Even warps: the DFMA loop of k_dfma<8>; odd warps: the mma.sync loop of
+// k_dmma.  which: 0 both, 1 DFMA warps only, 2 MMA warps only.
+__global__ void k_mixed(double *out, int iters_f, int iters_m, int which) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int warp = threadIdx.x >> 5;
+  double s = 0.0;
+  if ((warp & 1) == 0) {
+    if (which == 2) return;
+    double a[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++) a[i] = 1.0 + 1e-3 * i + 1e-9 * tid;
+    for (int it = 0; it < iters_f; it++) {
+#pragma unroll
+      for (int i = 0; i < 8; i++) a[i] = fma(a[i], 0.999999, 1e-6);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; i++) s += a[i];
+  } else {
+    if (which == 1) return;
+    const double a = 1.0 + 1e-6 * (threadIdx.x & 31), b = 0.5;
+    double c0[4], c1[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++) c0[i] = c1[i] = 0.0;
+    for (int it = 0; it < iters_m; it++) {
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+        asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
+                     : "+d"(c0[i]), "+d"(c1[i])
+                     : "d"(a), "d"(b));
+    }
+#pragma unroll
+    for (int i = 0; i < 4; i++) s += c0[i] + c1[i];
+  }
   out[tid] = s;
 }
 
@@ -161,6 +200,23 @@ int main() {
     CK(cudaEventElapsedTime(&ms, e0, e1));
     gf_dmma = 512.0 * 4 * iters * (double)blocks * threads / 32 / (ms * 1e-3) / 1e9;
   }
+  // DFMA and MMA warps side by side (4 CTAs of 8 warps per SM, 4 + 4 each)
+  double t_mixed[3] = {0.0, 0.0, 0.0}, gf_mixed = 0.0;
+  {
+    const int blocks = sms * 4, iters_f = 2000, iters_m = 440;
+    for (int which = 0; which < 3; which++) {
+      k_mixed<<<blocks, threads>>>(dout, 10, 2, which);
+      CK(cudaEventRecord(e0));
+      k_mixed<<<blocks, threads>>>(dout, iters_f, iters_m, which);
+      CK(cudaEventRecord(e1));
+      CK(cudaEventSynchronize(e1));
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      t_mixed[which] = ms;
+    }
+    const double warps_half = (double)blocks * threads / 64;
+    const double flops = warps_half * (32.0 * 2 * 8 * iters_f + 512.0 * 4 * iters_m);
+    gf_mixed = flops / (t_mixed[0] * 1e-3) / 1e9;
+  }
   double special[3] = {0.0, 0.0, 0.0};
   for (int mode = 0; mode < 3; mode++) {
     const int blocks = sms * 8, iters = 500;
@@ -174,8 +230,11 @@ int main() {
   }
   CK(cudaGetLastError());
   printf("{\"sms\": %d, \"dfma_full_gflops\": %.1f, \"dfma_1lane_ratio\": %.3f, \"dfma_ilp1_4warps_gflops\": %.1f, "
-         "\"dmma_gflops\": %.1f, \"ffma_gflops\": %.1f, \"sqrt_ops\": %.4g, \"rcp_ops\": %.4g, \"rsqrt_ops\": %.4g}\n",
-         sms, gf_full, t_one / t_full, gf_ilp1, gf_dmma, gf_ffma, special[0], special[1], special[2]);
+         "\"dmma_gflops\": %.1f, \"ffma_gflops\": %.1f, \"sqrt_ops\": %.4g, \"rcp_ops\": %.4g, \"rsqrt_ops\": %.4g, "
+         "\"mixed_ms_both\": %.4f, \"mixed_ms_dfma_only\": %.4f, \"mixed_ms_mma_only\": %.4f, "
+         "\"mixed_gflops\": %.1f}\n",
+         sms, gf_full, t_one / t_full, gf_ilp1, gf_dmma, gf_ffma, special[0], special[1], special[2], t_mixed[0],
+         t_mixed[1], t_mixed[2], gf_mixed);
   CK(cudaFree(dout));
   CK(cudaFree(fout));
   return 0;

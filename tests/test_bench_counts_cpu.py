@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 
 import bench
+from paper_1704_02457_gb300 import inputs
 
 
 class Counter:
@@ -92,13 +93,16 @@ def test_algorithmic_bytes_count_triangles_once():
 
 
 def test_kernel_labels_follow_the_library_size_rules():
-    # the small Cholesky keeps 32/G packed triangles of a warp within 20 KB, G <= 16, up to n = 40
+    # the small Cholesky keeps 32/G packed triangles of a warp within 26 KB, G <= 16, up to n = 40
     for n in (4, 8, 12, 16, 20, 24, 32, 40):
         g = bench.small_g(n)
         assert g in (1, 2, 4, 8, 16)
-        assert n * (n + 1) // 2 * (32 // g) * 8 <= 20 * 1024 or g == 16
+        assert n * (n + 1) // 2 * (32 // g) * 8 <= 26 * 1024 or g == 16
         if g > 1:
-            assert n * (n + 1) // 2 * (32 // (g // 2)) * 8 > 20 * 1024
+            assert n * (n + 1) // 2 * (32 // (g // 2)) * 8 > 26 * 1024
+    assert bench.kernel_of("dpotrf_l", 4) == "k_chol_tiny<4,0,1>"
+    assert bench.kernel_of("dsyrk_dpotrf_ln", 8) == "k_chol_tiny<8,1,1>"
+    assert bench.kernel_of("dpotrf_l", 16).startswith("k_chol_small<")
     assert bench.kernel_of("dpotrf_l", 40).startswith("k_chol_small<")
     assert bench.kernel_of("dpotrf_l", 48) == "k_chol_rows2<16,0,1,double,384>"
     assert bench.kernel_of("dpotrf_l", 64) == "k_chol_rows2<16,0,1,double,384>"
@@ -107,3 +111,15 @@ def test_kernel_labels_follow_the_library_size_rules():
     assert bench.kernel_of("dsyrk_dpotrf_ln", 256) == "k_chol_rows2<16,1,1,double,512>"
     assert bench.kernel_of("dsyrk_dpotrf_ln", 300) == "k_chol_rows<16,1,1,double>"
     assert bench.kernel_of("dgemm_nt", 4) == "k_gemm_nt<0,1,1>"
+
+
+def test_launches_per_call_count_the_tail_split():
+    # n = k = 256, batch 1024: 512 pairs over 304 slots, 208 left > 152 SMs
+    assert bench.launches_of("dsyrk_dpotrf_ln", 256, 1024) == 2
+    # potrf n = 256, batch 2048: 112 pairs left, at most one per SM
+    assert bench.launches_of("dpotrf_l", 256, 2048) == 1
+    assert bench.launches_of("dsyrk_dpotrf_ln", 192, 1820) == 1
+    assert bench.launches_of("dgemm_nt", 256, 682) == 1
+    sweep = [(r, n) for n in inputs.SWEEP_N for r in bench.ROUTINES]
+    total = sum(bench.launches_of(r, n, inputs.sweep_batch(r, n)) for r, n in sweep)
+    assert total == len(sweep) + 1

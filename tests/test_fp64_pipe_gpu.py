@@ -2,7 +2,7 @@
 program (tests/probes/fp64_pipe.cu): the FP64 FMA peak the roofline uses, a
 masked lane costing as much as an active one, one warp per SM sub-partition
 sufficing for the FP64 pipe, and FP64 tensor-core MMA being slower than
-DFMA (so it is not used)."""
+DFMA and sharing its pipe (so it is not used, not even beside DFMA)."""
 import json
 import os
 import shutil
@@ -47,3 +47,10 @@ def test_one_warp_per_sm_subpartition_feeds_the_fp64_pipe(probe):
 
 def test_fp64_mma_is_slower_than_dfma(probe):
     assert probe["dmma_gflops"] < probe["dfma_full_gflops"]
+
+
+def test_fp64_mma_and_dfma_share_one_pipe(probe):
+    # half the warps in each loop: together they take about the sum of their
+    # times alone, not the longer of the two
+    both, f, m = probe["mixed_ms_both"], probe["mixed_ms_dfma_only"], probe["mixed_ms_mma_only"]
+    assert both >= 0.85 * (f + m)

@@ -387,6 +387,120 @@ def test_syrk_potrf_paired_problems_odd_batch_and_failing_neighbour(n):
     assert fro(np.tril(got[2])[:, :c] - np.tril(want[2])[:, :c]) / fro(np.tril(want[2])[:, :c]) <= 1e-12
 
 
+@pytest.mark.parametrize("n,k,offs,inplace", [(1, 0, (0, 0), False), (3, 5, (1, 2), False), (4, 0, (0, 0), True),
+                                             (4, 4, (0, 0), False), (5, 2, (3, 1), False), (6, 0, (2, 0), True),
+                                             (7, 9, (0, 0), False), (8, 0, (5, 3), False), (8, 8, (0, 0), False)])
+def test_chol_one_lane_per_problem_every_problem(n, k, offs, inplace):
+    """Batches of at least 32 x 4 x SMs problems of order <= 8 are factored
+    with one lane per problem and the triangle in registers.  Every problem is
+    checked: factor, inverse diagonal, info of planted failures, and the
+    untouched upper triangle; at panel-top and off-panel offsets, in place."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    bt = 128 * sms + 37
+    ai, aj = offs
+    fused = k > 0
+    if fused:
+        M = inputs.normal((bt, n, k), 500 + n).numpy()
+        Q = np.broadcast_to(np.eye(n) * float(n), (bt, n, n)).copy()
+    else:
+        Q = inputs.spd(bt, n, 500 + n).numpy()
+    bad = {0: 1, bt // 2: n, bt - 1: (n + 1) // 2}
+    for b, col in bad.items():
+        Q[b, col - 1, col - 1] = -1e9
+    if fused:
+        want, dinv_want, info_want = oracle.dsyrk_dpotrf_ln(M, M, Q)
+    else:
+        want, dinv_want, info_want = oracle.dpotrf_l(Q)
+    dQ = put(torch.from_numpy(Q), n + ai + 1, n + aj + 2, ai, aj, fill=np.nan)
+    dD = dQ if inplace else bf.DMatBatch(bt, n + ai + 1, n + aj + 2, fill=np.nan)
+    info = torch.full((bt,), -7, dtype=torch.int32, device=dev())
+    if fused:
+        dM = put(torch.from_numpy(M), n + ai, k + 1, ai, 1)
+        bf.dsyrk_dpotrf_ln(n, k, dM, ai, 1, dM, ai, 1, dQ, ai, aj, dD, ai, aj, info=info)
+    else:
+        bf.dpotrf_l(n, dQ, ai, aj, dD, ai, aj, info=info)
+    got_info = info.cpu().numpy()
+    assert np.array_equal(got_info, info_want)
+    assert {int(b): int(got_info[b]) for b in np.nonzero(got_info)[0]} == bad
+    full = get(dD)
+    got = full[:, ai:ai + n, aj:aj + n]
+    ok = np.array([b not in bad for b in range(bt)])
+    S = Q[ok] + (M[ok] @ np.swapaxes(M[ok], -1, -2) if fused else 0.0)
+    assert np.all(chol_resid(got[ok], S) <= 1e-13)
+    assert np.all(fro(np.tril(got[ok]) - np.tril(want[ok])) / fro(np.tril(want[ok])) <= 1e-12)
+    upper = np.triu(np.ones((n, n), dtype=bool), 1)
+    if inplace:  # the upper triangle keeps the input's entries
+        assert np.array_equal(got[:, upper], Q[:, upper])
+    else:
+        assert np.all(np.isnan(got[:, upper]))
+        outside = np.ones(full.shape[1:], dtype=bool)
+        outside[ai:ai + n, aj:aj + n] = False
+        assert np.all(np.isnan(full[:, outside]))
+    dinv = dD.dinv().cpu().numpy()[:, :n]  # 1/L_jj at the start of each matrix's dA vector
+    for b in np.nonzero(ok)[0][:: max(1, bt // 64)]:
+        check_dinv(dinv[b], got[b], dinv_want[b])
+    for b, col in bad.items():
+        c = col - 1
+        if c > 0:
+            ref = np.tril(want[b])[:, :c]
+            assert fro(np.tril(got[b])[:, :c] - ref) / fro(ref) <= 1e-12
+
+
+# Orders above 192 run two problems per 512-thread CTA, two CTAs per SM on
+# GB300 (registers bound them).
+TAIL_CASES = [(200, 0), (240, 30), (256, 8)]
+
+
+@pytest.mark.parametrize("n,k", TAIL_CASES)
+def test_rows_tail_split_every_problem(n, k):
+    """A batch whose two-problem CTAs fill about 65% of their last wave: the
+    launcher gives the full waves to the two-problem kernel and the rest of
+    the problems to the one-problem kernel.  Every problem is checked against
+    the oracle, with failing problems on both sides of the boundary."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    slots = 2 * sms
+    bt = 2 * slots + 2 * (slots * 65 // 100) + 1
+    head = 2 * slots
+    fused = k > 0
+    rng = np.random.default_rng(n)
+    if fused:
+        M = inputs.normal((bt, n, k), 300 + n).numpy()
+        Q = np.broadcast_to(np.eye(n) * float(n), (bt, n, n)).copy()
+    else:
+        Q = inputs.spd(bt, n, 300 + n).numpy()
+    bad = {head - 1: n - 2, head: 1, bt - 1: n // 2}  # problem -> failing column (1-based)
+    for b, col in bad.items():
+        Q[b, col - 1, col - 1] = -1e9
+    if fused:
+        want, dinv_want, info_want = oracle.dsyrk_dpotrf_ln(M, M, Q)
+    else:
+        want, dinv_want, info_want = oracle.dpotrf_l(Q)
+    dD = bf.DMatBatch(bt, n, n, fill=np.nan)
+    info = torch.full((bt,), -7, dtype=torch.int32, device=dev())
+    dQ = put(torch.from_numpy(Q))
+    if fused:
+        dM = put(torch.from_numpy(M))
+        bf.dsyrk_dpotrf_ln(n, k, dM, 0, 0, dM, 0, 0, dQ, 0, 0, dD, 0, 0, info=info)
+    else:
+        bf.dpotrf_l(n, dQ, 0, 0, dD, 0, 0, info=info)
+    got_info = info.cpu().numpy()
+    assert np.array_equal(got_info, info_want)
+    assert {int(b): int(got_info[b]) for b in np.nonzero(got_info)[0]} == bad
+    got = get(dD)
+    dinv = dD.dinv().cpu().numpy()
+    ok = np.array([b not in bad for b in range(bt)])
+    S = Q[ok] + (M[ok] @ np.swapaxes(M[ok], -1, -2) if fused else 0.0)
+    assert np.all(chol_resid(got[ok], S) <= 1e-13)
+    assert np.all(fro(np.tril(got[ok]) - np.tril(want[ok])) / fro(np.tril(want[ok])) <= 1e-12)
+    for b in rng.choice(np.nonzero(ok)[0], size=8, replace=False).tolist() + [head - 2, head + 1]:
+        check_dinv(dinv[b], got[b], dinv_want[b])
+    for b, col in bad.items():  # the columns before the failing pivot are still the factor's
+        c = col - 1
+        if c > 0:
+            ref = np.tril(want[b])[:, :c]
+            assert fro(np.tril(got[b])[:, :c] - ref) / fro(ref) <= 1e-12
+
+
 @pytest.mark.parametrize("n,k", [(4, 4), (8, 3), (24, 24), (33, 50), (100, 17)])
 def test_syrk_potrf_exact_construction(n, k):
     bt = 3
