@@ -748,6 +748,12 @@ def run_gpu(args):
         print(json.dumps(result))
 
 
+# Input and output slots of the end-to-end pipeline (GiB-sized device
+# buffers).  Measured on one box, same order of runs: 3/3 366 ms, 6/3 354 ms,
+# 8/4 362 ms, 4/2 386 ms per step.
+E2E_IN_SLOTS, E2E_OUT_SLOTS = 6, 3
+
+
 def run_e2e(pts, args, dev, world):
     """The same step through the public API with host buffers.  Every step, for
     every point: copy its inputs from pinned host memory (column-major, as a
@@ -821,32 +827,60 @@ def run_e2e(pts, args, dev, world):
             order.append(plan[hi])
         lo, hi = lo + 1, hi - 1
     plan = order
-    # Six streams take the points in turn, each with its own staging buffers,
-    # so that host-to-device copies, kernels and device-to-host copies of
-    # different points run at the same time (4 / 6 / 8 streams measured
-    # 667-723 / 771 / 728 GFLOP/s).
-    NS = 6
+    # Three-stage pipeline on three streams joined by events: host-to-device
+    # copies into a ring of NI input slots, then (compute stream) pack, the
+    # routine and unpack into a ring of NO output slots, then device-to-host
+    # copies.  A copy into a slot waits only for the pack that last read it,
+    # so the host-to-device direction of the link never waits behind a
+    # kernel or an outgoing copy.
+    NI, NO = E2E_IN_SLOTS, E2E_OUT_SLOTS
+    max_in = max(sum(h.numel() for _, h in ins) for _, ins in plan)
     max_sz = max(p.batch * p.n * p.n for p in pts)
-    streams = [torch.cuda.Stream() for _ in range(NS)]
-    slots = [[torch.empty(max_sz, dtype=torch.float64, device=dev) for _ in range(3)] for _ in range(NS)]
-    out_dev = [torch.empty(max_sz, dtype=torch.float64, device=dev) for _ in range(NS)]
-    out_host = [torch.empty(max_sz, dtype=torch.float64, pin_memory=True) for _ in range(NS)]
+    s_in, s_run, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    in_dev = [torch.empty(max_in, dtype=torch.float64, device=dev) for _ in range(NI)]
+    out_dev = [torch.empty(max_sz, dtype=torch.float64, device=dev) for _ in range(NO)]
+    out_host = [torch.empty(max_sz, dtype=torch.float64, pin_memory=True) for _ in range(NO)]
+    in_ready = [torch.cuda.Event() for _ in range(NI)]
+    in_free = [torch.cuda.Event() for _ in range(NI)]
+    out_ready = [torch.cuda.Event() for _ in range(NO)]
+    out_free = [torch.cuda.Event() for _ in range(NO)]
+    used_in, used_out = [False] * NI, [False] * NO
     torch.cuda.synchronize()
+    count = [0]
 
     def e2e_step():
-        for j, (p, ins) in enumerate(plan):
-            si = j % NS
-            st = streams[si]
+        for p, ins in plan:
+            j = count[0]
+            count[0] += 1
+            si, oi = j % NI, j % NO
             sz = p.batch * p.n * p.n
-            with torch.cuda.stream(st):
-                for slot, (name, h) in zip(slots[si], ins):
-                    buf = slot[:sz].view(p.batch, p.n, p.n)
+            views, off = [], 0
+            for name, h in ins:
+                views.append((name, in_dev[si][off:off + h.numel()].view(h.shape)))
+                off += h.numel()
+            with torch.cuda.stream(s_in):
+                if used_in[si]:
+                    s_in.wait_event(in_free[si])
+                for (_, buf), (_, h) in zip(views, ins):
                     buf.copy_(h, non_blocking=True)
-                    bf.pack(buf, getattr(p, name), stream=st)
-                p.run(st)
-                ob = out_dev[si][:sz].view(p.batch, p.n, p.n)
-                bf.unpack(p.D, ob, stream=st)
-                out_host[si][:sz].copy_(out_dev[si][:sz], non_blocking=True)
+                in_ready[si].record(s_in)
+            used_in[si] = True
+            with torch.cuda.stream(s_run):
+                s_run.wait_event(in_ready[si])
+                for name, buf in views:
+                    bf.pack(buf, getattr(p, name), stream=s_run)
+                in_free[si].record(s_run)
+                p.run(s_run)
+                if used_out[oi]:
+                    s_run.wait_event(out_free[oi])
+                ob = out_dev[oi][:sz].view(p.batch, p.n, p.n)
+                bf.unpack(p.D, ob, stream=s_run)
+                out_ready[oi].record(s_run)
+            used_out[oi] = True
+            with torch.cuda.stream(s_out):
+                s_out.wait_event(out_ready[oi])
+                out_host[oi][:sz].copy_(out_dev[oi][:sz], non_blocking=True)
+                out_free[oi].record(s_out)
 
     steps = max(1, min(args.steps, 2))
     e2e_step()
@@ -863,7 +897,8 @@ def run_e2e(pts, args, dev, world):
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": steps,
             "ms_per_step": round(dt * 1e3, 2),
             "path": "pinned host column-major -> H2D -> bf_pack -> routine -> bf_unpack -> D2H, "
-                    "points issued small-n/large-n alternately and pipelined over 6 streams"}
+                    "points issued small-n/large-n alternately through a three-stage pipeline "
+                    "(copy-in, compute, copy-out streams; %d input and %d output slots)" % (NI, NO)}
 
 
 def run_mixed(args, dev, bt=8192, n=128, nrhs=4):
