@@ -259,14 +259,14 @@ class ClockSampler:
 class Point:
     """One (routine, n) sweep point: resident panel-major inputs and outputs."""
 
-    def __init__(self, routine, n, dev, seed):
+    def __init__(self, routine, n, dev, seed, batch=None):
         import torch
 
         import paper_1704_02457_gb300 as bf
         from paper_1704_02457_gb300 import inputs
 
         self.routine, self.n = routine, n
-        self.batch = bt = inputs.sweep_batch(routine, n)
+        self.batch = bt = inputs.sweep_batch(routine, n) if batch is None else batch
         self.flops = flops(routine, n) * bt
         self.roof = None
         mk = lambda X: bf.DMatBatch.from_colmajor(X, tight=True)  # noqa: E731
@@ -754,151 +754,168 @@ def run_gpu(args):
 E2E_IN_SLOTS, E2E_OUT_SLOTS = 6, 3
 
 
-def run_e2e(pts, args, dev, world):
-    """The same step through the public API with host buffers.  Every step, for
+class E2EPipeline:
+    """The sweep through the public API with host buffers.  Every step, for
     every point: copy its inputs from pinned host memory (column-major, as a
-    user holds them) to the device, pack them (bf_pack), run the routine, unpack
-    the result (bf_unpack) and copy it back to pinned host memory.
+    user holds them) to the device, pack them (bf_pack), run the routine,
+    unpack the result (bf_unpack) and copy it back to pinned host memory.
 
     Host inputs are kept in per-n pinned pools that the routines of that n
     share: a pool of N(0,1) data (gemm A, B, C; syrk A, C; trsm B; syrk_potrf
     M), a pool of SPD matrices (potrf), one of Cholesky factors (trsm) and one
-    of n*I (syrk_potrf).  Device staging buffers are reused across points."""
-    import torch
+    of n*I (syrk_potrf).  `plan` lists (point, [(operand, pinned host
+    input)]) in issue order.
 
-    import paper_1704_02457_gb300 as bf
-    from paper_1704_02457_gb300 import inputs
+    Issue order: alternately from the small-n end (copy-bound: ~1 GiB of
+    inputs for little arithmetic) and the large-n end (compute-bound) of the
+    sweep, so that the copies of one kind overlap the kernels of the other.
+    The points are independent; the work per step is unchanged.
 
-    stream = torch.cuda.current_stream()
-    by_n = {}
-    for p in pts:
-        by_n.setdefault(p.n, []).append(p)
-    pools = {}
-    for n, group in by_n.items():
-        pool = {}
-        need_norm = max(p.batch * n * n * {"dgemm_nt": 3, "dsyrk_ln": 2, "dtrsm_rltn": 1,
-                                             "dsyrk_dpotrf_ln": 1}.get(p.routine, 0) for p in group)
-        if need_norm:
-            h = torch.empty(need_norm, dtype=torch.float64, pin_memory=True)
-            h.copy_(inputs.normal((need_norm,), 7000 + n, dev))
-            pool["norm"] = h
-        for p in group:
-            bt = p.batch
-            if p.routine == "dpotrf_l":
-                h = torch.empty((bt, n, n), dtype=torch.float64, pin_memory=True)
-                h.copy_(inputs.spd(bt, n, 7100 + n, dev))
-                pool["spd"] = h
+    Three-stage pipeline on three streams joined by events: host-to-device
+    copies into a ring of E2E_IN_SLOTS input slots, then (compute stream)
+    pack, the routine and unpack into a ring of E2E_OUT_SLOTS output slots,
+    then device-to-host copies.  A copy into a slot waits only for the pack
+    that last read it, so the host-to-device direction of the link never
+    waits behind a kernel or an outgoing copy."""
+
+    def __init__(self, pts, dev):
+        import torch
+
+        from paper_1704_02457_gb300 import inputs
+
+        by_n = {}
+        for p in pts:
+            by_n.setdefault(p.n, []).append(p)
+        pools = {}
+        for n, group in by_n.items():
+            pool = {}
+            need_norm = max(p.batch * n * n * {"dgemm_nt": 3, "dsyrk_ln": 2, "dtrsm_rltn": 1,
+                                                 "dsyrk_dpotrf_ln": 1}.get(p.routine, 0) for p in group)
+            if need_norm:
+                h = torch.empty(need_norm, dtype=torch.float64, pin_memory=True)
+                h.copy_(inputs.normal((need_norm,), 7000 + n, dev))
+                pool["norm"] = h
+            for p in group:
+                bt = p.batch
+                if p.routine == "dpotrf_l":
+                    h = torch.empty((bt, n, n), dtype=torch.float64, pin_memory=True)
+                    h.copy_(inputs.spd(bt, n, 7100 + n, dev))
+                    pool["spd"] = h
+                elif p.routine == "dtrsm_rltn":
+                    h = torch.empty((bt, n, n), dtype=torch.float64, pin_memory=True)
+                    h.copy_(p.L.to_colmajor().transpose(1, 2))
+                    pool["fac"] = h
+                elif p.routine == "dsyrk_dpotrf_ln":
+                    h = torch.zeros((bt, n, n), dtype=torch.float64, pin_memory=True)
+                    h.diagonal(dim1=1, dim2=2).fill_(float(n))
+                    pool["q"] = h
+            pools[n] = pool
+        plan = []
+        self.h2d = self.d2h = 0
+        for p in pts:
+            n, bt, pool = p.n, p.batch, pools[p.n]
+            sz = bt * n * n
+            norm = lambda i: pool["norm"][i * sz:(i + 1) * sz].view(bt, n, n)  # noqa: E731
+            if p.routine == "dgemm_nt":
+                ins = [("A", norm(0)), ("B", norm(1)), ("C", norm(2))]
+            elif p.routine == "dsyrk_ln":
+                ins = [("A", norm(0)), ("C", norm(1))]
+            elif p.routine == "dpotrf_l":
+                ins = [("C", pool["spd"])]
             elif p.routine == "dtrsm_rltn":
-                h = torch.empty((bt, n, n), dtype=torch.float64, pin_memory=True)
-                h.copy_(p.L.to_colmajor().transpose(1, 2))
-                pool["fac"] = h
-            elif p.routine == "dsyrk_dpotrf_ln":
-                h = torch.zeros((bt, n, n), dtype=torch.float64, pin_memory=True)
-                h.diagonal(dim1=1, dim2=2).fill_(float(n))
-                pool["q"] = h
-        pools[n] = pool
-    plan = []
-    h2d = d2h = 0
-    for p in pts:
-        n, bt, pool = p.n, p.batch, pools[p.n]
-        sz = bt * n * n
-        norm = lambda i: pool["norm"][i * sz:(i + 1) * sz].view(bt, n, n)  # noqa: E731
-        if p.routine == "dgemm_nt":
-            ins = [("A", norm(0)), ("B", norm(1)), ("C", norm(2))]
-        elif p.routine == "dsyrk_ln":
-            ins = [("A", norm(0)), ("C", norm(1))]
-        elif p.routine == "dpotrf_l":
-            ins = [("C", pool["spd"])]
-        elif p.routine == "dtrsm_rltn":
-            ins = [("L", pool["fac"]), ("B", norm(0))]
-        else:
-            ins = [("A", norm(0)), ("C", pool["q"])]
-        h2d += sum(h.numel() * 8 for _, h in ins)
-        d2h += sz * 8
-        plan.append((p, ins))
-    # Issue order: alternately from the small-n end (copy-bound: ~1 GiB of
-    # inputs for little arithmetic) and the large-n end (compute-bound) of
-    # the sweep, so that the copies of one kind overlap the kernels of the
-    # other.  The points are independent; the work per step is unchanged.
-    lo, hi, order = 0, len(plan) - 1, []
-    while lo <= hi:
-        order.append(plan[lo])
-        if hi != lo:
-            order.append(plan[hi])
-        lo, hi = lo + 1, hi - 1
-    plan = order
-    # Three-stage pipeline on three streams joined by events: host-to-device
-    # copies into a ring of NI input slots, then (compute stream) pack, the
-    # routine and unpack into a ring of NO output slots, then device-to-host
-    # copies.  A copy into a slot waits only for the pack that last read it,
-    # so the host-to-device direction of the link never waits behind a
-    # kernel or an outgoing copy.
-    NI, NO = E2E_IN_SLOTS, E2E_OUT_SLOTS
-    max_in = max(sum(h.numel() for _, h in ins) for _, ins in plan)
-    max_sz = max(p.batch * p.n * p.n for p in pts)
-    s_in, s_run, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
-    in_dev = [torch.empty(max_in, dtype=torch.float64, device=dev) for _ in range(NI)]
-    out_dev = [torch.empty(max_sz, dtype=torch.float64, device=dev) for _ in range(NO)]
-    out_host = [torch.empty(max_sz, dtype=torch.float64, pin_memory=True) for _ in range(NO)]
-    in_ready = [torch.cuda.Event() for _ in range(NI)]
-    in_free = [torch.cuda.Event() for _ in range(NI)]
-    out_ready = [torch.cuda.Event() for _ in range(NO)]
-    out_free = [torch.cuda.Event() for _ in range(NO)]
-    used_in, used_out = [False] * NI, [False] * NO
-    torch.cuda.synchronize()
-    count = [0]
+                ins = [("L", pool["fac"]), ("B", norm(0))]
+            else:
+                ins = [("A", norm(0)), ("C", pool["q"])]
+            self.h2d += sum(h.numel() * 8 for _, h in ins)
+            self.d2h += sz * 8
+            plan.append((p, ins))
+        lo, hi, order = 0, len(plan) - 1, []
+        while lo <= hi:
+            order.append(plan[lo])
+            if hi != lo:
+                order.append(plan[hi])
+            lo, hi = lo + 1, hi - 1
+        self.plan = order
+        self.NI, self.NO = E2E_IN_SLOTS, E2E_OUT_SLOTS
+        max_in = max(sum(h.numel() for _, h in ins) for _, ins in self.plan)
+        max_sz = max(p.batch * p.n * p.n for p in pts)
+        self.s_in, self.s_run, self.s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+        self.in_dev = [torch.empty(max_in, dtype=torch.float64, device=dev) for _ in range(self.NI)]
+        self.out_dev = [torch.empty(max_sz, dtype=torch.float64, device=dev) for _ in range(self.NO)]
+        self.out_host = [torch.empty(max_sz, dtype=torch.float64, pin_memory=True) for _ in range(self.NO)]
+        self.in_ready = [torch.cuda.Event() for _ in range(self.NI)]
+        self.in_free = [torch.cuda.Event() for _ in range(self.NI)]
+        self.out_ready = [torch.cuda.Event() for _ in range(self.NO)]
+        self.out_free = [torch.cuda.Event() for _ in range(self.NO)]
+        self.used_in, self.used_out = [False] * self.NI, [False] * self.NO
+        self.count = 0
+        torch.cuda.synchronize()
 
-    def e2e_step():
-        for p, ins in plan:
-            j = count[0]
-            count[0] += 1
-            si, oi = j % NI, j % NO
+    def step(self, out_targets=None):
+        """Issue one step.  out_targets: optional pinned host tensors, one per
+        entry of `plan`, that receive the points' results instead of the
+        output ring's host buffers (for checking)."""
+        import torch
+
+        import paper_1704_02457_gb300 as bf
+
+        for jp, (p, ins) in enumerate(self.plan):
+            j = self.count
+            self.count += 1
+            si, oi = j % self.NI, j % self.NO
             sz = p.batch * p.n * p.n
             views, off = [], 0
             for name, h in ins:
-                views.append((name, in_dev[si][off:off + h.numel()].view(h.shape)))
+                views.append((name, self.in_dev[si][off:off + h.numel()].view(h.shape)))
                 off += h.numel()
-            with torch.cuda.stream(s_in):
-                if used_in[si]:
-                    s_in.wait_event(in_free[si])
+            with torch.cuda.stream(self.s_in):
+                if self.used_in[si]:
+                    self.s_in.wait_event(self.in_free[si])
                 for (_, buf), (_, h) in zip(views, ins):
                     buf.copy_(h, non_blocking=True)
-                in_ready[si].record(s_in)
-            used_in[si] = True
-            with torch.cuda.stream(s_run):
-                s_run.wait_event(in_ready[si])
+                self.in_ready[si].record(self.s_in)
+            self.used_in[si] = True
+            with torch.cuda.stream(self.s_run):
+                self.s_run.wait_event(self.in_ready[si])
                 for name, buf in views:
-                    bf.pack(buf, getattr(p, name), stream=s_run)
-                in_free[si].record(s_run)
-                p.run(s_run)
-                if used_out[oi]:
-                    s_run.wait_event(out_free[oi])
-                ob = out_dev[oi][:sz].view(p.batch, p.n, p.n)
-                bf.unpack(p.D, ob, stream=s_run)
-                out_ready[oi].record(s_run)
-            used_out[oi] = True
-            with torch.cuda.stream(s_out):
-                s_out.wait_event(out_ready[oi])
-                out_host[oi][:sz].copy_(out_dev[oi][:sz], non_blocking=True)
-                out_free[oi].record(s_out)
+                    bf.pack(buf, getattr(p, name), stream=self.s_run)
+                self.in_free[si].record(self.s_run)
+                p.run(self.s_run)
+                if self.used_out[oi]:
+                    self.s_run.wait_event(self.out_free[oi])
+                ob = self.out_dev[oi][:sz].view(p.batch, p.n, p.n)
+                bf.unpack(p.D, ob, stream=self.s_run)
+                self.out_ready[oi].record(self.s_run)
+            self.used_out[oi] = True
+            with torch.cuda.stream(self.s_out):
+                self.s_out.wait_event(self.out_ready[oi])
+                dst = out_targets[jp].view(-1)[:sz] if out_targets is not None else self.out_host[oi][:sz]
+                dst.copy_(self.out_dev[oi][:sz], non_blocking=True)
+                self.out_free[oi].record(self.s_out)
 
+
+def run_e2e(pts, args, dev, world):
+    """The end-to-end leg: E2EPipeline steps timed on the host clock."""
+    import torch
+
+    pipe = E2EPipeline(pts, dev)
     steps = max(1, min(args.steps, 2))
-    e2e_step()
+    pipe.step()
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     t0 = time.perf_counter()
     for _ in range(steps):
-        e2e_step()
+        pipe.step()
     torch.cuda.synchronize()
     dt = max_over_ranks((time.perf_counter() - t0) / steps, world, dev)
     step_flops = sum(p.flops for p in pts)
     return {"value": round(job_rate(step_flops, dt, world), 2), "unit": "GFLOP/s",
-            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": steps,
+            "h2d_bytes_per_step": int(pipe.h2d), "d2h_bytes_per_step": int(pipe.d2h), "steps": steps,
             "ms_per_step": round(dt * 1e3, 2),
             "path": "pinned host column-major -> H2D -> bf_pack -> routine -> bf_unpack -> D2H, "
                     "points issued small-n/large-n alternately through a three-stage pipeline "
-                    "(copy-in, compute, copy-out streams; %d input and %d output slots)" % (NI, NO)}
+                    "(copy-in, compute, copy-out streams; %d input and %d output slots)" % (pipe.NI, pipe.NO)}
 
 
 def run_mixed(args, dev, bt=8192, n=128, nrhs=4):

@@ -17,10 +17,12 @@
 //    factorization.
 //
 // One CTA per system.  The factor lives packed in shared memory (column l at
-// cs(l), element (i, l) at cs(l) + i), one warp solves one right-hand side
-// (column-oriented forward and backward substitution),
-// and the FP64 residual gives every thread one row of A, read from L2 in
-// panel-major order, for all right-hand sides at once.
+// cs(l), element (i, l) at cs(l) + i).  The FP64 solve gives one warp to one
+// right-hand side (column-oriented forward and backward substitution in
+// shared memory); the refinement's FP32 solves give one warp to four
+// right-hand sides held in registers.  The FP64 residual gives every thread
+// one row of A, read from L2 in panel-major order, for all right-hand sides
+// at once.
 #include <type_traits>
 
 #include "bf_internal.cuh"
@@ -82,6 +84,85 @@ __device__ __forceinline__ void warp_solve(const T *L, const T *dinv, T *v, int 
   }
 }
 
+// The single-precision solves of the refinement, d = L32^{-T} L32^{-1} r for
+// up to four right-hand sides k0..k0+3 by one warp, with the right-hand
+// sides in registers: lane l holds rows l, l + 32, ... (R slots) of each.
+// Column j's owner lane finishes y_j, one shuffle hands it to every lane,
+// and each lane updates its own rows; the four right-hand sides interleave,
+// so each step's shuffle latency is paid once for all of them.  Reads r from
+// r64 and adds d to x64 (both FP64, length n per right-hand side).
+template <int R>
+__device__ __forceinline__ void warp_solve_refine(const float *L, const float *dinv, const double *r64,
+                                                  double *x64, int n, int nrhs, int k0) {
+  const int lane = threadIdx.x & 31;
+  float v[R][4];
+#pragma unroll
+  for (int s = 0; s < R; s++)
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const int i = s * 32 + lane;
+      v[s][q] = (i < n && k0 + q < nrhs) ? (float)r64[(k0 + q) * n + i] : 0.0f;
+    }
+  // L y = r
+#pragma unroll
+  for (int s = 0; s < R; s++) {
+    for (int l = 0; l < 32; l++) {
+      const int j = s * 32 + l;
+      if (j >= n) break;
+      const float dj = dinv[j];
+      const int cs = col_start(j, n);
+      float y[4];
+#pragma unroll
+      for (int q = 0; q < 4; q++) y[q] = __shfl_sync(FULL, v[s][q], l) * dj;
+      if (lane == l) {
+#pragma unroll
+        for (int q = 0; q < 4; q++) v[s][q] = y[q];
+      }
+#pragma unroll
+      for (int t = s; t < R; t++) {
+        const int i = t * 32 + lane;
+        if (i > j && i < n) {
+          const float lij = L[cs + i];
+#pragma unroll
+          for (int q = 0; q < 4; q++) v[t][q] = fmaf(-lij, y[q], v[t][q]);
+        }
+      }
+    }
+  }
+  // L^T d = y, from the bottom up: L(j, i) = L^T(i, j) sits in packed column i
+#pragma unroll
+  for (int s = R - 1; s >= 0; s--) {
+    for (int l = 31; l >= 0; l--) {
+      const int j = s * 32 + l;
+      if (j >= n) continue;
+      const float dj = dinv[j];
+      float xj[4];
+#pragma unroll
+      for (int q = 0; q < 4; q++) xj[q] = __shfl_sync(FULL, v[s][q], l) * dj;
+      if (lane == l) {
+#pragma unroll
+        for (int q = 0; q < 4; q++) v[s][q] = xj[q];
+      }
+#pragma unroll
+      for (int t = 0; t <= s; t++) {
+        const int i = t * 32 + lane;
+        if (i < j) {
+          const float lji = L[col_start(i, n) + j];
+#pragma unroll
+          for (int q = 0; q < 4; q++) v[t][q] = fmaf(-lji, xj[q], v[t][q]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < R; s++)
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const int i = s * 32 + lane;
+      if (i < n && k0 + q < nrhs) x64[(k0 + q) * n + i] += (double)v[s][q];
+    }
+}
+
 // Column l of packed element e: column l starts at l(2n - l + 1)/2, so l is
 // the smaller root of l^2 - (2n+1) l + 2e = 0, corrected for rounding.
 __device__ __forceinline__ int packed_col(int e, int n) {
@@ -133,8 +214,17 @@ __device__ __forceinline__ void residual(int n, const double *pa, const Op &A, c
   }
 }
 
+// Resident CTAs the refinement kernel is compiled for: 4 caps it at 64
+// registers (no spills), so that shared memory (the FP32 factor, 42 KB at
+// n = 128) rather than registers bounds it, at 5 CTAs per SM.  Measured at
+// n = 128, 8192 systems, 4 right-hand sides: 4.16 ms at 116 registers (4
+// CTAs), 3.83 ms at 64.
+#ifndef BF_POSV_MINB
+#define BF_POSV_MINB 4
+#endif
+
 template <bool MIXED>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(256, MIXED ? BF_POSV_MINB : 1)
 k_posv(int n, int nrhs, Op A, const float *l32, long long sl32, const int *info32, Op Lf, Op B,
        OpW X, double tol, int max_iter, int *iters, double *resid) {
   using TL = typename std::conditional<MIXED, float, double>::type;
@@ -142,7 +232,7 @@ k_posv(int n, int nrhs, Op A, const float *l32, long long sl32, const int *info3
   const int b = blockIdx.x;
   const int t = threadIdx.x, T = blockDim.x;
   const int NE = n * (n + 1) / 2;
-  // shared memory: [x64 | r64 (MIXED)] [red] [L (TL)] [dinv (TL)] [v (TL)]
+  // shared memory: [x64 | r64 (MIXED)] [red] [L (TL)] [dinv (TL)] [v (TL, FP64 solve only)]
   double *x64 = smem_d;
   double *r64 = x64 + (MIXED ? nrhs * n : 0);
   double *red = r64 + (MIXED ? nrhs * n : 0);
@@ -210,12 +300,18 @@ k_posv(int n, int nrhs, Op A, const float *l32, long long sl32, const int *info3
   double rel = 0.0;
   bool done = false;
   for (; it < max_iter && !done; it++) {
-    // d = A32^{-1} r in single precision
-    for (int e = t; e < nrhs * n; e += T) v[e] = (TL)r64[e];
-    __syncthreads();
-    for (int k = warp; k < nrhs; k += nwarps) warp_solve<TL>(L, dinv, v + k * n, n);
-    __syncthreads();
-    for (int e = t; e < nrhs * n; e += T) x64[e] += (double)v[e];
+    // x += A32^{-1} r in single precision, four right-hand sides per warp
+    if constexpr (MIXED) {
+      for (int k0 = warp * 4; k0 < nrhs; k0 += nwarps * 4) {
+        switch ((n + 31) / 32) {
+          case 1: warp_solve_refine<1>(L, dinv, r64, x64, n, nrhs, k0); break;
+          case 2: warp_solve_refine<2>(L, dinv, r64, x64, n, nrhs, k0); break;
+          case 3: warp_solve_refine<3>(L, dinv, r64, x64, n, nrhs, k0); break;
+          case 4: warp_solve_refine<4>(L, dinv, r64, x64, n, nrhs, k0); break;
+          default: warp_solve_refine<5>(L, dinv, r64, x64, n, nrhs, k0); break;
+        }
+      }
+    }
     __syncthreads();
     // r = b - A x in FP64; thread i owns row i for every right-hand side
     double rs = 0.0, xs = 0.0;
@@ -229,11 +325,28 @@ k_posv(int n, int nrhs, Op A, const float *l32, long long sl32, const int *info3
       case 7: residual<7>(n, pa, A, pb, B, x64, r64, rs, xs); break;
       default: residual<8>(n, pa, A, pb, B, x64, r64, rs, xs); break;
     }
-    const double rn = sqrt(block_sum(rs, red));
-    const double xn = sqrt(block_sum(xs, red));
-    rel = rn / (anrm * xn);
-    done = rel <= tol;  // the same value in every thread
+    // both sums in one reduction; one thread forms the relative residual
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      rs += __shfl_xor_sync(FULL, rs, o);
+      xs += __shfl_xor_sync(FULL, xs, o);
+    }
+    if ((t & 31) == 0) {
+      red[warp] = rs;
+      red[16 + warp] = xs;
+    }
     __syncthreads();
+    if (t == 0) {
+      double rsum = 0.0, xsum = 0.0;
+      for (int w = 0; w < nwarps; w++) {
+        rsum += red[w];
+        xsum += red[16 + w];
+      }
+      red[31] = sqrt(rsum) / (anrm * sqrt(xsum));
+    }
+    __syncthreads();
+    rel = red[31];
+    done = rel <= tol;  // the same value in every thread
   }
   double *px = X.p + b * X.stride;
   for (int e = t; e < nrhs * n; e += T) {
@@ -294,7 +407,9 @@ size_t posv_smem(bool mixed, int n, int nrhs) {
   const size_t ne = (size_t)n * (n + 1) / 2;
   const size_t tl = mixed ? 4 : 8;
   size_t bytes = (mixed ? 2 * (size_t)nrhs * n * 8 : 0) + 32 * 8;
-  bytes += (((ne + 3) & ~(size_t)3) + (((size_t)n + 3) & ~(size_t)3) + (size_t)nrhs * n) * tl;
+  // the FP64 solve works on a copy of the right-hand sides in shared memory;
+  // the refinement keeps its single-precision ones in registers
+  bytes += (((ne + 3) & ~(size_t)3) + (((size_t)n + 3) & ~(size_t)3) + (mixed ? 0 : (size_t)nrhs * n)) * tl;
   return bytes;
 }
 

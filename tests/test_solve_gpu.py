@@ -75,7 +75,7 @@ def test_potrs_integer_exact_and_in_place():
     assert np.array_equal(get(dB), X.numpy())
 
 
-@pytest.mark.parametrize("n,nrhs,bt", [(8, 1, 33), (32, 4, 40), (128, 4, 64), (150, 2, 9)])
+@pytest.mark.parametrize("n,nrhs,bt", [(8, 1, 33), (32, 4, 40), (97, 6, 20), (128, 4, 64), (150, 2, 9), (160, 8, 12)])
 def test_mixed_reaches_1e12_on_cond_up_to_1e6(n, nrhs, bt):
     A, cond = inputs.spd_cond(bt, n, 420 + n, log10_cond=(2.0, 6.0))
     B = inputs.normal((bt, n, nrhs), 421)
