@@ -149,6 +149,8 @@ def kernel_of(routine, n):
         return f"k_chol_tiny<{n},{fused},1>"
     if n <= 40 and small_g(n):
         return f"k_chol_small<{small_g(n)},{fused},1>"
+    if 64 < n <= 128:
+        return f"k_chol_rows2<16,{fused},1,double,256>"
     if n <= 192:
         return f"k_chol_rows2<16,{fused},1,double,384>"
     if n <= 256:

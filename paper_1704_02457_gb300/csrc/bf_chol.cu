@@ -422,6 +422,15 @@ struct __align__(16) RowsSmem {
 #define BF_ROWS_P2_MAX_N_FUSED 256
 #endif
 
+// 64 < n <= 128: the two-problem kernel built for 4 CTAs of 256 threads per
+// SM (64 registers) rather than 2 of 384 (78-80 registers), so that more
+// CTAs keep the FP64 pipe fed while one factors a diagonal block.  Measured:
+// potrf n = 96 968 -> 998, n = 128 1018 -> 1061; syrk_potrf n = 128
+// 1101 -> 1118 GFLOP/s; at n = 48 and 64 it was 0.5-1% slower.
+#ifndef BF_ROWS_P2_T256
+#define BF_ROWS_P2_T256 1
+#endif
+
 #ifndef BF_ROWS_KUNROLL
 #define BF_ROWS_KUNROLL 4
 #endif
@@ -696,7 +705,7 @@ k_chol_rows(int batch, int n, int k, Op A, Op B, Op C, OpWT<T> D, T *dinv, long 
 // Two problems per CTA, up to MAXT/2 rows; registers bounded so that two
 // CTAs of MAXT threads fit an SM.
 template <int BW, bool FUSED, bool ALIGNED, typename T, int MAXT>
-__global__ void __launch_bounds__(MAXT, 2)
+__global__ void __launch_bounds__(MAXT, MAXT <= 256 ? 4 : 2)
 k_chol_rows2(int batch, int n, int k, Op A, Op B, Op C, OpWT<T> D, T *dinv, long long sdinv, int *info) {
   chol_rows_body<BW, 2, FUSED, ALIGNED, T>(blockIdx.x * 2, batch, n, k, A, B, C, D, dinv, sdinv, info);
 }
@@ -826,6 +835,8 @@ cudaError_t launch_rows(bool aligned, int batch, int n, int k, Op A, Op B, Op C,
                         long long sdinv, int *info, cudaStream_t s) {
   if constexpr (sizeof(T) == 8 || BF_ROWS_P2_FP32) {  // by default the FP32 factor keeps one problem per CTA
     constexpr int p2_max = FUSED ? BF_ROWS_P2_MAX_N_FUSED : BF_ROWS_P2_MAX_N;
+    if (BF_ROWS_P2_T256 && n > 64 && n <= 128)
+      return launch_rows_pairs<256, FUSED, T>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
     if (n <= 192 && n <= p2_max)
       return launch_rows_pairs<384, FUSED, T>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
     if (n <= p2_max)
