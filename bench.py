@@ -99,18 +99,6 @@ TRAFFIC = {
         "blob": "2cc3b29e43bfc36765f132c96806ac9719670d40",
         "profile": "profiles/k_gemm_nt_n256.md",
     },
-    ("k_chol_rows2<16,1,1,double,512>", "dsyrk_dpotrf_ln", 256): {
-        "bytes": 5684378880 + 266692352,
-        "src": "paper_1704_02457_gb300/csrc/bf_chol.cu",
-        "blob": "14e8434c67321ab73502d2863abf62a38e0bbc76",
-        "profile": "profiles/k_chol_rows2_syrk_potrf_n256.md",
-    },
-    ("k_chol_rows2<16,1,1,double,384>", "dsyrk_dpotrf_ln", 128): {
-        "bytes": 1884979200 + 281203200,
-        "src": "paper_1704_02457_gb300/csrc/bf_chol.cu",
-        "blob": "14e8434c67321ab73502d2863abf62a38e0bbc76",
-        "profile": "profiles/k_chol_rows2_syrk_potrf_n128.md",
-    },
 }
 
 
@@ -149,12 +137,14 @@ def kernel_of(routine, n):
         return f"k_chol_tiny<{n},{fused},1>"
     if n <= 40 and small_g(n):
         return f"k_chol_small<{small_g(n)},{fused},1>"
-    if 64 < n <= 128:
-        return f"k_chol_rows2<16,{fused},1,double,256>"
+    if n <= 64:
+        return f"k_chol_rows2<16,{fused},1,double,128,6>"
+    if n <= 128:
+        return f"k_chol_rows2<16,{fused},1,double,256,4>"
     if n <= 192:
-        return f"k_chol_rows2<16,{fused},1,double,384>"
+        return f"k_chol_rows2<16,{fused},1,double,384,3>"
     if n <= 256:
-        return f"k_chol_rows2<16,{fused},1,double,512>"
+        return f"k_chol_rows2<16,{fused},1,double,512,2>"
     return f"k_chol_rows<16,{fused},1,double>"
 
 

@@ -427,8 +427,25 @@ struct __align__(16) RowsSmem {
 // CTAs keep the FP64 pipe fed while one factors a diagonal block.  Measured:
 // potrf n = 96 968 -> 998, n = 128 1018 -> 1061; syrk_potrf n = 128
 // 1101 -> 1118 GFLOP/s; at n = 48 and 64 it was 0.5-1% slower.
-#ifndef BF_ROWS_P2_T256
-#define BF_ROWS_P2_T256 1
+// Resident CTAs per SM that each build of the two-problem kernel is
+// compiled for (its register bound: 65536 / (threads x CTAs)).  More CTAs
+// keep the FP64 pipe fed while one factors a diagonal block; fewer registers
+// slow the k-loops.  Measured (GFLOP/s):
+//   n <= 64,  128 threads: 6 CTAs (80 registers); 8 (64) was 0.5-1% slower
+//   n <= 128, 256 threads: 4 (64) against 3 (80): potrf n = 96 968 -> 998,
+//                          n = 128 1018 -> 1061; syrk_potrf n = 128 1101 -> 1118
+//   n <= 192, 384 threads: 3 (56, some spills) against 2 (78-80): potrf
+//                          n = 144 911 -> 1052, n = 192 1041 -> 1103;
+//                          syrk_potrf n = 144 1041 -> 1129, n = 192 1125 -> 1157
+//   n <= 256, 512 threads: 2 (64)
+#ifndef BF_ROWS_P2_MINB128
+#define BF_ROWS_P2_MINB128 6
+#endif
+#ifndef BF_ROWS_P2_MINB256
+#define BF_ROWS_P2_MINB256 4
+#endif
+#ifndef BF_ROWS_P2_MINB384
+#define BF_ROWS_P2_MINB384 3
 #endif
 
 #ifndef BF_ROWS_KUNROLL
@@ -702,10 +719,10 @@ k_chol_rows(int batch, int n, int k, Op A, Op B, Op C, OpWT<T> D, T *dinv, long 
   chol_rows_body<BW, 1, FUSED, ALIGNED, T>(blockIdx.x, batch, n, k, A, B, C, D, dinv, sdinv, info);
 }
 
-// Two problems per CTA, up to MAXT/2 rows; registers bounded so that two
+// Two problems per CTA, up to MAXT/2 rows; registers bounded so that MINB
 // CTAs of MAXT threads fit an SM.
-template <int BW, bool FUSED, bool ALIGNED, typename T, int MAXT>
-__global__ void __launch_bounds__(MAXT, MAXT <= 256 ? 4 : 2)
+template <int BW, bool FUSED, bool ALIGNED, typename T, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB)
 k_chol_rows2(int batch, int n, int k, Op A, Op B, Op C, OpWT<T> D, T *dinv, long long sdinv, int *info) {
   chol_rows_body<BW, 2, FUSED, ALIGNED, T>(blockIdx.x * 2, batch, n, k, A, B, C, D, dinv, sdinv, info);
 }
@@ -753,8 +770,9 @@ k_chol_rows_v(int batch, const bf_dsize *size, const bf_dsub *A, const bf_dsub *
 constexpr int ROWS_BW = 16;
 
 
-// MAXT: the launch bound of the two-problem kernel (0 for one problem per CTA)
-template <int MAXT, bool FUSED, bool ALIGNED, typename T>
+// MAXT, MINB: the launch bounds of the two-problem kernel (MAXT = 0: one
+// problem per CTA)
+template <int MAXT, int MINB, bool FUSED, bool ALIGNED, typename T>
 cudaError_t launch_rows_p(int batch, int n, int k, Op A, Op B, Op C, OpWT<T> D, T *dinv, long long sdinv,
                           int *info, cudaStream_t s) {
   constexpr int P = MAXT ? 2 : 1;
@@ -764,16 +782,16 @@ cudaError_t launch_rows_p(int batch, int n, int k, Op A, Op B, Op C, OpWT<T> D, 
   if constexpr (P == 1)
     k_chol_rows<ROWS_BW, FUSED, ALIGNED, T><<<blocks, threads, 0, s>>>(batch, n, k, A, B, C, D, dinv, sdinv, info);
   else
-    k_chol_rows2<ROWS_BW, FUSED, ALIGNED, T, MAXT>
+    k_chol_rows2<ROWS_BW, FUSED, ALIGNED, T, MAXT, MINB>
         <<<blocks, threads, 0, s>>>(batch, n, k, A, B, C, D, dinv, sdinv, info);
   return cudaGetLastError();
 }
 
-template <int MAXT, bool FUSED, typename T>
+template <int MAXT, int MINB, bool FUSED, typename T>
 cudaError_t launch_rows_a(bool aligned, int batch, int n, int k, Op A, Op B, Op C, OpWT<T> D, T *dinv,
                           long long sdinv, int *info, cudaStream_t s) {
-  return aligned ? launch_rows_p<MAXT, FUSED, true, T>(batch, n, k, A, B, C, D, dinv, sdinv, info, s)
-                 : launch_rows_p<MAXT, FUSED, false, T>(batch, n, k, A, B, C, D, dinv, sdinv, info, s);
+  return aligned ? launch_rows_p<MAXT, MINB, FUSED, true, T>(batch, n, k, A, B, C, D, dinv, sdinv, info, s)
+                 : launch_rows_p<MAXT, MINB, FUSED, false, T>(batch, n, k, A, B, C, D, dinv, sdinv, info, s);
 }
 
 // Tail balance of the two-problem kernel at n > 192 (512-thread CTAs, two
@@ -803,15 +821,15 @@ inline Op shift_op(Op o, long long b) {
   return o;
 }
 
-template <int MAXT, bool FUSED, typename T>
+template <int MAXT, int MINB, bool FUSED, typename T>
 cudaError_t launch_rows_pairs(bool aligned, int batch, int n, int k, Op A, Op B, Op C, OpWT<T> D, T *dinv,
                               long long sdinv, int *info, cudaStream_t s) {
   int pairs_cut = 0;  // pairs that go to the two-problem kernel when the tail is split
   if (BF_ROWS_TAIL_FILL > 0 && MAXT > 384 && n > 192) {
     static std::atomic<int> occ[64 * 17];
     const int threads = ((n + 15) / 16) * 32;
-    const void *fn = aligned ? (const void *)k_chol_rows2<ROWS_BW, FUSED, true, T, MAXT>
-                             : (const void *)k_chol_rows2<ROWS_BW, FUSED, false, T, MAXT>;
+    const void *fn = aligned ? (const void *)k_chol_rows2<ROWS_BW, FUSED, true, T, MAXT, MINB>
+                             : (const void *)k_chol_rows2<ROWS_BW, FUSED, false, T, MAXT, MINB>;
     const int sms = device_sm_count();
     const long long slots = (long long)resident_ctas(fn, threads, occ) * sms;
     const long long pairs = (batch + 1) / 2;
@@ -821,11 +839,11 @@ cudaError_t launch_rows_pairs(bool aligned, int batch, int n, int k, Op A, Op B,
     }
   }
   if (pairs_cut == 0)
-    return launch_rows_a<MAXT, FUSED, T>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
+    return launch_rows_a<MAXT, MINB, FUSED, T>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
   const int head = 2 * pairs_cut;
-  cudaError_t e = launch_rows_a<MAXT, FUSED, T>(aligned, head, n, k, A, B, C, D, dinv, sdinv, info, s);
+  cudaError_t e = launch_rows_a<MAXT, MINB, FUSED, T>(aligned, head, n, k, A, B, C, D, dinv, sdinv, info, s);
   if (e != cudaSuccess) return e;
-  return launch_rows_a<0, FUSED, T>(aligned, batch - head, n, k, shift_op(A, head), shift_op(B, head),
+  return launch_rows_a<0, 1, FUSED, T>(aligned, batch - head, n, k, shift_op(A, head), shift_op(B, head),
                                     shift_op(C, head), shift_op(D, head), dinv ? dinv + head * sdinv : nullptr,
                                     sdinv, info ? info + head : nullptr, s);
 }
@@ -835,15 +853,19 @@ cudaError_t launch_rows(bool aligned, int batch, int n, int k, Op A, Op B, Op C,
                         long long sdinv, int *info, cudaStream_t s) {
   if constexpr (sizeof(T) == 8 || BF_ROWS_P2_FP32) {  // by default the FP32 factor keeps one problem per CTA
     constexpr int p2_max = FUSED ? BF_ROWS_P2_MAX_N_FUSED : BF_ROWS_P2_MAX_N;
-    if (BF_ROWS_P2_T256 && n > 64 && n <= 128)
-      return launch_rows_pairs<256, FUSED, T>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
+    if (n <= 64 && n <= p2_max)
+      return launch_rows_pairs<128, BF_ROWS_P2_MINB128, FUSED, T>(aligned, batch, n, k, A, B, C, D, dinv, sdinv,
+                                                                  info, s);
+    if (n <= 128 && n <= p2_max)
+      return launch_rows_pairs<256, BF_ROWS_P2_MINB256, FUSED, T>(aligned, batch, n, k, A, B, C, D, dinv, sdinv,
+                                                                  info, s);
     if (n <= 192 && n <= p2_max)
-      return launch_rows_pairs<384, FUSED, T>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
+      return launch_rows_pairs<384, BF_ROWS_P2_MINB384, FUSED, T>(aligned, batch, n, k, A, B, C, D, dinv, sdinv,
+                                                                  info, s);
     if (n <= p2_max)
-      return launch_rows_pairs<2 * (p2_max > 192 ? p2_max : 192), FUSED, T>(aligned, batch, n, k, A, B, C, D,
-                                                                          dinv, sdinv, info, s);
+      return launch_rows_pairs<512, 2, FUSED, T>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
   }
-  return launch_rows_a<0, FUSED, T>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
+  return launch_rows_a<0, 1, FUSED, T>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
 }
 
 // Lanes per problem of k_chol_small: the smallest G (at most 16) whose

@@ -104,13 +104,13 @@ def test_kernel_labels_follow_the_library_size_rules():
     assert bench.kernel_of("dsyrk_dpotrf_ln", 8) == "k_chol_tiny<8,1,1>"
     assert bench.kernel_of("dpotrf_l", 16).startswith("k_chol_small<")
     assert bench.kernel_of("dpotrf_l", 40).startswith("k_chol_small<")
-    assert bench.kernel_of("dpotrf_l", 48) == "k_chol_rows2<16,0,1,double,384>"
-    assert bench.kernel_of("dpotrf_l", 64) == "k_chol_rows2<16,0,1,double,384>"
-    assert bench.kernel_of("dpotrf_l", 96) == "k_chol_rows2<16,0,1,double,256>"
-    assert bench.kernel_of("dsyrk_dpotrf_ln", 128) == "k_chol_rows2<16,1,1,double,256>"
-    assert bench.kernel_of("dpotrf_l", 256) == "k_chol_rows2<16,0,1,double,512>"
-    assert bench.kernel_of("dsyrk_dpotrf_ln", 192) == "k_chol_rows2<16,1,1,double,384>"
-    assert bench.kernel_of("dsyrk_dpotrf_ln", 256) == "k_chol_rows2<16,1,1,double,512>"
+    assert bench.kernel_of("dpotrf_l", 48) == "k_chol_rows2<16,0,1,double,128,6>"
+    assert bench.kernel_of("dpotrf_l", 64) == "k_chol_rows2<16,0,1,double,128,6>"
+    assert bench.kernel_of("dpotrf_l", 96) == "k_chol_rows2<16,0,1,double,256,4>"
+    assert bench.kernel_of("dsyrk_dpotrf_ln", 128) == "k_chol_rows2<16,1,1,double,256,4>"
+    assert bench.kernel_of("dpotrf_l", 256) == "k_chol_rows2<16,0,1,double,512,2>"
+    assert bench.kernel_of("dsyrk_dpotrf_ln", 192) == "k_chol_rows2<16,1,1,double,384,3>"
+    assert bench.kernel_of("dsyrk_dpotrf_ln", 256) == "k_chol_rows2<16,1,1,double,512,2>"
     assert bench.kernel_of("dsyrk_dpotrf_ln", 300) == "k_chol_rows<16,1,1,double>"
     assert bench.kernel_of("dgemm_nt", 4) == "k_gemm_nt<0,1,1>"
 
