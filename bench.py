@@ -135,10 +135,12 @@ def kernel_of(routine, n):
     fused = int(routine == "dsyrk_dpotrf_ln")
     if n <= 8:  # the sweep's batches give one lane per problem
         return f"k_chol_tiny<{n},{fused},1>"
-    if n <= 40 and small_g(n):
+    if n <= 31 and small_g(n):
         return f"k_chol_small<{small_g(n)},{fused},1>"
     if n <= 64:
-        return f"k_chol_rows2<16,{fused},1,double,128,6>"
+        return f"k_chol_rows4<{fused},1,double,256,4>"
+    if n <= 88:
+        return f"k_chol_rows4<{fused},1,double,512,2>"
     if n <= 128:
         return f"k_chol_rows2<16,{fused},1,double,256,4>"
     if n <= 192:

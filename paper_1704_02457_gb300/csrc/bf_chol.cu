@@ -16,7 +16,7 @@
 //    one warp per SM sub-partition): one lane per problem, the whole
 //    triangle in registers, factored right-looking with compile-time indices.
 //
-//  k_chol_small (n <= 40): a warp holds Q = 32/G problems, G lanes per
+//  k_chol_small (n <= 31): a warp holds Q = 32/G problems, G lanes per
 //    problem.  The lower triangles live packed in shared memory, problem q's
 //    element e at sm[e*Q' + q], Q' = Q + 1 for Q >= 16: the odd pitch puts
 //    the elements that the load and store phases copy for one problem (lanes
@@ -26,14 +26,16 @@
 //    problems.  For syrk_potrf the A*B^T sum is added in 4x4 register blocks
 //    straight into the shared-memory triangle before the factorization.
 //
-//  k_chol_rows (n <= 512): one thread per row, blocks of 16 columns held in
-//    registers, P problems per CTA (P = 2 up to n = 256: a warp holds 16 rows
-//    of each of the two problems, so the diagonal block of a block column is
-//    one full warp, which computes only the block's lower triangle, spread
-//    evenly over its lanes; P = 1 above).  For block column [c0, c0+16):
+//  k_chol_rows4 / k_chol_rows2 / k_chol_rows (n <= 512): one thread per row,
+//    blocks of BW columns held in registers, P problems per CTA, a warp
+//    holding 32/P rows of each: P = 4 with BW = 8 for n = 32..88, P = 2 with
+//    BW = 16 up to n = 256, P = 1 above.  With P*BW = 32 the diagonal block
+//    of a block column is one full warp, which computes only the block's
+//    lower triangle, spread evenly over its lanes.  For block column
+//    [c0, c0+BW):
 //      (a) acc = C[i][c0..]  (+ A[i][:] * B[c0..][:]^T for syrk_potrf)
 //      (b) acc -= L[i][0:c0] * L[c0..][0:c0]^T            (gemm_nt downdate)
-//      (c) the lanes of rows c0..c0+15 factor the diagonal block in
+//      (c) the lanes of rows c0..c0+BW-1 factor the diagonal block in
 //          registers with warp shuffles (potrf_l kernel on a register block)
 //      (d) the rows below solve against it (trsm_rltn kernel)
 //    The operand rows shared by a problem's threads, B[c0..][l..] and
@@ -438,6 +440,29 @@ struct __align__(16) RowsSmem {
 //                          n = 144 911 -> 1052, n = 192 1041 -> 1103;
 //                          syrk_potrf n = 144 1041 -> 1129, n = 192 1125 -> 1157
 //   n <= 256, 512 threads: 2 (64)
+// Orders factored four problems per CTA (k_chol_rows4), per routine.
+// Measured against the small kernel below and the two-problem kernel above
+// (GFLOP/s, potrf / syrk_potrf):
+//   n = 32: 626 -> 730 / 849 -> 1024     n = 48: 709 -> 896 / 1013 -> 1097
+//   n = 40: 593 -> 821 / 892 -> 1065     n = 64: 853 -> 979 / 1088 -> 1136
+//   n = 72: 713 -> 961 / 899 -> 1091     n = 88: 789 -> 915 / 941 -> 1048
+// At n = 96 and 128 the two-problem kernel is 2-4% faster; below 32 the
+// small kernel is (n = 28: 596 against 490, n = 16: 578 against 371).
+#ifndef BF_ROWS_P4_MIN_N
+#define BF_ROWS_P4_MIN_N 32
+#endif
+#ifndef BF_ROWS_P4_MAX_N
+#define BF_ROWS_P4_MAX_N 88
+#endif
+#ifndef BF_ROWS_P4_MIN_N_FUSED
+#define BF_ROWS_P4_MIN_N_FUSED 32
+#endif
+#ifndef BF_ROWS_P4_MAX_N_FUSED
+#define BF_ROWS_P4_MAX_N_FUSED 88
+#endif
+#ifndef BF_ROWS_P4_MINB256
+#define BF_ROWS_P4_MINB256 4
+#endif
 #ifndef BF_ROWS_P2_MINB128
 #define BF_ROWS_P2_MINB128 6
 #endif
@@ -470,19 +495,23 @@ struct RowMap {
   }
 };
 
-// Balanced split of a 16 x 16 lower triangle (136 entries) over 16 lanes:
-// lane s takes row s up to column min(s, 8), and lanes s <= 6 also take row
-// 15 - s from column 9 on.  Slot m (0..8) of lane s is entry (row, col);
-// lanes 0..7 use slots 0..7, lanes 8..15 slots 0..8.
+// Balanced split of a BW x BW lower triangle over BW lanes, H = BW/2: lane s
+// takes row s up to column min(s, H), and lanes s <= H - 2 also take row
+// BW-1-s from column H+1 on.  Slot m (0..H) of lane s is entry (row, col);
+// lanes below H use slots 0..H-1, the others 0..H.  For BW = 16 that is at
+// most 9 entries a lane for the triangle's 136 (8.5 on average); for BW = 8,
+// 5 for 36.
+template <int BW>
 __device__ __forceinline__ void split_slot(int s, int m, int &row, int &col, bool &valid) {
-  if (s >= 8 || m <= s) {
+  constexpr int H = BW / 2;
+  if (s >= H || m <= s) {
     row = s;
     col = m;
     valid = m <= s;
   } else {
-    row = 15 - s;
-    col = 8 + m - s;
-    valid = m <= 7;
+    row = BW - 1 - s;
+    col = H + m - s;
+    valid = m <= H - 1;
   }
 }
 
@@ -507,9 +536,10 @@ __device__ __forceinline__ void rows_block(RowsSmem<T, BW, P> &S, const RowMap<P
   // block (16 rows of each problem) computes only the block's lower triangle
   // in (a') and (b), spread over its lanes by split_slot: at most 9 FMAs per
   // step a lane instead of 16.  Its rows are gathered back before (c).
-  constexpr bool SPLIT = BF_ROWS_SPLIT && (P == 2 && BW == 16 && W == 16);
+  constexpr int H = BW / 2, NSLOT = H + 1;
+  constexpr bool SPLIT = BF_ROWS_SPLIT && (P * BW == 32 && W == BW && BW >= 8);
   const bool dwarp = SPLIT && ((t >> 5) == c0 / RPW);  // warp-uniform
-  const int s16 = rm.lane & 15;                         // row within the diagonal block
+  const int sb = rm.lane & (BW - 1);                    // row within the diagonal block
 
   // (a) C[i][c0 + jj] for the lower part of the block column.  The diagonal
   // warp keeps its 9 triangle slots in acc[0..8] until it gathers its rows,
@@ -537,18 +567,18 @@ __device__ __forceinline__ void rows_block(RowsSmem<T, BW, P> &S, const RowMap<P
       }
       __syncthreads();
       if (dwarp) {
-        const int ro = 15 - s16, smax = s16 >= 8 ? 8 : s16;  // slots m <= smax are on the lane's own row
-        const bool own_ok = me_valid && s16 < w, oth_ok = me_valid && s16 <= 6 && ro < w;
+        const int ro = BW - 1 - sb, smax = min(sb, H);  // slots m <= smax are on the lane's own row
+        const bool own_ok = me_valid && sb < w, oth_ok = me_valid && sb <= H - 2 && ro < w;
         const double *arow_o = pa + pm_off(A.i0 + min(c0 + ro, n - 1), A.j0, A.cn);
-        const int obase = max(0, 8 - s16);  // other-row slot m reads column 8 + m - s16
+        const int obase = max(0, H - sb);  // other-row slot m reads column H + m - sb
         for (int ll = 0; ll < kc; ll++) {
           const T xo = own_ok ? (T)__ldg(arow + (long long)(l0 + ll) * PS) : (T)0;
           const T xt = oth_ok ? (T)__ldg(arow_o + (long long)(l0 + ll) * PS) : (T)0;
           const T *st = S.stage[p][ll];
 #pragma unroll
-          for (int m = 0; m < 9; m++) {
+          for (int m = 0; m < NSLOT; m++) {
             const bool own = m <= smax;
-            acc[m] = fma_t(own ? xo : xt, own ? st[m] : st[min(obase + m, 15)], acc[m]);
+            acc[m] = fma_t(own ? xo : xt, own ? st[m] : st[min(obase + m, BW - 1)], acc[m]);
           }
         }
       } else if (active) {
@@ -583,14 +613,14 @@ __device__ __forceinline__ void rows_block(RowsSmem<T, BW, P> &S, const RowMap<P
       }
       __syncthreads();
       if (dwarp) {
-        const int smax = s16 >= 8 ? 8 : s16, obase = max(0, 8 - s16);
+        const int smax = min(sb, H), obase = max(0, H - sb);
         for (int ll = 0; ll < kc; ll++) {
           const T *st = S.stage[p][ll];
-          const T xo = st[s16], xt = st[15 - s16];
+          const T xo = st[sb], xt = st[BW - 1 - sb];
 #pragma unroll
-          for (int m = 0; m < 9; m++) {
+          for (int m = 0; m < NSLOT; m++) {
             const bool own = m <= smax;
-            acc[m] = fma_t(-(own ? xo : xt), own ? st[m] : st[min(obase + m, 15)], acc[m]);
+            acc[m] = fma_t(-(own ? xo : xt), own ? st[m] : st[min(obase + m, BW - 1)], acc[m]);
           }
         }
       } else if (active) {
@@ -611,18 +641,18 @@ __device__ __forceinline__ void rows_block(RowsSmem<T, BW, P> &S, const RowMap<P
   // the diagonal warp: slots to shared memory, then each lane its row, plus C
   if (dwarp) {
 #pragma unroll
-    for (int m = 0; m < 9; m++) {
+    for (int m = 0; m < NSLOT; m++) {
       int row, col;
       bool ok;
-      split_slot(s16, m, row, col, ok);
+      split_slot<BW>(sb, m, row, col, ok);
       if (ok) S.Ls[p][row][col] = acc[m];
     }
     __syncwarp();
 #pragma unroll
     for (int jj = 0; jj < W; jj++) {
-      const bool lower = jj <= s16;
-      const T cv = (me_valid && s16 < w && jj < w && lower) ? (T)pc[pm_off(C.i0 + i, C.j0 + c0 + jj, C.cn)] : (T)0;
-      acc[jj] = cv + (lower ? S.Ls[p][s16][jj] : (T)0);
+      const bool lower = jj <= sb;
+      const T cv = (me_valid && sb < w && jj < w && lower) ? (T)pc[pm_off(C.i0 + i, C.j0 + c0 + jj, C.cn)] : (T)0;
+      acc[jj] = cv + (lower ? S.Ls[p][sb][jj] : (T)0);
     }
     __syncwarp();
   }
@@ -701,13 +731,18 @@ __device__ __forceinline__ void chol_rows_body(int b0, int batch, int n, int k, 
   if (threadIdx.x < P) S.bad[threadIdx.x] = 0;
   __syncthreads();
   for (int c0 = 0; c0 < n; c0 += BW) {
-    const int w8 = (min(BW, n - c0) + 7) & ~7;
-    if (w8 == 8)
-      rows_block<8, BW, P, FUSED, ALIGNED, T>(S, rm, c0, n, k, b0, batch, me_valid, pa, pc, pd, A, B, C, D, dinv,
-                                              sdinv);
-    else
-      rows_block<16, BW, P, FUSED, ALIGNED, T>(S, rm, c0, n, k, b0, batch, me_valid, pa, pc, pd, A, B, C, D, dinv,
-                                               sdinv);
+    if constexpr (BW == 8) {
+      rows_block<8, 8, P, FUSED, ALIGNED, T>(S, rm, c0, n, k, b0, batch, me_valid, pa, pc, pd, A, B, C, D, dinv,
+                                             sdinv);
+    } else {
+      const int w8 = (min(BW, n - c0) + 7) & ~7;
+      if (w8 == 8)
+        rows_block<8, BW, P, FUSED, ALIGNED, T>(S, rm, c0, n, k, b0, batch, me_valid, pa, pc, pd, A, B, C, D, dinv,
+                                                sdinv);
+      else
+        rows_block<16, BW, P, FUSED, ALIGNED, T>(S, rm, c0, n, k, b0, batch, me_valid, pa, pc, pd, A, B, C, D,
+                                                 dinv, sdinv);
+    }
   }
   if (info && threadIdx.x < P && b0 + (int)threadIdx.x < batch) info[b0 + threadIdx.x] = S.bad[threadIdx.x];
 }
@@ -725,6 +760,15 @@ template <int BW, bool FUSED, bool ALIGNED, typename T, int MAXT, int MINB>
 __global__ void __launch_bounds__(MAXT, MINB)
 k_chol_rows2(int batch, int n, int k, Op A, Op B, Op C, OpWT<T> D, T *dinv, long long sdinv, int *info) {
   chol_rows_body<BW, 2, FUSED, ALIGNED, T>(blockIdx.x * 2, batch, n, k, A, B, C, D, dinv, sdinv, info);
+}
+
+// Four problems per CTA with 8-column blocks: a warp holds 8 rows of each
+// of four problems, so each rsqrt and shuffle step of a diagonal block's
+// factorization serves four problems instead of two.  Up to MAXT/4 rows.
+template <bool FUSED, bool ALIGNED, typename T, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB)
+k_chol_rows4(int batch, int n, int k, Op A, Op B, Op C, OpWT<T> D, T *dinv, long long sdinv, int *info) {
+  chol_rows_body<8, 4, FUSED, ALIGNED, T>(blockIdx.x * 4, batch, n, k, A, B, C, D, dinv, sdinv, info);
 }
 
 // Descriptor-array form: CTA b factors problem b of its own order (rows past
@@ -784,6 +828,18 @@ cudaError_t launch_rows_p(int batch, int n, int k, Op A, Op B, Op C, OpWT<T> D, 
   else
     k_chol_rows2<ROWS_BW, FUSED, ALIGNED, T, MAXT, MINB>
         <<<blocks, threads, 0, s>>>(batch, n, k, A, B, C, D, dinv, sdinv, info);
+  return cudaGetLastError();
+}
+
+template <int MAXT, int MINB, bool FUSED, typename T>
+cudaError_t launch_rows4(bool aligned, int batch, int n, int k, Op A, Op B, Op C, OpWT<T> D, T *dinv,
+                         long long sdinv, int *info, cudaStream_t s) {
+  const int threads = ((n + 7) / 8) * 32;
+  const unsigned blocks = (unsigned)((batch + 3) / 4);
+  if (aligned)
+    k_chol_rows4<FUSED, true, T, MAXT, MINB><<<blocks, threads, 0, s>>>(batch, n, k, A, B, C, D, dinv, sdinv, info);
+  else
+    k_chol_rows4<FUSED, false, T, MAXT, MINB><<<blocks, threads, 0, s>>>(batch, n, k, A, B, C, D, dinv, sdinv, info);
   return cudaGetLastError();
 }
 
@@ -853,6 +909,13 @@ cudaError_t launch_rows(bool aligned, int batch, int n, int k, Op A, Op B, Op C,
                         long long sdinv, int *info, cudaStream_t s) {
   if constexpr (sizeof(T) == 8 || BF_ROWS_P2_FP32) {  // by default the FP32 factor keeps one problem per CTA
     constexpr int p2_max = FUSED ? BF_ROWS_P2_MAX_N_FUSED : BF_ROWS_P2_MAX_N;
+    constexpr int p4_min = FUSED ? BF_ROWS_P4_MIN_N_FUSED : BF_ROWS_P4_MIN_N;
+    constexpr int p4_max = FUSED ? BF_ROWS_P4_MAX_N_FUSED : BF_ROWS_P4_MAX_N;
+    if (n >= p4_min && n <= p4_max && n <= 64)
+      return launch_rows4<256, BF_ROWS_P4_MINB256, FUSED, T>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info,
+                                                            s);
+    if (n >= p4_min && n <= p4_max && n <= 128)
+      return launch_rows4<512, 2, FUSED, T>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
     if (n <= 64 && n <= p2_max)
       return launch_rows_pairs<128, BF_ROWS_P2_MINB128, FUSED, T>(aligned, batch, n, k, A, B, C, D, dinv, sdinv,
                                                                   info, s);
@@ -882,11 +945,10 @@ cudaError_t launch_rows(bool aligned, int batch, int n, int k, Op A, Op B, Op C,
 #endif
 constexpr long long SMALL_SMEM_BUDGET = BF_SMALL_SMEM_BUDGET_KB * 1024;
 
-// Largest order factored by k_chol_small; the row kernel takes over above
-// (measured with the triangle split: at n = 48 the two-problem row kernel is
-// 12% faster for potrf and 9% for syrk_potrf, at n = 40 it is slower).
+// Largest order factored by k_chol_small; the four-problem row kernel takes
+// over above (see BF_ROWS_P4_MIN_N).
 #ifndef BF_CHOL_SMALL_MAX_N
-#define BF_CHOL_SMALL_MAX_N 40
+#define BF_CHOL_SMALL_MAX_N 31
 #endif
 int pick_small_g(int n) {
   const long long ne = (long long)n * (n + 1) / 2;

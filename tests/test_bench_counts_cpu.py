@@ -103,9 +103,11 @@ def test_kernel_labels_follow_the_library_size_rules():
     assert bench.kernel_of("dpotrf_l", 4) == "k_chol_tiny<4,0,1>"
     assert bench.kernel_of("dsyrk_dpotrf_ln", 8) == "k_chol_tiny<8,1,1>"
     assert bench.kernel_of("dpotrf_l", 16).startswith("k_chol_small<")
-    assert bench.kernel_of("dpotrf_l", 40).startswith("k_chol_small<")
-    assert bench.kernel_of("dpotrf_l", 48) == "k_chol_rows2<16,0,1,double,128,6>"
-    assert bench.kernel_of("dpotrf_l", 64) == "k_chol_rows2<16,0,1,double,128,6>"
+    assert bench.kernel_of("dpotrf_l", 24).startswith("k_chol_small<")
+    assert bench.kernel_of("dpotrf_l", 40) == "k_chol_rows4<0,1,double,256,4>"
+    assert bench.kernel_of("dpotrf_l", 48) == "k_chol_rows4<0,1,double,256,4>"
+    assert bench.kernel_of("dpotrf_l", 64) == "k_chol_rows4<0,1,double,256,4>"
+    assert bench.kernel_of("dsyrk_dpotrf_ln", 88) == "k_chol_rows4<1,1,double,512,2>"
     assert bench.kernel_of("dpotrf_l", 96) == "k_chol_rows2<16,0,1,double,256,4>"
     assert bench.kernel_of("dsyrk_dpotrf_ln", 128) == "k_chol_rows2<16,1,1,double,256,4>"
     assert bench.kernel_of("dpotrf_l", 256) == "k_chol_rows2<16,0,1,double,512,2>"

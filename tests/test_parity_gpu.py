@@ -358,9 +358,10 @@ def test_syrk_potrf_config_form(n, k):
     check_dinv(dD.dinv().cpu().numpy(), got, dinv_want)
 
 
-@pytest.mark.parametrize("n", [65, 100, 192])
+@pytest.mark.parametrize("n", [65, 100, 192, 250])
 def test_syrk_potrf_paired_problems_odd_batch_and_failing_neighbour(n):
-    """Up to n = 192 the row kernel factors two problems per CTA.  With an odd
+    """From n = 89 to 256 the row kernel factors two problems per CTA (n = 65
+    takes the four-problem kernel, which this covers as well).  With an odd
     batch the last CTA has one problem; a failing problem must not disturb the
     other problem of its CTA."""
     bt, k = 5, 7
@@ -499,6 +500,55 @@ def test_rows_tail_split_every_problem(n, k):
         if c > 0:
             ref = np.tril(want[b])[:, :c]
             assert fro(np.tril(got[b])[:, :c] - ref) / fro(ref) <= 1e-12
+
+
+@pytest.mark.parametrize("n,k,offs", [(32, 0, (0, 0)), (37, 9, (0, 0)), (40, 0, (1, 2)), (57, 20, (0, 0)),
+                                      (64, 64, (5, 3)), (71, 0, (0, 0)), (88, 30, (0, 0))])
+def test_four_problem_ctas_every_problem(n, k, offs):
+    """Orders 32..88 are factored four problems per CTA with 8-column blocks.
+    A batch of 11 leaves the last CTA three problems; failures sit at two
+    positions of one CTA and at the batch's end, the rest of each CTA must
+    be unaffected.  Ragged orders leave a partial last block."""
+    bt = 11
+    ai, aj = offs
+    fused = k > 0
+    if fused:
+        M = inputs.normal((bt, n, k), 700 + n).numpy()
+        Q = np.broadcast_to(np.eye(n) * float(n), (bt, n, n)).copy()
+    else:
+        Q = inputs.spd(bt, n, 700 + n).numpy()
+    bad = {4: 1, 6: n - 3, 10: (n + 1) // 2}  # CTA 1 holds problems 4..7, the last CTA 8..10
+    for b, col in bad.items():
+        Q[b, col - 1, col - 1] = -1e9
+    if fused:
+        want, dinv_want, info_want = oracle.dsyrk_dpotrf_ln(M, M, Q)
+    else:
+        want, dinv_want, info_want = oracle.dpotrf_l(Q)
+    dQ = put(torch.from_numpy(Q), n + ai, n + aj, ai, aj)
+    dD = bf.DMatBatch(bt, n + ai, n + aj, fill=np.nan)
+    info = torch.full((bt,), -7, dtype=torch.int32, device=dev())
+    if fused:
+        dM = put(torch.from_numpy(M), n + ai, k + 2, ai, 2)
+        bf.dsyrk_dpotrf_ln(n, k, dM, ai, 2, dM, ai, 2, dQ, ai, aj, dD, ai, aj, info=info)
+    else:
+        bf.dpotrf_l(n, dQ, ai, aj, dD, ai, aj, info=info)
+    got_info = info.cpu().numpy()
+    assert np.array_equal(got_info, info_want)
+    assert {int(b): int(got_info[b]) for b in np.nonzero(got_info)[0]} == bad
+    got = get(dD)[:, ai:, aj:]
+    dinv = dD.dinv().cpu().numpy()[:, :n]
+    for b in range(bt):
+        if b in bad:
+            c = bad[b] - 1
+            if c > 0:
+                ref = np.tril(want[b])[:, :c]
+                assert fro(np.tril(got[b])[:, :c] - ref) / fro(ref) <= 1e-12
+            continue
+        S = Q[b] + (M[b] @ M[b].T if fused else 0.0)
+        assert chol_resid(got[b], S) <= 1e-13
+        assert fro(np.tril(got[b]) - np.tril(want[b])) / fro(np.tril(want[b])) <= 1e-12
+        assert np.all(np.isnan(got[b][np.triu(np.ones((n, n), dtype=bool), 1)]))
+        check_dinv(dinv[b], got[b], dinv_want[b])
 
 
 @pytest.mark.parametrize("n,k", [(4, 4), (8, 3), (24, 24), (33, 50), (100, 17)])
