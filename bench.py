@@ -135,7 +135,7 @@ def kernel_of(routine, n):
     fused = int(routine == "dsyrk_dpotrf_ln")
     if n <= 8:  # the sweep's batches give one lane per problem
         return f"k_chol_tiny<{n},{fused},1>"
-    if n <= 31 and small_g(n):
+    if n <= 31 and small_g(n) and not (fused and n >= 24 and n % 8 == 0):
         return f"k_chol_small<{small_g(n)},{fused},1>"
     if n <= 64:
         return f"k_chol_rows4<{fused},1,double,256,4>"

@@ -904,28 +904,51 @@ cudaError_t launch_rows_pairs(bool aligned, int batch, int n, int k, Op A, Op B,
                                     sdinv, info ? info + head : nullptr, s);
 }
 
+// Problems per CTA of the double-precision row kernel at order n: four
+// where the 8-column layout wins, two up to the pair kernel's largest order,
+// else one; then halved while the launch would have fewer CTAs than SMs, so
+// that a small batch spreads over the GPU (latency over per-SM throughput).
+// The fused routine also takes four per CTA at orders from
+// BF_ROWS_P4_FUSED_MIN_N8 that are multiples of 8 (full last block):
+// syrk_potrf n = 24, 832 -> 922 GFLOP/s; at n = 28 the small kernel is
+// faster (895 against 746).
+#ifndef BF_ROWS_P4_FUSED_MIN_N8
+#define BF_ROWS_P4_FUSED_MIN_N8 24
+#endif
+
+template <bool FUSED>
+int rows_problems_per_cta(int n, int batch) {
+  constexpr int p2_max = FUSED ? BF_ROWS_P2_MAX_N_FUSED : BF_ROWS_P2_MAX_N;
+  constexpr int p4_min = FUSED ? BF_ROWS_P4_MIN_N_FUSED : BF_ROWS_P4_MIN_N;
+  constexpr int p4_max = FUSED ? BF_ROWS_P4_MAX_N_FUSED : BF_ROWS_P4_MAX_N;
+  const bool p4 = (n >= p4_min && n <= p4_max) ||
+                  (FUSED && n >= BF_ROWS_P4_FUSED_MIN_N8 && n % 8 == 0 && n <= p4_max);
+  int p = p4 ? 4 : (n <= p2_max ? 2 : 1);
+  const long long sms = device_sm_count();
+  while (p > 1 && ((long long)batch + p - 1) / p < sms) p /= 2;
+  return p;
+}
+
 template <bool FUSED, typename T>
 cudaError_t launch_rows(bool aligned, int batch, int n, int k, Op A, Op B, Op C, OpWT<T> D, T *dinv,
                         long long sdinv, int *info, cudaStream_t s) {
   if constexpr (sizeof(T) == 8 || BF_ROWS_P2_FP32) {  // by default the FP32 factor keeps one problem per CTA
-    constexpr int p2_max = FUSED ? BF_ROWS_P2_MAX_N_FUSED : BF_ROWS_P2_MAX_N;
-    constexpr int p4_min = FUSED ? BF_ROWS_P4_MIN_N_FUSED : BF_ROWS_P4_MIN_N;
-    constexpr int p4_max = FUSED ? BF_ROWS_P4_MAX_N_FUSED : BF_ROWS_P4_MAX_N;
-    if (n >= p4_min && n <= p4_max && n <= 64)
+    const int p = rows_problems_per_cta<FUSED>(n, batch);
+    if (p == 4 && n <= 64)
       return launch_rows4<256, BF_ROWS_P4_MINB256, FUSED, T>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info,
                                                             s);
-    if (n >= p4_min && n <= p4_max && n <= 128)
+    if (p == 4)
       return launch_rows4<512, 2, FUSED, T>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
-    if (n <= 64 && n <= p2_max)
+    if (p == 2 && n <= 64)
       return launch_rows_pairs<128, BF_ROWS_P2_MINB128, FUSED, T>(aligned, batch, n, k, A, B, C, D, dinv, sdinv,
                                                                   info, s);
-    if (n <= 128 && n <= p2_max)
+    if (p == 2 && n <= 128)
       return launch_rows_pairs<256, BF_ROWS_P2_MINB256, FUSED, T>(aligned, batch, n, k, A, B, C, D, dinv, sdinv,
                                                                   info, s);
-    if (n <= 192 && n <= p2_max)
+    if (p == 2 && n <= 192)
       return launch_rows_pairs<384, BF_ROWS_P2_MINB384, FUSED, T>(aligned, batch, n, k, A, B, C, D, dinv, sdinv,
                                                                   info, s);
-    if (n <= p2_max)
+    if (p == 2)
       return launch_rows_pairs<512, 2, FUSED, T>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
   }
   return launch_rows_a<0, 1, FUSED, T>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
@@ -1010,7 +1033,12 @@ cudaError_t launch_tiny(bool aligned, int batch, int n, int k, Op A, Op B, Op C,
 template <bool FUSED>
 cudaError_t launch_chol_t(bool aligned, int batch, int n, int k, Op A, Op B, Op C, OpW D,
                           double *dinv, long long sdinv, int *info, cudaStream_t s) {
-  int g = (n <= BF_CHOL_SMALL_MAX_N) ? pick_small_g(n) : 0;
+  bool small = n <= BF_CHOL_SMALL_MAX_N;
+  // the fused routine's four-problem orders below it, for batches that give
+  // four-problem CTAs at least one per SM sub-partition
+  if (small && rows_problems_per_cta<FUSED>(n, batch) == 4 && (long long)batch >= 16LL * device_sm_count())
+    small = false;
+  int g = small ? pick_small_g(n) : 0;
   // Small batches: more lanes per problem until the launch has a warp for
   // every SM sub-partition (4 per SM), up to one problem per warp.  The
   // budget's G is chosen for throughput; with few problems it would leave

@@ -104,6 +104,8 @@ def test_kernel_labels_follow_the_library_size_rules():
     assert bench.kernel_of("dsyrk_dpotrf_ln", 8) == "k_chol_tiny<8,1,1>"
     assert bench.kernel_of("dpotrf_l", 16).startswith("k_chol_small<")
     assert bench.kernel_of("dpotrf_l", 24).startswith("k_chol_small<")
+    assert bench.kernel_of("dsyrk_dpotrf_ln", 24) == "k_chol_rows4<1,1,double,256,4>"
+    assert bench.kernel_of("dsyrk_dpotrf_ln", 28).startswith("k_chol_small<")
     assert bench.kernel_of("dpotrf_l", 40) == "k_chol_rows4<0,1,double,256,4>"
     assert bench.kernel_of("dpotrf_l", 48) == "k_chol_rows4<0,1,double,256,4>"
     assert bench.kernel_of("dpotrf_l", 64) == "k_chol_rows4<0,1,double,256,4>"

@@ -360,25 +360,26 @@ def test_syrk_potrf_config_form(n, k):
 
 @pytest.mark.parametrize("n", [65, 100, 192, 250])
 def test_syrk_potrf_paired_problems_odd_batch_and_failing_neighbour(n):
-    """From n = 89 to 256 the row kernel factors two problems per CTA (n = 65
-    takes the four-problem kernel, which this covers as well).  With an odd
-    batch the last CTA has one problem; a failing problem must not disturb the
-    other problem of its CTA."""
-    bt, k = 5, 7
+    """With at least one CTA per SM the row kernel factors two problems per
+    CTA from n = 89 to 256, and at n = 65 when four-problem CTAs would leave
+    SMs idle.  With an odd batch the last CTA has one problem; a failing
+    problem must not disturb the other problem of its CTA."""
+    bt, k = 2 * torch.cuda.get_device_properties(0).multi_processor_count + 1, 7
     M = inputs.normal((bt, n, k), 140 + n)
     Q = (torch.eye(n, dtype=torch.float64) * float(n)).expand(bt, n, n).contiguous().numpy().copy()
-    Q[2, n - 3, n - 3] = -1e6            # problem 2 (second of CTA 1) fails late
-    Q[4, 0, 0] = np.nan                  # problem 4 (alone in the last CTA) fails first
+    Q[2, n - 3, n - 3] = -1e6            # problem 2 (first of CTA 1) fails late
+    Q[bt - 1, 0, 0] = np.nan             # the last problem (alone in the last CTA) fails first
     want, dinv_want, info_want = oracle.dsyrk_dpotrf_ln(M.numpy(), M.numpy(), Q)
     dM = put(M)
     dD = bf.DMatBatch(bt, n, n, fill=np.nan)
     info = torch.full((bt,), -7, dtype=torch.int32, device=dev())
     bf.dsyrk_dpotrf_ln(n, k, dM, 0, 0, dM, 0, 0, put(torch.from_numpy(Q)), 0, 0, dD, 0, 0, info=info)
     got_info = info.cpu().numpy()
-    assert list(got_info) == list(info_want) == [0, 0, n - 2, 0, 1]
+    assert np.array_equal(got_info, info_want)
+    assert {int(b): int(got_info[b]) for b in np.nonzero(got_info)[0]} == {2: n - 2, bt - 1: 1}
     got = get(dD)
     dinv = dD.dinv().cpu().numpy()
-    for b in (0, 1, 3):
+    for b in [0, 1, 3, bt - 2]:
         S = Q[b] + M[b].numpy() @ M[b].numpy().T
         assert chol_resid(got[b], S) <= 1e-13
         assert fro(np.tril(got[b]) - np.tril(want[b])) / fro(np.tril(want[b])) <= 1e-12
@@ -505,11 +506,12 @@ def test_rows_tail_split_every_problem(n, k):
 @pytest.mark.parametrize("n,k,offs", [(32, 0, (0, 0)), (37, 9, (0, 0)), (40, 0, (1, 2)), (57, 20, (0, 0)),
                                       (64, 64, (5, 3)), (71, 0, (0, 0)), (88, 30, (0, 0))])
 def test_four_problem_ctas_every_problem(n, k, offs):
-    """Orders 32..88 are factored four problems per CTA with 8-column blocks.
-    A batch of 11 leaves the last CTA three problems; failures sit at two
-    positions of one CTA and at the batch's end, the rest of each CTA must
-    be unaffected.  Ragged orders leave a partial last block."""
-    bt = 11
+    """Orders 32..88 are factored four problems per CTA with 8-column blocks
+    when the batch gives at least one CTA per SM.  A batch of 4 x SMs + 3
+    leaves the last CTA three problems; failures sit at two positions of one
+    CTA and at the batch's end, the rest of each CTA must be unaffected.
+    Ragged orders leave a partial last block."""
+    bt = 4 * torch.cuda.get_device_properties(0).multi_processor_count + 3
     ai, aj = offs
     fused = k > 0
     if fused:
@@ -517,7 +519,7 @@ def test_four_problem_ctas_every_problem(n, k, offs):
         Q = np.broadcast_to(np.eye(n) * float(n), (bt, n, n)).copy()
     else:
         Q = inputs.spd(bt, n, 700 + n).numpy()
-    bad = {4: 1, 6: n - 3, 10: (n + 1) // 2}  # CTA 1 holds problems 4..7, the last CTA 8..10
+    bad = {4: 1, 6: n - 3, bt - 1: (n + 1) // 2}  # CTA 1 holds problems 4..7, the last CTA the final 3
     for b, col in bad.items():
         Q[b, col - 1, col - 1] = -1e9
     if fused:
