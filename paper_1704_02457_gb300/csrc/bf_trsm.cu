@@ -23,7 +23,15 @@ namespace {
 
 constexpr int KC = 32;        // columns of L per staged downdate chunk
 constexpr int SPITCH = 34;    // stage row pitch (even: 16-byte pair loads)
-constexpr int MAX_ROWS = 256; // rows per CTA
+// Rows of X per CTA above which a problem's rows are split over several
+// CTAs (rows are independent; each CTA stages the L blocks it needs).
+// Measured with the sweep's batches: trsm n = 192 1204 -> 1225 GFLOP/s at
+// 128 (n = 256 unchanged); 64 also slowed n = 96 (1216 -> 1183).
+#ifndef BF_TRSM_MAX_ROWS
+#define BF_TRSM_MAX_ROWS 128
+#endif
+constexpr int MAX_ROWS = 256;                // rows per CTA at most
+constexpr int CHUNK_ROWS = BF_TRSM_MAX_ROWS;  // rows per CTA when a problem is split
 
 __host__ __device__ __forceinline__ int ls_region(int W) { return W * (W + 1) + W + 1; }
 
@@ -229,9 +237,9 @@ cudaError_t launch_trsm_rltn_v(int batch, const bf_dsize *size, double alpha, co
 cudaError_t launch_trsm_rltn(int batch, int m, int n, double alpha, Op L, const double *dinv,
                              long long sdinv, Op B, OpW D, cudaStream_t s) {
   int P = 1, R = m, chunks = 1;
-  if (m > MAX_ROWS) {
-    R = MAX_ROWS;
-    chunks = (m + MAX_ROWS - 1) / MAX_ROWS;
+  if (m > CHUNK_ROWS) {
+    chunks = (m + CHUNK_ROWS - 1) / CHUNK_ROWS;
+    R = ((m + chunks - 1) / chunks + 31) / 32 * 32;  // even chunks, whole warps
   } else if (n <= 32) {
     // a single column block: pack as many problems as fit in 256 rows
     P = max(1, MAX_ROWS / m);

@@ -287,7 +287,8 @@ def test_potrf_offsets_and_in_place(n, offs):
 
 # ------------------------------------------------------------------- trsm_rltn
 
-TRSM_SHAPES = [(1, 1), (4, 4), (7, 3), (24, 24), (30, 33), (33, 30), (64, 64), (5, 100), (300, 40), (256, 256), (600, 20)]
+TRSM_SHAPES = [(1, 1), (4, 4), (7, 3), (24, 24), (30, 33), (33, 30), (64, 64), (5, 100), (129, 64), (192, 150), (300, 40),
+               (256, 256), (600, 20)]
 
 
 @pytest.mark.parametrize("m,n", TRSM_SHAPES)
