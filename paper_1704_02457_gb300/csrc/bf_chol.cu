@@ -28,7 +28,7 @@
 //
 //  k_chol_rows4 / k_chol_rows2 / k_chol_rows (n <= 512): one thread per row,
 //    blocks of BW columns held in registers, P problems per CTA, a warp
-//    holding 32/P rows of each: P = 4 with BW = 8 for n = 32..88, P = 2 with
+//    holding 32/P rows of each: P = 4 with BW = 8 for n = 32..96, P = 2 with
 //    BW = 16 up to n = 256, P = 1 above.  With P*BW = 32 the diagonal block
 //    of a block column is one full warp, which computes only the block's
 //    lower triangle, spread evenly over its lanes.  For block column
@@ -440,28 +440,34 @@ struct __align__(16) RowsSmem {
 //                          n = 144 911 -> 1052, n = 192 1041 -> 1103;
 //                          syrk_potrf n = 144 1041 -> 1129, n = 192 1125 -> 1157
 //   n <= 256, 512 threads: 2 (64)
-// Orders factored four problems per CTA (k_chol_rows4), per routine.
+// Orders factored four problems per CTA (k_chol_rows4), per routine, in
+// builds of 256 threads x 4 CTAs per SM (n <= 64) and 384 x 3 (n <= 96).
 // Measured against the small kernel below and the two-problem kernel above
 // (GFLOP/s, potrf / syrk_potrf):
 //   n = 32: 626 -> 730 / 849 -> 1024     n = 48: 709 -> 896 / 1013 -> 1097
 //   n = 40: 593 -> 821 / 892 -> 1065     n = 64: 853 -> 979 / 1088 -> 1136
-//   n = 72: 713 -> 961 / 899 -> 1091     n = 88: 789 -> 915 / 941 -> 1048
-// At n = 96 and 128 the two-problem kernel is 2-4% faster; below 32 the
-// small kernel is (n = 28: 596 against 490, n = 16: 578 against 371).
+//   n = 72: 713 -> 1009 / 899 -> 1112    n = 88: 789 -> 1022 / 941 -> 1097
+//   n = 96: 1001 -> 1058 / 1144 -> 1152
+// At n = 112 it ties and at n = 128 the two-problem kernel is 4% faster (at
+// 512 threads, 2 CTAs per SM); below 32 the small kernel is faster (n = 28:
+// 596 against 490, n = 16: 578 against 371).
 #ifndef BF_ROWS_P4_MIN_N
 #define BF_ROWS_P4_MIN_N 32
 #endif
 #ifndef BF_ROWS_P4_MAX_N
-#define BF_ROWS_P4_MAX_N 88
+#define BF_ROWS_P4_MAX_N 96
 #endif
 #ifndef BF_ROWS_P4_MIN_N_FUSED
 #define BF_ROWS_P4_MIN_N_FUSED 32
 #endif
 #ifndef BF_ROWS_P4_MAX_N_FUSED
-#define BF_ROWS_P4_MAX_N_FUSED 88
+#define BF_ROWS_P4_MAX_N_FUSED 96
 #endif
 #ifndef BF_ROWS_P4_MINB256
 #define BF_ROWS_P4_MINB256 4
+#endif
+#ifndef BF_ROWS_P4_MINB384
+#define BF_ROWS_P4_MINB384 3
 #endif
 #ifndef BF_ROWS_P2_MINB128
 #define BF_ROWS_P2_MINB128 6
@@ -936,6 +942,9 @@ cudaError_t launch_rows(bool aligned, int batch, int n, int k, Op A, Op B, Op C,
     const int p = rows_problems_per_cta<FUSED>(n, batch);
     if (p == 4 && n <= 64)
       return launch_rows4<256, BF_ROWS_P4_MINB256, FUSED, T>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info,
+                                                            s);
+    if (p == 4 && n <= 96)
+      return launch_rows4<384, BF_ROWS_P4_MINB384, FUSED, T>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info,
                                                             s);
     if (p == 4)
       return launch_rows4<512, 2, FUSED, T>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);

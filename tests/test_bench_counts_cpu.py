@@ -109,8 +109,8 @@ def test_kernel_labels_follow_the_library_size_rules():
     assert bench.kernel_of("dpotrf_l", 40) == "k_chol_rows4<0,1,double,256,4>"
     assert bench.kernel_of("dpotrf_l", 48) == "k_chol_rows4<0,1,double,256,4>"
     assert bench.kernel_of("dpotrf_l", 64) == "k_chol_rows4<0,1,double,256,4>"
-    assert bench.kernel_of("dsyrk_dpotrf_ln", 88) == "k_chol_rows4<1,1,double,512,2>"
-    assert bench.kernel_of("dpotrf_l", 96) == "k_chol_rows2<16,0,1,double,256,4>"
+    assert bench.kernel_of("dsyrk_dpotrf_ln", 88) == "k_chol_rows4<1,1,double,384,3>"
+    assert bench.kernel_of("dpotrf_l", 96) == "k_chol_rows4<0,1,double,384,3>"
     assert bench.kernel_of("dsyrk_dpotrf_ln", 128) == "k_chol_rows2<16,1,1,double,256,4>"
     assert bench.kernel_of("dpotrf_l", 256) == "k_chol_rows2<16,0,1,double,512,2>"
     assert bench.kernel_of("dsyrk_dpotrf_ln", 192) == "k_chol_rows2<16,1,1,double,384,3>"

@@ -505,9 +505,10 @@ def test_rows_tail_split_every_problem(n, k):
 
 
 @pytest.mark.parametrize("n,k,offs", [(32, 0, (0, 0)), (37, 9, (0, 0)), (40, 0, (1, 2)), (57, 20, (0, 0)),
-                                      (64, 64, (5, 3)), (71, 0, (0, 0)), (88, 30, (0, 0))])
+                                      (64, 64, (5, 3)), (71, 0, (0, 0)), (88, 30, (0, 0)), (93, 0, (2, 1)),
+                                      (96, 12, (0, 0))])
 def test_four_problem_ctas_every_problem(n, k, offs):
-    """Orders 32..88 are factored four problems per CTA with 8-column blocks
+    """Orders 32..96 are factored four problems per CTA with 8-column blocks
     when the batch gives at least one CTA per SM.  A batch of 4 x SMs + 3
     leaves the last CTA three problems; failures sit at two positions of one
     CTA and at the batch's end, the rest of each CTA must be unaffected.
