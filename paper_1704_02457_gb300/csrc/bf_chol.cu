@@ -417,6 +417,13 @@ struct __align__(16) RowsSmem {
 #ifndef BF_ROWS_SPLIT
 #define BF_ROWS_SPLIT 1  // balanced triangle split of the diagonal warp's k-loops
 #endif
+// The split in the descriptor-array kernel's one-problem CTAs, in the blocks
+// whose diagonal half-warp has an idle partner (c0 % 32 == 16).  Not in
+// k_chol_rows: there the extra registers (70 -> 118) cost a resident CTA,
+// measured 1019 -> 984 GFLOP/s at syrk_potrf n = 256 (the tail launch).
+#ifndef BF_ROWS_SPLIT_P1
+#define BF_ROWS_SPLIT_P1 1
+#endif
 #ifndef BF_ROWS_P2_FP32
 #define BF_ROWS_P2_FP32 0
 #endif
@@ -526,7 +533,7 @@ __device__ __forceinline__ void split_slot(int s, int m, int &row, int &col, boo
 // diagonal block's rows c0..c0+BW-1 of problem p are lanes
 // p*RPW + c0%RPW + (0..BW-1) of warp c0/RPW (BW divides RPW and c0 is a
 // multiple of BW).
-template <int W, int BW, int P, bool FUSED, bool ALIGNED, typename T>
+template <int W, int BW, int P, bool FUSED, bool ALIGNED, typename T, bool S1>
 __device__ __forceinline__ void rows_block(RowsSmem<T, BW, P> &S, const RowMap<P> &rm, int c0, int n, int k,
                                            int b0, int batch, bool me_valid, const double *pa, const double *pc,
                                            T *pd, Op A, Op B, Op C, OpWT<T> D, T *dinv, long long sdinv) {
@@ -542,9 +549,13 @@ __device__ __forceinline__ void rows_block(RowsSmem<T, BW, P> &S, const RowMap<P
   // block (16 rows of each problem) computes only the block's lower triangle
   // in (a') and (b), spread over its lanes by split_slot: at most 9 FMAs per
   // step a lane instead of 16.  Its rows are gathered back before (c).
+  // With one problem per CTA the diagonal block fills half a warp; the split
+  // applies when the other half holds rows above the block (c0 % 32 == 16),
+  // which then idle, and only the diagonal half scatters its slots.
   constexpr int H = BW / 2, NSLOT = H + 1;
-  constexpr bool SPLIT = BF_ROWS_SPLIT && (P * BW == 32 && W == BW && BW >= 8);
-  const bool dwarp = SPLIT && ((t >> 5) == c0 / RPW);  // warp-uniform
+  constexpr bool SPLIT = BF_ROWS_SPLIT && (P * BW == 32 || (P == 1 && BW == 16 && S1)) && W == BW && BW >= 8;
+  const bool dwarp = SPLIT && ((t >> 5) == c0 / RPW) && (P > 1 || c0 % 32 == 16);  // warp-uniform
+  const bool dhalf = P > 1 || (rm.lane >> 4) == 1;  // a lane of the diagonal block (in a split warp)
   const int sb = rm.lane & (BW - 1);                    // row within the diagonal block
 
   // (a) C[i][c0 + jj] for the lower part of the block column.  The diagonal
@@ -651,13 +662,14 @@ __device__ __forceinline__ void rows_block(RowsSmem<T, BW, P> &S, const RowMap<P
       int row, col;
       bool ok;
       split_slot<BW>(sb, m, row, col, ok);
-      if (ok) S.Ls[p][row][col] = acc[m];
+      if (ok && dhalf) S.Ls[p][row][col] = acc[m];
     }
     __syncwarp();
 #pragma unroll
     for (int jj = 0; jj < W; jj++) {
       const bool lower = jj <= sb;
-      const T cv = (me_valid && sb < w && jj < w && lower) ? (T)pc[pm_off(C.i0 + i, C.j0 + c0 + jj, C.cn)] : (T)0;
+      const T cv = (me_valid && dhalf && sb < w && jj < w && lower) ? (T)pc[pm_off(C.i0 + i, C.j0 + c0 + jj, C.cn)]
+                                                                      : (T)0;
       acc[jj] = cv + (lower ? S.Ls[p][sb][jj] : (T)0);
     }
     __syncwarp();
@@ -724,7 +736,7 @@ __device__ __forceinline__ void rows_block(RowsSmem<T, BW, P> &S, const RowMap<P
 // CTA = P problems of the batch (problems blockIdx.x*P + p), threads laid out
 // by RowMap<P>.  Problems past the end of the batch (last CTA) run along
 // without touching memory.
-template <int BW, int P, bool FUSED, bool ALIGNED, typename T>
+template <int BW, int P, bool FUSED, bool ALIGNED, typename T, bool S1 = false>
 __device__ __forceinline__ void chol_rows_body(int b0, int batch, int n, int k, Op A, Op B, Op C, OpWT<T> D,
                                                T *dinv, long long sdinv, int *info) {
   __shared__ RowsSmem<T, BW, P> S;
@@ -738,16 +750,16 @@ __device__ __forceinline__ void chol_rows_body(int b0, int batch, int n, int k, 
   __syncthreads();
   for (int c0 = 0; c0 < n; c0 += BW) {
     if constexpr (BW == 8) {
-      rows_block<8, 8, P, FUSED, ALIGNED, T>(S, rm, c0, n, k, b0, batch, me_valid, pa, pc, pd, A, B, C, D, dinv,
-                                             sdinv);
+      rows_block<8, 8, P, FUSED, ALIGNED, T, S1>(S, rm, c0, n, k, b0, batch, me_valid, pa, pc, pd, A, B, C, D,
+                                                 dinv, sdinv);
     } else {
       const int w8 = (min(BW, n - c0) + 7) & ~7;
       if (w8 == 8)
-        rows_block<8, BW, P, FUSED, ALIGNED, T>(S, rm, c0, n, k, b0, batch, me_valid, pa, pc, pd, A, B, C, D, dinv,
-                                                sdinv);
+        rows_block<8, BW, P, FUSED, ALIGNED, T, S1>(S, rm, c0, n, k, b0, batch, me_valid, pa, pc, pd, A, B, C, D,
+                                                    dinv, sdinv);
       else
-        rows_block<16, BW, P, FUSED, ALIGNED, T>(S, rm, c0, n, k, b0, batch, me_valid, pa, pc, pd, A, B, C, D,
-                                                 dinv, sdinv);
+        rows_block<16, BW, P, FUSED, ALIGNED, T, S1>(S, rm, c0, n, k, b0, batch, me_valid, pa, pc, pd, A, B, C, D,
+                                                     dinv, sdinv);
     }
   }
   if (info && threadIdx.x < P && b0 + (int)threadIdx.x < batch) info[b0 + threadIdx.x] = S.bad[threadIdx.x];
@@ -812,7 +824,8 @@ k_chol_rows_v(int batch, const bf_dsize *size, const bf_dsub *A, const bf_dsub *
   // the inverse-diagonal array holds min(m, n) entries of its matrix
   const bf_dmat &dm = D[b].mat;
   double *dv = (want_dinv && dm.dA && D[b].j + m <= min(dm.m, dm.n)) ? dm.dA + D[b].j : nullptr;
-  chol_rows_body<BW, 1, FUSED, false, double>(0, 1, m, k, a, bb, c, d, dv, 0, info ? info + b : nullptr);
+  chol_rows_body<BW, 1, FUSED, false, double, BF_ROWS_SPLIT_P1 != 0>(0, 1, m, k, a, bb, c, d, dv, 0,
+                                                                    info ? info + b : nullptr);
 }
 
 // Block width of k_chol_rows: 16-column blocks halve the work the diagonal
