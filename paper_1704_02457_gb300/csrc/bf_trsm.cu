@@ -27,6 +27,12 @@ constexpr int SPITCH = 34;    // stage row pitch (even: 16-byte pair loads)
 // CTAs (rows are independent; each CTA stages the L blocks it needs).
 // Measured with the sweep's batches: trsm n = 192 1204 -> 1225 GFLOP/s at
 // 128 (n = 256 unchanged); 64 also slowed n = 96 (1216 -> 1183).
+// Rows of a CTA that packs whole small problems (n <= 32).  Measured: 128
+// against 256 took trsm n = 24 1049 -> 1057 and n = 32 1140 -> 1154 GFLOP/s,
+// the other sweep sizes unchanged within noise.
+#ifndef BF_TRSM_PACK_ROWS
+#define BF_TRSM_PACK_ROWS 128
+#endif
 #ifndef BF_TRSM_MAX_ROWS
 #define BF_TRSM_MAX_ROWS 128
 #endif
@@ -242,7 +248,7 @@ cudaError_t launch_trsm_rltn(int batch, int m, int n, double alpha, Op L, const 
     R = ((m + chunks - 1) / chunks + 31) / 32 * 32;  // even chunks, whole warps
   } else if (n <= 32) {
     // a single column block: pack as many problems as fit in 256 rows
-    P = max(1, MAX_ROWS / m);
+    P = max(1, BF_TRSM_PACK_ROWS / m);
   } else {
     // blocked: up to 4 problems, enough to fill whole warps
     while (P < 4 && 2 * P * m <= MAX_ROWS && (P * m) % 32 != 0) P *= 2;
