@@ -714,6 +714,12 @@ def run_gpu(args):
     }
     result["per_routine_gflops"] = {r: round(v[0] / (v[1] * 1e-3) / 1e9, 2) for r, v in per_routine.items()}
 
+    # The end-to-end leg first: it pins about 60 GB of host memory, and host
+    # DMA runs slower once the other legs have fragmented the host's memory
+    # (measured on one box: 843 GFLOP/s right after the sweep, 500-700 after
+    # the other legs).
+    if not args.no_e2e:
+        result["e2e"] = run_e2e(pts, args, dev, world)
     if not args.no_mixed:
         result["mixed_vs_fp64"] = run_mixed(args, dev)
     if not args.no_riccati:
@@ -726,8 +732,6 @@ def run_gpu(args):
         result["config1"] = run_config1(args, dev)
     if not args.no_vbatched:
         result["vbatched"] = run_vbatched(args, dev)
-    if not args.no_e2e:
-        result["e2e"] = run_e2e(pts, args, dev, world)
     if rank == 0 and world == 1 and not args.no_cpu:
         sampler = OracleSampler(spec, budget_s=args.cpu_budget)
         rates = sampler.rates()
