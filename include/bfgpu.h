@@ -104,7 +104,7 @@ size_t bf_memsize_dmat(int m, int n);
  * mem (mem must be non-NULL and BF_ALIGN-aligned). */
 int bf_create_dmat(int m, int n, bf_dmat *sA, void *mem);
 
-/* Panel height of this build (BF_PS). */
+/* Panel height the library was compiled with (BF_PS). */
 int bf_panel_height(void);
 
 /* ---- packing (Sec. 4.3.3; the packing routines of Appendix A.3) ---------- */
