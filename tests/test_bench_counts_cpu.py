@@ -129,3 +129,40 @@ def test_launches_per_call_count_the_tail_split():
     sweep = [(r, n) for n in inputs.SWEEP_N for r in bench.ROUTINES]
     total = sum(bench.launches_of(r, n, inputs.sweep_batch(r, n)) for r, n in sweep)
     assert total == len(sweep) + 1
+
+
+def _chol_defaults():
+    """The size thresholds of the Cholesky launchers, from their #define defaults."""
+    import os
+    import re
+    src = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                            "paper_1704_02457_gb300", "csrc", "bf_chol.cu")).read()
+    vals = {}
+    for name in ("BF_CHOL_TINY_MAX_N", "BF_CHOL_SMALL_MAX_N", "BF_ROWS_P4_MIN_N", "BF_ROWS_P4_MAX_N",
+                 "BF_ROWS_P4_FUSED_MIN_N8", "BF_SMALL_SMEM_BUDGET_KB", "BF_ROWS_P2_MAX_N"):
+        m = re.search(r"#define %s (\d+)" % name, src)
+        assert m, name
+        vals[name] = int(m.group(1))
+    return vals
+
+
+def test_kernel_labels_match_the_launchers_thresholds():
+    # bench.kernel_of names the kernel each sweep point launches; it must move
+    # with the library's thresholds
+    v = _chol_defaults()
+    assert v["BF_CHOL_TINY_MAX_N"] == 8
+    for n in range(1, v["BF_CHOL_TINY_MAX_N"] + 1):
+        assert bench.kernel_of("dpotrf_l", n).startswith("k_chol_tiny<")
+    assert bench.kernel_of("dpotrf_l", v["BF_CHOL_SMALL_MAX_N"]).startswith("k_chol_small<")
+    assert bench.kernel_of("dpotrf_l", v["BF_ROWS_P4_MIN_N"]).startswith("k_chol_rows4<")
+    assert bench.kernel_of("dpotrf_l", v["BF_ROWS_P4_MAX_N"]).startswith("k_chol_rows4<")
+    assert bench.kernel_of("dpotrf_l", v["BF_ROWS_P4_MAX_N"] + 1).startswith("k_chol_rows2<")
+    assert bench.kernel_of("dpotrf_l", v["BF_ROWS_P2_MAX_N"]).startswith("k_chol_rows2<")
+    assert bench.kernel_of("dpotrf_l", v["BF_ROWS_P2_MAX_N"] + 1).startswith("k_chol_rows<")
+    n8 = v["BF_ROWS_P4_FUSED_MIN_N8"]
+    assert bench.kernel_of("dsyrk_dpotrf_ln", n8).startswith("k_chol_rows4<")
+    assert bench.kernel_of("dsyrk_dpotrf_ln", n8 + 4).startswith("k_chol_small<")
+    # the small kernel's lanes per problem follow the same shared-memory budget
+    for n in range(v["BF_CHOL_TINY_MAX_N"] + 1, v["BF_CHOL_SMALL_MAX_N"] + 1):
+        g = bench.small_g(n)
+        assert n * (n + 1) // 2 * (32 // g) * 8 <= v["BF_SMALL_SMEM_BUDGET_KB"] * 1024 or g == 16
