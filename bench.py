@@ -112,9 +112,10 @@ def _git_blob_hash(path):
 
 
 def small_g(n):
-    """Lanes per problem the small Cholesky kernel uses at order n."""
+    """Lanes per problem the small Cholesky kernel uses at order n (at least 2:
+    one lane per problem is the register kernel's, up to n = 8)."""
     ne = n * (n + 1) // 2
-    g = 1
+    g = 2
     while g <= 16:
         if ne * (32 // g) * 8 <= 26 * 1024:
             return g

@@ -985,6 +985,13 @@ cudaError_t launch_rows(bool aligned, int batch, int n, int k, Op A, Op B, Op C,
 // gives G = 2, 4, 8 at n = 16, 24, 32 (budgets of 40 and 80 KB were slower
 // there) and G = 8 rather than 16 at n = 33..40 (n = 40: potrf 550 -> 593,
 // syrk_potrf 806 -> 894 GFLOP/s).
+// Fewest lanes per problem of k_chol_small.  One lane per problem serves
+// orders up to 8 in registers (k_chol_tiny); walking a whole problem
+// through shared memory it is latency-bound: n = 12 measured 476 GFLOP/s at
+// G = 1 and 517 at G = 2.
+#ifndef BF_SMALL_MIN_G
+#define BF_SMALL_MIN_G 2
+#endif
 #ifndef BF_SMALL_SMEM_BUDGET_KB
 #define BF_SMALL_SMEM_BUDGET_KB 26
 #endif
@@ -997,7 +1004,7 @@ constexpr long long SMALL_SMEM_BUDGET = BF_SMALL_SMEM_BUDGET_KB * 1024;
 #endif
 int pick_small_g(int n) {
   const long long ne = (long long)n * (n + 1) / 2;
-  for (int g = 1; g <= 16; g *= 2)
+  for (int g = BF_SMALL_MIN_G; g <= 16; g *= 2)
     if (ne * (32 / g) * 8 <= SMALL_SMEM_BUDGET) return g;
   return (ne * 2 * 8 <= 48 * 1024) ? 16 : 0;
 }
@@ -1060,6 +1067,10 @@ cudaError_t launch_chol_t(bool aligned, int batch, int n, int k, Op A, Op B, Op 
   // four-problem CTAs at least one per SM sub-partition
   if (small && rows_problems_per_cta<FUSED>(n, batch) == 4 && (long long)batch >= 16LL * device_sm_count())
     small = false;
+  // enough problems for one lane each to give every SM sub-partition a
+  // warp: the register kernel
+  if (small && n <= BF_CHOL_TINY_MAX_N && (long long)batch >= 32LL * 4 * device_sm_count())
+    return launch_tiny<FUSED>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
   int g = small ? pick_small_g(n) : 0;
   // Small batches: more lanes per problem until the launch has a warp for
   // every SM sub-partition (4 per SM), up to one problem per warp.  The
@@ -1067,9 +1078,6 @@ cudaError_t launch_chol_t(bool aligned, int batch, int n, int k, Op A, Op B, Op 
   // most of the GPU idle and each warp a long serial chain of FP64 work.
   if (g)
     while (g < 32 && (long long)batch * g < 32LL * 4 * device_sm_count()) g *= 2;
-  // enough problems for one lane each: the register kernel
-  if (g == 1 && n <= BF_CHOL_TINY_MAX_N)
-    return launch_tiny<FUSED>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
   switch (g) {
     case 1: return launch_small_g<1, FUSED>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
     case 2: return launch_small_g<2, FUSED>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);

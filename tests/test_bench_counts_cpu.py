@@ -96,9 +96,9 @@ def test_kernel_labels_follow_the_library_size_rules():
     # the small Cholesky keeps 32/G packed triangles of a warp within 26 KB, G <= 16, up to n = 40
     for n in (4, 8, 12, 16, 20, 24, 32, 40):
         g = bench.small_g(n)
-        assert g in (1, 2, 4, 8, 16)
+        assert g in (2, 4, 8, 16)
         assert n * (n + 1) // 2 * (32 // g) * 8 <= 26 * 1024 or g == 16
-        if g > 1:
+        if g > 2:
             assert n * (n + 1) // 2 * (32 // (g // 2)) * 8 > 26 * 1024
     assert bench.kernel_of("dpotrf_l", 4) == "k_chol_tiny<4,0,1>"
     assert bench.kernel_of("dsyrk_dpotrf_ln", 8) == "k_chol_tiny<8,1,1>"
