@@ -359,11 +359,11 @@ def test_syrk_potrf_config_form(n, k):
     check_dinv(dD.dinv().cpu().numpy(), got, dinv_want)
 
 
-@pytest.mark.parametrize("n", [65, 100, 192, 250])
+@pytest.mark.parametrize("n", [48, 65, 100, 192, 250])
 def test_syrk_potrf_paired_problems_odd_batch_and_failing_neighbour(n):
     """With at least one CTA per SM the row kernel factors two problems per
-    CTA from n = 89 to 256, and at n = 65 when four-problem CTAs would leave
-    SMs idle.  With an odd batch the last CTA has one problem; a failing
+    CTA from n = 97 to 256, and at n = 48 and 65 when four-problem CTAs would
+    leave SMs idle.  With an odd batch the last CTA has one problem; a failing
     problem must not disturb the other problem of its CTA."""
     bt, k = 2 * torch.cuda.get_device_properties(0).multi_processor_count + 1, 7
     M = inputs.normal((bt, n, k), 140 + n)
