@@ -368,9 +368,7 @@ int bf_driccati_sqrt_batched(int batch, int N, const bf_riccati_prob *probs, con
                              int max_nx, int max_nu, int threads, void *stream);
 
 /* The mixed-precision solver above, for callers that cannot allocate
- * device memory.  The paper has no counterpart: its routines take external
- * memory from the caller (Appendix A.1.2) but have no solver that needs
- * scratch.
+ * device memory.  The paper has no counterpart.
  *
  * Who needs it: a caller that has no way to hand over a workspace.  A
  * controller running a fixed-period loop may forbid allocation there,
@@ -378,7 +376,8 @@ int bf_driccati_sqrt_batched(int batch, int N, const bf_riccati_prob *probs, con
  * plugin may run inside a host application that owns all device memory.
  *
  * Same arguments, checks, results and error codes as
- * bf_dposv_mixed_batched, minus work / work_bytes.  The scratch is a fixed
+ * bf_dposv_mixed_batched, minus work / work_bytes.  Argument errors are
+ * reported first; only a valid call that does not fit gets BF_ERR_TOO_LARGE.  The scratch is a fixed
  * array of BF_NOALLOC_WORK_BYTES (16 MiB) inside this library's device
  * memory; every GPU that loads the library holds it until the process exits.
  *   - Problems need bf_dposv_mixed_worksize(batch, n) <= BF_NOALLOC_WORK_BYTES
@@ -386,7 +385,9 @@ int bf_driccati_sqrt_batched(int batch, int N, const bf_riccati_prob *probs, con
  *     BF_ERR_TOO_LARGE and launch nothing.
  *   - The first call on a device looks up the array's address
  *     (cudaGetSymbolAddress) with that device current.  Make that first call
- *     before any stream capture on the device.
+ *     before any stream capture on the device.  The address is kept for the
+ *     life of the process: no cudaDeviceReset (or other reset of the
+ *     device's primary context) may come between calls.
  *   - All calls share the array, and it keeps the last call's contents.
  *     Nothing in it needs to start at zero.  Calls whose kernels overlap on
  *     the GPU race on it; serialize them (one stream, one thread at a time).
@@ -423,6 +424,14 @@ typedef struct {
 typedef struct {
   int m, n, k; /* sizes of one problem; unused members are ignored */
 } bf_dsize;
+
+/* Host-side check of one operand record with the rules the kernels apply to
+ * it on the device: a valid descriptor (non-NULL 8-byte-aligned pA, ps ==
+ * BF_PS, 0 <= m <= pm, pm a multiple of ps, cn >= n) and a rows x cols
+ * sub-matrix at (i, j) inside it (bounds compared in 64-bit arithmetic).
+ * Returns 1 if the record is valid, 0 if not (or if rec is NULL).  Touches
+ * neither the matrix nor the device. */
+int bf_dsub_valid(const bf_dsub *rec, int rows, int cols);
 
 /* gemm_nt per problem: D <- alpha A B^T + beta C with sizes (m, n, k); C is
  * not read (nor checked) when beta == 0.  Operands: A, B, C, D. */

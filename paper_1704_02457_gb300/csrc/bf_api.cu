@@ -19,8 +19,9 @@ int check_op(const bf_dmat *s, int ri, int cj, int rows, int cols, long long str
   if (!s || s->ps != PS || !s->pA || !aligned_to(s->pA, 8) || s->m < 0 || s->n < 0 ||
       s->pm < s->m || s->pm % PS != 0 || s->cn < s->n)
     return 1;
-  if (ri < 0 || ri + rows > s->m) return 2;
-  if (cj < 0 || cj + cols > s->n) return 3;
+  // 64-bit sums: an offset near INT_MAX must fail here, not wrap round
+  if (ri < 0 || (long long)ri + rows > (long long)s->m) return 2;
+  if (cj < 0 || (long long)cj + cols > (long long)s->n) return 3;
   if (stride < 0) return 4;
   if (output && batch > 1 && stride < (long long)s->pm * s->cn) return 4;
   return 0;
@@ -399,11 +400,15 @@ size_t bf_dposv_mixed_worksize(int batch, int n) {
   return l32 + info;
 }
 
-int bf_dposv_mixed_batched(int batch, int n, int nrhs, const bf_dmat *sA, int ai, int aj,
-                           long long strideA, const bf_dmat *sB, int bi, int bj, long long strideB,
-                           const bf_dmat *sX, int xi, int xj, long long strideX, double tol,
-                           int max_iter, int *iters, double *resid, void *work, size_t work_bytes,
-                           void *stream) {
+}  // extern "C"
+
+// Checks of the arguments the two mixed-precision solver entry points share
+// (positions 1..19); returns 0, a negative position or BF_ERR_UNSUPPORTED.
+// A zero-sized call passes, and the caller returns 0 for it.
+int bf::posv_mixed_check(int batch, int n, int nrhs, const bf_dmat *sA, int ai, int aj, long long strideA,
+                         const bf_dmat *sB, int bi, int bj, long long strideB, const bf_dmat *sX, int xi,
+                         int xj, long long strideX, double tol, int max_iter, const int *iters,
+                         const double *resid) {
   if (batch < 0) return -1;
   if (n < 0) return -2;
   if (nrhs < 0) return -3;
@@ -417,6 +422,20 @@ int bf_dposv_mixed_batched(int batch, int n, int nrhs, const bf_dmat *sA, int ai
   if (max_iter < 1) return -17;
   if (iters && !aligned_to(iters, 4)) return -18;
   if (resid && !aligned_to(resid, 8)) return -19;
+  return 0;
+}
+
+extern "C" {
+
+int bf_dposv_mixed_batched(int batch, int n, int nrhs, const bf_dmat *sA, int ai, int aj,
+                           long long strideA, const bf_dmat *sB, int bi, int bj, long long strideB,
+                           const bf_dmat *sX, int xi, int xj, long long strideX, double tol,
+                           int max_iter, int *iters, double *resid, void *work, size_t work_bytes,
+                           void *stream) {
+  if (int r = posv_mixed_check(batch, n, nrhs, sA, ai, aj, strideA, sB, bi, bj, strideB, sX, xi, xj,
+                               strideX, tol, max_iter, iters, resid))
+    return r;
+  if (batch == 0 || n == 0 || nrhs == 0) return 0;
   if (!work || !aligned_to(work, BF_ALIGN)) return -20;
   if (work_bytes < bf_dposv_mixed_worksize(batch, n)) return -21;
   const size_t pm = ((size_t)n + PS - 1) / PS * PS;
@@ -479,6 +498,8 @@ int bf_dgelqf(int m, int n, const bf_dmat *sC, int ci, int cj, const bf_dmat *sD
   static const int map[14] = {0, 0, 1, 2, 3, 4, 5, 0, 6, 7, 8, 0, 9, 0};
   return -map[-r];
 }
+
+int bf_dsub_valid(const bf_dsub *rec, int rows, int cols) { return rec && dsub_ok(*rec, rows, cols) ? 1 : 0; }
 
 // ----------------------------------------------- descriptor-array batched forms
 // Host checks cover the call's own arguments; each problem's record is

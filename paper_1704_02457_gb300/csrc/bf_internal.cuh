@@ -118,14 +118,17 @@ inline int resident_ctas(const void *fn, int threads, std::atomic<int> (&cache)[
   return nb;
 }
 
-// Device-side check of one operand record of the descriptor-array forms:
-// the same rules as the host's check of a strided operand.
-__device__ __forceinline__ bool dsub_ok(const bf_dsub &s, int rows, int cols) {
+// Check of one operand record of the descriptor-array forms, run by the
+// kernels on the device (and by bf_dsub_valid on the host): the same rules as
+// the host's check of a strided operand.  The bounds are compared in 64-bit
+// arithmetic, so that no offset or size near INT_MAX can wrap round and pass.
+__host__ __device__ __forceinline__ bool dsub_ok(const bf_dsub &s, int rows, int cols) {
   const bf_dmat &d = s.mat;
   if (!d.pA || d.ps != PS || ((unsigned long long)d.pA & 7ull) || d.m < 0 || d.n < 0 || d.pm < d.m ||
-      d.pm % PS != 0 || d.cn < d.n)
+      d.pm % PS != 0 || d.cn < d.n || rows < 0 || cols < 0)
     return false;
-  return s.i >= 0 && s.i + rows <= d.m && s.j >= 0 && s.j + cols <= d.n;
+  return s.i >= 0 && (long long)s.i + rows <= (long long)d.m && s.j >= 0 &&
+         (long long)s.j + cols <= (long long)d.n;
 }
 
 __device__ __forceinline__ Op dsub_op(const bf_dsub &s) { return Op{s.mat.pA, 0, s.mat.cn, s.i, s.j}; }
@@ -154,6 +157,13 @@ __device__ __forceinline__ double recip_newton(double d) {
   e = fma(-d, r, 1.0);
   return fma(r, e, r);
 }
+
+// Argument checks shared by bf_dposv_mixed_batched and its allocation-free
+// form (argument positions 1..19 of both signatures).
+int posv_mixed_check(int batch, int n, int nrhs, const bf_dmat *sA, int ai, int aj, long long strideA,
+                     const bf_dmat *sB, int bi, int bj, long long strideB, const bf_dmat *sX, int xi,
+                     int xj, long long strideX, double tol, int max_iter, const int *iters,
+                     const double *resid);
 
 // LU with partial pivoting (square n <= 128) and Householder LQ (m*n <= 16384).
 cudaError_t launch_getrf(int batch, int n, Op C, OpW D, int *ipiv, long long sipiv, int *info, cudaStream_t s);

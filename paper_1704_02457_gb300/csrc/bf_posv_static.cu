@@ -17,7 +17,9 @@
 //     launch nothing.
 //   - The first call on each device looks up the array's device address with
 //     cudaGetSymbolAddress, with that device current.  Make that first call
-//     before any stream capture on the device.
+//     before any stream capture on the device.  The address is kept for the
+//     life of the process, so no cudaDeviceReset (or other reset of the
+//     device's primary context) may come between calls: the array can move.
 //   - Every call shares the one array, and it keeps the last call's contents.
 //     Nothing in it needs to start at zero: the factorization writes every
 //     factor element and status word that the solve later reads.  Calls whose
@@ -61,9 +63,11 @@ extern "C" int bf_dposv_mixed_batched_noalloc(int batch, int n, int nrhs, const 
                                               int xi, int xj, long long strideX, double tol,
                                               int max_iter, int *iters, double *resid,
                                               void *stream) {
-  if (batch < 0) return -1;
-  if (n < 0) return -2;
-  if (nrhs < 0) return -3;
+  // argument errors first, with the workspace form's codes; only a valid
+  // call that does not fit the array gets BF_ERR_TOO_LARGE
+  if (int r = bf::posv_mixed_check(batch, n, nrhs, sA, ai, aj, strideA, sB, bi, bj, strideB, sX, xi, xj,
+                                   strideX, tol, max_iter, iters, resid))
+    return r;
   if (batch == 0 || n == 0 || nrhs == 0) return 0;
   if (bf_dposv_mixed_worksize(batch, n) > (size_t)BF_NOALLOC_WORK_BYTES) return BF_ERR_TOO_LARGE;
   void *scratch = nullptr;

@@ -212,3 +212,72 @@ def test_riccati_argument_checks(lib):
     assert g(1, 4, p, None, 8, 2, 48, None) == -7
     assert g(1, 4, p, None, 8, 2, 1024, None) == -7
     assert g(1, 4, p, None, 200, 20, 0, None) == _abi.BF_ERR_UNSUPPORTED
+
+
+INT_MAX = 2**31 - 1
+
+
+def test_offsets_near_int_max_fail_before_launch(lib):
+    # ai + rows would wrap round in 32-bit arithmetic; the host check must
+    # still refuse the operand (the argument position of the offset) before
+    # anything is launched
+    A, B, C, D = (_desc(8, 8) for _ in range(4))
+    r = ctypes.byref
+    g = lib.bf_dgemm_nt_batched
+    big = INT_MAX - 4
+    assert g(1, 8, 8, 8, 1.0, r(A), big, 0, 0, r(B), 0, 0, 0, 1.0, r(C), 0, 0, 0, r(D), 0, 0, 0, None) == -7
+    assert g(1, 8, 8, 8, 1.0, r(A), 0, big, 0, r(B), 0, 0, 0, 1.0, r(C), 0, 0, 0, r(D), 0, 0, 0, None) == -8
+    assert g(1, 8, 8, 8, 1.0, r(A), 0, 0, 0, r(B), 0, 0, 0, 1.0, r(C), 0, 0, 0, r(D), big, 0, 0, None) == -20
+    assert g(1, 8, 8, 8, 1.0, r(A), 0, 0, 0, r(B), 0, 0, 0, 1.0, r(C), 0, 0, 0, r(D), 0, INT_MAX, 0, None) == -21
+    assert lib.bf_dpotrf_l_batched(1, 8, r(C), big, 0, 0, r(D), 0, 0, 0, None, 0, None, None) == -4
+    assert lib.bf_dtrsm_rltn_batched(1, 8, 8, 1.0, r(A), 0, big, 0, None, 0, r(B), 0, 0, 0, r(D), 0, 0, 0,
+                                     None) == -7
+    assert lib.bf_unpack_dmat_batched(1, 8, 8, r(A), big, 0, 0, ctypes.c_void_p(0x20000), 8, 64, None) == -5
+
+
+def _dsub(m, n, i, j):
+    s = _abi.bf_dsub()
+    s.mat = _desc(m, n)
+    s.i, s.j = i, j
+    return s
+
+
+def test_descriptor_record_check_on_the_host(lib):
+    # the rules the descriptor-array kernels apply to each record on the device
+    ok = lib.bf_dsub_valid
+    r = ctypes.byref
+    assert ok(r(_dsub(8, 8, 0, 0)), 8, 8) == 1
+    assert ok(r(_dsub(8, 8, 3, 2)), 5, 6) == 1
+    assert ok(r(_dsub(8, 8, 3, 2)), 6, 6) == 0
+    assert ok(r(_dsub(8, 8, 3, 2)), 5, 7) == 0
+    assert ok(r(_dsub(8, 8, -1, 0)), 1, 1) == 0
+    assert ok(r(_dsub(8, 8, 0, 0)), -1, 1) == 0
+    # offsets near INT_MAX must not wrap round into a passing check
+    assert ok(r(_dsub(8, 8, INT_MAX - 4, 0)), 8, 8) == 0
+    assert ok(r(_dsub(8, 8, 0, INT_MAX)), 8, 8) == 0
+    assert ok(r(_dsub(8, 8, INT_MAX, INT_MAX)), INT_MAX, INT_MAX) == 0
+    bad = _dsub(8, 8, 0, 0)
+    bad.mat.ps = 8
+    assert ok(r(bad), 1, 1) == 0
+    bad = _dsub(8, 8, 0, 0)
+    bad.mat.pA = 0x10004
+    assert ok(r(bad), 1, 1) == 0
+    assert ok(None, 1, 1) == 0
+
+
+def test_noalloc_solver_reports_argument_errors_before_size(lib):
+    # an order beyond the solver's limit is BF_ERR_UNSUPPORTED, a bad operand
+    # its argument position, whatever the batch: only a valid call that does
+    # not fit the fixed array is BF_ERR_TOO_LARGE
+    r = ctypes.byref
+    g = lib.bf_dposv_mixed_batched_noalloc
+    A, B, X = _desc(200, 200), _desc(200, 8), _desc(200, 8, addr=0x20000)
+    sa, sb = 200 * 200, 200 * 8
+    assert g(4096, 161, 4, r(A), 0, 0, sa, r(B), 0, 0, sb, r(X), 0, 0, sb, 1e-12, 10, None, None,
+             None) == _abi.BF_ERR_UNSUPPORTED
+    assert g(4096, 128, 4, None, 0, 0, sa, r(B), 0, 0, sb, r(X), 0, 0, sb, 1e-12, 10, None, None, None) == -4
+    assert g(4096, 128, 4, r(A), 0, 0, sa, r(B), 0, 0, sb, r(X), 0, 0, sb, -1.0, 10, None, None, None) == -16
+    assert g(4096, 128, 4, r(A), 0, 0, sa, r(B), 0, 0, sb, r(X), 0, 0, sb, 1e-12, 0, None, None, None) == -17
+    assert g(4096, 128, 4, r(A), 0, 0, sa, r(B), 0, 0, sb, r(X), 0, 0, sb, 1e-12, 10, None, None,
+             None) == _abi.BF_ERR_TOO_LARGE
+    assert g(0, 128, 4, None, 0, 0, 0, None, 0, 0, 0, None, 0, 0, 0, 1e-12, 10, None, None, None) == 0
