@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 
 import oracle
+from tests import test_oracle_bruteforce as bf
 from tests import test_oracle_pins as pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "bf_oracle.c")
@@ -48,12 +49,27 @@ MUTANTS = {
     "gelqf_beta_sign": ("double beta = -copysign(sqrt(alpha * alpha + s), alpha);",
                         "double beta = copysign(sqrt(alpha * alpha + s), alpha);"),
     "gelqf_drops_w_update": ("      EL(D, ldd, r, i) -= t * w;\n", "\n"),
+    # single-precision accumulators: exact on the small-integer pins, so only
+    # the brute-force comparison in extended precision can catch them
+    "gemm_float_accumulator": ("double s = 0.0;\n      for (int l = 0; l < k; l++) s += EL(A, lda, i, l) * EL(B, ldb, j, l);\n      double c = (beta == 0.0) ? 0.0 : beta * EL(C, ldc, i, j);\n      EL(D, ldd, i, j) = alpha * s + c;\n    }\n  }\n}\n\n/* gemm_nn",
+                               "float s = 0.0f;\n      for (int l = 0; l < k; l++) s += EL(A, lda, i, l) * EL(B, ldb, j, l);\n      double c = (beta == 0.0) ? 0.0 : beta * EL(C, ldc, i, j);\n      EL(D, ldd, i, j) = alpha * s + c;\n    }\n  }\n}\n\n/* gemm_nn"),
+    "potrf_float_accumulator": ("for (int l = 0; l < j; l++) s -= EL(D, ldd, i, l) * EL(D, ldd, j, l);\n      EL(D, ldd, i, j) = s / ljj;",
+                                "float acc = 0.0f;\n      for (int l = 0; l < j; l++) acc += EL(D, ldd, i, l) * EL(D, ldd, j, l);\n      s -= acc;\n      EL(D, ldd, i, j) = s / ljj;"),
+    "trsm_float_accumulator": ("double s = alpha * EL(B, ldb, i, j);\n      for (int l = 0; l < j; l++) s -= EL(D, ldd, i, l) * EL(L, ldl, j, l);",
+                               "double s = alpha * EL(B, ldb, i, j);\n      float acc = 0.0f;\n      for (int l = 0; l < j; l++) acc += EL(D, ldd, i, l) * EL(L, ldl, j, l);\n      s -= acc;"),
     "pack_row_in_panel": ("(size_t)c * (size_t)ps + (size_t)(r % ps)", "(size_t)c * (size_t)ps + (size_t)((r + 1) % ps)"),
 }
 
 
-def _battery():
-    """Run a representative subset of the pins; return True if all pass."""
+# mutants that the pins without the extended-precision brute force miss
+BRUTE_ONLY = ("gemm_float_accumulator", "potrf_float_accumulator", "trsm_float_accumulator")
+
+
+def _battery(brute=True):
+    """Run a representative subset of the pins; return True if all pass.
+
+    brute=False leaves out the brute-force comparisons in extended precision
+    (test_oracle_bruteforce), to show which mutants only those catch."""
     checks = [
         lambda: pins.test_gemm_nt_integer_exact(7, 5, 9, -2.0, 3.0),
         lambda: pins.test_gemm_nt_transposition_is_detected(),
@@ -72,6 +88,12 @@ def _battery():
         lambda: pins.test_getrf_matches_lapack(9),
         lambda: pins.test_gelqf_matches_qr_of_transpose(12, 20),
     ]
+    if brute:
+        checks += [
+            lambda: bf.test_gemm_nt_against_exact_rationals(7, 5, 6, -0.7, 1.3),
+            lambda: bf.test_trsm_rltn_against_exact_rationals(5, 7, -1.7),
+            lambda: bf.test_potrf_l_against_60_digit_evaluation(8),
+        ]
     for c in checks:
         try:
             c()
@@ -84,8 +106,7 @@ def test_unmutated_oracle_passes_battery():
     assert _battery()
 
 
-@pytest.mark.parametrize("name", sorted(MUTANTS))
-def test_mutant_is_caught(name, tmp_path):
+def _build_mutant(name, tmp_path):
     old, new = MUTANTS[name]
     src = open(SRC).read()
     assert src.count(old) == 1, f"mutation anchor for {name} not unique"
@@ -93,11 +114,29 @@ def test_mutant_is_caught(name, tmp_path):
     mpath.write_text(src.replace(old, new))
     so = tmp_path / "libmutant.so"
     subprocess.run(["gcc", *oracle.CFLAGS, "-o", str(so), str(mpath), "-lm"], check=True)
+    return so
+
+
+def _run_battery(so, brute=True):
     # run the battery in a child process so that a mutant cannot disturb this one
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     code = ("import sys; sys.path.insert(0, %r); import oracle; "
             "oracle.build = lambda force=False: %r; "
             "from tests.test_oracle_mutants import _battery; "
-            "sys.exit(0 if _battery() else 3)") % (root, str(so))
-    rc = subprocess.run([sys.executable, "-c", code], cwd=root).returncode
+            "sys.exit(0 if _battery(brute=%r) else 3)") % (root, str(so), brute)
+    return subprocess.run([sys.executable, "-c", code], cwd=root).returncode
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(name, tmp_path):
+    rc = _run_battery(_build_mutant(name, tmp_path))
     assert rc == 3, f"mutant {name} survived the pins (rc={rc})"
+
+
+@pytest.mark.parametrize("name", BRUTE_ONLY)
+def test_mutant_is_caught_only_by_the_brute_force(name, tmp_path):
+    # survives every other pin of the battery (its errors vanish on small
+    # integers), and is caught once the extended-precision comparisons run
+    so = _build_mutant(name, tmp_path)
+    assert _run_battery(so, brute=False) == 0, f"{name} is caught without the brute force"
+    assert _run_battery(so, brute=True) == 3
