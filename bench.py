@@ -747,17 +747,19 @@ def run_gpu(args):
         print(json.dumps(result))
 
 
-# Input and output slots of the end-to-end pipeline (GiB-sized device
-# buffers).  Measured on one box, same order of runs: 3/3 366 ms, 6/3 354 ms,
-# 8/4 362 ms, 4/2 386 ms per step.
-E2E_IN_SLOTS, E2E_OUT_SLOTS = 6, 3
+# Host output buffers of the end-to-end pipeline (a ring; nothing reads
+# them back during the timed steps).
+E2E_OUT_SLOTS = 3
 
 
 class E2EPipeline:
-    """The sweep through the public API with host buffers.  Every step, for
-    every point: copy its inputs from pinned host memory (column-major, as a
-    user holds them) to the device, pack them (bf_pack), run the routine,
-    unpack the result (bf_unpack) and copy it back to pinned host memory.
+    """The sweep through the public C ABI with host buffers.  Every step, for
+    every point: pack its inputs from pinned host memory (column-major, as a
+    user holds them) into its panel-major operands with bf_pack_dmat_batched,
+    run the routine, and unpack the result into pinned host memory with
+    bf_unpack_dmat_batched.  The library reaches the pinned host memory
+    directly (mapped), so these two calls are the host-to-device and
+    device-to-host transfers: nothing else copies.
 
     Host inputs are kept in per-n pinned pools that the routines of that n
     share: a pool of N(0,1) data (gemm A, B, C; syrk A, C; trsm B; syrk_potrf
@@ -765,17 +767,14 @@ class E2EPipeline:
     of n*I (syrk_potrf).  `plan` lists (point, [(operand, pinned host
     input)]) in issue order.
 
-    Issue order: alternately from the small-n end (copy-bound: ~1 GiB of
+    Issue order: alternately from the small-n end (transfer-bound: ~1 GiB of
     inputs for little arithmetic) and the large-n end (compute-bound) of the
-    sweep, so that the copies of one kind overlap the kernels of the other.
+    sweep, so that the transfers of one kind overlap the kernels of the other.
     The points are independent; the work per step is unchanged.
 
-    Three-stage pipeline on three streams joined by events: host-to-device
-    copies into a ring of E2E_IN_SLOTS input slots, then (compute stream)
-    pack, the routine and unpack into a ring of E2E_OUT_SLOTS output slots,
-    then device-to-host copies.  A copy into a slot waits only for the pack
-    that last read it, so the host-to-device direction of the link never
-    waits behind a kernel or an outgoing copy."""
+    Three streams joined by events: packs (host -> device), routines, unpacks
+    (device -> host).  A point's pack waits only for the previous step's
+    unpack of the same point (its operands and result are then free)."""
 
     def __init__(self, pts, dev):
         import torch
@@ -835,18 +834,14 @@ class E2EPipeline:
                 order.append(plan[hi])
             lo, hi = lo + 1, hi - 1
         self.plan = order
-        self.NI, self.NO = E2E_IN_SLOTS, E2E_OUT_SLOTS
-        max_in = max(sum(h.numel() for _, h in ins) for _, ins in self.plan)
+        self.NO = E2E_OUT_SLOTS
         max_sz = max(p.batch * p.n * p.n for p in pts)
         self.s_in, self.s_run, self.s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
-        self.in_dev = [torch.empty(max_in, dtype=torch.float64, device=dev) for _ in range(self.NI)]
-        self.out_dev = [torch.empty(max_sz, dtype=torch.float64, device=dev) for _ in range(self.NO)]
         self.out_host = [torch.empty(max_sz, dtype=torch.float64, pin_memory=True) for _ in range(self.NO)]
-        self.in_ready = [torch.cuda.Event() for _ in range(self.NI)]
-        self.in_free = [torch.cuda.Event() for _ in range(self.NI)]
-        self.out_ready = [torch.cuda.Event() for _ in range(self.NO)]
-        self.out_free = [torch.cuda.Event() for _ in range(self.NO)]
-        self.used_in, self.used_out = [False] * self.NI, [False] * self.NO
+        self.in_ready = [torch.cuda.Event() for _ in self.plan]
+        self.run_done = [torch.cuda.Event() for _ in self.plan]
+        self.out_done = [torch.cuda.Event() for _ in self.plan]
+        self.started = False
         self.count = 0
         torch.cuda.synchronize()
 
@@ -859,42 +854,83 @@ class E2EPipeline:
         import paper_1704_02457_gb300 as bf
 
         for jp, (p, ins) in enumerate(self.plan):
-            j = self.count
+            oi = self.count % self.NO
             self.count += 1
-            si, oi = j % self.NI, j % self.NO
             sz = p.batch * p.n * p.n
-            views, off = [], 0
-            for name, h in ins:
-                views.append((name, self.in_dev[si][off:off + h.numel()].view(h.shape)))
-                off += h.numel()
             with torch.cuda.stream(self.s_in):
-                if self.used_in[si]:
-                    self.s_in.wait_event(self.in_free[si])
-                for (_, buf), (_, h) in zip(views, ins):
-                    buf.copy_(h, non_blocking=True)
-                self.in_ready[si].record(self.s_in)
-            self.used_in[si] = True
+                if self.started:
+                    self.s_in.wait_event(self.out_done[jp])
+                for name, h in ins:
+                    bf.pack(h, getattr(p, name), stream=self.s_in)
+                self.in_ready[jp].record(self.s_in)
             with torch.cuda.stream(self.s_run):
-                self.s_run.wait_event(self.in_ready[si])
-                for name, buf in views:
-                    bf.pack(buf, getattr(p, name), stream=self.s_run)
-                self.in_free[si].record(self.s_run)
+                self.s_run.wait_event(self.in_ready[jp])
                 p.run(self.s_run)
-                if self.used_out[oi]:
-                    self.s_run.wait_event(self.out_free[oi])
-                ob = self.out_dev[oi][:sz].view(p.batch, p.n, p.n)
-                bf.unpack(p.D, ob, stream=self.s_run)
-                self.out_ready[oi].record(self.s_run)
-            self.used_out[oi] = True
+                self.run_done[jp].record(self.s_run)
             with torch.cuda.stream(self.s_out):
-                self.s_out.wait_event(self.out_ready[oi])
+                self.s_out.wait_event(self.run_done[jp])
                 dst = out_targets[jp].view(-1)[:sz] if out_targets is not None else self.out_host[oi][:sz]
-                dst.copy_(self.out_dev[oi][:sz], non_blocking=True)
-                self.out_free[oi].record(self.s_out)
+                bf.unpack(p.D, dst.view(p.batch, p.n, p.n), stream=self.s_out)
+                self.out_done[jp].record(self.s_out)
+        self.started = True
+
+
+def link_probe(dev, nbytes=1 << 30, reps=3):
+    """Host-link bandwidth in this run, for reading e2e against its bound:
+    copy-engine H2D / D2H (torch copies between pinned host and device
+    memory), both directions at once, and the library's own transfers
+    (bf_pack_dmat_batched from / bf_unpack_dmat_batched to pinned host
+    memory) alone and at once.  GB/s, best of `reps`."""
+    import torch
+
+    import paper_1704_02457_gb300 as bf
+
+    n = 64
+    bt = nbytes // (8 * n * n)
+    h_in = torch.empty((bt, n, n), dtype=torch.float64, pin_memory=True).fill_(1.0)
+    h_out = torch.empty((bt, n, n), dtype=torch.float64, pin_memory=True)
+    d_a = torch.empty((bt, n, n), dtype=torch.float64, device=dev)
+    d_b = torch.empty((bt, n, n), dtype=torch.float64, device=dev)
+    P = bf.DMatBatch(bt, n, n, tight=True)
+    Q = bf.DMatBatch(bt, n, n, tight=True)
+    Q.storage.fill_(2.0)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    nb = bt * n * n * 8
+
+    def best(fn, nbytes_moved):
+        out = 0.0
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            out = max(out, nbytes_moved / (time.perf_counter() - t0) / 1e9)
+        return round(out, 1)
+
+    def both(f_in, f_out):
+        def go():
+            with torch.cuda.stream(s1):
+                f_in()
+            with torch.cuda.stream(s2):
+                f_out()
+        return go
+
+    ce_in = lambda: d_a.copy_(h_in, non_blocking=True)  # noqa: E731
+    ce_out = lambda: h_out.copy_(d_b, non_blocking=True)  # noqa: E731
+    bf_in = lambda: bf.pack(h_in, P, stream=torch.cuda.current_stream())  # noqa: E731
+    bf_out = lambda: bf.unpack(Q, h_out, stream=torch.cuda.current_stream())  # noqa: E731
+    res = {"copy_engine_h2d_gbs": best(ce_in, nb), "copy_engine_d2h_gbs": best(ce_out, nb),
+           "copy_engine_both_gbs_each": best(both(ce_in, ce_out), nb),
+           "bf_pack_from_host_gbs": best(bf_in, nb), "bf_unpack_to_host_gbs": best(bf_out, nb),
+           "bf_both_gbs_each": best(both(bf_in, bf_out), nb), "bytes": nb}
+    del h_in, h_out, d_a, d_b, P, Q
+    torch.cuda.empty_cache()
+    return res
 
 
 def run_e2e(pts, args, dev, world):
-    """The end-to-end leg: E2EPipeline steps timed on the host clock."""
+    """The end-to-end leg: E2EPipeline steps timed on the host clock, plus a
+    probe of the host link in the same run."""
     import torch
 
     pipe = E2EPipeline(pts, dev)
@@ -909,12 +945,21 @@ def run_e2e(pts, args, dev, world):
     torch.cuda.synchronize()
     dt = max_over_ranks((time.perf_counter() - t0) / steps, world, dev)
     step_flops = sum(p.flops for p in pts)
+    h2d, d2h = pipe.h2d, pipe.d2h
+    del pipe
+    torch.cuda.empty_cache()
+    link = link_probe(dev)
+    # the time the host link alone needs for the step's transfers, at the
+    # library's measured rate with both directions at once (they overlap)
+    each = link["bf_both_gbs_each"] * 1e9
+    bound_ms = max(h2d, d2h) / each * 1e3 if each > 0 else None
     return {"value": round(job_rate(step_flops, dt, world), 2), "unit": "GFLOP/s",
-            "h2d_bytes_per_step": int(pipe.h2d), "d2h_bytes_per_step": int(pipe.d2h), "steps": steps,
-            "ms_per_step": round(dt * 1e3, 2),
-            "path": "pinned host column-major -> H2D -> bf_pack -> routine -> bf_unpack -> D2H, "
-                    "points issued small-n/large-n alternately through a three-stage pipeline "
-                    "(copy-in, compute, copy-out streams; %d input and %d output slots)" % (pipe.NI, pipe.NO)}
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "steps": steps, "ms_per_step": round(dt * 1e3, 2), "link": link,
+            "link_bound_ms": round(bound_ms, 2) if bound_ms else None,
+            "path": "pinned host column-major -> bf_pack_dmat_batched (reads the host directly) -> routine "
+                    "-> bf_unpack_dmat_batched (writes the host directly), points issued small-n/large-n "
+                    "alternately on three streams (pack, compute, unpack)"}
 
 
 def run_mixed(args, dev, bt=8192, n=128, nrhs=4):

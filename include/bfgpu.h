@@ -109,14 +109,42 @@ int bf_panel_height(void);
 
 /* ---- packing (Sec. 4.3.3; the packing routines of Appendix A.3) ---------- */
 
-/* Copies, for each of `batch` problems, the m x n column-major matrix at
- * A + b*strideA (device memory, leading dimension lda >= max(1, m)) into the
- * sub-matrix (bi, bj) of the panel-major matrix sB (problem stride strideB).
- * Elements of sB outside the sub-matrix are not written. */
+/* Packing converts between a column-major matrix (leading dimension lda:
+ * element (i, j) at A[i + j*lda]) and a sub-matrix of a panel-major one
+ * (Sec. 4.3.3 address formula above).  The column-major side may be
+ *   - device (or managed) memory: a kernel copies;
+ *   - host memory that is pinned or registered with the CUDA runtime (and so
+ *     mapped into the device's address space): a kernel copies, reading or
+ *     writing the host memory directly over the host link;
+ *   - plain (pageable) host memory: one cudaMemcpy2DAsync per problem and
+ *     group of ps rows (a panel's rows are ps consecutive doubles on both
+ *     sides).  This path is slow for many small matrices; pin or register
+ *     the buffer for speed.
+ * The kind is found with cudaPointerGetAttributes; for a batched call it is
+ * that of the first problem's matrix, and all problems must lie in one
+ * allocation.  The panel-major side is device memory, as everywhere.
+ * Host buffers must stay valid until the copy is done: the calls are
+ * asynchronous on `stream`, except that a copy to pageable host memory
+ * returns only once it is complete.  Nothing is allocated.
+ * Elements of the destination outside the copied sub-matrix are not
+ * written. */
+
+/* Packs the m x n column-major matrix A (host or device, lda >= max(1, m))
+ * into the sub-matrix (bi, bj) of the panel-major matrix sB. */
+int bf_pack_dmat(int m, int n, const double *A, int lda, const bf_dmat *sB, int bi, int bj,
+                 void *stream);
+
+/* Unpacks the m x n sub-matrix (ai, aj) of sA into the column-major matrix
+ * B (host or device, ldb >= max(1, m)). */
+int bf_unpack_dmat(int m, int n, const bf_dmat *sA, int ai, int aj, double *B, int ldb,
+                   void *stream);
+
+/* Batched forms: problem b's column-major matrix is at A + b*strideA (B +
+ * b*strideB for unpack; strides in doubles), its panel-major one at
+ * sB->pA + b*strideB (sA->pA + b*strideA). */
 int bf_pack_dmat_batched(int batch, int m, int n, const double *A, int lda, long long strideA,
                          const bf_dmat *sB, int bi, int bj, long long strideB, void *stream);
 
-/* The inverse copy: sub-matrix (ai, aj) of sA into the column-major B. */
 int bf_unpack_dmat_batched(int batch, int m, int n, const bf_dmat *sA, int ai, int aj,
                            long long strideA, double *B, int ldb, long long strideB, void *stream);
 

@@ -66,6 +66,8 @@ SIGNATURES = {
     "bf_memsize_dmat": (_c_sz, [_c_int, _c_int]),
     "bf_create_dmat": (_c_int, [_c_int, _c_int, _P, _c_vp]),
     "bf_panel_height": (_c_int, []),
+    "bf_pack_dmat": (_c_int, [_c_int, _c_int, _c_vp, _c_int, _P, _c_int, _c_int, _c_vp]),
+    "bf_unpack_dmat": (_c_int, [_c_int, _c_int, _P, _c_int, _c_int, _c_vp, _c_int, _c_vp]),
     "bf_pack_dmat_batched": (_c_int, [_c_int, _c_int, _c_int, _c_vp, _c_int, _c_ll, *_M, _c_vp]),
     "bf_unpack_dmat_batched": (_c_int, [_c_int, _c_int, _c_int, *_M, _c_vp, _c_int, _c_ll, _c_vp]),
     "bf_dgemm_nt_batched": (_c_int, [_c_int, _c_int, _c_int, _c_int, _c_d, *_M, *_M, _c_d, *_M, *_M, _c_vp]),

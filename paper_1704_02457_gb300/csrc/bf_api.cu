@@ -121,6 +121,20 @@ int bf_unpack_dmat_batched(int batch, int m, int n, const bf_dmat *sA, int ai, i
                               (cudaStream_t)stream));
 }
 
+int bf_pack_dmat(int m, int n, const double *A, int lda, const bf_dmat *sB, int bi, int bj, void *stream) {
+  const int r = bf_pack_dmat_batched(1, m, n, A, lda, 0, sB, bi, bj, 0, stream);
+  if (r >= 0) return r;
+  static const int map[11] = {0, 0, 1, 2, 3, 4, 0, 5, 6, 7, 0};
+  return -map[-r];
+}
+
+int bf_unpack_dmat(int m, int n, const bf_dmat *sA, int ai, int aj, double *B, int ldb, void *stream) {
+  const int r = bf_unpack_dmat_batched(1, m, n, sA, ai, aj, 0, B, ldb, 0, stream);
+  if (r >= 0) return r;
+  static const int map[11] = {0, 0, 1, 2, 3, 4, 5, 0, 6, 7, 0};
+  return -map[-r];
+}
+
 // ---------------------------------------------------------------- gemm / syrk
 
 static int gemm_like(bool syrk, int batch, int m, int n, int k, double alpha, const bf_dmat *sA,

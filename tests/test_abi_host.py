@@ -281,3 +281,23 @@ def test_noalloc_solver_reports_argument_errors_before_size(lib):
     assert g(4096, 128, 4, r(A), 0, 0, sa, r(B), 0, 0, sb, r(X), 0, 0, sb, 1e-12, 10, None, None,
              None) == _abi.BF_ERR_TOO_LARGE
     assert g(0, 128, 4, None, 0, 0, 0, None, 0, 0, 0, None, 0, 0, 0, 1e-12, 10, None, None, None) == 0
+
+
+def test_single_problem_pack_reports_its_own_positions(lib):
+    r = ctypes.byref
+    D = _desc(8, 8)
+    h = ctypes.c_void_p(0x30000)
+    assert lib.bf_pack_dmat(-1, 8, h, 8, r(D), 0, 0, None) == -1
+    assert lib.bf_pack_dmat(8, -1, h, 8, r(D), 0, 0, None) == -2
+    assert lib.bf_pack_dmat(8, 8, None, 8, r(D), 0, 0, None) == -3
+    assert lib.bf_pack_dmat(8, 8, h, 7, r(D), 0, 0, None) == -4
+    assert lib.bf_pack_dmat(8, 8, h, 8, None, 0, 0, None) == -5
+    assert lib.bf_pack_dmat(8, 8, h, 8, r(D), 1, 0, None) == -6
+    assert lib.bf_pack_dmat(8, 8, h, 8, r(D), 0, 1, None) == -7
+    assert lib.bf_pack_dmat(0, 8, None, 0, None, 0, 0, None) == 0
+    assert lib.bf_unpack_dmat(8, 8, None, 0, 0, h, 8, None) == -3
+    assert lib.bf_unpack_dmat(8, 8, r(D), INT_MAX, 0, h, 8, None) == -4
+    assert lib.bf_unpack_dmat(8, 8, r(D), 0, 1, h, 8, None) == -5
+    assert lib.bf_unpack_dmat(8, 8, r(D), 0, 0, None, 8, None) == -6
+    assert lib.bf_unpack_dmat(8, 8, r(D), 0, 0, h, 3, None) == -7
+    assert lib.bf_unpack_dmat(8, 0, None, 0, 0, None, 0, None) == 0

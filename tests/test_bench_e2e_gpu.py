@@ -1,8 +1,7 @@
-"""The end-to-end pipeline of bench.py (copy-in, compute and copy-out streams
-joined by events, with rings of staging slots) gives, for every point, exactly
-the result of the same point run alone on one stream: no input slot is
-overwritten before its pack reads it, and no output slot before its copy to
-the host."""
+"""The end-to-end pipeline of bench.py (pack-from-host, compute and
+unpack-to-host streams joined by events) gives, for every point, exactly the
+result of the same point run alone on one stream: no operand is repacked
+before the previous step's routine and unpack of that point are done."""
 import pytest
 import torch
 
@@ -26,7 +25,7 @@ def test_e2e_pipeline_equals_each_point_run_alone():
     dev = torch.device("cuda")
     pts = [bench.Point(r, n, dev, seed=900 + i, batch=bt) for i, (r, n, bt) in enumerate(SPEC)]
     pipe = bench.E2EPipeline(pts, dev)
-    assert len(pipe.plan) > max(pipe.NI, pipe.NO)
+    assert len(pipe.plan) > pipe.NO
     outs = [torch.empty(p.batch * p.n * p.n, dtype=torch.float64, pin_memory=True) for p, _ in pipe.plan]
     pipe.step()
     pipe.step(outs)  # the second step's results land in one host buffer per point
