@@ -427,6 +427,54 @@ int bf_dposv_mixed_batched_noalloc(int batch, int n, int nrhs, const bf_dmat *sA
                                    double *resid, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * Kernel layouts (the hook of the autotuner).
+ *
+ * The paper's library is built in size-specialized variants for each target
+ * (Sec. 5.1: HP2, HP2F).  Here each routine has several kernel layouts
+ * (problems per CTA, lanes per problem, a split k-loop), and a built-in rule
+ * picks one from the order and the batch size.  A caller that has timed the
+ * candidates -- the package's autotuner -- can force one per (routine, order,
+ * batch size class).  The results do not depend on the layout beyond
+ * rounding (summation order), except where a layout has no kernel for the
+ * order, which bf_layout_set refuses.
+ *
+ * routine:  0 gemm_nt, 1 syrk_ln, 2 potrf_l, 3 trsm_rltn, 4 syrk_potrf_ln.
+ * order:    m for gemm_nt, syrk_ln, potrf_l and syrk_potrf_ln; n (the order
+ *           of L) for trsm_rltn.  Orders above 511 share one entry.
+ * batch:    the entry covers the batch sizes with the same floor(log2(batch)).
+ * layout:   0 = the built-in rule; 1 .. bf_layout_count(routine) - 1:
+ *   gemm_nt, syrk_ln:   1, 2, 3 = the k-loop of a 4x4 block on 1, 2, 4 lanes
+ *   potrf_l, syrk_potrf_ln:
+ *                       1 one lane per problem, in registers (order <= 8)
+ *                       2..6 a warp shared by 16, 8, 4, 2, 1 problems, the
+ *                         triangles in shared memory (order <= 31)
+ *                       7 one thread per row, 1, 2 or 4 problems per CTA
+ *                       8 one problem per CTA of four warps (order <= 32)
+ *   trsm_rltn:          1 one thread per row of X
+ *                       2, 3, 4 = 2, 4, 8 lanes per row (order <= 32)
+ * The table is process-wide (all devices) and not synchronized with calls in
+ * flight: set it before the calls it should affect.
+ * ------------------------------------------------------------------------ */
+
+/* Number of layouts of `routine` (entry 0, the rule, included); 0 for an
+ * unknown routine. */
+int bf_layout_count(int routine);
+
+/* Forces `layout` for (routine, order, batch class); layout 0 restores the
+ * rule.  Returns 0, -1..-4 for a bad argument, or BF_ERR_UNSUPPORTED if the
+ * layout has no kernel for that order. */
+int bf_layout_set(int routine, int order, int batch, int layout);
+
+/* The layout a call of `routine` with these sizes would use now (the forced
+ * one, else the rule's): gemm_nt (m, n, k), syrk_ln (m, -, k), potrf_l (m),
+ * trsm_rltn (m, n), syrk_potrf_ln (m, -, k); unused sizes are ignored.
+ * Returns the layout (>= 1) or -1..-5 for a bad argument. */
+int bf_layout_get(int routine, int batch, int m, int n, int k);
+
+/* Restores the built-in rule everywhere. */
+void bf_layout_reset(void);
+
+/* ---------------------------------------------------------------------------
  * Descriptor-array batched forms: uneven sizes in one launch.
  *
  * The strided forms need every problem of a call to share sizes and layout.

@@ -88,6 +88,10 @@ SIGNATURES = {
                                         _c_vp]),
     "bf_dsyrk_dpotrf_ln_vbatched": (_c_int, [_c_int, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_int, _c_vp, _c_int,
                                              _c_vp, _c_vp]),
+    "bf_layout_count": (_c_int, [_c_int]),
+    "bf_layout_set": (_c_int, [_c_int, _c_int, _c_int, _c_int]),
+    "bf_layout_get": (_c_int, [_c_int, _c_int, _c_int, _c_int, _c_int]),
+    "bf_layout_reset": (None, []),
     "bf_dsub_valid": (_c_int, [ctypes.POINTER(bf_dsub), _c_int, _c_int]),
     "bf_dgetrf_batched": (_c_int, [_c_int, _c_int, *_M, *_M, _c_vp, _c_ll, _c_vp, _c_vp]),
     "bf_dgetrf": (_c_int, [_c_int, _P, _c_int, _c_int, _P, _c_int, _c_int, _c_vp, _c_vp, _c_vp]),

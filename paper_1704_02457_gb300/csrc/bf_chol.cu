@@ -60,15 +60,6 @@ __device__ __forceinline__ void tri_index(int t, int &tr, int &tc) {
   tc = t - r * (r + 1) / 2;
 }
 
-// 8-byte asynchronous global -> shared copy (cp.async, bypasses registers)
-__device__ __forceinline__ void cp_async8(double *dst, const double *src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
-}
-
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.wait_all;\n" ::: "memory");
-}
 
 // packed lower column-major: column l starts at cs(l); element (i, l) at cs(l) + i
 __device__ __forceinline__ int col_start(int l, int n) { return (l * (2 * n - l + 1)) / 2 - l; }
@@ -1059,9 +1050,14 @@ cudaError_t launch_tiny(bool aligned, int batch, int n, int k, Op A, Op B, Op C,
   }
 }
 
+// The built-in choice of layout for potrf / syrk_potrf (the LAYOUT_CHOL_*
+// candidates of bf_internal.cuh).
 template <bool FUSED>
-cudaError_t launch_chol_t(bool aligned, int batch, int n, int k, Op A, Op B, Op C, OpW D,
-                          double *dinv, long long sdinv, int *info, cudaStream_t s) {
+int chol_rule(int batch, int n) {
+  // few problems of a small order: one problem per CTA over an SM's four
+  // sub-partitions (the latency kernel)
+  if (n <= BF_CHOL_LAT_MAX_N && (long long)batch <= (long long)BF_CHOL_LAT_MAX_BATCH_PER_SM * device_sm_count())
+    return LAYOUT_CHOL_LAT;
   bool small = n <= BF_CHOL_SMALL_MAX_N;
   // the fused routine's four-problem orders below it, for batches that give
   // four-problem CTAs at least one per SM sub-partition
@@ -1070,7 +1066,7 @@ cudaError_t launch_chol_t(bool aligned, int batch, int n, int k, Op A, Op B, Op 
   // enough problems for one lane each to give every SM sub-partition a
   // warp: the register kernel
   if (small && n <= BF_CHOL_TINY_MAX_N && (long long)batch >= 32LL * 4 * device_sm_count())
-    return launch_tiny<FUSED>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
+    return LAYOUT_CHOL_TINY;
   int g = small ? pick_small_g(n) : 0;
   // Small batches: more lanes per problem until the launch has a warp for
   // every SM sub-partition (4 per SM), up to one problem per warp.  The
@@ -1079,18 +1075,54 @@ cudaError_t launch_chol_t(bool aligned, int batch, int n, int k, Op A, Op B, Op 
   if (g)
     while (g < 32 && (long long)batch * g < 32LL * 4 * device_sm_count()) g *= 2;
   switch (g) {
-    case 1: return launch_small_g<1, FUSED>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
-    case 2: return launch_small_g<2, FUSED>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
-    case 4: return launch_small_g<4, FUSED>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
-    case 8: return launch_small_g<8, FUSED>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
-    case 16: return launch_small_g<16, FUSED>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
-    case 32: return launch_small_g<32, FUSED>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
-    default: break;
+    case 2: return LAYOUT_CHOL_SMALL_G2;
+    case 4: return LAYOUT_CHOL_SMALL_G4;
+    case 8: return LAYOUT_CHOL_SMALL_G8;
+    case 16: return LAYOUT_CHOL_SMALL_G16;
+    case 32: return LAYOUT_CHOL_SMALL_G32;
+    default: return LAYOUT_CHOL_ROWS;
   }
-  return launch_rows<FUSED, double>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
+}
+
+template <bool FUSED>
+cudaError_t launch_chol_t(bool aligned, int batch, int n, int k, Op A, Op B, Op C, OpW D,
+                          double *dinv, long long sdinv, int *info, cudaStream_t s) {
+  int lay = layout_forced(FUSED ? ROUTINE_SYRK_POTRF : ROUTINE_POTRF, n, batch);
+  if (lay <= 0) lay = chol_rule<FUSED>(batch, n);
+  switch (lay) {
+    case LAYOUT_CHOL_TINY: return launch_tiny<FUSED>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
+    case LAYOUT_CHOL_SMALL_G2: return launch_small_g<2, FUSED>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
+    case LAYOUT_CHOL_SMALL_G4: return launch_small_g<4, FUSED>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
+    case LAYOUT_CHOL_SMALL_G8: return launch_small_g<8, FUSED>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
+    case LAYOUT_CHOL_SMALL_G16:
+      return launch_small_g<16, FUSED>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
+    case LAYOUT_CHOL_SMALL_G32:
+      return launch_small_g<32, FUSED>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
+    case LAYOUT_CHOL_LAT: return launch_chol_lat(FUSED, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
+    default: return launch_rows<FUSED, double>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
+  }
 }
 
 }  // namespace
+
+int chol_layout_rule(bool fused, int batch, int n) {
+  return fused ? chol_rule<true>(batch, n) : chol_rule<false>(batch, n);
+}
+
+bool chol_layout_ok(int layout, int n) {
+  switch (layout) {
+    case LAYOUT_CHOL_TINY: return n <= BF_CHOL_TINY_MAX_N;
+    case LAYOUT_CHOL_SMALL_G2: case LAYOUT_CHOL_SMALL_G4: case LAYOUT_CHOL_SMALL_G8:
+    case LAYOUT_CHOL_SMALL_G16: case LAYOUT_CHOL_SMALL_G32: {
+      // the triangles of the warp's problems must fit the kernel's shared memory
+      const int g = 2 << (layout - LAYOUT_CHOL_SMALL_G2);
+      return n <= BF_CHOL_SMALL_MAX_N && (long long)n * (n + 1) / 2 * small_pitch(32 / g) * 8 <= 200 * 1024;
+    }
+    case LAYOUT_CHOL_ROWS: return n <= CHOL_MAX_N;
+    case LAYOUT_CHOL_LAT: return n <= BF_CHOL_LAT_MAX_N;
+    default: return false;
+  }
+}
 
 cudaError_t launch_chol(bool fused, int batch, int n, int k, Op A, Op B, Op C, OpW D,
                         double *dinv, long long sdinv, int *info, bool aligned, cudaStream_t s) {

@@ -316,6 +316,13 @@ cudaError_t launch_gemm_nt_v(bool syrk, int batch, const bf_dsize *size, double 
   return cudaGetLastError();
 }
 
+int gemm_layout_rule(bool syrk, int batch, int m, int n, int k) {
+  const int tr = (m + 3) / 4, tcn = (n + 3) / 4;
+  const long long total = (long long)batch * (syrk ? tr * (tr + 1) / 2 : tr * tcn);
+  if (total < 2LL * 4 * 32 * device_sm_count()) return (k >= 16) ? LAYOUT_GEMM_KS4 : (k >= 8 ? LAYOUT_GEMM_KS2 : LAYOUT_GEMM_KS1);
+  return LAYOUT_GEMM_KS1;
+}
+
 cudaError_t launch_gemm_nt(bool syrk, int batch, int m, int n, int k, double alpha, Op A, Op B,
                            double beta, Op C, OpW D, bool aligned, cudaStream_t s) {
   const int tr = (m + 3) / 4, tcn = (n + 3) / 4;
@@ -324,8 +331,9 @@ cudaError_t launch_gemm_nt(bool syrk, int batch, int m, int n, int k, double alp
   // Small batches (fewer than two blocks per lane of every SM sub-partition's
   // warp slot): split k over 2 or 4 lanes per block, so the launch spreads
   // over the SMs instead of leaving each warp a long serial k-loop.
-  int ks = 1;
-  if (total < 2LL * 4 * 32 * device_sm_count()) ks = (k >= 16) ? 4 : (k >= 8 ? 2 : 1);
+  int lay = layout_forced(syrk ? ROUTINE_SYRK_LN : ROUTINE_GEMM_NT, m, batch);
+  if (lay <= 0) lay = gemm_layout_rule(syrk, batch, m, n, k);
+  const int ks = lay == LAYOUT_GEMM_KS4 ? 4 : (lay == LAYOUT_GEMM_KS2 ? 2 : 1);
   if (ks == 4) return launch_gemm_ks<4>(syrk, aligned, total, batch, m, n, k, alpha, A, B, beta, C, D, tcn, tiles_pp, s);
   if (ks == 2) return launch_gemm_ks<2>(syrk, aligned, total, batch, m, n, k, alpha, A, B, beta, C, D, tcn, tiles_pp, s);
   return launch_gemm_ks<1>(syrk, aligned, total, batch, m, n, k, alpha, A, B, beta, C, D, tcn, tiles_pp, s);

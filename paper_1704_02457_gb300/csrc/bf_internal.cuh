@@ -134,6 +134,14 @@ __host__ __device__ __forceinline__ bool dsub_ok(const bf_dsub &s, int rows, int
 __device__ __forceinline__ Op dsub_op(const bf_dsub &s) { return Op{s.mat.pA, 0, s.mat.cn, s.i, s.j}; }
 __device__ __forceinline__ OpW dsub_opw(const bf_dsub &s) { return OpW{s.mat.pA, 0, s.mat.cn, s.i, s.j}; }
 
+// 8-byte asynchronous global -> shared copy (cp.async, bypasses registers)
+__device__ __forceinline__ void cp_async8(double *dst, const double *src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // Launchers of the descriptor-array forms (problems checked on the device).
 cudaError_t launch_gemm_nt_v(bool syrk, int batch, const bf_dsize *size, double alpha, const bf_dsub *A,
                              const bf_dsub *B, double beta, const bf_dsub *C, const bf_dsub *D, int max_m,
@@ -180,6 +188,56 @@ cudaError_t launch_pack(int batch, int m, int n, const double *A, int lda, long 
                         cudaStream_t s);
 cudaError_t launch_unpack(int batch, int m, int n, Op A, double *B, int ldb, long long sB,
                           cudaStream_t s);
+
+// ---- kernel layouts (the candidates that bf_layout_set can force and the
+// autotuner times; 0 everywhere means the built-in rule) --------------------
+enum {
+  ROUTINE_GEMM_NT = 0,
+  ROUTINE_SYRK_LN = 1,
+  ROUTINE_POTRF = 2,
+  ROUTINE_TRSM_RLTN = 3,
+  ROUTINE_SYRK_POTRF = 4,
+  ROUTINE_COUNT = 5
+};
+// gemm_nt / syrk_ln: the k-loop of a 4x4 block split over KS lanes
+enum { LAYOUT_GEMM_KS1 = 1, LAYOUT_GEMM_KS2 = 2, LAYOUT_GEMM_KS4 = 3, LAYOUT_GEMM_COUNT = 4 };
+// potrf / syrk_potrf
+enum {
+  LAYOUT_CHOL_TINY = 1,      // one lane per problem, registers (n <= 8)
+  LAYOUT_CHOL_SMALL_G2 = 2,  // k_chol_small with G = 2, 4, 8, 16, 32 lanes per problem (n <= 31)
+  LAYOUT_CHOL_SMALL_G4 = 3,
+  LAYOUT_CHOL_SMALL_G8 = 4,
+  LAYOUT_CHOL_SMALL_G16 = 5,
+  LAYOUT_CHOL_SMALL_G32 = 6,
+  LAYOUT_CHOL_ROWS = 7,      // one thread per row, problems per CTA by rule (n <= 512)
+  LAYOUT_CHOL_LAT = 8,       // one problem per CTA of four warps (n <= 32)
+  LAYOUT_CHOL_COUNT = 9
+};
+// trsm_rltn
+enum { LAYOUT_TRSM_ROWS = 1, LAYOUT_TRSM_LAT2 = 2, LAYOUT_TRSM_LAT4 = 3, LAYOUT_TRSM_LAT8 = 4, LAYOUT_TRSM_COUNT = 5 };
+
+// Layout forced for (routine, n, batch) by bf_layout_set, or 0.
+int layout_forced(int routine, int n, int batch);
+// The built-in rules, and whether a candidate supports order n.
+int chol_layout_rule(bool fused, int batch, int n);
+bool chol_layout_ok(int layout, int n);
+int gemm_layout_rule(bool syrk, int batch, int m, int n, int k);
+int trsm_layout_rule(int batch, int m, int n);
+bool trsm_layout_ok(int layout, int n);
+
+// Latency kernels (bf_latency.cu): one problem per CTA of four warps for
+// potrf / syrk_potrf, R = lanes lanes per row for trsm; order <= 32.
+cudaError_t launch_chol_lat(bool fused, int batch, int n, int k, Op A, Op B, Op C, OpW D, double *dinv,
+                            long long sdinv, int *info, cudaStream_t s);
+cudaError_t launch_trsm_lat(int lanes, int batch, int m, int n, double alpha, Op L, const double *dinv,
+                            long long sdinv, Op B, OpW D, cudaStream_t s);
+#ifndef BF_CHOL_LAT_MAX_N
+#define BF_CHOL_LAT_MAX_N 32
+#endif
+// the latency kernel serves batches of at most this many problems per SM
+#ifndef BF_CHOL_LAT_MAX_BATCH_PER_SM
+#define BF_CHOL_LAT_MAX_BATCH_PER_SM 2
+#endif
 
 // Largest order the factorization kernels accept.
 constexpr int CHOL_MAX_N = 512;

@@ -27,13 +27,6 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 
-__device__ __forceinline__ void cp_async8(double *dst, const double *src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
-}
-
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
-
 // Pivot key of x: the bits of |x| as a signed integer (for non-negative
 // doubles the IEEE order is the integer order), -1 for NaN, so that the
 // pivot search compares on the integer pipes instead of issuing FP64

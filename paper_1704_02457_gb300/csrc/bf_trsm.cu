@@ -240,8 +240,30 @@ cudaError_t launch_trsm_rltn_v(int batch, const bf_dsize *size, double alpha, co
   return cudaGetLastError();
 }
 
+// The latency kernel (R lanes per row) where one thread per row would
+// leave SM sub-partitions idle: at most BF_TRSM_LAT_ROWS_PER_SM rows of X
+// per SM over the batch.
+#ifndef BF_TRSM_LAT_ROWS_PER_SM
+#define BF_TRSM_LAT_ROWS_PER_SM 64
+#endif
+int trsm_layout_rule(int batch, int m, int n) {
+  if (n <= 32 && (long long)batch * m <= (long long)BF_TRSM_LAT_ROWS_PER_SM * device_sm_count())
+    return LAYOUT_TRSM_LAT4;
+  return LAYOUT_TRSM_ROWS;
+}
+
+bool trsm_layout_ok(int layout, int n) {
+  if (layout == LAYOUT_TRSM_ROWS) return n <= TRSM_MAX_N;
+  return layout > LAYOUT_TRSM_ROWS && layout < LAYOUT_TRSM_COUNT && n <= 32;
+}
+
 cudaError_t launch_trsm_rltn(int batch, int m, int n, double alpha, Op L, const double *dinv,
                              long long sdinv, Op B, OpW D, cudaStream_t s) {
+  int lay = layout_forced(ROUTINE_TRSM_RLTN, n, batch);
+  if (lay <= 0) lay = trsm_layout_rule(batch, m, n);
+  if (lay == LAYOUT_TRSM_LAT2 || lay == LAYOUT_TRSM_LAT4 || lay == LAYOUT_TRSM_LAT8)
+    return launch_trsm_lat(lay == LAYOUT_TRSM_LAT2 ? 2 : (lay == LAYOUT_TRSM_LAT4 ? 4 : 8), batch, m, n, alpha, L,
+                           dinv, sdinv, B, D, s);
   int P = 1, R = m, chunks = 1;
   if (m > CHUNK_ROWS) {
     chunks = (m + CHUNK_ROWS - 1) / CHUNK_ROWS;

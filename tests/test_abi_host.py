@@ -301,3 +301,34 @@ def test_single_problem_pack_reports_its_own_positions(lib):
     assert lib.bf_unpack_dmat(8, 8, r(D), 0, 0, None, 8, None) == -6
     assert lib.bf_unpack_dmat(8, 8, r(D), 0, 0, h, 3, None) == -7
     assert lib.bf_unpack_dmat(8, 0, None, 0, 0, None, 0, None) == 0
+
+
+def test_layout_table(lib):
+    # the autotuner's hook: candidates per routine, refused where a layout has
+    # no kernel for the order, and the rule restored by layout 0 / reset
+    assert [lib.bf_layout_count(r) for r in range(5)] == [4, 4, 9, 5, 9]
+    assert lib.bf_layout_count(5) == 0
+    assert lib.bf_layout_set(5, 24, 128, 1) == -1
+    assert lib.bf_layout_set(2, -1, 128, 1) == -2
+    assert lib.bf_layout_set(2, 24, 0, 1) == -3
+    assert lib.bf_layout_set(2, 24, 128, 9) == -4
+    assert lib.bf_layout_set(2, 24, 128, 1) == _abi.BF_ERR_UNSUPPORTED  # registers: order <= 8
+    assert lib.bf_layout_set(2, 40, 128, 8) == _abi.BF_ERR_UNSUPPORTED  # latency kernel: order <= 32
+    assert lib.bf_layout_set(3, 40, 128, 3) == _abi.BF_ERR_UNSUPPORTED
+    assert lib.bf_layout_get(2, 0, 24, 0, 0) == -2
+    try:
+        rule = lib.bf_layout_get(4, 128, 24, 0, 24)
+        assert 1 <= rule <= 8
+        assert lib.bf_layout_set(4, 24, 128, 7) == 0
+        assert lib.bf_layout_get(4, 128, 24, 0, 24) == 7
+        assert lib.bf_layout_get(4, 255, 24, 0, 24) == 7   # same batch class (128..255)
+        assert lib.bf_layout_get(4, 256, 24, 0, 24) == rule or lib.bf_layout_get(4, 256, 24, 0, 24) != 7
+        assert lib.bf_layout_set(4, 24, 128, 0) == 0
+        assert lib.bf_layout_get(4, 128, 24, 0, 24) == rule
+        assert lib.bf_layout_set(3, 24, 128, 2) == 0
+        assert lib.bf_layout_get(3, 128, 24, 24, 0) == 2
+        assert lib.bf_layout_set(0, 1000, 7, 3) == 0      # orders above 511 share an entry
+        assert lib.bf_layout_get(0, 7, 700, 700, 700) == 3
+    finally:
+        lib.bf_layout_reset()
+    assert lib.bf_layout_get(3, 128, 24, 24, 0) == lib.bf_layout_get(3, 129, 24, 24, 0)
