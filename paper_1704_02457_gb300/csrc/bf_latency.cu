@@ -60,55 +60,108 @@ constexpr int LAT_KC = 32;
 constexpr int LKP = LAT_KC + 1;
 // Off-diagonal elements go to the first three warps, the diagonal to the last.
 constexpr int LAT_OFF = LAT_T - 32;
-constexpr int LAT_RO = (LAT_N * (LAT_N - 1) / 2 + LAT_OFF - 1) / LAT_OFF;
 
-// Row and column of entry e of the strictly lower triangle listed column by
-// column from the last column back, e = t (t + 1) / 2 + o with o <= t:
-// column n - 2 - t, row n - 1 - t + o.  The trailing part of step j (columns
-// j+1 and later) is then the first (n-j-1)(n-j-2)/2 entries.
-__device__ __forceinline__ void off_entry(int e, int n, int &i, int &m) {
-  int t = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
-  if (t * (t + 1) / 2 > e) t--;
-  if ((t + 1) * (t + 2) / 2 <= e) t++;
-  m = n - 2 - t;
-  i = m + 1 + (e - t * (t + 1) / 2);
+// t and o with e = t (t + 1) / 2 + o, 0 <= o <= t, for e < 528 (t < 32),
+// as a table in global memory: (t << 8) | o at entry e.  A load of it
+// overlaps the operand loads, where computing t from a square root cost more
+// than a microsecond of dependent integer work per CTA.
+struct TriTable {
+  unsigned short v[LAT_N * (LAT_N + 1) / 2];
+  constexpr TriTable() : v() {
+    int e = 0;
+    for (int t = 0; t < LAT_N; t++)
+      for (int o = 0; o <= t; o++) v[e++] = (unsigned short)((t << 8) | o);
+  }
+};
+__device__ constexpr TriTable g_tri{};
+
+__device__ __forceinline__ void tri_split(int e, int &t, int &o) {
+  const unsigned x = __ldg(&g_tri.v[e]);
+  t = (int)(x >> 8);
+  o = (int)(x & 255u);
 }
 
-template <bool FUSED>
+// Row and column of entry e of the strictly lower triangle listed column by
+// column from the last column back: e = t (t + 1) / 2 + o, column n - 2 - t,
+// row n - 1 - t + o.  The trailing part of step j (columns j+1 and later) is
+// then the first (n-j-1)(n-j-2)/2 entries.
+__device__ __forceinline__ void off_entry(int e, int n, int &i, int &m) {
+  int t, o;
+  tri_split(e, t, o);
+  m = n - 2 - t;
+  i = m + 1 + o;
+}
+
+// Address of row r, column 0 of problem b's operand (column c is 4 c further:
+// the panel-major column stride, Sec. 4.3.3)
+__device__ __forceinline__ const double *row_base(const Op &o, int b, int r) {
+  return o.p + (long long)b * o.stride + pm_off(o.i0 + r, o.j0, o.cn);
+}
+
+// NB: the order rounded up to the instantiated width (8, 16, 24 or 32), which
+// sizes the per-thread slot arrays.
+template <bool FUSED, int NB>
 __global__ void __launch_bounds__(LAT_T)
 k_chol_lat(int n, int k, Op A, Op B, Op C, OpW D, double *dinv, long long sdinv, int *info) {
+  // owned off-diagonal elements and fused-update items per thread
+  constexpr int RO = (NB * (NB - 1) / 2 + LAT_OFF - 1) / LAT_OFF;
+  constexpr int RQ = (NB * (NB + 1) + LAT_T - 1) / LAT_T;
   __shared__ double S[LAT_N * LP];
-  __shared__ double AB[FUSED ? 2 * LAT_N * LKP : 1];  // rows of A, then rows of B
-  __shared__ double colb[2][LAT_N];                    // the current column, double buffered
-  __shared__ double iv[LAT_N];                         // 1 / d_j
-  __shared__ double rs[LAT_N];                         // rsqrt(d_j)
+  __shared__ double AB[FUSED ? 2 * LAT_N * LKP : 1];      // rows of A, then rows of B
+  __shared__ double part[FUSED ? LAT_N * (LAT_N + 1) : 1];  // sums of the fused update's items
+  __shared__ double colb[2][LAT_N];                         // the current column, double buffered
+  __shared__ double iv[LAT_N];                              // 1 / d_j
+  __shared__ double rs[LAT_N];                              // rsqrt(d_j)
   const int b = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const bool diag_warp = warp == LAT_T / 32 - 1;
   const int nod = n * (n - 1) / 2;
+  const int ne = n * (n + 1) / 2;
 
   // C's lower triangle (a warp per column, a lane per row) and the first
   // columns of A and B, asynchronously
+  const double *crow = lane < n ? row_base(C, b, lane) : nullptr;
+  const double *arow = FUSED && lane < n && k > 0 ? row_base(A, b, lane) : nullptr;
+  const double *brow = FUSED && lane < n && k > 0 ? row_base(B, b, lane) : nullptr;
   for (int j = warp; j < n; j += LAT_T / 32)
-    if (lane < n && lane >= j) cp_async8(&S[lane * LP + j], elem(C, b, lane, j));
+    if (lane < n && lane >= j) cp_async8(&S[lane * LP + j], crow + PS * j);
   auto stage = [&](int l0, int kc) {
-    for (int l = warp; l < kc; l += LAT_T / 32)
-      if (lane < n) {
-        cp_async8(&AB[lane * LKP + l], elem(A, b, lane, l0 + l));
-        cp_async8(&AB[(LAT_N + lane) * LKP + l], elem(B, b, lane, l0 + l));
+    if (lane < n)
+      for (int l = warp; l < kc; l += LAT_T / 32) {
+        cp_async8(&AB[lane * LKP + l], arow + PS * (l0 + l));
+        cp_async8(&AB[(LAT_N + lane) * LKP + l], brow + PS * (l0 + l));
       }
   };
   if (FUSED && k > 0) stage(0, min(LAT_KC, k));
 
+  // The fused update's items: an element (row-major order of the lower
+  // triangle) or, when that evens out the work of the threads, half of its
+  // k-range; thread t takes items t + 128 r.
+  const int sp = (FUSED && k > 0 && k <= LAT_KC &&
+                  ((ne * 2 + LAT_T - 1) / LAT_T) * ((k + 1) / 2) < ((ne + LAT_T - 1) / LAT_T) * k) ? 2 : 1;
+  const int nq = ne * sp;
+  int qi[RQ], qm[RQ], qh[RQ];
+  if (FUSED && k > 0) {
+#pragma unroll
+    for (int r = 0; r < RQ; r++) {
+      const int q = tid + LAT_T * r;
+      qi[r] = qm[r] = qh[r] = 0;
+      if (q < nq) {
+        tri_split(sp == 2 ? q >> 1 : q, qi[r], qm[r]);
+        qh[r] = sp == 2 ? (q & 1) : 0;
+      }
+    }
+  }
+
   // The elements each thread owns for the whole factorization, in
   // registers: the first three warps the strictly lower triangle (entry
   // tid + 96 r), the last warp the diagonal (lane m owns (m, m)).
-  int ei[LAT_RO], em[LAT_RO];
-  double v[LAT_RO];
+  int ei[RO], em[RO];
+  double v[RO];
   double dg = 0.0;
   if (!diag_warp) {
 #pragma unroll
-    for (int r = 0; r < LAT_RO; r++) {
+    for (int r = 0; r < RO; r++) {
       const int e = tid + LAT_OFF * r;
       ei[r] = em[r] = 0;
       if (e < nod) off_entry(e, n, ei[r], em[r]);
@@ -116,15 +169,13 @@ k_chol_lat(int n, int k, Op A, Op B, Op C, OpW D, double *dinv, long long sdinv,
   }
   cp_async_wait_all();
   __syncthreads();
-  if (!diag_warp) {
-#pragma unroll
-    for (int r = 0; r < LAT_RO; r++) v[r] = (tid + LAT_OFF * r < nod) ? S[ei[r] * LP + em[r]] : 0.0;
-  } else if (lane < n) {
-    dg = S[lane * LP + lane];
-  }
 
   if (FUSED && k > 0) {
-    // + A B^T on the owned elements (the fused update of Sec. 4.7.2)
+    // + A B^T (the fused update of Sec. 4.7.2), items interleaved so that
+    // each thread runs up to RQ independent chains of FMAs
+    double acc[RQ];
+#pragma unroll
+    for (int r = 0; r < RQ; r++) acc[r] = 0.0;
     for (int l0 = 0; l0 < k; l0 += LAT_KC) {
       const int kc = min(LAT_KC, k - l0);
       if (l0 > 0) {
@@ -133,42 +184,61 @@ k_chol_lat(int n, int k, Op A, Op B, Op C, OpW D, double *dinv, long long sdinv,
         cp_async_wait_all();
         __syncthreads();
       }
-      if (!diag_warp) {
+      const int kh = (kc + sp - 1) / sp;
+      int len[RQ];
+      const double *pa[RQ], *pb[RQ];
 #pragma unroll
-        for (int r = 0; r < LAT_RO; r++) {
-          if (tid + LAT_OFF * r < nod) {
-            const double *ar = AB + ei[r] * LKP, *br = AB + (LAT_N + em[r]) * LKP;
-            double acc = v[r];
-            for (int l = 0; l < kc; l++) acc = fma(ar[l], br[l], acc);
-            v[r] = acc;
-          }
-        }
-      } else if (lane < n) {
-        const double *ar = AB + lane * LKP, *br = AB + (LAT_N + lane) * LKP;
-        double acc = dg;
-        for (int l = 0; l < kc; l++) acc = fma(ar[l], br[l], acc);
-        dg = acc;
+      for (int r = 0; r < RQ; r++) {
+        const int lo = qh[r] * kh;
+        len[r] = tid + LAT_T * r < nq ? min(kh, kc - lo) : 0;
+        pa[r] = AB + qi[r] * LKP + lo;
+        pb[r] = AB + (LAT_N + qm[r]) * LKP + lo;
+      }
+      for (int l = 0; l < kh; l++) {
+#pragma unroll
+        for (int r = 0; r < RQ; r++)
+          if (l < len[r]) acc[r] = fma(pa[r][l], pb[r][l], acc[r]);
       }
     }
+#pragma unroll
+    for (int r = 0; r < RQ; r++)
+      if (tid + LAT_T * r < nq) part[tid + LAT_T * r] = acc[r];
+    __syncthreads();
+  }
+
+  // owned values: C, plus the item sums in order
+  auto start_value = [&](int i, int m) {
+    double x = S[i * LP + m];
+    if (FUSED && k > 0) {
+      const int e = i * (i + 1) / 2 + m;
+      x += part[e * sp];
+      if (sp == 2) x += part[e * sp + 1];
+    }
+    return x;
+  };
+  if (!diag_warp) {
+#pragma unroll
+    for (int r = 0; r < RO; r++) v[r] = (tid + LAT_OFF * r < nod) ? start_value(ei[r], em[r]) : 0.0;
+  } else if (lane < n) {
+    dg = start_value(lane, lane);
   }
 
   // column 0, and 1 / d_0
   if (!diag_warp) {
 #pragma unroll
-    for (int r = 0; r < LAT_RO; r++)
+    for (int r = 0; r < RO; r++)
       if (tid + LAT_OFF * r < nod && em[r] == 0) colb[0][ei[r]] = v[r];
   } else if (lane == 0) {
-    colb[0][0] = dg;
     iv[0] = recip3(dg);
   }
   __syncthreads();
 
   // Right-looking, square-root free.  Step j: every owned element (i, m),
   // j < m <= i, takes S[i][m] -= S[i][j] (1/d_j) S[m][j], with column j read
-  // from colb; the owners of column j+1 publish it.  The diagonal lanes use
-  // S[m][m] -= S[m][j]^2 / d_j, and lane j+1, whose pivot is then final,
+  // from colb; the owners of column j+1 publish it.  The diagonal lanes take
+  // S[m][m] -= S[m][j]^2 (1/d_j), and lane j+1, whose pivot is then final,
   // forms 1/d_{j+1} for the next step: the chain from pivot to pivot is two
-  // FMAs and one reciprocal, with one barrier per column.
+  // FP64 operations and one reciprocal, with one barrier per column.
   for (int j = 0; j + 1 < n; j++) {
     const double invd = iv[j];
     const double *cj = colb[j & 1];
@@ -177,15 +247,12 @@ k_chol_lat(int n, int k, Op A, Op B, Op C, OpW D, double *dinv, long long sdinv,
       if (lane > j && lane < n) {
         const double x = cj[lane];
         dg = fma(-(x * x), invd, dg);
-        if (lane == j + 1) {
-          cn[lane] = dg;
-          iv[lane] = recip3(dg);
-        }
+        if (lane == j + 1) iv[lane] = recip3(dg);
       }
     } else {
       const int c = (n - j - 1) * (n - j - 2) / 2;
 #pragma unroll
-      for (int r = 0; r < LAT_RO; r++) {
+      for (int r = 0; r < RO; r++) {
         if (tid + LAT_OFF * r < c) {
           v[r] = fma(-(cj[ei[r]] * invd), cj[em[r]], v[r]);
           if (em[r] == j + 1) cn[ei[r]] = v[r];
@@ -210,12 +277,17 @@ k_chol_lat(int n, int k, Op A, Op B, Op C, OpW D, double *dinv, long long sdinv,
   __syncthreads();
   if (!diag_warp) {
 #pragma unroll
-    for (int r = 0; r < LAT_RO; r++)
+    for (int r = 0; r < RO; r++)
       if (tid + LAT_OFF * r < nod) *elem(D, b, ei[r], em[r]) = v[r] * rs[em[r]];
   }
 }
 
 // NB: the order rounded up to the instantiated width; R lanes per row.
+// The columns of L below the diagonal are scaled by the inverse diagonal in
+// shared memory, L'[c][j] = L[c][j] / L[j][j], so that a lane carries the
+// unscaled t_j = (alpha B - sum_{l<j} X_l L^T_l)_j, the downdate reads
+// t_c -= t_j L'[c][j], and X_j = t_j / L[j][j] is formed once at the end:
+// the chain from one column to the next is one shuffle and one FMA.
 template <int NB, int R>
 __global__ void __launch_bounds__(LAT_T)
 k_trsm_lat(int m, int n, double alpha, Op L, const double *dinv, long long sdinv, Op B, OpW D, int chunks) {
@@ -229,20 +301,24 @@ k_trsm_lat(int m, int n, double alpha, Op L, const double *dinv, long long sdinv
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   // L's lower triangle (a warp per column, a lane per row) and the inverse
   // diagonal go to shared memory asynchronously while the rows of B load
+  const double *lrow = lane < n ? row_base(L, b, lane) : nullptr;
   for (int j = warp; j < n; j += LAT_T / 32)
-    if (lane < n && lane >= j) cp_async8(&Ls[lane * PITCH + j], elem(L, b, lane, j));
+    if (lane < n && lane >= j) cp_async8(&Ls[lane * PITCH + j], lrow + PS * j);
   if (dinv)
     for (int j = tid; j < n; j += LAT_T) cp_async8(&dv[j], dinv + (long long)b * sdinv + j);
-  // a warp whose rows all lie past m only helps with the loads
+  // a warp whose rows all lie past m only helps with the set-up
   const bool warp_rows = row0 + (tid & ~31) / R < m;
   const int q = tid % R;
   const int row = row0 + tid / R;
   const bool active = row < m;
   double t[S];
+  {
+    const double *brow = active ? row_base(B, b, row) : nullptr;
 #pragma unroll
-  for (int s = 0; s < S; s++) {
-    const int c = q + R * s;
-    t[s] = (active && c < n) ? alpha * *elem(B, b, row, c) : 0.0;
+    for (int s = 0; s < S; s++) {
+      const int c = q + R * s;
+      t[s] = (active && c < n) ? alpha * brow[PS * c] : 0.0;
+    }
   }
   cp_async_wait_all();
   __syncthreads();
@@ -250,19 +326,30 @@ k_trsm_lat(int m, int n, double alpha, Op L, const double *dinv, long long sdinv
     for (int j = tid; j < n; j += LAT_T) dv[j] = recip3(Ls[j * PITCH + j]);
     __syncthreads();
   }
+  for (int e = tid; e < n * n; e += LAT_T) {
+    const int c = e / n, j = e - c * n;
+    if (c > j) Ls[c * PITCH + j] *= dv[j];
+  }
+  __syncthreads();
   if (!warp_rows) return;
 
   const int base = lane & ~(R - 1);
 #pragma unroll
   for (int j = 0; j < NB; j++) {
     if (j >= n) break;
-    const double xo = t[j / R] * dv[j];
-    const double x = __shfl_sync(0xffffffffu, xo, base + j % R);
-    if (active && q == j % R) *elem(D, b, row, j) = x;
+    const double x = __shfl_sync(0xffffffffu, t[j / R], base + j % R);
 #pragma unroll
     for (int s = (j + 1) / R; s < S; s++) {
       const int c = q + R * s;
       if (c > j && c < n) t[s] = fma(-x, Ls[c * PITCH + j], t[s]);
+    }
+  }
+  if (active) {
+    double *drow = D.p + (long long)b * D.stride + pm_off(D.i0 + row, D.j0, D.cn);
+#pragma unroll
+    for (int s = 0; s < S; s++) {
+      const int c = q + R * s;
+      if (c < n) drow[PS * c] = t[s] * dv[c];
     }
   }
 }
@@ -291,14 +378,25 @@ cudaError_t launch_trsm_lat_r(int batch, int m, int n, double alpha, Op L, const
 
 constexpr int CHOL_LAT_MAX_N = LAT_N;
 
+template <bool FUSED>
+cudaError_t launch_chol_lat_f(int batch, int n, int k, Op A, Op B, Op C, OpW D, double *dinv, long long sdinv,
+                              int *info, cudaStream_t s) {
+  if (n <= 8)
+    k_chol_lat<FUSED, 8><<<(unsigned)batch, LAT_T, 0, s>>>(n, k, A, B, C, D, dinv, sdinv, info);
+  else if (n <= 16)
+    k_chol_lat<FUSED, 16><<<(unsigned)batch, LAT_T, 0, s>>>(n, k, A, B, C, D, dinv, sdinv, info);
+  else if (n <= 24)
+    k_chol_lat<FUSED, 24><<<(unsigned)batch, LAT_T, 0, s>>>(n, k, A, B, C, D, dinv, sdinv, info);
+  else
+    k_chol_lat<FUSED, 32><<<(unsigned)batch, LAT_T, 0, s>>>(n, k, A, B, C, D, dinv, sdinv, info);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_chol_lat(bool fused, int batch, int n, int k, Op A, Op B, Op C, OpW D, double *dinv,
                             long long sdinv, int *info, cudaStream_t s) {
   if (n > CHOL_LAT_MAX_N) return cudaErrorInvalidValue;
-  if (fused)
-    k_chol_lat<true><<<(unsigned)batch, LAT_T, 0, s>>>(n, k, A, B, C, D, dinv, sdinv, info);
-  else
-    k_chol_lat<false><<<(unsigned)batch, LAT_T, 0, s>>>(n, k, A, B, C, D, dinv, sdinv, info);
-  return cudaGetLastError();
+  return fused ? launch_chol_lat_f<true>(batch, n, k, A, B, C, D, dinv, sdinv, info, s)
+               : launch_chol_lat_f<false>(batch, n, k, A, B, C, D, dinv, sdinv, info, s);
 }
 
 cudaError_t launch_trsm_lat(int lanes, int batch, int m, int n, double alpha, Op L, const double *dinv,
