@@ -963,10 +963,19 @@ def run_e2e(pts, args, dev, world):
 
 
 def run_mixed(args, dev, bt=8192, n=128, nrhs=4):
-    """Mixed precision vs plain FP64 on SPD solves (FP32 factor + FP64
-    iterative refinement to a 1e-12 relative residual, against potrf + potrs
-    in FP64): 8192 systems of order 128 with cond(A) log-uniform in
-    [1e2, 1e6] and 4 right-hand sides each."""
+    """Mixed precision vs plain FP64 on SPD solves to a 1e-12 relative
+    residual: 8192 systems of order 128 with cond(A) log-uniform in
+    [1e2, 1e6] and 4 right-hand sides each.  Arms:
+      fp64    potrf + potrs in FP64;
+      ffma    FP32 factor on the FP32 FMA pipe + FP64 iterative refinement;
+      bf16_tc, tf32_tc, 3xtf32_tc   blocked factor: FP64 diagonal blocks and
+              panels, trailing updates on the tensor cores (tcgen05) in BF16,
+              TF32 or split TF32, + the same FP64 refinement.
+    Per arm: time on the whole batch, and per cond band (1e2-1e3 ... 1e5-1e6)
+    the share of systems that reach 1e-12, their mean corrections, the
+    systems not converged within 30 corrections (iters -1) and those whose
+    factorization failed (iters -2), and the time of a batch of that band
+    alone."""
     import numpy as np
     import torch
 
@@ -975,25 +984,10 @@ def run_mixed(args, dev, bt=8192, n=128, nrhs=4):
 
     A, cond = inputs.spd_cond(bt, n, 9000, dev)
     B = inputs.normal((bt, n, nrhs), 9001, dev)
-    dA, dB = bf.DMatBatch.from_colmajor(A, tight=True), bf.DMatBatch.from_colmajor(B, tight=True)
-    dL = bf.DMatBatch(bt, n, n, tight=True, fill=0.0)
-    dX64, dXm = bf.DMatBatch(bt, n, nrhs, tight=True), bf.DMatBatch(bt, n, nrhs, tight=True)
-    info = torch.zeros(bt, dtype=torch.int32, device=dev)
-    iters = torch.zeros(bt, dtype=torch.int32, device=dev)
-    resid = torch.zeros(bt, dtype=torch.float64, device=dev)
-    work = None
     stream = torch.cuda.current_stream()
+    reps = max(3, args.steps)
 
-    def fp64():
-        bf.dpotrf_l(n, dA, 0, 0, dL, 0, 0, dinv=False, info=info, stream=stream)
-        bf.dpotrs_l(n, nrhs, dL, 0, 0, dB, 0, 0, dX64, 0, 0, stream=stream)
-
-    def mixed():
-        nonlocal work
-        work = bf.dposv_mixed(n, nrhs, dA, 0, 0, dB, 0, 0, dXm, 0, 0, tol=1e-12, max_iter=30,
-                              iters=iters, resid=resid, work=work, stream=stream)
-
-    def timeit(fn, reps):
+    def timeit(fn):
         for _ in range(3):
             fn()
         torch.cuda.synchronize()
@@ -1005,20 +999,89 @@ def run_mixed(args, dev, bt=8192, n=128, nrhs=4):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / reps
 
-    reps = max(3, args.steps)
-    t64 = timeit(fp64, reps)
-    tmx = timeit(mixed, reps)
-    it = iters.cpu().numpy()
-    # relative residuals ||B - A X||_F / (||A||_F ||X||_F), recomputed in FP64 on the device by torch
-    Xm = dXm.to_colmajor()
-    X64 = dX64.to_colmajor()
+    def arms_for(Ab, Bb):
+        """Callables of every arm on one batch, and their outputs."""
+        m = Ab.shape[0]
+        dA, dB = bf.DMatBatch.from_colmajor(Ab, tight=True), bf.DMatBatch.from_colmajor(Bb, tight=True)
+        dL = bf.DMatBatch(m, n, n, tight=True, fill=0.0)
+        out = {}
+        info = torch.zeros(m, dtype=torch.int32, device=dev)
+
+        def fp64(X=bf.DMatBatch(m, n, nrhs, tight=True)):
+            bf.dpotrf_l(n, dA, 0, 0, dL, 0, 0, dinv=False, info=info, stream=stream)
+            bf.dpotrs_l(n, nrhs, dL, 0, 0, dB, 0, 0, X, 0, 0, stream=stream)
+            return X, None
+
+        out["fp64"] = fp64
+        for name, prec in [("ffma", None), ("bf16_tc", "bf16"), ("tf32_tc", "tf32"), ("3xtf32_tc", "3xtf32")]:
+            X = bf.DMatBatch(m, n, nrhs, tight=True)
+            it = torch.zeros(m, dtype=torch.int32, device=dev)
+            res = torch.zeros(m, dtype=torch.float64, device=dev)
+            box = {"work": None}
+
+            def call(X=X, it=it, res=res, box=box, prec=prec):
+                if prec is None:
+                    box["work"] = bf.dposv_mixed(n, nrhs, dA, 0, 0, dB, 0, 0, X, 0, 0, tol=1e-12, max_iter=30,
+                                                 iters=it, resid=res, work=box["work"], stream=stream)
+                else:
+                    box["work"] = bf.dposv_mixed_tc(n, nrhs, dA, 0, 0, dB, 0, 0, X, 0, 0, prec=prec, tol=1e-12,
+                                                    max_iter=30, iters=it, resid=res, work=box["work"],
+                                                    stream=stream)
+                return X, it
+
+            out[name] = call
+        return out
 
     def rel(X):
         R = B - torch.bmm(A, X)
         return (torch.linalg.matrix_norm(R) / (torch.linalg.matrix_norm(A) * torch.linalg.matrix_norm(X))).cpu().numpy()
 
-    rm, r64 = rel(Xm), rel(X64)
+    arms = arms_for(A, B)
+    times, iters, resids = {}, {}, {}
+    for name, fn in arms.items():
+        times[name] = timeit(fn)
+        X, it = fn()
+        torch.cuda.synchronize()
+        iters[name] = it.cpu().numpy() if it is not None else None
+        resids[name] = rel(X.to_colmajor())
+    lc = np.log10(cond.cpu().numpy())
+    bands = [(2, 3), (3, 4), (4, 5), (5, 6)]
+    per_arm = {}
+    for name in arms:
+        it = iters[name]
+        entry = {"ms": round(times[name], 4), "speedup_vs_fp64": round(times["fp64"] / times[name], 3)}
+        if it is not None:
+            ok = it >= 1
+            entry["converged"] = int(ok.sum())
+            entry["not_converged_iters_-1"] = int((it == -1).sum())
+            entry["factorization_failed_iters_-2"] = int((it == -2).sum())
+            entry["max_rel_resid_converged"] = float(resids[name][ok].max()) if ok.any() else None
+            entry["mean_iters"] = round(float(it[ok].mean()), 3) if ok.any() else None
+            by_band = {}
+            for lo, hi in bands:
+                sel = (lc >= lo) & (lc < hi)
+                s_ok = ok[sel]
+                by_band[f"1e{lo}-1e{hi}"] = {
+                    "systems": int(sel.sum()), "converged_frac": round(float(s_ok.mean()), 4) if sel.any() else None,
+                    "mean_iters": round(float(it[sel][s_ok].mean()), 3) if s_ok.any() else None,
+                    "iters_-1": int((it[sel] == -1).sum()), "iters_-2": int((it[sel] == -2).sum())}
+            entry["by_cond"] = by_band
+        else:
+            entry["max_rel_resid"] = float(resids[name].max())
+        per_arm[name] = entry
+    # each band alone: the time of every arm on a batch of that band's systems
+    for lo, hi in bands:
+        idx = torch.from_numpy(np.nonzero((lc >= lo) & (lc < hi))[0]).to(dev)
+        if idx.numel() == 0:
+            continue
+        band_arms = arms_for(A.index_select(0, idx).contiguous(), B.index_select(0, idx).contiguous())
+        for name, fn in band_arms.items():
+            per_arm[name].setdefault("band_ms", {})[f"1e{lo}-1e{hi}"] = round(timeit(fn), 4)
+        del band_arms
+        torch.cuda.empty_cache()
     fl = bt * (n ** 3 / 3.0 + n ** 2 / 2.0 + n / 6.0 + 2.0 * n * n * nrhs)
+    t64, tmx = times["fp64"], times["ffma"]
+    it = iters["ffma"]
     hist = {int(k): int(v) for k, v in zip(*np.unique(it, return_counts=True))}
     return {
         "workload": "8192 SPD systems, n=128, cond log-uniform in [1e2,1e6] (Q diag(lam) Q^T), 4 RHS",
@@ -1027,9 +1090,11 @@ def run_mixed(args, dev, bt=8192, n=128, nrhs=4):
         "fp64_ms": round(t64, 4), "mixed_ms": round(tmx, 4), "speedup": round(t64 / tmx, 3),
         "fp64_gflops": round(fl / (t64 * 1e-3) / 1e9, 2),
         "mixed_gflops_equiv": round(fl / (tmx * 1e-3) / 1e9, 2),
-        "max_rel_resid_fp64": float(r64.max()), "max_rel_resid_mixed": float(rm.max()),
+        "max_rel_resid_fp64": float(resids["fp64"].max()),
+        "max_rel_resid_mixed": float(resids["ffma"][it >= 1].max()),
         "all_converged": bool((it >= 1).all()), "iters_hist": hist,
         "mean_iters": round(float(it[it >= 1].mean()), 3) if (it >= 1).any() else None,
+        "arms": per_arm,
     }
 
 

@@ -346,6 +346,48 @@ int bf_dposv_mixed_batched(int batch, int n, int nrhs, const bf_dmat *sA, int ai
                            int max_iter, int *iters, double *resid, void *work, size_t work_bytes,
                            void *stream);
 
+/* Bytes of device workspace bf_dposv_mixed_tc_batched needs. */
+size_t bf_dposv_mixed_tc_worksize(int batch, int n);
+
+/* Mixed-precision SPD solve whose factorization is blocked (not in the
+ * paper, which has separate single- and double-precision routines, Appendix
+ * A.3): for each block column of 32, the diagonal block is factored (potrf)
+ * and the panel below it solved (trsm) in FP64, and the trailing matrix is
+ * updated on the tensor cores in precision `prec`:
+ *     0  BF16 operands, FP32 accumulation
+ *     1  TF32 operands, FP32 accumulation
+ *     2  3xTF32: operands split as H + R (both TF32), H H^T + H R^T + R H^T
+ * (see bf_dsyrk_ln_tc_batched).  The factor, rounded to FP32, then drives the
+ * FP64 iterative refinement of bf_dposv_mixed_batched, with its tolerance,
+ * iteration limit and outcome codes (iters -1: not converged within
+ * max_iter; -2: a pivot of the blocked factorization failed).  The lower
+ * precisions converge only while cond(A) times their unit roundoff stays
+ * well below one; the others report -1.
+ * Arguments 1..19 as for bf_dposv_mixed_batched; work: device memory of at
+ * least bf_dposv_mixed_tc_worksize(batch, n) bytes, 256-byte aligned, owned
+ * by the caller.  Supports n <= 160 and 1 <= nrhs <= 8. */
+int bf_dposv_mixed_tc_batched(int batch, int n, int nrhs, const bf_dmat *sA, int ai, int aj,
+                              long long strideA, const bf_dmat *sB, int bi, int bj, long long strideB,
+                              const bf_dmat *sX, int xi, int xj, long long strideX, double tol,
+                              int max_iter, int *iters, double *resid, int prec, void *work,
+                              size_t work_bytes, void *stream);
+
+/* syrk_ln in reduced precision on the tensor cores, the trailing update of
+ * the blocked mixed-precision factorization (not in the paper, whose
+ * routines come in separate single- and double-precision versions, Appendix
+ * A.3):
+ *     lower(D) <- C - A * A^T
+ * A is m x k, C and D are m x m, all FP64; only the lower triangle of D is
+ * written.  The product A A^T is formed by tcgen05 MMAs with FP32
+ * accumulation from A rounded to `prec` (0 BF16, 1 TF32, 2 3xTF32 as above);
+ * the subtraction is FP64.  Supports m <= 128 and 1 <= k <= 32.  A's rows
+ * must start on a panel top (ai % BF_PS == 0), its storage be 16-byte
+ * aligned and strideA even, else -5 (its runs of 4 rows are copied by the
+ * bulk-copy engine).  C and D may coincide; A must not overlap D. */
+int bf_dsyrk_ln_tc_batched(int batch, int m, int k, int prec, const bf_dmat *sA, int ai, int aj,
+                           long long strideA, const bf_dmat *sC, int ci, int cj, long long strideC,
+                           const bf_dmat *sD, int di, int dj, long long strideD, void *stream);
+
 /* ---- backward Riccati recursion (Sec. 5.3) -------------------------------- */
 
 /* One MPC instance of bf_driccati_sqrt_batched, in device memory.  All

@@ -19,7 +19,7 @@ from ._abi import BF_ALIGN, BF_ERR_UNSUPPORTED, BF_PS, bf_dmat, load
 __all__ = [
     "BF_PS", "BF_ALIGN", "BF_ERR_UNSUPPORTED", "BfError", "DMatBatch", "bf_dmat", "load",
     "dgemm_nt", "dsyrk_ln", "dpotrf_l", "dtrsm_rltn", "dsyrk_dpotrf_ln", "pack", "unpack",
-    "dpotrs_l", "dposv_mixed", "dposv_mixed_worksize", "dgemm_nn", "dtrmm_rlnn", "dgetrf", "dgelqf",
+    "dpotrs_l", "dposv_mixed", "dposv_mixed_worksize", "dposv_mixed_tc", "dposv_mixed_tc_worksize", "dgemm_nn", "dtrmm_rlnn", "dgetrf", "dgelqf",
     "dsub_records", "dsize_records", "dgemm_nt_vbatched", "dsyrk_ln_vbatched", "dpotrf_l_vbatched",
     "dtrsm_rltn_vbatched", "dsyrk_dpotrf_ln_vbatched",
 ]
@@ -231,6 +231,34 @@ def dposv_mixed(n, nrhs, A, ai, aj, B, bi, bj, X, xi, xj, tol=1e-12, max_iter=30
         batch, n, nrhs, *_op(A, ai, aj), *_op(B, bi, bj), *_op(X, xi, xj), float(tol), int(max_iter),
         ctypes.c_void_p(iters.data_ptr()) if iters is not None else None,
         ctypes.c_void_p(resid.data_ptr()) if resid is not None else None,
+        ctypes.c_void_p(work.data_ptr()), work.numel() * work.element_size(), _stream(stream)))
+    return work
+
+
+def dposv_mixed_tc_worksize(batch, n):
+    return load().bf_dposv_mixed_tc_worksize(batch, n)
+
+
+TC_PRECISIONS = {"bf16": 0, "tf32": 1, "3xtf32": 2}
+
+
+def dposv_mixed_tc(n, nrhs, A, ai, aj, B, bi, bj, X, xi, xj, prec="3xtf32", tol=1e-12, max_iter=30, iters=None,
+                   resid=None, work=None, batch=None, stream=None):
+    """Mixed-precision SPD solve with a blocked factorization whose trailing
+    updates run on the tensor cores (bf_dposv_mixed_tc_batched); prec is
+    "bf16", "tf32" or "3xtf32".  work: a device tensor of at least
+    dposv_mixed_tc_worksize(batch, n) bytes (allocated here if None, returned)."""
+    torch = _torch()
+    batch = X.batch if batch is None else batch
+    need = dposv_mixed_tc_worksize(batch, n)
+    if work is None:
+        raw = torch.empty(need + BF_ALIGN, dtype=torch.uint8, device=X.storage.device)
+        off = (-raw.data_ptr()) % BF_ALIGN
+        work = raw[off:off + need]
+    _check("bf_dposv_mixed_tc_batched", load().bf_dposv_mixed_tc_batched(
+        batch, n, nrhs, *_op(A, ai, aj), *_op(B, bi, bj), *_op(X, xi, xj), float(tol), int(max_iter),
+        ctypes.c_void_p(iters.data_ptr()) if iters is not None else None,
+        ctypes.c_void_p(resid.data_ptr()) if resid is not None else None, TC_PRECISIONS[prec],
         ctypes.c_void_p(work.data_ptr()), work.numel() * work.element_size(), _stream(stream)))
     return work
 

@@ -114,6 +114,10 @@ SIGNATURES = {
     "bf_dposv_mixed_worksize": (_c_sz, [_c_int, _c_int]),
     "bf_dposv_mixed_batched": (_c_int, [_c_int, _c_int, _c_int, *_M, *_M, *_M, _c_d, _c_int, _c_vp,
                                         _c_vp, _c_vp, _c_sz, _c_vp]),
+    "bf_dposv_mixed_tc_worksize": (_c_sz, [_c_int, _c_int]),
+    "bf_dposv_mixed_tc_batched": (_c_int, [_c_int, _c_int, _c_int, *_M, *_M, *_M, _c_d, _c_int, _c_vp,
+                                           _c_vp, _c_int, _c_vp, _c_sz, _c_vp]),
+    "bf_dsyrk_ln_tc_batched": (_c_int, [_c_int, _c_int, _c_int, _c_int, *_M, *_M, *_M, _c_vp]),
     "bf_driccati_sqrt_batched": (_c_int, [_c_int, _c_int, _c_vp, _c_vp, _c_int, _c_int, _c_int, _c_vp]),
     "bf_dposv_mixed_batched_noalloc": (_c_int, [_c_int, _c_int, _c_int, *_M, *_M, *_M, _c_d, _c_int,
                                                 _c_vp, _c_vp, _c_vp]),

@@ -462,6 +462,60 @@ int bf_dposv_mixed_batched(int batch, int n, int nrhs, const bf_dmat *sA, int ai
                                   info32, fast, (cudaStream_t)stream));
 }
 
+static size_t round_up(size_t x) { return (x + BF_ALIGN - 1) / BF_ALIGN * BF_ALIGN; }
+
+size_t bf_dposv_mixed_tc_worksize(int batch, int n) {
+  if (batch <= 0 || n <= 0) return 0;
+  const size_t pm = ((size_t)n + PS - 1) / PS * PS, nblk = ((size_t)n + 31) / 32, bt = (size_t)batch;
+  return round_up(bt * pm * n * 8) + round_up(bt * n * 8) + round_up(bt * pm * n * 4) + round_up(nblk * bt * 4) +
+         round_up(bt * 4);
+}
+
+int bf_dposv_mixed_tc_batched(int batch, int n, int nrhs, const bf_dmat *sA, int ai, int aj, long long strideA,
+                              const bf_dmat *sB, int bi, int bj, long long strideB, const bf_dmat *sX, int xi,
+                              int xj, long long strideX, double tol, int max_iter, int *iters, double *resid,
+                              int prec, void *work, size_t work_bytes, void *stream) {
+  if (int r = posv_mixed_check(batch, n, nrhs, sA, ai, aj, strideA, sB, bi, bj, strideB, sX, xi, xj, strideX, tol,
+                               max_iter, iters, resid))
+    return r;
+  if (prec < 0 || prec > 2) return -20;
+  if (batch == 0 || n == 0 || nrhs == 0) return 0;
+  if (!work || !aligned_to(work, BF_ALIGN)) return -21;
+  if (work_bytes < bf_dposv_mixed_tc_worksize(batch, n)) return -22;
+  const size_t pm = ((size_t)n + PS - 1) / PS * PS, nblk = ((size_t)n + 31) / 32, bt = (size_t)batch;
+  char *w = (char *)work;
+  double *W = (double *)w;
+  w += round_up(bt * pm * n * 8);
+  double *dinv = (double *)w;
+  w += round_up(bt * n * 8);
+  float *l32 = (float *)w;
+  w += round_up(bt * pm * n * 4);
+  int *infos = (int *)w;
+  w += round_up(nblk * bt * 4);
+  int *info32 = (int *)w;
+  return status(launch_posv_mixed_tc(prec, batch, n, nrhs, make_op(sA, ai, aj, strideA), make_op(sB, bi, bj, strideB),
+                                     make_opw(sX, xi, xj, strideX), tol, max_iter, iters, resid, W, dinv, l32, infos,
+                                     info32, (cudaStream_t)stream));
+}
+
+int bf_dsyrk_ln_tc_batched(int batch, int m, int k, int prec, const bf_dmat *sA, int ai, int aj, long long strideA,
+                           const bf_dmat *sC, int ci, int cj, long long strideC, const bf_dmat *sD, int di, int dj,
+                           long long strideD, void *stream) {
+  if (batch < 0) return -1;
+  if (m < 0) return -2;
+  if (k < 0) return -3;
+  if (prec < 0 || prec > 2) return -4;
+  if (batch == 0 || m == 0) return 0;
+  if (m > 128 || k > 32 || k == 0) return BF_ERR_UNSUPPORTED;
+  if (int w = check_op(sA, ai, aj, m, k, strideA, batch, false)) return pos_err(w, 5);
+  if (int w = check_op(sC, ci, cj, m, m, strideC, batch, false)) return pos_err(w, 9);
+  if (int w = check_op(sD, di, dj, m, m, strideD, batch, true)) return pos_err(w, 13);
+  const Op A = make_op(sA, ai, aj, strideA);
+  if (!syrk_tc_ok(m, k, A)) return -5;  // rows off a panel top, or runs not 16-byte aligned
+  return status(launch_syrk_tc(prec, batch, m, k, A, make_op(sC, ci, cj, strideC), make_opw(sD, di, dj, strideD),
+                               nullptr, (cudaStream_t)stream));
+}
+
 // ------------------------------------------------------------ getrf / gelqf
 
 int bf_dgetrf_batched(int batch, int n, const bf_dmat *sC, int ci, int cj, long long strideC,

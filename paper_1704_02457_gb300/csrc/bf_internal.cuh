@@ -173,6 +173,22 @@ int posv_mixed_check(int batch, int n, int nrhs, const bf_dmat *sA, int ai, int 
                      int xj, long long strideX, double tol, int max_iter, const int *iters,
                      const double *resid);
 
+// The FP64 iterative refinement of the mixed-precision solvers, given the
+// FP32 factor l32 (panel-major, pm x n per problem) and its status info32.
+cudaError_t launch_posv_refine(int batch, int n, int nrhs, Op A, Op B, OpW X, double tol, int max_iter, int *iters,
+                               double *resid, const float *l32, const int *info32, cudaStream_t s);
+
+// Tensor-core trailing update lower(D) = C - L L^T (bf_tc.cu): L m x k, m <= 128,
+// k <= 32 even, L's rows on a panel top and 16-byte aligned; prec 0 BF16,
+// 1 TF32, 2 3xTF32.  err[b] = -3 if a wait timed out (err may be NULL).
+bool syrk_tc_ok(int m, int k, const Op &L);
+cudaError_t launch_syrk_tc(int prec, int batch, int m, int k, Op L, Op C, OpW D, int *err, cudaStream_t s);
+// Blocked mixed-precision factorization (FP64 diagonal blocks and panels,
+// tensor-core trailing updates) followed by the refinement.
+cudaError_t launch_posv_mixed_tc(int prec, int batch, int n, int nrhs, Op A, Op B, OpW X, double tol, int max_iter,
+                                 int *iters, double *resid, double *W, double *dinv, float *l32, int *infos,
+                                 int *info32, cudaStream_t s);
+
 // LU with partial pivoting (square n <= 128) and Householder LQ (m*n <= 16384).
 cudaError_t launch_getrf(int batch, int n, Op C, OpW D, int *ipiv, long long sipiv, int *info, cudaStream_t s);
 cudaError_t launch_gelqf(int batch, int m, int n, Op C, OpW D, double *tau, long long stau, cudaStream_t s);

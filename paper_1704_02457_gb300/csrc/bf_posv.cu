@@ -454,6 +454,13 @@ cudaError_t launch_posv_mixed(int batch, int n, int nrhs, Op A, Op B, OpW X, dou
   const OpWT<float> D{l32, (long long)pm * n, n, 0, 0};
   cudaError_t e = launch_chol_f32(batch, n, A, D, info32, aligned, s);
   if (e != cudaSuccess) return e;
+  return launch_posv_refine(batch, n, nrhs, A, B, X, tol, max_iter, iters, resid, l32, info32, s);
+}
+
+cudaError_t launch_posv_refine(int batch, int n, int nrhs, Op A, Op B, OpW X, double tol, int max_iter, int *iters,
+                               double *resid, const float *l32, const int *info32, cudaStream_t s) {
+  const int pm = (n + PS - 1) / PS * PS;
+  cudaError_t e;
   const size_t smem = posv_smem(true, n, nrhs);
   if (smem > 200 * 1024) return cudaErrorInvalidConfiguration;
   e = set_posv_smem_attr<true>();
