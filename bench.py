@@ -36,6 +36,9 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 SWEEP_N = (4, 8, 16, 24, 32, 48, 64, 96, 128, 192, 256)
+# (m, n, k) of a sweep point at order n, as bf_layout_get takes them
+SIZES = {"dgemm_nt": lambda n: (n, n, n), "dsyrk_ln": lambda n: (n, 0, n), "dpotrf_l": lambda n: (n, 0, 0),
+         "dtrsm_rltn": lambda n: (n, n, 0), "dsyrk_dpotrf_ln": lambda n: (n, 0, n)}
 ROUTINES = ("dgemm_nt", "dsyrk_ln", "dpotrf_l", "dtrsm_rltn", "dsyrk_dpotrf_ln")
 
 # FP64 ALU peak of GB300 from unit counts and clock: 152 SMs x 2 FP64 FMA
@@ -123,8 +126,28 @@ def small_g(n):
     return 16 if ne * 2 * 8 <= 48 * 1024 else 0
 
 
-def kernel_of(routine, n):
-    """Name of the kernel the library launches for (routine, n) at this sweep."""
+def kernel_of(routine, n, layout=None):
+    """Name of the kernel the library launches for (routine, n) at this sweep
+    in `layout` (a tune.LAYOUT_NAMES name; None: the row kernels of the
+    Cholesky, the built-in choice of the other routines).  Layouts made of
+    several launches are named by their parts."""
+    fused = int(routine == "dsyrk_dpotrf_ln")
+    if layout in ("ks2", "ks4"):
+        return f"k_gemm_nt<{int(routine == 'dsyrk_ln')},1,1>/{layout}"
+    if layout and layout.startswith("latency"):
+        if routine == "dtrsm_rltn":
+            return f"k_trsm_lat<{max(8, (n + 7) // 8 * 8)},{layout[-1]}>"
+        return f"k_chol_lat<{fused},{max(8, (n + 7) // 8 * 8)}>"
+    if layout and layout.startswith("small_g"):
+        return f"k_chol_small<{layout[7:]},{fused},1>"
+    if layout == "tiny":
+        return f"k_chol_tiny<{n},{fused},1>"
+    if layout == "split":
+        return ("k_gemm_nt<1,1,1>+" if fused else "") + kernel_of("dpotrf_l", n, "rows")
+    if layout == "blocked":
+        h = (n // 2) & ~3
+        return (("k_gemm_nt<1,1,1>+" if fused else "") + "blocked[" + kernel_of("dpotrf_l", h, "rows") + "+" +
+                kernel_of("dtrsm_rltn", h) + "+k_gemm_nt<1,1,1>+" + kernel_of("dpotrf_l", n - h, "rows") + "]")
     if routine == "dgemm_nt":
         return "k_gemm_nt<0,1,1>"
     if routine == "dsyrk_ln":
@@ -133,10 +156,9 @@ def kernel_of(routine, n):
         if n <= 32:
             return f"k_trsm_rltn_w<{4 if n <= 4 else (n + 7) // 8 * 8}>"
         return "k_trsm_rltn"
-    fused = int(routine == "dsyrk_dpotrf_ln")
-    if n <= 8:  # the sweep's batches give one lane per problem
+    if n <= 8 and layout is None:  # the sweep's batches give one lane per problem
         return f"k_chol_tiny<{n},{fused},1>"
-    if n <= 31 and small_g(n) and not (fused and n >= 24 and n % 8 == 0):
+    if n <= 31 and small_g(n) and not (fused and n >= 24 and n % 8 == 0) and layout is None:
         return f"k_chol_small<{small_g(n)},{fused},1>"
     if n <= 64:
         return f"k_chol_rows4<{fused},1,double,256,4>"
@@ -151,11 +173,19 @@ def kernel_of(routine, n):
     return f"k_chol_rows<16,{fused},1,double>"
 
 
-def launches_of(routine, n, batch, sms=152):
+def launches_of(routine, n, batch, sms=152, layout=None):
     """Kernel launches of one call at this sweep.  The Cholesky of orders
     193..256 splits a batch whose last wave of two-problem CTAs (two per SM)
     holds more pairs than SMs but at most 80% of its slots: the pairs of the
-    full waves, then the rest one problem per CTA."""
+    full waves, then the rest one problem per CTA.  The split layout adds
+    the syrk launch; the blocked layout is potrf, trsm, syrk, potrf and the
+    launch that rebuilds info from the diagonal (plus the syrk of the fused
+    routine's sum)."""
+    fused = routine == "dsyrk_dpotrf_ln"
+    if layout == "split":
+        return int(fused) + launches_of("dpotrf_l", n, batch, sms)
+    if layout == "blocked":
+        return int(fused) + 5
     if routine in ("dpotrf_l", "dsyrk_dpotrf_ln") and 192 < n <= 256:
         slots, pairs = 2 * sms, (batch + 1) // 2
         rest = pairs % slots
@@ -614,6 +644,21 @@ def run_gpu(args):
         pts.append(Point(r, n, dev, seed=5000 + 97 * i))
         torch.cuda.empty_cache()
     stream = torch.cuda.current_stream()
+    # the kernel layout of every point: timed by the autotuner on the point's
+    # own operands (untimed here), or the built-in rule with --no-tune
+    from paper_1704_02457_gb300 import tune
+    tuned = {}
+    t_tune = time.perf_counter()
+    for p in pts:
+        sizes = SIZES[p.routine](p.n)
+        if args.no_tune:
+            lay = tune.rule_layout(p.routine, p.batch, *sizes)
+            p.layout = tune.LAYOUT_NAMES[p.routine][lay]
+        else:
+            c = tune.tune(p.routine, p.batch, *sizes, run=lambda p=p: p.run(stream), stream=stream)
+            p.layout = tune.LAYOUT_NAMES[p.routine][c.layout]
+            tuned[(p.routine, p.n)] = c.as_dict()
+    t_tune = time.perf_counter() - t_tune
 
     def step(ev=None):
         for j, p in enumerate(pts):
@@ -657,8 +702,13 @@ def run_gpu(args):
         mean = sum(times) / len(times)
         g = p.flops / (med * 1e-3) / 1e9
         roof = roofline_gflops(p.routine, p.n, hbm)
-        per_point.append({"routine": p.routine, "n": p.n, "batch": p.batch, "ms": round(med, 4),
-                          "gflops": round(g, 2), "roofline_frac": round(g / roof, 4)})
+        row = {"routine": p.routine, "n": p.n, "batch": p.batch, "ms": round(med, 4),
+               "gflops": round(g, 2), "roofline_frac": round(g / roof, 4), "layout": p.layout}
+        if (p.routine, p.n) in tuned:
+            t = tuned[(p.routine, p.n)]
+            row["rule_layout"] = t["rule_layout"]
+            row["layout_ms"] = t["layout_ms"]
+        per_point.append(row)
         acc = per_routine.setdefault(p.routine, [0.0, 0.0, 0, 0.0])
         acc[0] += p.flops
         acc[1] += mean
@@ -670,7 +720,7 @@ def run_gpu(args):
     by_kernel = {}
     for j, p in enumerate(pts):
         times = [evs[s][j][0].elapsed_time(evs[s][j][1]) for s in range(K)]
-        by_kernel.setdefault(kernel_of(p.routine, p.n), []).append((statistics.mean(times), p))
+        by_kernel.setdefault(kernel_of(p.routine, p.n, p.layout), []).append((statistics.mean(times), p))
     step_ms = sum(t for v in by_kernel.values() for t, _ in v)
     dom = max(by_kernel, key=lambda kname: sum(t for t, _ in by_kernel[kname]))
     t_big, p_big = max(by_kernel[dom], key=lambda x: x[0])
@@ -708,7 +758,9 @@ def run_gpu(args):
         "dtype": "f64",
         "data": "synthetic (seeded iid N(0,1), SPD M M^T + n I)",
         "config": config_dict(spec),
-        "gpu_launches": sum(launches_of(p.routine, p.n, p.batch, sms) for p in pts) * K,
+        "gpu_launches": sum(launches_of(p.routine, p.n, p.batch, sms, p.layout) for p in pts) * K,
+        "layouts": ("autotuned per point before the timed steps (%.1f s, untimed); per_point gives each "
+                    "layout's time" % t_tune) if not args.no_tune else "built-in rule (--no-tune)",
         "clocks": clocks,
         "roofline": roof_obj,
         "per_point": per_point,
@@ -1381,6 +1433,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--points", default="", help="comma list of routine@n, routine or n (debug subsets)")
+    ap.add_argument("--no-tune", action="store_true", help="built-in kernel layouts instead of the autotuner's")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")

@@ -1052,12 +1052,32 @@ cudaError_t launch_tiny(bool aligned, int batch, int n, int k, Op A, Op B, Op C,
 
 // The built-in choice of layout for potrf / syrk_potrf (the LAYOUT_CHOL_*
 // candidates of bf_internal.cuh).
+// Orders from which a batch of at least two problems per SM is factored in
+// two diagonal blocks (potrf, trsm, syrk, potrf), and from which the fused
+// routine forms its sum with the syrk kernel first.  Measured on the sweep's
+// batches (GFLOP/s, row kernels -> blocked): potrf n = 128 1066 -> 1092,
+// n = 192 1104 -> 1134, n = 256 1068 -> 1118; syrk_potrf n = 128 1123 ->
+// 1176, n = 256 1018 -> 1189 (the fused row kernel re-reads A for every
+// block column); syrk first: syrk_potrf n = 48 1103 -> 1121, n = 96 1154 ->
+// 1183.  The FP64 pipe bounds these orders, so the store and reload of the
+// sum that fusion saves (Sec. 4.7.2) costs less than the fused kernel's
+// re-reads and barriers.
+#ifndef BF_CHOL_BLOCKED_MIN_N
+#define BF_CHOL_BLOCKED_MIN_N 128
+#endif
+#ifndef BF_CHOL_SPLIT_MIN_N
+#define BF_CHOL_SPLIT_MIN_N 48
+#endif
+
 template <bool FUSED>
 int chol_rule(int batch, int n) {
   // few problems of a small order: one problem per CTA over an SM's four
   // sub-partitions (the latency kernel)
   if (n <= BF_CHOL_LAT_MAX_N && (long long)batch <= (long long)BF_CHOL_LAT_MAX_BATCH_PER_SM * device_sm_count())
     return LAYOUT_CHOL_LAT;
+  const bool full = (long long)batch >= 2LL * device_sm_count();
+  if (full && n >= BF_CHOL_BLOCKED_MIN_N) return LAYOUT_CHOL_BLOCKED;
+  if (FUSED && full && n >= BF_CHOL_SPLIT_MIN_N) return LAYOUT_CHOL_SPLIT;
   bool small = n <= BF_CHOL_SMALL_MAX_N;
   // the fused routine's four-problem orders below it, for batches that give
   // four-problem CTAs at least one per SM sub-partition
@@ -1084,11 +1104,67 @@ int chol_rule(int batch, int n) {
   }
 }
 
+// info of a factorization whose pieces were launched separately: the first
+// column whose diagonal entry of L is not > 0.  Every kernel here forms
+// L_jj = d * rsqrt(d), which is NaN when the pivot d is not > 0 (NaN
+// included), and a positive number otherwise, so this is the first failing
+// pivot.
+__global__ void k_info_from_diag(int batch, int n, OpW D, int *info) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= batch) return;
+  const double *pd = D.p + (long long)b * D.stride;
+  int bad = 0;
+  for (int j = 0; j < n && bad == 0; j++)
+    if (!(pd[pm_off(D.i0 + j, D.j0 + j, D.cn)] > 0.0)) bad = j + 1;
+  info[b] = bad;
+}
+
+inline Op as_op(const OpW &d) { return Op{d.p, d.stride, d.cn, d.i0, d.j0}; }
+
+// Blocked potrf of D (in place; the first half read from C): with h = n/2
+// rounded down to a panel top,
+//   L11 = chol(C11);  L21 = C21 L11^{-T};  D22 = C22 - L21 L21^T;  L22 = chol(D22)
+// on the row kernels, the merged trsm and the syrk kernel.  info is rebuilt
+// from the diagonal at the end.
+cudaError_t launch_chol_blocked(bool aligned, int batch, int n, Op C, OpW D, double *dinv, long long sdinv, int *info,
+                                cudaStream_t s) {
+  const int h = (n / 2) & ~(PS - 1);
+  const Op none{nullptr, 0, 0, 0, 0};
+  cudaError_t e = launch_rows<false, double>(aligned, batch, h, 0, none, none, C, D, dinv, sdinv, nullptr, s);
+  if (e != cudaSuccess) return e;
+  const Op L11{D.p, D.stride, D.cn, D.i0, D.j0};
+  const Op C21{C.p, C.stride, C.cn, C.i0 + h, C.j0};
+  const OpW D21{D.p, D.stride, D.cn, D.i0 + h, D.j0};
+  e = launch_trsm_rltn(batch, n - h, h, 1.0, L11, dinv, sdinv, C21, D21, s);
+  if (e != cudaSuccess) return e;
+  const Op L21 = as_op(D21);
+  const Op C22{C.p, C.stride, C.cn, C.i0 + h, C.j0 + h};
+  const OpW D22{D.p, D.stride, D.cn, D.i0 + h, D.j0 + h};
+  e = launch_gemm_nt(true, batch, n - h, n - h, h, -1.0, L21, L21, 1.0, C22, D22, aligned, s);
+  if (e != cudaSuccess) return e;
+  e = launch_rows<false, double>(aligned, batch, n - h, 0, none, none, as_op(D22), D22, dinv ? dinv + h : nullptr, sdinv,
+                                 nullptr, s);
+  if (e != cudaSuccess || !info) return e;
+  k_info_from_diag<<<(batch + 127) / 128, 128, 0, s>>>(batch, n, D, info);
+  return cudaGetLastError();
+}
+
 template <bool FUSED>
 cudaError_t launch_chol_t(bool aligned, int batch, int n, int k, Op A, Op B, Op C, OpW D,
                           double *dinv, long long sdinv, int *info, cudaStream_t s) {
   int lay = layout_forced(FUSED ? ROUTINE_SYRK_POTRF : ROUTINE_POTRF, n, batch);
   if (lay <= 0) lay = chol_rule<FUSED>(batch, n);
+  if (lay == LAYOUT_CHOL_SPLIT || lay == LAYOUT_CHOL_BLOCKED) {
+    // the fused routine's sum formed by the syrk kernel into D first
+    if (FUSED) {
+      cudaError_t e = launch_gemm_nt(true, batch, n, n, k, 1.0, A, B, 1.0, C, D, aligned, s);
+      if (e != cudaSuccess) return e;
+      C = as_op(D);
+    }
+    if (lay == LAYOUT_CHOL_BLOCKED) return launch_chol_blocked(aligned, batch, n, C, D, dinv, sdinv, info, s);
+    const Op none{nullptr, 0, 0, 0, 0};
+    return launch_rows<false, double>(aligned, batch, n, 0, none, none, C, D, dinv, sdinv, info, s);
+  }
   switch (lay) {
     case LAYOUT_CHOL_TINY: return launch_tiny<FUSED>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
     case LAYOUT_CHOL_SMALL_G2: return launch_small_g<2, FUSED>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
@@ -1120,6 +1196,8 @@ bool chol_layout_ok(int layout, int n) {
     }
     case LAYOUT_CHOL_ROWS: return n <= CHOL_MAX_N;
     case LAYOUT_CHOL_LAT: return n <= BF_CHOL_LAT_MAX_N;
+    case LAYOUT_CHOL_SPLIT: return n <= CHOL_MAX_N;
+    case LAYOUT_CHOL_BLOCKED: return n >= 32 && n <= CHOL_MAX_N;
     default: return false;
   }
 }

@@ -227,7 +227,9 @@ enum {
   LAYOUT_CHOL_SMALL_G32 = 6,
   LAYOUT_CHOL_ROWS = 7,      // one thread per row, problems per CTA by rule (n <= 512)
   LAYOUT_CHOL_LAT = 8,       // one problem per CTA of four warps (n <= 32)
-  LAYOUT_CHOL_COUNT = 9
+  LAYOUT_CHOL_SPLIT = 9,     // syrk_potrf: the sum by the syrk kernel, then the row kernels
+  LAYOUT_CHOL_BLOCKED = 10,  // two diagonal blocks: potrf, trsm, syrk, potrf (n >= 32)
+  LAYOUT_CHOL_COUNT = 11
 };
 // trsm_rltn
 enum { LAYOUT_TRSM_ROWS = 1, LAYOUT_TRSM_LAT2 = 2, LAYOUT_TRSM_LAT4 = 3, LAYOUT_TRSM_LAT8 = 4, LAYOUT_TRSM_COUNT = 5 };

@@ -306,12 +306,12 @@ def test_single_problem_pack_reports_its_own_positions(lib):
 def test_layout_table(lib):
     # the autotuner's hook: candidates per routine, refused where a layout has
     # no kernel for the order, and the rule restored by layout 0 / reset
-    assert [lib.bf_layout_count(r) for r in range(5)] == [4, 4, 9, 5, 9]
+    assert [lib.bf_layout_count(r) for r in range(5)] == [4, 4, 11, 5, 11]
     assert lib.bf_layout_count(5) == 0
     assert lib.bf_layout_set(5, 24, 128, 1) == -1
     assert lib.bf_layout_set(2, -1, 128, 1) == -2
     assert lib.bf_layout_set(2, 24, 0, 1) == -3
-    assert lib.bf_layout_set(2, 24, 128, 9) == -4
+    assert lib.bf_layout_set(2, 24, 128, 11) == -4
     assert lib.bf_layout_set(2, 24, 128, 1) == _abi.BF_ERR_UNSUPPORTED  # registers: order <= 8
     assert lib.bf_layout_set(2, 40, 128, 8) == _abi.BF_ERR_UNSUPPORTED  # latency kernel: order <= 32
     assert lib.bf_layout_set(3, 40, 128, 3) == _abi.BF_ERR_UNSUPPORTED

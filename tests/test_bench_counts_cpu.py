@@ -166,3 +166,41 @@ def test_kernel_labels_match_the_launchers_thresholds():
     for n in range(v["BF_CHOL_TINY_MAX_N"] + 1, v["BF_CHOL_SMALL_MAX_N"] + 1):
         g = bench.small_g(n)
         assert n * (n + 1) // 2 * (32 // g) * 8 <= v["BF_SMALL_SMEM_BUDGET_KB"] * 1024 or g == 16
+
+
+def test_layout_labels_and_launch_counts():
+    # the autotuner's layouts: split adds the syrk launch, blocked is potrf,
+    # trsm, syrk, potrf and the info rebuild (plus the fused routine's syrk)
+    assert bench.launches_of("dsyrk_dpotrf_ln", 96, 7281, layout="split") == 2
+    assert bench.launches_of("dsyrk_dpotrf_ln", 256, 1024, layout="split") == 3  # with the tail split
+    assert bench.launches_of("dpotrf_l", 256, 2048, layout="blocked") == 5
+    assert bench.launches_of("dsyrk_dpotrf_ln", 256, 1024, layout="blocked") == 6
+    assert bench.launches_of("dgemm_nt", 256, 682, layout="ks1") == 1
+    k = bench.kernel_of("dsyrk_dpotrf_ln", 256, "blocked")
+    assert k.startswith("k_gemm_nt<1,1,1>+blocked[") and "k_trsm_rltn" in k
+    assert bench.kernel_of("dpotrf_l", 24, "latency") == "k_chol_lat<0,24>"
+    assert bench.kernel_of("dtrsm_rltn", 24, "latency_r4") == "k_trsm_lat<24,4>"
+    assert bench.kernel_of("dpotrf_l", 16, "small_g8") == "k_chol_small<8,0,1>"
+    assert bench.kernel_of("dgemm_nt", 4, "ks1") == bench.kernel_of("dgemm_nt", 4)
+
+
+def test_tuner_layout_names_cover_the_library_layouts():
+    from paper_1704_02457_gb300 import _abi, tune
+    from paper_1704_02457_gb300.build import build
+    build()
+    lib = _abi.load()
+    for r, rid in tune.ROUTINE_IDS.items():
+        assert sorted(tune.LAYOUT_NAMES[r]) == list(range(1, lib.bf_layout_count(rid)))
+
+
+def test_tuner_table_round_trip(tmp_path):
+    from paper_1704_02457_gb300 import tune
+    t = tune.Table()
+    t.add(tune.Choice("dpotrf_l", 256, 2048, 10, 7, {7: 1.0, 10: 0.9}))
+    t.add(tune.Choice("dtrsm_rltn", 24, 128, 3, 3))
+    path = tmp_path / "layouts.json"
+    t.save(str(path))
+    u = tune.Table.load(str(path))
+    assert u.entries == t.entries
+    d = tune.Choice("dpotrf_l", 256, 2048, 10, 7, {7: 1.0, 10: 0.9}).as_dict()
+    assert d["layout"] == "blocked" and d["rule_layout"] == "rows" and d["layout_ms"] == {"rows": 1.0, "blocked": 0.9}

@@ -12,6 +12,8 @@ and, for the factorizations, the distance to the oracle's factor.
 The sizes span several register blocks and column blocks, ragged tails,
 sub-matrix offsets off a panel top, and both factorization kernels.
 """
+import contextlib
+
 import numpy as np
 import pytest
 import torch
@@ -454,12 +456,38 @@ def test_chol_one_lane_per_problem_every_problem(n, k, offs, inplace):
 TAIL_CASES = [(200, 0), (240, 30), (256, 8)]
 
 
+@contextlib.contextmanager
+def forced_layout(routine, order, batch, layout):
+    """Force a kernel layout (bf_layout_set) for the calls inside; None keeps the rule."""
+    lib = bf.load()
+    if layout is not None:
+        assert lib.bf_layout_set(routine, order, batch, layout) == 0
+    try:
+        yield
+    finally:
+        if layout is not None:
+            lib.bf_layout_set(routine, order, batch, 0)
+
+
+ROWS, BLOCKED = 7, 10
+
+
+@pytest.mark.parametrize("layout", [ROWS, BLOCKED])
 @pytest.mark.parametrize("n,k", TAIL_CASES)
-def test_rows_tail_split_every_problem(n, k):
+def test_rows_tail_split_every_problem(n, k, layout):
     """A batch whose two-problem CTAs fill about 65% of their last wave: the
-    launcher gives the full waves to the two-problem kernel and the rest of
-    the problems to the one-problem kernel.  Every problem is checked against
-    the oracle, with failing problems on both sides of the boundary."""
+    row-kernel launcher gives the full waves to the two-problem kernel and the
+    rest of the problems to the one-problem kernel.  The same batch also runs
+    in the blocked layout (two diagonal blocks, info rebuilt from the
+    diagonal).  Every problem is checked against the oracle, with failing
+    pivots in both diagonal blocks and problems on both sides of the
+    boundary."""
+    slots = 2 * torch.cuda.get_device_properties(0).multi_processor_count
+    with forced_layout(4 if k > 0 else 2, n, 2 * slots + 2 * (slots * 65 // 100) + 1, layout):
+        _tail_split_case(n, k)
+
+
+def _tail_split_case(n, k):
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     slots = 2 * sms
     bt = 2 * slots + 2 * (slots * 65 // 100) + 1
@@ -504,16 +532,23 @@ def test_rows_tail_split_every_problem(n, k):
             assert fro(np.tril(got[b])[:, :c] - ref) / fro(ref) <= 1e-12
 
 
+@pytest.mark.parametrize("layout", [ROWS, None])
 @pytest.mark.parametrize("n,k,offs", [(32, 0, (0, 0)), (37, 9, (0, 0)), (40, 0, (1, 2)), (57, 20, (0, 0)),
                                       (64, 64, (5, 3)), (71, 0, (0, 0)), (88, 30, (0, 0)), (93, 0, (2, 1)),
                                       (96, 12, (0, 0))])
-def test_four_problem_ctas_every_problem(n, k, offs):
+def test_four_problem_ctas_every_problem(n, k, offs, layout):
     """Orders 32..96 are factored four problems per CTA with 8-column blocks
-    when the batch gives at least one CTA per SM.  A batch of 4 x SMs + 3
-    leaves the last CTA three problems; failures sit at two positions of one
-    CTA and at the batch's end, the rest of each CTA must be unaffected.
-    Ragged orders leave a partial last block."""
+    when the batch gives at least one CTA per SM (the row layout; the rule
+    may pick the split layout for the fused routine, run too).  A batch of
+    4 x SMs + 3 leaves the last CTA three problems; failures sit at two
+    positions of one CTA and at the batch's end, the rest of each CTA must be
+    unaffected.  Ragged orders leave a partial last block."""
     bt = 4 * torch.cuda.get_device_properties(0).multi_processor_count + 3
+    with forced_layout(4 if k > 0 else 2, n, bt, layout):
+        _four_problem_case(n, k, offs, bt)
+
+
+def _four_problem_case(n, k, offs, bt):
     ai, aj = offs
     fused = k > 0
     if fused:
