@@ -253,8 +253,10 @@ cudaError_t launch_trsm_lat(int lanes, int batch, int m, int n, double alpha, Op
 #define BF_CHOL_LAT_MAX_N 32
 #endif
 // the latency kernel serves batches of at most this many problems per SM
+// (measured single launches, potrf / syrk_potrf n = 8..32: the latency
+// kernel is fastest up to 512 problems, ties the others at 1024)
 #ifndef BF_CHOL_LAT_MAX_BATCH_PER_SM
-#define BF_CHOL_LAT_MAX_BATCH_PER_SM 2
+#define BF_CHOL_LAT_MAX_BATCH_PER_SM 4
 #endif
 
 // Largest order the factorization kernels accept.
