@@ -216,7 +216,9 @@ int bf_dsyrk_ln(int m, int k, double alpha, const bf_dmat *sA, int ai, int aj,
  * is not read); B and D are m x n and may coincide.  If dinv is not NULL it
  * holds, for problem b, the n values 1/L[j][j] at dinv + b*strideDinv (as
  * written by bf_dpotrf_l_batched) and the solve uses them instead of
- * dividing (Sec. 4.7.1).  Supports n <= 4096; any m. */
+ * dividing (Sec. 4.7.1); without dinv the library forms the reciprocals
+ * from the hardware approximation, which treats a subnormal L[j][j] as zero:
+ * columns >= j of X are then NaN.  Supports n <= 4096; any m. */
 int bf_dtrsm_rltn_batched(int batch, int m, int n, double alpha,
                           const bf_dmat *sL, int li, int lj, long long strideL,
                           const double *dinv, long long strideDinv,

@@ -781,26 +781,30 @@ k_chol_rows4(int batch, int n, int k, Op A, Op B, Op C, OpWT<T> D, T *dinv, long
 }
 
 // Descriptor-array form: CTA b factors problem b of its own order (rows past
-// it idle), after checking the problem's record.
-template <int BW, bool FUSED>
+// it idle), after checking the problem's record.  AFTER_SYRK: the second
+// launch of syrk_potrf in two launches (the syrk kernel has formed
+// C + A B^T in D): the record is checked with the fused routine's rules, as
+// the syrk launch checked it, and D is factored in place.
+template <int BW, bool FUSED, bool AFTER_SYRK = false>
 __global__ void __launch_bounds__(512)
 k_chol_rows_v(int batch, const bf_dsize *size, const bf_dsub *A, const bf_dsub *B, const bf_dsub *C,
               const bf_dsub *D, int want_dinv, int *info, int max_m, int *status) {
+  constexpr bool REC = FUSED || AFTER_SYRK;  // the record has the fused operands
   const int b = blockIdx.x;
   if (b >= batch) return;
-  const int m = size[b].m, k = FUSED ? size[b].k : 0;
+  const int m = size[b].m, k = REC ? size[b].k : 0;
   int err = 0;
   if (m < 0 || k < 0 || m > max_m)
     err = -1;
   else if (m > 0) {
-    if (FUSED && k > 0 && !dsub_ok(A[b], m, k))
+    if (REC && k > 0 && !dsub_ok(A[b], m, k))
       err = -2;
-    else if (FUSED && k > 0 && !dsub_ok(B[b], m, k))
+    else if (REC && k > 0 && !dsub_ok(B[b], m, k))
       err = -3;
     else if (!dsub_ok(C[b], m, m))
-      err = FUSED ? -4 : -2;
+      err = REC ? -4 : -2;
     else if (!dsub_ok(D[b], m, m))
-      err = FUSED ? -5 : -3;
+      err = REC ? -5 : -3;
   }
   if (threadIdx.x == 0 && status) status[b] = err;
   if (err != 0) return;
@@ -808,7 +812,7 @@ k_chol_rows_v(int batch, const bf_dsize *size, const bf_dsub *A, const bf_dsub *
     if (threadIdx.x == 0 && info) info[b] = 0;
     return;
   }
-  const Op c = dsub_op(C[b]);
+  const Op c = AFTER_SYRK ? dsub_op(D[b]) : dsub_op(C[b]);
   const Op a = (FUSED && k > 0) ? dsub_op(A[b]) : c;  // k == 0: A and B are never read
   const Op bb = (FUSED && k > 0) ? dsub_op(B[b]) : c;
   const OpW d = dsub_opw(D[b]);
@@ -1208,11 +1212,34 @@ cudaError_t launch_chol(bool fused, int batch, int n, int k, Op A, Op B, Op C, O
                : launch_chol_t<false>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
 }
 
+// The descriptor-array syrk_potrf can form the sum with the syrk kernel
+// first (the strided form's split layout) when the layout entry of
+// (syrk_potrf, max_m, batch) asks for it.  By default it stays fused: on
+// 4096 problems of order U{8..128} the two launches measured 588 against
+// 623 GFLOP/s (632 against 724 with the records sorted by decreasing order),
+// the descriptor-array syrk reaching only 646-672 GFLOP/s on those sizes.
+#ifndef BF_CHOL_V_SPLIT_MIN_N
+#define BF_CHOL_V_SPLIT_MIN_N (1 << 30)
+#endif
+
 cudaError_t launch_chol_v(bool fused, int batch, const bf_dsize *size, const bf_dsub *A, const bf_dsub *B,
                           const bf_dsub *C, const bf_dsub *D, bool want_dinv, int *info, int max_m, int *status,
                           cudaStream_t s) {
   const int threads = ((max_m + 31) / 32) * 32;
   if (threads > 512 || threads == 0) return cudaErrorInvalidConfiguration;
+  // the layout entry of (syrk_potrf, max_m, batch) may force either form
+  const int lay = fused ? layout_forced(ROUTINE_SYRK_POTRF, max_m, batch) : 0;
+  const bool two = lay > 0 ? (lay == LAYOUT_CHOL_SPLIT || lay == LAYOUT_CHOL_BLOCKED) : max_m >= BF_CHOL_V_SPLIT_MIN_N;
+  if (fused && two) {
+    // C + A B^T by the syrk kernel into D (its records checked there, no
+    // status written), then D factored in place by a launch that checks the
+    // same records with the same rules and reports status
+    cudaError_t e = launch_gemm_nt_v(true, batch, size, 1.0, A, B, 1.0, C, D, max_m, max_m, nullptr, s);
+    if (e != cudaSuccess) return e;
+    k_chol_rows_v<ROWS_BW, false, true>
+        <<<batch, threads, 0, s>>>(batch, size, A, B, C, D, want_dinv, info, max_m, status);
+    return cudaGetLastError();
+  }
   if (fused)
     k_chol_rows_v<ROWS_BW, true><<<batch, threads, 0, s>>>(batch, size, A, B, C, D, want_dinv, info, max_m, status);
   else

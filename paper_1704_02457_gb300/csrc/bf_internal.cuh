@@ -156,7 +156,8 @@ cudaError_t launch_trsm_rltn_v(int batch, const bf_dsize *size, double alpha, co
 // 1/d by Newton-Raphson iteration r <- r + r (1 - d r) from the hardware's
 // approximate reciprocal (rcp.approx.ftz.f64); two steps take it to full
 // double precision.  Used where one reciprocal is shared by a column of
-// multiplications, instead of an IEEE divide.  Subnormal d flushes to zero.
+// multiplications, instead of an IEEE divide.  The approximation flushes a
+// subnormal d to zero, and the result is then NaN (tested).
 __device__ __forceinline__ double recip_newton(double d) {
   double r;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));

@@ -321,6 +321,27 @@ def test_trsm_integer_exact(m, n):
     assert np.array_equal(get(dD), X.numpy())
 
 
+@pytest.mark.parametrize("layout", [None, 1])
+@pytest.mark.parametrize("n", [8, 24, 40])
+def test_trsm_subnormal_diagonal_without_inverse_gives_nan_from_that_column(n, layout):
+    """The reciprocal of L_jj that the library forms (no dinv) starts from the
+    hardware approximation, which flushes a subnormal L_jj to zero: that
+    column and the later ones become NaN, while the earlier columns are the
+    oracle's.  (The oracle's division gives +-inf or huge values there.)"""
+    bt, m, j = 3, 5, n // 2
+    L = inputs.chol_factor(bt, n, 80 + n).numpy().copy()
+    L[:, j, j] = 1e-310  # subnormal
+    B = inputs.normal((bt, m, n), 81).numpy()
+    want = oracle.dtrsm_rltn(1.0, L, B)
+    with forced_layout(3, n, bt, layout):
+        dD = bf.DMatBatch(bt, m, n)
+        bf.dtrsm_rltn(m, n, 1.0, put(torch.from_numpy(L)), 0, 0, put(torch.from_numpy(B)), 0, 0, dD, 0, 0)
+        X = get(dD)
+    assert np.all(np.isnan(X[:, :, j:]))
+    assert np.allclose(X[:, :, :j], want[:, :, :j], rtol=1e-12, atol=0)
+    assert not np.all(np.isfinite(want[:, :, j]) & (np.abs(want[:, :, j]) < 1e300))
+
+
 @pytest.mark.parametrize("n", [8, 24, 64])
 def test_potrf_then_trsm_with_inverse_diagonal_in_place(n):
     bt, m = 4, n + 5

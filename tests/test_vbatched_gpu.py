@@ -199,3 +199,62 @@ def test_syrk_potrf_uneven_matches_oracle():
         m = sizes[b][0]
         got = np.tril(get(D[b])[:m, b % 3:b % 3 + m])
         assert np.linalg.norm(got - np.tril(want[b])) <= 1e-12 * np.linalg.norm(want[b])
+
+
+@pytest.mark.parametrize("two_launches", [False, True])
+@pytest.mark.parametrize("max_m", [40, 89])
+def test_syrk_potrf_bad_records_failing_pivot_untouched_outputs(max_m, two_launches):
+    # the fused row kernel, or (layout entry "split") the syrk kernel, then the
+    # factorization in place (two launches checking the same records).  Either
+    # way a bad record is reported and its output left untouched, a failing
+    # pivot is reported in info, and the strictly upper part of D is never
+    # written.
+    rng = np.random.default_rng(max_m)
+    nb = 9
+    lib = bf.load()
+    if two_launches:
+        assert lib.bf_layout_set(4, max_m, nb, 9) == 0
+    try:
+        _syrk_potrf_bad_records(rng, nb, max_m)
+    finally:
+        lib.bf_layout_set(4, max_m, nb, 0)
+
+
+def _syrk_potrf_bad_records(rng, nb, max_m):
+    sizes, A, C, D, want = [], [], [], [], []
+    for b in range(nb):
+        m, k = int(rng.integers(4, 40)), int(rng.integers(1, 30))
+        M = rng.standard_normal((m, k))
+        Q = m * np.eye(m)
+        if b == 5:
+            Q[m // 2, m // 2] = -1e6  # failing pivot
+        sizes.append((m, 0, k))
+        A.append(put(M, 0, 0))
+        C.append(put(Q, 0, 0))
+        D.append(blank(m, m, 0, 0, fill=np.nan))
+        want.append(oracle.dsyrk_dpotrf_ln(M, M, Q))
+    sizes[3] = (max_m + 1, 0, 2)  # above max_m: status -1
+    a_rec = [(X, 0, 0, 0) for X in A]
+    a_rec[4] = (A[4], 0, 3, 0)  # A's rows run past the matrix: status -2
+    d_rec = [(X, 0, 0, 0) for X in D]
+    d_rec[7] = (D[7], 0, 0, 3)  # D's columns run past the matrix: status -5
+    Ar = bf.dsub_records(a_rec)
+    info = torch.full((nb,), -7, dtype=torch.int32, device="cuda")
+    status = torch.full((nb,), 99, dtype=torch.int32, device="cuda")
+    bf.dsyrk_dpotrf_ln_vbatched(nb, bf.dsize_records(sizes), Ar, Ar, bf.dsub_records([(X, 0, 0, 0) for X in C]),
+                                bf.dsub_records(d_rec), max_m, info=info, status=status)
+    st, inf = status.cpu().numpy(), info.cpu().numpy()
+    assert st[3] == -1 and st[4] == -2 and st[7] == -5
+    assert all(st[b] == 0 for b in range(nb) if b not in (3, 4, 7))
+    assert inf[5] == want[5][2] and inf[5] > 0
+    for b in range(nb):
+        got = get(D[b])
+        if b in (3, 4, 7):
+            assert np.all(np.isnan(got))  # skipped: untouched
+            continue
+        m = sizes[b][0]
+        got = got[:m, :m]
+        assert np.all(np.isnan(got[np.triu(np.ones((m, m), dtype=bool), 1)]))
+        if b != 5:
+            assert inf[b] == 0
+            assert np.linalg.norm(np.tril(got) - np.tril(want[b][0])) <= 1e-12 * np.linalg.norm(want[b][0])
