@@ -1030,14 +1030,18 @@ def run_e2e(pts, args, dev, world):
     del pipe
     torch.cuda.empty_cache()
     link = link_probe(dev)
-    # the time the host link alone needs for the step's transfers, at the
-    # library's measured rate with both directions at once (they overlap)
+    # the time the host link alone needs for the step's transfers: a lower
+    # bound with each direction at the library's one-way rate (full duplex),
+    # and the time at its measured rate with both directions at once
+    r_in, r_out = link["bf_pack_from_host_gbs"] * 1e9, link["bf_unpack_to_host_gbs"] * 1e9
     each = link["bf_both_gbs_each"] * 1e9
-    bound_ms = max(h2d, d2h) / each * 1e3 if each > 0 else None
+    bound_ms = max(h2d / r_in, d2h / r_out) * 1e3 if r_in > 0 and r_out > 0 else None
+    shared_ms = max(h2d, d2h) / each * 1e3 if each > 0 else None
     return {"value": round(job_rate(step_flops, dt, world), 2), "unit": "GFLOP/s",
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
             "steps": steps, "ms_per_step": round(dt * 1e3, 2), "link": link,
             "link_bound_ms": round(bound_ms, 2) if bound_ms else None,
+            "link_both_directions_ms": round(shared_ms, 2) if shared_ms else None,
             "path": "pinned host column-major -> bf_pack_dmat_batched (reads the host directly) -> routine "
                     "-> bf_unpack_dmat_batched (writes the host directly), points issued small-n/large-n "
                     "alternately on three streams (pack, compute, unpack)"}
