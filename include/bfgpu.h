@@ -256,8 +256,14 @@ int bf_dpotrf_l(int m, const bf_dmat *sC, int ci, int cj, const bf_dmat *sD, int
  * the largest |a(i, j)|; ipiv[b*strideIpiv + j] (device, 0-based) receives
  * it, and row j was swapped with it over the whole matrix.  info (device, may
  * be NULL): 0, or j+1 for the first exactly zero pivot (that column is then
- * neither scaled nor used to update).  C and D may coincide.  Supports
- * n <= 128. */
+ * neither scaled nor used to update).  C and D coincide or do not overlap.
+ * Supports n <= 512.  Above n = 128 the factorization is blocked by columns
+ * of 32 (the right-looking blocked form of the same algorithm: each panel
+ * factorized column by column with the same pivot rule, its row swaps then
+ * applied to the other columns, U12 = L11^{-1} A12, A22 -= L21 U12), so the
+ * results agree with the unblocked order up to rounding; where a zero pivot
+ * column meets non-finite entries the blocked update can turn 0 * inf into
+ * NaN where the unblocked form skips the update. */
 int bf_dgetrf_batched(int batch, int n, const bf_dmat *sC, int ci, int cj, long long strideC,
                       const bf_dmat *sD, int di, int dj, long long strideD, int *ipiv,
                       long long strideIpiv, int *info, void *stream);
@@ -482,9 +488,11 @@ int bf_dposv_mixed_batched_noalloc(int batch, int n, int nrhs, const bf_dmat *sA
  * rounding (summation order), except where a layout has no kernel for the
  * order, which bf_layout_set refuses.
  *
- * routine:  0 gemm_nt, 1 syrk_ln, 2 potrf_l, 3 trsm_rltn, 4 syrk_potrf_ln.
+ * routine:  0 gemm_nt, 1 syrk_ln, 2 potrf_l, 3 trsm_rltn, 4 syrk_potrf_ln,
+ *           5 getrf.
  * order:    m for gemm_nt, syrk_ln, potrf_l and syrk_potrf_ln; n (the order
- *           of L) for trsm_rltn.  Orders above 511 share one entry.
+ *           of L) for trsm_rltn; n for getrf.  Orders above 511 share one
+ *           entry.
  * batch:    the entry covers the batch sizes with the same floor(log2(batch)).
  * layout:   0 = the built-in rule; 1 .. bf_layout_count(routine) - 1:
  *   gemm_nt, syrk_ln:   1, 2, 3 = the k-loop of a 4x4 block on 1, 2, 4 lanes
@@ -494,8 +502,17 @@ int bf_dposv_mixed_batched_noalloc(int batch, int n, int nrhs, const bf_dmat *sA
  *                         triangles in shared memory (order <= 31)
  *                       7 one thread per row, 1, 2 or 4 problems per CTA
  *                       8 one problem per CTA of four warps (order <= 32)
+ *                       9 syrk_potrf_ln only: the sum by the syrk kernel
+ *                         into D, then layout 7 on D (order >= 48)
+ *                       10 blocked: two diagonal blocks, potrf, trsm,
+ *                         syrk, potrf (order >= 32)
  *   trsm_rltn:          1 one thread per row of X
  *                       2, 3, 4 = 2, 4, 8 lanes per row (order <= 32)
+ *   getrf:              1 a warp shared by 32 / G problems (order <= 128)
+ *                       2 one CTA per problem, the matrix in shared
+ *                         memory (order <= 128)
+ *                       3 blocked by columns of 32: panel, swaps and
+ *                         triangular solve, gemm_nn update (order <= 512)
  * The table is process-wide (all devices) and not synchronized with calls in
  * flight: set it before the calls it should affect.
  * ------------------------------------------------------------------------ */
@@ -511,7 +528,8 @@ int bf_layout_set(int routine, int order, int batch, int layout);
 
 /* The layout a call of `routine` with these sizes would use now (the forced
  * one, else the rule's): gemm_nt (m, n, k), syrk_ln (m, -, k), potrf_l (m),
- * trsm_rltn (m, n), syrk_potrf_ln (m, -, k); unused sizes are ignored.
+ * trsm_rltn (m, n), syrk_potrf_ln (m, -, k), getrf (n); unused sizes are
+ * ignored.
  * Returns the layout (>= 1) or -1..-5 for a bad argument. */
 int bf_layout_get(int routine, int batch, int m, int n, int k);
 

@@ -29,6 +29,7 @@ int layout_count(int routine) {
     case ROUTINE_GEMM_NT: case ROUTINE_SYRK_LN: return LAYOUT_GEMM_COUNT;
     case ROUTINE_POTRF: case ROUTINE_SYRK_POTRF: return LAYOUT_CHOL_COUNT;
     case ROUTINE_TRSM_RLTN: return LAYOUT_TRSM_COUNT;
+    case ROUTINE_GETRF: return LAYOUT_LU_COUNT;
     default: return 0;
   }
 }
@@ -38,6 +39,7 @@ bool layout_ok(int routine, int layout, int n) {
     case ROUTINE_GEMM_NT: case ROUTINE_SYRK_LN: return layout >= 1 && layout < LAYOUT_GEMM_COUNT;
     case ROUTINE_POTRF: case ROUTINE_SYRK_POTRF: return chol_layout_ok(layout, n);
     case ROUTINE_TRSM_RLTN: return trsm_layout_ok(layout, n);
+    case ROUTINE_GETRF: return getrf_layout_ok(layout, n);
     default: return false;
   }
 }
@@ -81,6 +83,7 @@ int bf_layout_get(int routine, int batch, int m, int n, int k) {
     case ROUTINE_SYRK_LN: return gemm_layout_rule(true, batch, m, m, k);
     case ROUTINE_POTRF: return chol_layout_rule(false, batch, m);
     case ROUTINE_SYRK_POTRF: return chol_layout_rule(true, batch, m);
+    case ROUTINE_GETRF: return getrf_layout_rule(batch, m);
     default: return trsm_layout_rule(batch, m, n);
   }
 }

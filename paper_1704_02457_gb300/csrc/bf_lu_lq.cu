@@ -302,6 +302,155 @@ k_getrf_rows(int n, int ld, Op C, OpW D, int *ipiv, long long sipiv, int *info) 
   if (info && t == 0) info[b] = first_zero;
 }
 
+// ---------------------------------------------------------------------------
+// Blocked getrf for orders above the one-CTA kernels' shared memory: per
+// block column of width w (32), a tall panel factorization, the panel's row
+// swaps applied to the other columns, U12 = L11^{-1} A12 and the trailing
+// update A22 -= L21 U12 by the gemm_nn kernel (the blocked right-looking
+// form of the same algorithm: the same pivot rule, applied column by column
+// inside the panel).
+// ---------------------------------------------------------------------------
+
+// The m x w panel at (j0, j0) of D (rows j0.., columns j0..j0+w-1), one CTA
+// per problem, T >= m threads: the steps of k_getrf_rows on a tall panel.
+// Pivot rows go to ipiv as global rows (j0 + local row).  A zero pivot is
+// left in place (no swap, no update); info is rebuilt from U's diagonal.
+__global__ void __launch_bounds__(512)
+k_getrf_panel(int m, int w, int ld, int j0, OpW D, int *ipiv, long long sipiv) {
+  extern __shared__ double sm[];
+  __shared__ long long red_k[16];
+  __shared__ double red_s[16];
+  __shared__ int red_i[16];
+  const int b = blockIdx.x, t = threadIdx.x, T_ = blockDim.x;
+  const Op P{D.p, D.stride, D.cn, D.i0 + j0, D.j0 + j0};
+  rows_load(sm, ld, m, w, P.p + b * P.stride, P);
+  for (int j = 0; j < w; j++) {
+    const double x = (t >= j && t < m) ? sm[j * ld + t] : CUDART_NAN;
+    const double djj = sm[j * ld + j];
+    const long long key = pivot_key(x);
+    double pv;
+    const int p = cta_argmax_v(key, key >= 0 ? t : m, x, &pv, red_k, red_i, red_s);
+    const bool keep = (p >= m) || pivot_key(djj) < 0;
+    const int pr = keep ? j : p;
+    const double piv = keep ? djj : pv;
+    if (t == 0) ipiv[b * sipiv + j0 + j] = j0 + pr;
+    if (piv == 0.0) {
+      __syncthreads();
+      continue;
+    }
+    if (pr != j && t < w && t != j) {
+      const double y = sm[t * ld + j];
+      sm[t * ld + j] = sm[t * ld + pr];
+      sm[t * ld + pr] = y;
+    }
+    if (t < 32) {
+      const double r = recip_newton(piv);
+      for (int i = j + 1 + t; i < m; i += 32) sm[j * ld + i] = ((i == pr) ? djj : sm[j * ld + i]) * r;
+      if (t == 0) sm[j * ld + j] = piv;
+    }
+    __syncthreads();
+    const int R = m - j - 1;
+    if (R > 0 && j + 1 < w) {
+      int c = j + 1 + t / R, i = j + 1 + t % R;
+      const int dc = T_ / R, di = T_ % R;
+      while (c < w) {
+        sm[c * ld + i] = fma(-sm[j * ld + i], sm[c * ld + j], sm[c * ld + i]);
+        c += dc;
+        i += di;
+        if (i >= m) {
+          i -= R;
+          c++;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  rows_store(sm, ld, m, w, D.p + b * D.stride, OpW{D.p, D.stride, D.cn, D.i0 + j0, D.j0 + j0});
+}
+
+// The panel's swaps (rows j0+s and ipiv[j0+s], s < w, in order) applied to
+// the n - w columns outside the panel, thread per column; then, right of the
+// panel, U12 = L11^{-1} A12 (L11 unit lower, w x w) by forward substitution,
+// the column in registers.  A column of L11 whose pivot was exactly zero is
+// skipped, as the unblocked factorization skips its update.
+__global__ void __launch_bounds__(256)
+k_getrf_swap_solve(int n, int w, int j0, OpW D, const int *ipiv, long long sipiv) {
+  __shared__ double L11[32 * 33];
+  __shared__ int pv[32];
+  __shared__ int nz[32];
+  const int b = blockIdx.x, t = threadIdx.x;
+  double *pd = D.p + (long long)b * D.stride;
+  auto at = [&](int r, int c) -> double & { return pd[pm_off(D.i0 + r, D.j0 + c, D.cn)]; };
+  if (t < w) {
+    pv[t] = ipiv[b * sipiv + j0 + t];
+    nz[t] = at(j0 + t, j0 + t) != 0.0;
+  }
+  for (int e = t; e < w * w; e += blockDim.x) {
+    const int r = e / w, c = e % w;
+    L11[r * 33 + c] = r > c ? at(j0 + r, j0 + c) : 0.0;
+  }
+  __syncthreads();
+  for (int u = t; u < n - w; u += blockDim.x) {
+    const int c = u < j0 ? u : u + w;
+    for (int s2 = 0; s2 < w; s2++) {
+      const int r1 = j0 + s2, r2 = pv[s2];
+      if (r2 != r1) {
+        const double y = at(r1, c);
+        at(r1, c) = at(r2, c);
+        at(r2, c) = y;
+      }
+    }
+    if (c >= j0 + w) {
+      double x[32];
+#pragma unroll
+      for (int r = 0; r < 32; r++)
+        if (r < w) x[r] = at(j0 + r, c);
+#pragma unroll
+      for (int r = 1; r < 32; r++) {
+        if (r < w) {
+          double acc = x[r];
+#pragma unroll
+          for (int l = 0; l < r; l++)
+            if (nz[l]) acc = fma(-L11[r * 33 + l], x[l], acc);
+          x[r] = acc;
+        }
+      }
+#pragma unroll
+      for (int r = 1; r < 32; r++)
+        if (r < w) at(j0 + r, c) = x[r];
+    }
+  }
+}
+
+// info: the first exactly zero pivot of U's diagonal (a zero pivot is left
+// in place and the column neither scaled nor used, so U_jj = 0 there and
+// nowhere before).
+__global__ void k_getrf_info(int batch, int n, OpW D, int *info) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= batch) return;
+  const double *pd = D.p + (long long)b * D.stride;
+  int z = 0;
+  for (int j = 0; j < n && z == 0; j++)
+    if (pd[pm_off(D.i0 + j, D.j0 + j, D.cn)] == 0.0) z = j + 1;
+  info[b] = z;
+}
+
+// copy of the n x n sub-matrices C into D (the blocked getrf works in
+// place), in panel-major order so that consecutive threads touch
+// consecutive doubles
+__global__ void k_copy_sub(int batch, int n, Op C, OpW D) {
+  const long long per = (long long)((n + PS - 1) / PS) * PS * n, total = per * batch;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(e / per);
+    const long long x = e - (long long)b * per;
+    const int r4 = (int)(x % PS), c = (int)((x / PS) % n), r = (int)(x / ((long long)PS * n)) * PS + r4;
+    if (r < n)
+      D.p[(long long)b * D.stride + pm_off(D.i0 + r, D.j0 + c, D.cn)] =
+          C.p[(long long)b * C.stride + pm_off(C.i0 + r, C.j0 + c, C.cn)];
+  }
+}
+
 // gelqf, one CTA per problem.  Per row i, two barriers:
 //  (1) warp 0 forms beta, tau and 1/(alpha - beta) from alpha and the norm
 //      of a(i, i+1:n) (computed ahead, see (2)), scales the row into the
@@ -416,6 +565,11 @@ int pick_g(size_t bytes_per_problem) {
 #define BF_LU_BIG_THREADS 256
 #endif
 constexpr int LU_BIG_THREADS = BF_LU_BIG_THREADS;
+// Order from which the rule takes the blocked getrf; block column width.
+#ifndef BF_LU_BLOCKED_MIN_N
+#define BF_LU_BLOCKED_MIN_N 129
+#endif
+constexpr int LU_NB = 32;
 
 cudaError_t set_smem(const void *fn, size_t smem) {
   if (smem <= 48 * 1024) return cudaSuccess;
@@ -444,13 +598,69 @@ cudaError_t run_gelqf(int batch, int m, int n, Op C, OpW D, double *tau, long lo
 
 }  // namespace
 
+int getrf_layout_rule(int batch, int n) {
+  (void)batch;
+  if (n < BF_LU_ROWS_MIN) return LAYOUT_LU_WARP;
+  return n < BF_LU_BLOCKED_MIN_N ? LAYOUT_LU_ROWS : LAYOUT_LU_BLOCKED;
+}
+
+bool getrf_layout_ok(int layout, int n) {
+  switch (layout) {
+    case LAYOUT_LU_WARP: case LAYOUT_LU_ROWS: return n <= LU_ONE_CTA_MAX_N;
+    case LAYOUT_LU_BLOCKED: return n <= GETRF_MAX_N;
+    default: return false;
+  }
+}
+
+namespace {
+
+// Blocked getrf: for each block column j0 (width w = LU_NB, the last one
+// narrower) the panel factorization, the panel's swaps on the other columns
+// with U12 = L11^{-1} A12, and the trailing update A22 <- A22 - L21 U12 by
+// the gemm_nn kernel; in place in D (C copied there first unless the two
+// coincide).  Each launch covers the whole batch.
+cudaError_t launch_getrf_blocked(int batch, int n, Op C, OpW D, int *ipiv, long long sipiv, int *info,
+                                 cudaStream_t s) {
+  const bool same = C.p == D.p && C.stride == D.stride && C.cn == D.cn && C.i0 == D.i0 && C.j0 == D.j0;
+  if (!same) {
+    const long long total = (long long)((n + PS - 1) / PS) * PS * n * batch;
+    k_copy_sub<<<(unsigned)std::min<long long>((total + 255) / 256, 4096), 256, 0, s>>>(batch, n, C, D);
+  }
+  const bool aligned = (D.i0 % PS) == 0 && (D.stride % 2) == 0 && ((uintptr_t)D.p % 16) == 0;
+  for (int j0 = 0; j0 < n; j0 += LU_NB) {
+    const int w = std::min(LU_NB, n - j0), m = n - j0, ld = m | 1;
+    const size_t smem = (size_t)ld * w * sizeof(double);
+    cudaError_t e = set_smem((const void *)k_getrf_panel, smem);
+    if (e != cudaSuccess) return e;
+    k_getrf_panel<<<batch, std::max(64, (m + 31) / 32 * 32), smem, s>>>(m, w, ld, j0, D, ipiv, sipiv);
+    if (n > w)
+      k_getrf_swap_solve<<<batch, std::min(256, (n - w + 31) / 32 * 32), 0, s>>>(n, w, j0, D, ipiv, sipiv);
+    const int r = m - w;
+    if (r > 0) {
+      e = launch_gemm_nn(false, batch, r, r, w, -1.0, Op{D.p, D.stride, D.cn, D.i0 + j0 + w, D.j0 + j0},
+                         Op{D.p, D.stride, D.cn, D.i0 + j0, D.j0 + j0 + w}, 1.0,
+                         Op{D.p, D.stride, D.cn, D.i0 + j0 + w, D.j0 + j0 + w},
+                         OpW{D.p, D.stride, D.cn, D.i0 + j0 + w, D.j0 + j0 + w}, aligned, s);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  if (info) k_getrf_info<<<(batch + 127) / 128, 128, 0, s>>>(batch, n, D, info);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
 cudaError_t launch_getrf(int batch, int n, Op C, OpW D, int *ipiv, long long sipiv, int *info, cudaStream_t s) {
-  if (n >= BF_LU_ROWS_MIN) {
+  const int forced = layout_forced(ROUTINE_GETRF, n, batch);
+  const int lay = (forced > 0 && getrf_layout_ok(forced, n)) ? forced : getrf_layout_rule(batch, n);
+  if (lay == LAYOUT_LU_BLOCKED) return launch_getrf_blocked(batch, n, C, D, ipiv, sipiv, info, s);
+  if (lay == LAYOUT_LU_ROWS) {
     const int ld = n | 1;
     const size_t smem = (size_t)ld * n * sizeof(double);
     cudaError_t e = set_smem((const void *)k_getrf_rows, smem);
     if (e != cudaSuccess) return e;
-    k_getrf_rows<<<batch, n > 96 ? LU_BIG_THREADS : (n > 64 ? 256 : 128), smem, s>>>(n, ld, C, D, ipiv, sipiv, info);
+    const int T = std::max(n > 96 ? LU_BIG_THREADS : (n > 64 ? 256 : 128), (n + 31) / 32 * 32);
+    k_getrf_rows<<<batch, T, smem, s>>>(n, ld, C, D, ipiv, sipiv, info);
     return cudaGetLastError();
   }
   switch (pick_g((size_t)n * n * 8)) {

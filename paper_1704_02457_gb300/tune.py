@@ -20,7 +20,7 @@ from dataclasses import dataclass, field
 
 from ._abi import load
 
-ROUTINE_IDS = {"dgemm_nt": 0, "dsyrk_ln": 1, "dpotrf_l": 2, "dtrsm_rltn": 3, "dsyrk_dpotrf_ln": 4}
+ROUTINE_IDS = {"dgemm_nt": 0, "dsyrk_ln": 1, "dpotrf_l": 2, "dtrsm_rltn": 3, "dsyrk_dpotrf_ln": 4, "dgetrf": 5}
 
 LAYOUT_NAMES = {
     "dgemm_nt": {1: "ks1", 2: "ks2", 3: "ks4"},
@@ -28,6 +28,7 @@ LAYOUT_NAMES = {
     "dpotrf_l": {1: "tiny", 2: "small_g2", 3: "small_g4", 4: "small_g8", 5: "small_g16", 6: "small_g32", 7: "rows",
                  8: "latency", 9: "split", 10: "blocked"},
     "dtrsm_rltn": {1: "rows", 2: "latency_r2", 3: "latency_r4", 4: "latency_r8"},
+    "dgetrf": {1: "warp", 2: "rows", 3: "blocked"},
 }
 LAYOUT_NAMES["dsyrk_dpotrf_ln"] = LAYOUT_NAMES["dpotrf_l"]
 

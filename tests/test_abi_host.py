@@ -128,7 +128,7 @@ def test_argument_errors_are_reported_before_launch(lib):
     assert lib.bf_dgelqf(8, 8, r(C), 1, 0, r(D), 0, 0, ip, None) == -4
     # sizes beyond what the factorization kernels implement
     big = _desc(600, 600)
-    assert lib.bf_dgetrf_batched(1, 129, r(big), 0, 0, 0, r(big), 0, 0, 0, ip, 0, None, None) == _abi.BF_ERR_UNSUPPORTED
+    assert lib.bf_dgetrf_batched(1, 513, r(big), 0, 0, 0, r(big), 0, 0, 0, ip, 0, None, None) == _abi.BF_ERR_UNSUPPORTED
     assert lib.bf_dgelqf_batched(1, 129, 128, r(big), 0, 0, 0, r(big), 0, 0, 0, ip, 0, None) == _abi.BF_ERR_UNSUPPORTED
     assert lib.bf_dpotrf_l_batched(1, 600, r(big), 0, 0, 0, r(big), 0, 0, 0, None, 0, None, None) == _abi.BF_ERR_UNSUPPORTED
 
@@ -306,9 +306,11 @@ def test_single_problem_pack_reports_its_own_positions(lib):
 def test_layout_table(lib):
     # the autotuner's hook: candidates per routine, refused where a layout has
     # no kernel for the order, and the rule restored by layout 0 / reset
-    assert [lib.bf_layout_count(r) for r in range(5)] == [4, 4, 11, 5, 11]
-    assert lib.bf_layout_count(5) == 0
-    assert lib.bf_layout_set(5, 24, 128, 1) == -1
+    assert [lib.bf_layout_count(r) for r in range(6)] == [4, 4, 11, 5, 11, 4]
+    assert lib.bf_layout_count(6) == 0
+    assert lib.bf_layout_set(6, 24, 128, 1) == -1
+    assert lib.bf_layout_set(5, 129, 128, 2) == _abi.BF_ERR_UNSUPPORTED  # getrf in shared memory: n <= 128
+    assert lib.bf_layout_set(5, 513, 128, 3) == _abi.BF_ERR_UNSUPPORTED  # blocked getrf: n <= 512
     assert lib.bf_layout_set(2, -1, 128, 1) == -2
     assert lib.bf_layout_set(2, 24, 0, 1) == -3
     assert lib.bf_layout_set(2, 24, 128, 11) == -4
@@ -329,6 +331,11 @@ def test_layout_table(lib):
         assert lib.bf_layout_get(3, 128, 24, 24, 0) == 2
         assert lib.bf_layout_set(0, 1000, 7, 3) == 0      # orders above 511 share an entry
         assert lib.bf_layout_get(0, 7, 700, 700, 700) == 3
+        assert lib.bf_layout_get(5, 64, 16, 0, 0) == 1      # getrf rule: warp, rows, blocked
+        assert lib.bf_layout_get(5, 64, 64, 0, 0) == 2
+        assert lib.bf_layout_get(5, 64, 200, 0, 0) == 3
+        assert lib.bf_layout_set(5, 100, 64, 3) == 0
+        assert lib.bf_layout_get(5, 64, 100, 0, 0) == 3
     finally:
         lib.bf_layout_reset()
     assert lib.bf_layout_get(3, 128, 24, 24, 0) == lib.bf_layout_get(3, 129, 24, 24, 0)

@@ -117,7 +117,7 @@ def test_kkt_normal_equations_composition(nx, nc):
 
 # -------------------------------------------------------------------- getrf
 
-@pytest.mark.parametrize("n", [1, 3, 8, 17, 31, 32, 33, 64, 100, 128])
+@pytest.mark.parametrize("n", [1, 3, 8, 17, 31, 32, 33, 64, 100, 128, 129, 192, 256])
 def test_getrf_matches_oracle(n):
     bt = 33 if n <= 32 else 3
     A = inputs.normal((bt, n, n), 1500 + n)
@@ -155,7 +155,7 @@ def test_getrf_integer_exact_offsets_and_zero_pivot():
     assert int(info[3]) == 1 and list(info.cpu().numpy()[:3]) == [0, 0, 0]
 
 
-@pytest.mark.parametrize("n", [5, 40])
+@pytest.mark.parametrize("n", [5, 40, 150])
 def test_getrf_nan_entries_follow_the_oracles_pivot_rule(n):
     """NaN entries never become the pivot; a NaN diagonal keeps its row."""
     bt = 3
@@ -174,6 +174,133 @@ def test_getrf_nan_entries_follow_the_oracles_pivot_rule(n):
         fin = ~np.isnan(LUo)
         assert np.allclose(LU[b][fin], LUo[fin], rtol=1e-12, atol=1e-12)
     assert piv[0, 0] == 0 and piv[1, 0] == 2
+
+
+# ------------------------------------------------------------ blocked getrf
+#
+# Above order 128 the factorization is blocked by columns of 32 (panel,
+# swaps and U12 = L11^{-1} A12, gemm_nn update of A22).  The layout table can
+# force the blocked form at any order, and the one-CTA forms at order <= 128,
+# so every layout is checked against the oracle on the same inputs.
+
+GETRF = 5
+LU_WARP, LU_ROWS, LU_BLOCKED = 1, 2, 3
+
+
+def _getrf_forced(lay, n, bt, *args, **kw):
+    lib = bf.load()
+    assert lib.bf_layout_set(GETRF, n, bt, lay) == 0
+    try:
+        bf.dgetrf(n, *args, **kw)
+        torch.cuda.synchronize()
+    finally:
+        lib.bf_layout_set(GETRF, n, bt, 0)
+
+
+@pytest.mark.parametrize("n", [2, 31, 32, 33, 63, 64, 65, 100, 128])
+@pytest.mark.parametrize("lay", [LU_WARP, LU_ROWS, LU_BLOCKED])
+def test_getrf_every_layout_matches_oracle(lay, n):
+    bt = 5
+    A = inputs.normal((bt, n, n), 1900 + n)
+    dD = bf.DMatBatch(bt, n, n, fill=np.nan)
+    ipiv = torch.full((bt, n), -1, dtype=torch.int32, device="cuda")
+    info = torch.full((bt,), -7, dtype=torch.int32, device="cuda")
+    _getrf_forced(lay, n, bt, put(A), 0, 0, dD, 0, 0, ipiv, info=info)
+    LU, piv = get(dD), ipiv.cpu().numpy()
+    assert np.all(info.cpu().numpy() == 0)
+    for b in range(bt):
+        LUo, pivo, _ = oracle.dgetrf(A[b].numpy())
+        assert np.array_equal(piv[b], pivo), (lay, b)
+        assert np.linalg.norm(LU[b] - LUo) <= 1e-12 * np.linalg.norm(LUo), lay
+
+
+def _int_lu(n, rng, zero_at=None):
+    """L U with L unit lower in {-1, 0, 1} and U integer with power-of-two
+    diagonal: every column's largest entry is its first (ties go to the
+    first row), so partial pivoting swaps nothing and every step is exact.
+    U[zero_at, zero_at] = 0 makes the first zero pivot that column."""
+    L = np.tril(rng.integers(-1, 2, size=(n, n)), -1) + np.eye(n, dtype=np.int64)
+    U = np.triu(rng.integers(-4, 5, size=(n, n)), 1)
+    U[np.arange(n), np.arange(n)] = 2 ** rng.integers(3, 6, size=n)
+    if zero_at is not None:
+        U[zero_at, zero_at] = 0
+    return (L @ U).astype(float), L, U
+
+
+@pytest.mark.parametrize("n,forced", [(40, True), (136, False), (200, False)])
+def test_blocked_getrf_integer_exact_and_zero_pivot(n, forced):
+    rng = np.random.default_rng(7 + n)
+    As, Ls, Us = zip(*[_int_lu(n, rng) for _ in range(3)])
+    Az, _, _ = _int_lu(n, rng, zero_at=n - 1)
+    A = torch.from_numpy(np.stack(list(As) + [Az, np.zeros((n, n))]))
+    bt = A.shape[0]
+    dD = bf.DMatBatch(bt, n + 3, n + 2, fill=5.0)
+    ipiv = torch.full((bt, n), -1, dtype=torch.int32, device="cuda")
+    info = torch.full((bt,), -7, dtype=torch.int32, device="cuda")
+    args = (put(A, 3, 2), 3, 2, dD, 3, 1, ipiv)
+    if forced:
+        _getrf_forced(LU_BLOCKED, n, bt, *args, info=info)
+    else:
+        bf.dgetrf(n, *args, info=info)
+    whole = get(dD)
+    LU = whole[:, 3:3 + n, 1:1 + n]
+    piv = ipiv.cpu().numpy()
+    for b in range(3):
+        want = np.tril(Ls[b], -1) + np.triu(Us[b])
+        assert np.array_equal(LU[b], want), b
+        assert np.array_equal(piv[b], np.arange(n))
+    assert list(info.cpu().numpy()) == [0, 0, 0, n, 1]
+    assert np.array_equal(piv[3], np.arange(n)) and np.array_equal(piv[4], np.arange(n))
+    outside = np.ones(whole.shape[1:], dtype=bool)
+    outside[3:3 + n, 1:1 + n] = False
+    assert np.all(whole[:, outside] == 5.0)
+
+
+@pytest.mark.parametrize("n", [150, 256])
+def test_blocked_getrf_in_place_with_offsets(n):
+    """In place at a sub-matrix offset off a panel top (the trailing update
+    then takes the unaligned loads); the rest of the matrix untouched."""
+    bt = 3
+    A = inputs.normal((bt, n, n), 1950 + n)
+    dA = put(A, 2, 1, fill=3.0)
+    ipiv = torch.zeros((bt, n), dtype=torch.int32, device="cuda")
+    info = torch.full((bt,), -7, dtype=torch.int32, device="cuda")
+    bf.dgetrf(n, dA, 2, 1, dA, 2, 1, ipiv, info=info)
+    whole = get(dA)
+    assert np.all(info.cpu().numpy() == 0)
+    for b in range(bt):
+        LUo, pivo, _ = oracle.dgetrf(A[b].numpy())
+        assert np.linalg.norm(whole[b, 2:, 1:] - LUo) <= 1e-12 * np.linalg.norm(LUo)
+        assert np.array_equal(ipiv[b].cpu().numpy(), pivo)
+    assert np.all(whole[:, :2, :] == 3.0) and np.all(whole[:, :, :1] == 3.0)
+
+
+def test_blocked_getrf_full_size_sampled():
+    """The bench's largest getrf workload (512 problems of order 256, one
+    call), sampled problems against the oracle; all of them reconstruct."""
+    bt, n = 512, 256
+    A = inputs.normal((bt, n, n), 1990)
+    dD = bf.DMatBatch(bt, n, n)
+    ipiv = torch.full((bt, n), -1, dtype=torch.int32, device="cuda")
+    info = torch.full((bt,), -7, dtype=torch.int32, device="cuda")
+    bf.dgetrf(n, put(A), 0, 0, dD, 0, 0, ipiv, info=info)
+    LU, piv = get(dD), ipiv.cpu().numpy()
+    assert np.all(info.cpu().numpy() == 0)
+    for b in (0, 1, 255, 511):
+        LUo, pivo, _ = oracle.dgetrf(A[b].numpy())
+        assert np.array_equal(piv[b], pivo)
+        assert np.linalg.norm(LU[b] - LUo) <= 1e-12 * np.linalg.norm(LUo)
+    # P A = L U for every problem (L, U from the stored factor)
+    Lt = torch.from_numpy(np.tril(LU, -1) + np.eye(n))
+    Ut = torch.from_numpy(np.triu(LU))
+    PA = A.clone()
+    for j in range(n):
+        p = torch.from_numpy(piv[:, j]).long()
+        rows = torch.arange(bt)
+        rj, rp = PA[rows, j].clone(), PA[rows, p].clone()
+        PA[rows, j], PA[rows, p] = rp, rj
+    res = torch.linalg.matrix_norm(PA - Lt @ Ut) / torch.linalg.matrix_norm(A)
+    assert float(res.max()) <= 1e-13 * n
 
 
 # -------------------------------------------------------------------- gelqf
