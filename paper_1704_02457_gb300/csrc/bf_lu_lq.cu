@@ -314,9 +314,11 @@ k_getrf_rows(int n, int ld, Op C, OpW D, int *ipiv, long long sipiv, int *info) 
 // The m x w panel at (j0, j0) of D (rows j0.., columns j0..j0+w-1), one CTA
 // per problem, T >= m threads: the steps of k_getrf_rows on a tall panel.
 // Pivot rows go to ipiv as global rows (j0 + local row).  A zero pivot is
-// left in place (no swap, no update); info is rebuilt from U's diagonal.
+// left in place (no swap, no update).  info: the first panel (j0 = 0) sets
+// it, a later one only records a zero pivot where none came before (the
+// panels of a problem run in stream order).
 __global__ void __launch_bounds__(512)
-k_getrf_panel(int m, int w, int ld, int j0, OpW D, int *ipiv, long long sipiv) {
+k_getrf_panel(int m, int w, int ld, int j0, OpW D, int *ipiv, long long sipiv, int *info) {
   extern __shared__ double sm[];
   __shared__ long long red_k[16];
   __shared__ double red_s[16];
@@ -324,6 +326,7 @@ k_getrf_panel(int m, int w, int ld, int j0, OpW D, int *ipiv, long long sipiv) {
   const int b = blockIdx.x, t = threadIdx.x, T_ = blockDim.x;
   const Op P{D.p, D.stride, D.cn, D.i0 + j0, D.j0 + j0};
   rows_load(sm, ld, m, w, P.p + b * P.stride, P);
+  int first_zero = 0;
   for (int j = 0; j < w; j++) {
     const double x = (t >= j && t < m) ? sm[j * ld + t] : CUDART_NAN;
     const double djj = sm[j * ld + j];
@@ -335,6 +338,7 @@ k_getrf_panel(int m, int w, int ld, int j0, OpW D, int *ipiv, long long sipiv) {
     const double piv = keep ? djj : pv;
     if (t == 0) ipiv[b * sipiv + j0 + j] = j0 + pr;
     if (piv == 0.0) {
+      if (first_zero == 0) first_zero = j0 + j + 1;
       __syncthreads();
       continue;
     }
@@ -366,88 +370,165 @@ k_getrf_panel(int m, int w, int ld, int j0, OpW D, int *ipiv, long long sipiv) {
     __syncthreads();
   }
   rows_store(sm, ld, m, w, D.p + b * D.stride, OpW{D.p, D.stride, D.cn, D.i0 + j0, D.j0 + j0});
+  if (info && t == 0 && (j0 == 0 || (first_zero != 0 && info[b] == 0))) info[b] = first_zero;
 }
 
-// The panel's swaps (rows j0+s and ipiv[j0+s], s < w, in order) applied to
-// the n - w columns outside the panel, thread per column; then, right of the
-// panel, U12 = L11^{-1} A12 (L11 unit lower, w x w) by forward substitution,
-// the column in registers.  A column of L11 whose pivot was exactly zero is
-// skipped, as the unblocked factorization skips its update.
-__global__ void __launch_bounds__(256)
+// The panel's row interchanges (rows j0+s and ipiv[j0+s], s < w, in order)
+// applied to the n - w columns outside the panel, then, right of the panel,
+// U12 = L11^{-1} A12 (L11 unit lower, w x w) by forward substitution.
+//
+// The w interchanges compose to a permutation of at most 2w rows: row
+// mv_to[k] receives the old row mv_from[k].  Warp 0 forms it in registers
+// (lane q holds positions q and 32 + q; a row is found by a ballot) and keeps
+// the rows that move; the CTA applies it to the columns in chunks: every
+// thread reads its elements of a chunk, the CTA synchronizes, every thread
+// writes them -- independent loads instead of a chain of dependent swaps per
+// column.  Then the solve, through shared memory (below); a column of L11
+// whose pivot was exactly zero is skipped, as the unblocked factorization
+// skips its update.
+constexpr int SWAP_T = 256;
+constexpr int SWAP_R = 8;  // elements per thread and chunk
+
+__global__ void __launch_bounds__(SWAP_T)
 k_getrf_swap_solve(int n, int w, int j0, OpW D, const int *ipiv, long long sipiv) {
+  extern __shared__ double Xs[];  // 32 x SWAP_T
   __shared__ double L11[32 * 33];
-  __shared__ int pv[32];
+  __shared__ int mv_to[64], mv_from[64];
   __shared__ int nz[32];
+  __shared__ int n_mv;
   const int b = blockIdx.x, t = threadIdx.x;
   double *pd = D.p + (long long)b * D.stride;
   auto at = [&](int r, int c) -> double & { return pd[pm_off(D.i0 + r, D.j0 + c, D.cn)]; };
-  if (t < w) {
-    pv[t] = ipiv[b * sipiv + j0 + t];
-    nz[t] = at(j0 + t, j0 + t) != 0.0;
+  if (t < 32) {
+    const int lane = t;
+    const int pvl = lane < w ? ipiv[b * sipiv + j0 + lane] : -1;
+    int trA = lane < w ? j0 + lane : -1, srcA = trA, trB = -1, srcB = -1;
+    int k = w;
+    for (int s2 = 0; s2 < w; s2++) {
+      const int p = __shfl_sync(FULL, pvl, s2);
+      if (p == j0 + s2) continue;
+      const unsigned mA = __ballot_sync(FULL, trA == p), mB = __ballot_sync(FULL, trB == p);
+      int pos;
+      if (mA) {
+        pos = __ffs(mA) - 1;
+      } else if (mB) {
+        pos = 32 + __ffs(mB) - 1;
+      } else {
+        pos = k++;
+        if (pos < 32 && lane == pos) trA = srcA = p;
+        if (pos >= 32 && lane == pos - 32) trB = srcB = p;
+      }
+      const int vs = __shfl_sync(FULL, srcA, s2);
+      const int vp = pos < 32 ? __shfl_sync(FULL, srcA, pos) : __shfl_sync(FULL, srcB, pos - 32);
+      if (lane == s2) srcA = vp;
+      if (pos < 32 && lane == pos) srcA = vs;
+      if (pos >= 32 && lane == pos - 32) srcB = vs;
+    }
+    // compact the rows that move (source differs from destination)
+    const bool mvA = trA >= 0 && srcA != trA, mvB = trB >= 0 && srcB != trB;
+    const unsigned bA = __ballot_sync(FULL, mvA), bB = __ballot_sync(FULL, mvB);
+    const unsigned below = (1u << lane) - 1u;
+    if (mvA) {
+      const int q = __popc(bA & below);
+      mv_to[q] = trA;
+      mv_from[q] = srcA;
+    }
+    if (mvB) {
+      const int q = __popc(bA) + __popc(bB & below);
+      mv_to[q] = trB;
+      mv_from[q] = srcB;
+    }
+    if (lane == 0) n_mv = __popc(bA) + __popc(bB);
+    if (lane < w) nz[lane] = at(j0 + lane, j0 + lane) != 0.0;
   }
-  for (int e = t; e < w * w; e += blockDim.x) {
+  for (int e = t; e < w * w; e += SWAP_T) {
     const int r = e / w, c = e % w;
     L11[r * 33 + c] = r > c ? at(j0 + r, j0 + c) : 0.0;
   }
   __syncthreads();
-  for (int u = t; u < n - w; u += blockDim.x) {
-    const int c = u < j0 ? u : u + w;
-    for (int s2 = 0; s2 < w; s2++) {
-      const int r1 = j0 + s2, r2 = pv[s2];
-      if (r2 != r1) {
-        const double y = at(r1, c);
-        at(r1, c) = at(r2, c);
-        at(r2, c) = y;
+  // chunks of whole columns (every moved row of a column in the same chunk,
+  // so that no chunk reads an element an earlier one has written); columns
+  // fastest within a chunk
+  const int cols = n - w, nm = n_mv;
+  const int cpc = nm > 0 ? (SWAP_T * SWAP_R) / nm : cols;
+  for (int u0 = 0; nm > 0 && u0 < cols; u0 += cpc) {
+    const int cc = min(cpc, cols - u0), total = cc * nm;
+    double v[SWAP_R];
+#pragma unroll
+    for (int i = 0; i < SWAP_R; i++) {
+      const int e = i * SWAP_T + t;
+      if (e < total) {
+        const int k = e / cc, u = u0 + e - k * cc;
+        v[i] = at(mv_from[k], u < j0 ? u : u + w);
       }
     }
-    if (c >= j0 + w) {
-      double x[32];
+    __syncthreads();
 #pragma unroll
-      for (int r = 0; r < 32; r++)
-        if (r < w) x[r] = at(j0 + r, c);
+    for (int i = 0; i < SWAP_R; i++) {
+      const int e = i * SWAP_T + t;
+      if (e < total) {
+        const int k = e / cc, u = u0 + e - k * cc;
+        at(mv_to[k], u < j0 ? u : u + w) = v[i];
+      }
+    }
+    __syncthreads();
+  }
+  // U12 = L11^{-1} A12 in chunks of SWAP_T columns staged in shared memory
+  // (row r of the chunk at Xs[r * SWAP_T + u]): loaded and stored with
+  // consecutive threads on consecutive columns, solved by a thread per
+  // column, four rows at a time (one load of x(l) feeds four FMAs).
+  for (int c0 = j0 + w; c0 < n; c0 += SWAP_T) {
+    const int cc = min(SWAP_T, n - c0);
+    for (int e = t; e < w * cc; e += SWAP_T) {
+      const int r = e / cc, u = e - r * cc;
+      Xs[r * SWAP_T + u] = at(j0 + r, c0 + u);
+    }
+    __syncthreads();
+    if (t < cc) {
+      for (int r0 = 0; r0 < w; r0 += 4) {
+        double acc[4];
 #pragma unroll
-      for (int r = 1; r < 32; r++) {
-        if (r < w) {
-          double acc = x[r];
+        for (int q = 0; q < 4; q++) acc[q] = r0 + q < w ? Xs[(r0 + q) * SWAP_T + t] : 0.0;
+#pragma unroll 2
+        for (int l = 0; l < r0; l++) {
+          if (nz[l]) {
+            const double xl = Xs[l * SWAP_T + t];
 #pragma unroll
-          for (int l = 0; l < r; l++)
-            if (nz[l]) acc = fma(-L11[r * 33 + l], x[l], acc);
-          x[r] = acc;
+            for (int q = 0; q < 4; q++) acc[q] = fma(-L11[(r0 + q) * 33 + l], xl, acc[q]);
+          }
         }
-      }
+        // the 4 x 4 diagonal block (rows past w are never stored)
 #pragma unroll
-      for (int r = 1; r < 32; r++)
-        if (r < w) at(j0 + r, c) = x[r];
+        for (int q = 1; q < 4; q++)
+#pragma unroll
+          for (int l = 0; l < q; l++)
+            if (r0 + q < w && nz[r0 + l]) acc[q] = fma(-L11[(r0 + q) * 33 + r0 + l], acc[l], acc[q]);
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+          if (r0 + q < w) Xs[(r0 + q) * SWAP_T + t] = acc[q];
+      }
     }
+    __syncthreads();
+    for (int e = t; e < (w - 1) * cc; e += SWAP_T) {
+      const int r = 1 + e / cc, u = e - (r - 1) * cc;
+      at(j0 + r, c0 + u) = Xs[r * SWAP_T + u];
+    }
+    __syncthreads();
   }
 }
 
-// info: the first exactly zero pivot of U's diagonal (a zero pivot is left
-// in place and the column neither scaled nor used, so U_jj = 0 there and
-// nowhere before).
-__global__ void k_getrf_info(int batch, int n, OpW D, int *info) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= batch) return;
-  const double *pd = D.p + (long long)b * D.stride;
-  int z = 0;
-  for (int j = 0; j < n && z == 0; j++)
-    if (pd[pm_off(D.i0 + j, D.j0 + j, D.cn)] == 0.0) z = j + 1;
-  info[b] = z;
-}
-
 // copy of the n x n sub-matrices C into D (the blocked getrf works in
-// place), in panel-major order so that consecutive threads touch
-// consecutive doubles
+// place): problems along grid y, each problem's elements in panel-major
+// order along x, so that consecutive threads touch consecutive doubles
 __global__ void k_copy_sub(int batch, int n, Op C, OpW D) {
-  const long long per = (long long)((n + PS - 1) / PS) * PS * n, total = per * batch;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int b = (int)(e / per);
-    const long long x = e - (long long)b * per;
-    const int r4 = (int)(x % PS), c = (int)((x / PS) % n), r = (int)(x / ((long long)PS * n)) * PS + r4;
-    if (r < n)
-      D.p[(long long)b * D.stride + pm_off(D.i0 + r, D.j0 + c, D.cn)] =
-          C.p[(long long)b * C.stride + pm_off(C.i0 + r, C.j0 + c, C.cn)];
+  const int per = ((n + PS - 1) / PS) * PS * n;
+  for (int b = blockIdx.y; b < batch; b += gridDim.y) {
+    const double *pc = C.p + (long long)b * C.stride;
+    double *pd = D.p + (long long)b * D.stride;
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < per; x += gridDim.x * blockDim.x) {
+      const int r4 = x & (PS - 1), q = x / PS, c = q % n, r = (q / n) * PS + r4;
+      if (r < n) pd[pm_off(D.i0 + r, D.j0 + c, D.cn)] = pc[pm_off(C.i0 + r, C.j0 + c, C.cn)];
+    }
   }
 }
 
@@ -567,7 +648,7 @@ int pick_g(size_t bytes_per_problem) {
 constexpr int LU_BIG_THREADS = BF_LU_BIG_THREADS;
 // Order from which the rule takes the blocked getrf; block column width.
 #ifndef BF_LU_BLOCKED_MIN_N
-#define BF_LU_BLOCKED_MIN_N 129
+#define BF_LU_BLOCKED_MIN_N 96
 #endif
 constexpr int LU_NB = 32;
 
@@ -623,8 +704,8 @@ cudaError_t launch_getrf_blocked(int batch, int n, Op C, OpW D, int *ipiv, long 
                                  cudaStream_t s) {
   const bool same = C.p == D.p && C.stride == D.stride && C.cn == D.cn && C.i0 == D.i0 && C.j0 == D.j0;
   if (!same) {
-    const long long total = (long long)((n + PS - 1) / PS) * PS * n * batch;
-    k_copy_sub<<<(unsigned)std::min<long long>((total + 255) / 256, 4096), 256, 0, s>>>(batch, n, C, D);
+    const int per = ((n + PS - 1) / PS) * PS * n;
+    k_copy_sub<<<dim3((per + 255) / 256, std::min(batch, 65535)), 256, 0, s>>>(batch, n, C, D);
   }
   const bool aligned = (D.i0 % PS) == 0 && (D.stride % 2) == 0 && ((uintptr_t)D.p % 16) == 0;
   for (int j0 = 0; j0 < n; j0 += LU_NB) {
@@ -632,9 +713,13 @@ cudaError_t launch_getrf_blocked(int batch, int n, Op C, OpW D, int *ipiv, long 
     const size_t smem = (size_t)ld * w * sizeof(double);
     cudaError_t e = set_smem((const void *)k_getrf_panel, smem);
     if (e != cudaSuccess) return e;
-    k_getrf_panel<<<batch, std::max(64, (m + 31) / 32 * 32), smem, s>>>(m, w, ld, j0, D, ipiv, sipiv);
-    if (n > w)
-      k_getrf_swap_solve<<<batch, std::min(256, (n - w + 31) / 32 * 32), 0, s>>>(n, w, j0, D, ipiv, sipiv);
+    k_getrf_panel<<<batch, std::max(64, (m + 31) / 32 * 32), smem, s>>>(m, w, ld, j0, D, ipiv, sipiv, info);
+    if (n > w) {
+      const size_t xs = (size_t)32 * SWAP_T * sizeof(double);
+      e = set_smem((const void *)k_getrf_swap_solve, xs);
+      if (e != cudaSuccess) return e;
+      k_getrf_swap_solve<<<batch, SWAP_T, xs, s>>>(n, w, j0, D, ipiv, sipiv);
+    }
     const int r = m - w;
     if (r > 0) {
       e = launch_gemm_nn(false, batch, r, r, w, -1.0, Op{D.p, D.stride, D.cn, D.i0 + j0 + w, D.j0 + j0},
@@ -644,7 +729,6 @@ cudaError_t launch_getrf_blocked(int batch, int n, Op C, OpW D, int *ipiv, long 
       if (e != cudaSuccess) return e;
     }
   }
-  if (info) k_getrf_info<<<(batch + 127) / 128, 128, 0, s>>>(batch, n, D, info);
   return cudaGetLastError();
 }
 
