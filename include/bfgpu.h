@@ -277,7 +277,12 @@ int bf_dgetrf(int n, const bf_dmat *sC, int ci, int cj, const bf_dmat *sD, int d
  * from the right row by row (i < min(m, n)); beta = -sign(alpha) ||(alpha,
  * x)||.  L is the lower triangle of D, x_i is left in the strictly upper
  * part of row i, tau (device) receives tau_i at tau + b*strideTau + i, and
- * Q = H_{k-1} ... H_0.  C and D may coincide.  Supports m * n <= 16384. */
+ * Q = H_{k-1} ... H_0.  C and D coincide or do not overlap.  Supports
+ * m * n <= 16384, and any m, n <= 512: there the factorization is blocked by
+ * rows of 32 -- each panel by the steps above, then its reflectors applied to
+ * the rows below at once as the block reflector I - V^T T V (compact WY form,
+ * T upper triangular), so the results agree with the row-by-row order up to
+ * rounding. */
 int bf_dgelqf_batched(int batch, int m, int n, const bf_dmat *sC, int ci, int cj, long long strideC,
                       const bf_dmat *sD, int di, int dj, long long strideD, double *tau,
                       long long strideTau, void *stream);
@@ -489,9 +494,11 @@ int bf_dposv_mixed_batched_noalloc(int batch, int n, int nrhs, const bf_dmat *sA
  * order, which bf_layout_set refuses.
  *
  * routine:  0 gemm_nt, 1 syrk_ln, 2 potrf_l, 3 trsm_rltn, 4 syrk_potrf_ln,
- *           5 getrf.
+ *           5 getrf, 6 gelqf.
  * order:    m for gemm_nt, syrk_ln, potrf_l and syrk_potrf_ln; n (the order
- *           of L) for trsm_rltn; n for getrf.  Orders above 511 share one
+ *           of L) for trsm_rltn; n for getrf; the column count n for gelqf
+ *           (a forced gelqf layout that has no kernel for the call's m x n
+ *           leaves that call to the rule).  Orders above 511 share one
  *           entry.
  * batch:    the entry covers the batch sizes with the same floor(log2(batch)).
  * layout:   0 = the built-in rule; 1 .. bf_layout_count(routine) - 1:
@@ -511,8 +518,11 @@ int bf_dposv_mixed_batched_noalloc(int batch, int n, int nrhs, const bf_dmat *sA
  *   getrf:              1 a warp shared by 32 / G problems (order <= 128)
  *                       2 one CTA per problem, the matrix in shared
  *                         memory (order <= 128)
- *                       3 blocked by columns of 32: panel, swaps and
- *                         triangular solve, gemm_nn update (order <= 512)
+ *                       3, 4 blocked by columns of 32, 16: panel, swaps
+ *                         and triangular solve, gemm_nn update (order <= 512)
+ *   gelqf:              1, 2 as for getrf (m * n <= 16384)
+ *                       3, 4 blocked by rows of 32, 16: panel, block
+ *                         reflector applied to the rows below (m, n <= 512)
  * The table is process-wide (all devices) and not synchronized with calls in
  * flight: set it before the calls it should affect.
  * ------------------------------------------------------------------------ */
@@ -528,8 +538,8 @@ int bf_layout_set(int routine, int order, int batch, int layout);
 
 /* The layout a call of `routine` with these sizes would use now (the forced
  * one, else the rule's): gemm_nt (m, n, k), syrk_ln (m, -, k), potrf_l (m),
- * trsm_rltn (m, n), syrk_potrf_ln (m, -, k), getrf (n); unused sizes are
- * ignored.
+ * trsm_rltn (m, n), syrk_potrf_ln (m, -, k), getrf (n), gelqf (m, n);
+ * unused sizes are ignored.
  * Returns the layout (>= 1) or -1..-5 for a bad argument. */
 int bf_layout_get(int routine, int batch, int m, int n, int k);
 

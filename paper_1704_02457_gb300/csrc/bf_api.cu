@@ -549,7 +549,7 @@ int bf_dgelqf_batched(int batch, int m, int n, const bf_dmat *sC, int ci, int cj
   if (m < 0) return -2;
   if (n < 0) return -3;
   if (batch == 0 || m == 0 || n == 0) return 0;
-  if ((long long)m * n > GELQF_MAX_MN) return BF_ERR_UNSUPPORTED;
+  if ((long long)m * n > GELQF_ONE_CTA_MAX_MN && (m > GELQF_MAX_DIM || n > GELQF_MAX_DIM)) return BF_ERR_UNSUPPORTED;
   if (int w = check_op(sC, ci, cj, m, n, strideC, batch, false)) return pos_err(w, 4);
   if (int w = check_op(sD, di, dj, m, n, strideD, batch, true)) return pos_err(w, 8);
   const int k = m < n ? m : n;

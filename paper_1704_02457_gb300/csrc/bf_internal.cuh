@@ -190,13 +190,14 @@ cudaError_t launch_posv_mixed_tc(int prec, int batch, int n, int nrhs, Op A, Op 
                                  int *iters, double *resid, double *W, double *dinv, float *l32, int *infos,
                                  int *info32, cudaStream_t s);
 
-// LU with partial pivoting (square n <= 512; above 128 blocked) and
-// Householder LQ (m*n <= 16384).
+// LU with partial pivoting (square n <= 512; blocked from n = 96) and
+// Householder LQ (m*n <= 16384, or m, n <= 512 blocked).
 cudaError_t launch_getrf(int batch, int n, Op C, OpW D, int *ipiv, long long sipiv, int *info, cudaStream_t s);
 cudaError_t launch_gelqf(int batch, int m, int n, Op C, OpW D, double *tau, long long stau, cudaStream_t s);
 constexpr int GETRF_MAX_N = 512;
 constexpr int LU_ONE_CTA_MAX_N = 128;  // the whole-matrix-in-shared-memory getrf kernels
-constexpr int GELQF_MAX_MN = 16384;
+constexpr int GELQF_ONE_CTA_MAX_MN = 16384;  // the whole-matrix-in-shared-memory gelqf kernels
+constexpr int GELQF_MAX_DIM = 512;           // the blocked gelqf: m, n <= 512
 
 // Backward Riccati recursion, square-root form (one CTA per instance).
 size_t riccati_smem(int max_nx, int max_nu);
@@ -217,7 +218,8 @@ enum {
   ROUTINE_TRSM_RLTN = 3,
   ROUTINE_SYRK_POTRF = 4,
   ROUTINE_GETRF = 5,
-  ROUTINE_COUNT = 6
+  ROUTINE_GELQF = 6,
+  ROUTINE_COUNT = 7
 };
 // gemm_nt / syrk_ln: the k-loop of a 4x4 block split over KS lanes
 enum { LAYOUT_GEMM_KS1 = 1, LAYOUT_GEMM_KS2 = 2, LAYOUT_GEMM_KS4 = 3, LAYOUT_GEMM_COUNT = 4 };
@@ -238,8 +240,11 @@ enum {
 // trsm_rltn
 enum { LAYOUT_TRSM_ROWS = 1, LAYOUT_TRSM_LAT2 = 2, LAYOUT_TRSM_LAT4 = 3, LAYOUT_TRSM_LAT8 = 4, LAYOUT_TRSM_COUNT = 5 };
 // getrf: one warp per 32/G problems (n <= 128), one CTA per problem (n <=
-// 128), blocked by columns of 32 (n <= 512)
-enum { LAYOUT_LU_WARP = 1, LAYOUT_LU_ROWS = 2, LAYOUT_LU_BLOCKED = 3, LAYOUT_LU_COUNT = 4 };
+// 128), blocked by columns of 32 or 16 (n <= 512)
+enum { LAYOUT_LU_WARP = 1, LAYOUT_LU_ROWS = 2, LAYOUT_LU_BLOCKED = 3, LAYOUT_LU_BLOCKED16 = 4, LAYOUT_LU_COUNT = 5 };
+// gelqf: one warp per 32/G problems, one CTA per problem (both m*n <=
+// 16384), blocked by rows of 32 or 16 (m, n <= 512)
+enum { LAYOUT_LQ_WARP = 1, LAYOUT_LQ_ROWS = 2, LAYOUT_LQ_BLOCKED = 3, LAYOUT_LQ_BLOCKED16 = 4, LAYOUT_LQ_COUNT = 5 };
 
 // Layout forced for (routine, n, batch) by bf_layout_set, or 0.
 int layout_forced(int routine, int n, int batch);
@@ -251,6 +256,8 @@ int trsm_layout_rule(int batch, int m, int n);
 bool trsm_layout_ok(int layout, int n);
 int getrf_layout_rule(int batch, int n);
 bool getrf_layout_ok(int layout, int n);
+int gelqf_layout_rule(int batch, int m, int n);
+bool gelqf_layout_ok(int layout, int m, int n);
 
 // Latency kernels (bf_latency.cu): one problem per CTA of four warps for
 // potrf / syrk_potrf, R = lanes lanes per row for trsm; order <= 32.

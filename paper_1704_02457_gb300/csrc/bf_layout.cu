@@ -30,6 +30,7 @@ int layout_count(int routine) {
     case ROUTINE_POTRF: case ROUTINE_SYRK_POTRF: return LAYOUT_CHOL_COUNT;
     case ROUTINE_TRSM_RLTN: return LAYOUT_TRSM_COUNT;
     case ROUTINE_GETRF: return LAYOUT_LU_COUNT;
+    case ROUTINE_GELQF: return LAYOUT_LQ_COUNT;
     default: return 0;
   }
 }
@@ -40,6 +41,8 @@ bool layout_ok(int routine, int layout, int n) {
     case ROUTINE_POTRF: case ROUTINE_SYRK_POTRF: return chol_layout_ok(layout, n);
     case ROUTINE_TRSM_RLTN: return trsm_layout_ok(layout, n);
     case ROUTINE_GETRF: return getrf_layout_ok(layout, n);
+    // keyed by the column count n; the row count is checked at the call
+    case ROUTINE_GELQF: return gelqf_layout_ok(layout, 1, n);
     default: return false;
   }
 }
@@ -75,15 +78,16 @@ int bf_layout_get(int routine, int batch, int m, int n, int k) {
   if (m < 0) return -3;
   if (n < 0) return -4;
   if (k < 0) return -5;
-  const int order = routine == ROUTINE_TRSM_RLTN ? n : m;
+  const int order = (routine == ROUTINE_TRSM_RLTN || routine == ROUTINE_GELQF) ? n : m;
   const int forced = layout_forced(routine, order, batch);
-  if (forced > 0) return forced;
+  if (forced > 0 && (routine != ROUTINE_GELQF || gelqf_layout_ok(forced, m, n))) return forced;
   switch (routine) {
     case ROUTINE_GEMM_NT: return gemm_layout_rule(false, batch, m, n, k);
     case ROUTINE_SYRK_LN: return gemm_layout_rule(true, batch, m, m, k);
     case ROUTINE_POTRF: return chol_layout_rule(false, batch, m);
     case ROUTINE_SYRK_POTRF: return chol_layout_rule(true, batch, m);
     case ROUTINE_GETRF: return getrf_layout_rule(batch, m);
+    case ROUTINE_GELQF: return gelqf_layout_rule(batch, m, n);
     default: return trsm_layout_rule(batch, m, n);
   }
 }

@@ -386,7 +386,7 @@ k_getrf_panel(int m, int w, int ld, int j0, OpW D, int *ipiv, long long sipiv, i
 // column.  Then the solve, through shared memory (below); a column of L11
 // whose pivot was exactly zero is skipped, as the unblocked factorization
 // skips its update.
-constexpr int SWAP_T = 256;
+constexpr int SWAP_T = 128;
 constexpr int SWAP_R = 8;  // elements per thread and chunk
 
 __global__ void __launch_bounds__(SWAP_T)
@@ -517,19 +517,28 @@ k_getrf_swap_solve(int n, int w, int j0, OpW D, const int *ipiv, long long sipiv
   }
 }
 
-// copy of the n x n sub-matrices C into D (the blocked getrf works in
-// place): problems along grid y, each problem's elements in panel-major
+// copy of the m x n sub-matrices C into D (the blocked factorizations work
+// in place): problems along grid y, each problem's elements in panel-major
 // order along x, so that consecutive threads touch consecutive doubles
-__global__ void k_copy_sub(int batch, int n, Op C, OpW D) {
-  const int per = ((n + PS - 1) / PS) * PS * n;
+__global__ void k_copy_sub(int batch, int m, int n, Op C, OpW D) {
+  const int per = ((m + PS - 1) / PS) * PS * n;
   for (int b = blockIdx.y; b < batch; b += gridDim.y) {
     const double *pc = C.p + (long long)b * C.stride;
     double *pd = D.p + (long long)b * D.stride;
     for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < per; x += gridDim.x * blockDim.x) {
       const int r4 = x & (PS - 1), q = x / PS, c = q % n, r = (q / n) * PS + r4;
-      if (r < n) pd[pm_off(D.i0 + r, D.j0 + c, D.cn)] = pc[pm_off(C.i0 + r, C.j0 + c, C.cn)];
+      if (r < m) pd[pm_off(D.i0 + r, D.j0 + c, D.cn)] = pc[pm_off(C.i0 + r, C.j0 + c, C.cn)];
     }
   }
+}
+
+bool same_op(const Op &C, const OpW &D) {
+  return C.p == D.p && C.stride == D.stride && C.cn == D.cn && C.i0 == D.i0 && C.j0 == D.j0;
+}
+
+void copy_sub(int batch, int m, int n, Op C, OpW D, cudaStream_t s) {
+  const int per = ((m + PS - 1) / PS) * PS * n;
+  k_copy_sub<<<dim3((per + 255) / 256, std::min(batch, 65535)), 256, 0, s>>>(batch, m, n, C, D);
 }
 
 // gelqf, one CTA per problem.  Per row i, two barriers:
@@ -622,6 +631,167 @@ k_gelqf_rows(int m, int n, int ld, Op C, OpW D, double *tau, long long stau) {
   rows_store(sm, ld, m, n, D.p + b * D.stride, D);
 }
 
+// ---------------------------------------------------------------------------
+// Blocked gelqf for the sizes above the one-CTA kernels' shared memory: per
+// block of ib (<= 32) rows, the panel (rows i..i+ib-1, columns i..n-1) is
+// factorized by k_gelqf_rows, then its ib reflectors are applied to the rows
+// below at once, as the block reflector of the compact WY form (rowwise):
+//     H_i H_{i+1} ... H_{i+ib-1} = I - V^T T V,
+// V the ib x (n-i) reflector rows (unit leading entry, zeros before it), T
+// upper triangular with T(j, j) = tau_j and T(0:j, j) = -tau_j T(0:j, 0:j)
+// (V(0:j, :) v_j^T).  The rows below become A2 - ((A2 V^T) T) V: the same
+// products as applying the reflectors one by one, in another order.
+// ---------------------------------------------------------------------------
+constexpr int LQ_T = 256;    // threads of the apply kernel
+constexpr int LQ_RB = 32;    // rows of A2 per step
+constexpr int LQ_RPC = 128;  // rows of A2 per CTA
+
+size_t lq_apply_smem(int nb, int nc) {
+  const int ldv = nc | 1;
+  return ((size_t)nb * ldv + (size_t)(2 * nb + LQ_RB) * (nb + 1)) * sizeof(double);
+}
+
+// The apply step for panel i (NB = 16 or 32 rows per panel): CTA (b, y)
+// takes rows i+ib + [y*LQ_RPC, (y+1)*LQ_RPC) of problem b.  Shared memory:
+// V (NB rows, those past ib zero), G = V V^T (upper), T (upper, zero
+// elsewhere) and a W block.  Every CTA of a problem forms G and T itself (no
+// workspace; NB/(8 rows) of the update's FMAs).  Thread layouts are chosen so that the
+// shared-memory reads of V within a warp fall in distinct banks (V's row
+// stride is odd).
+template <int NB>
+__global__ void __launch_bounds__(LQ_T)
+k_gelqf_apply(int m, int n, int i, int ib, OpW D, const double *tau, long long stau) {
+  constexpr int NQ = NB / 8;    // W columns per thread
+  constexpr int LDT = NB + 1;  // row stride of G, T and W
+  extern __shared__ double sh[];
+  const int nc = n - i, ldv = nc | 1;
+  double *Vs = sh;
+  double *Gm = Vs + NB * ldv;
+  double *Tm = Gm + NB * LDT;
+  double *Wt = Tm + NB * LDT;
+  const int b = blockIdx.x, t = threadIdx.x;
+  double *pd = D.p + (long long)b * D.stride;
+  auto at = [&](int r, int c) -> double & { return pd[pm_off(D.i0 + r, D.j0 + c, D.cn)]; };
+  for (int e = t; e < NB * nc; e += LQ_T) {
+    const int s = e / nc, c = e - s * nc;
+    Vs[s * ldv + c] = (s >= ib || c < s) ? 0.0 : (c == s ? 1.0 : at(i + s, i + c));
+  }
+  __syncthreads();
+  // G(a, q) = v_a . v_q for a < q < ib, pairs numbered by q so that a warp's
+  // dot products have similar lengths; v_q is zero before column q
+  const int npair = ib * (ib - 1) / 2;
+  for (int p = t; p < npair; p += LQ_T) {
+    int q = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)p)) * 0.5f);
+    while (q * (q - 1) / 2 > p) q--;
+    while ((q + 1) * q / 2 <= p) q++;
+    const int a = p - q * (q - 1) / 2;
+    double g0 = 0.0, g1 = 0.0;
+    int c = q;
+    for (; c + 1 < nc; c += 2) {
+      g0 = fma(Vs[a * ldv + c], Vs[q * ldv + c], g0);
+      g1 = fma(Vs[a * ldv + c + 1], Vs[q * ldv + c + 1], g1);
+    }
+    if (c < nc) g0 = fma(Vs[a * ldv + c], Vs[q * ldv + c], g0);
+    Gm[a * LDT + q] = g0 + g1;
+  }
+  __syncthreads();
+  // T, column by column on warp 0; lane a only reads the entries T(a, q) it
+  // wrote itself, so the columns need no synchronization between lanes
+  if (t < NB) {
+    const double *tb = tau + b * stau + i;
+    for (int j = 0; j < NB; j++) {
+      if (j >= ib) {  // past the panel's reflectors: T zero (G is not formed there)
+        Tm[t * LDT + j] = 0.0;
+        continue;
+      }
+      const double tj = tb[j];
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      int q = t;
+      for (; q + 3 < j; q += 4) {
+        s0 = fma(Tm[t * LDT + q], Gm[q * LDT + j], s0);
+        s1 = fma(Tm[t * LDT + q + 1], Gm[(q + 1) * LDT + j], s1);
+        s2 = fma(Tm[t * LDT + q + 2], Gm[(q + 2) * LDT + j], s2);
+        s3 = fma(Tm[t * LDT + q + 3], Gm[(q + 3) * LDT + j], s3);
+      }
+      for (; q < j; q++) s0 = fma(Tm[t * LDT + q], Gm[q * LDT + j], s0);
+      Tm[t * LDT + j] = t < j ? -tj * ((s0 + s1) + (s2 + s3)) : (t == j ? tj : 0.0);
+    }
+  }
+  __syncthreads();
+  const int m2 = m - i - ib;
+  const int rbeg = blockIdx.y * LQ_RPC, rend = min(m2, rbeg + LQ_RPC);
+  const int wr = t >> 3, ws = t & 7;  // W(wr, ws + 8q), q < NQ
+  for (int r0 = rbeg; r0 < rend; r0 += LQ_RB) {
+    const int rows = min(LQ_RB, rend - r0);
+    const int rg = i + ib + r0;  // first row of the block in the matrix
+    // W = A2 V^T: the eight threads of a row read its entries straight from
+    // global memory (one sector serves them), eight at a time ahead of use
+    double w4[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; q++) w4[q] = 0.0;
+    if (wr < rows) {
+      const double *arow = pd + pm_off(D.i0 + rg + wr, D.j0 + i, D.cn);  // column c at arow + c * PS
+      int c = 0;
+      for (; c + 8 <= nc; c += 8) {
+        double a[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) a[k] = arow[(c + k) * PS];
+#pragma unroll
+        for (int k = 0; k < 8; k++)
+#pragma unroll
+          for (int q = 0; q < NQ; q++) w4[q] = fma(a[k], Vs[(ws + 8 * q) * ldv + c + k], w4[q]);
+      }
+      for (; c < nc; c++) {
+        const double a = arow[c * PS];
+#pragma unroll
+        for (int q = 0; q < NQ; q++) w4[q] = fma(a, Vs[(ws + 8 * q) * ldv + c], w4[q]);
+      }
+    }
+    __syncthreads();  // the previous step's update has read Wt
+#pragma unroll
+    for (int q = 0; q < NQ; q++) Wt[wr * LDT + ws + 8 * q] = w4[q];
+    __syncthreads();
+    // W <- W T (T upper: W T(:, s) sums W(:, 0..s))
+    double u4[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; q++) u4[q] = 0.0;
+    for (int q2 = 0; q2 < NB; q2++) {
+      const double wq = Wt[wr * LDT + q2];
+#pragma unroll
+      for (int q = 0; q < NQ; q++) u4[q] = fma(wq, Tm[q2 * LDT + ws + 8 * q], u4[q]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NQ; q++) Wt[wr * LDT + ws + 8 * q] = u4[q];
+    __syncthreads();
+    // A2 <- A2 - W V, thread (row ur, columns uc + 8k of each chunk of 64)
+    const int ur = t >> 3, uc = t & 7;
+    if (ur < rows) {
+      for (int c0 = 0; c0 < nc; c0 += 64) {
+        double acc[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+          const int c = c0 + uc + 8 * k;
+          acc[k] = c < nc ? at(rg + ur, i + c) : 0.0;
+        }
+        for (int s = 0; s < ib; s++) {
+          const double w = Wt[ur * LDT + s];
+#pragma unroll
+          for (int k = 0; k < 8; k++) {
+            const int c = min(c0 + uc + 8 * k, nc - 1);
+            acc[k] = fma(-w, Vs[s * ldv + c], acc[k]);
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+          const int c = c0 + uc + 8 * k;
+          if (c < nc) at(rg + ur, i + c) = acc[k];
+        }
+      }
+    }
+  }
+}
+
 // Lanes per problem of the one-warp kernels: the smallest G whose matrices
 // for the warp's 32/G problems fit 20 KB (many resident warps per SM hide the
 // latency of the per-column pivot and reciprocal); else one problem per warp.
@@ -646,11 +816,15 @@ int pick_g(size_t bytes_per_problem) {
 #define BF_LU_BIG_THREADS 256
 #endif
 constexpr int LU_BIG_THREADS = BF_LU_BIG_THREADS;
-// Order from which the rule takes the blocked getrf; block column width.
+// Orders from which the rule takes the blocked forms (measured on square
+// sweeps: getrf blocked by 32 columns and gelqf blocked by 16 rows win from
+// n = 96, the one-CTA forms at n = 64).
+#ifndef BF_LQ_BLOCKED_MIN
+#define BF_LQ_BLOCKED_MIN 96
+#endif
 #ifndef BF_LU_BLOCKED_MIN_N
 #define BF_LU_BLOCKED_MIN_N 96
 #endif
-constexpr int LU_NB = 32;
 
 cudaError_t set_smem(const void *fn, size_t smem) {
   if (smem <= 48 * 1024) return cudaSuccess;
@@ -688,28 +862,24 @@ int getrf_layout_rule(int batch, int n) {
 bool getrf_layout_ok(int layout, int n) {
   switch (layout) {
     case LAYOUT_LU_WARP: case LAYOUT_LU_ROWS: return n <= LU_ONE_CTA_MAX_N;
-    case LAYOUT_LU_BLOCKED: return n <= GETRF_MAX_N;
+    case LAYOUT_LU_BLOCKED: case LAYOUT_LU_BLOCKED16: return n <= GETRF_MAX_N;
     default: return false;
   }
 }
 
 namespace {
 
-// Blocked getrf: for each block column j0 (width w = LU_NB, the last one
-// narrower) the panel factorization, the panel's swaps on the other columns
+// Blocked getrf: for each block column j0 (width w = nb, 16 or 32, the last
+// one narrower) the panel factorization, the panel's swaps on the other columns
 // with U12 = L11^{-1} A12, and the trailing update A22 <- A22 - L21 U12 by
 // the gemm_nn kernel; in place in D (C copied there first unless the two
 // coincide).  Each launch covers the whole batch.
-cudaError_t launch_getrf_blocked(int batch, int n, Op C, OpW D, int *ipiv, long long sipiv, int *info,
+cudaError_t launch_getrf_blocked(int nb, int batch, int n, Op C, OpW D, int *ipiv, long long sipiv, int *info,
                                  cudaStream_t s) {
-  const bool same = C.p == D.p && C.stride == D.stride && C.cn == D.cn && C.i0 == D.i0 && C.j0 == D.j0;
-  if (!same) {
-    const int per = ((n + PS - 1) / PS) * PS * n;
-    k_copy_sub<<<dim3((per + 255) / 256, std::min(batch, 65535)), 256, 0, s>>>(batch, n, C, D);
-  }
+  if (!same_op(C, D)) copy_sub(batch, n, n, C, D, s);
   const bool aligned = (D.i0 % PS) == 0 && (D.stride % 2) == 0 && ((uintptr_t)D.p % 16) == 0;
-  for (int j0 = 0; j0 < n; j0 += LU_NB) {
-    const int w = std::min(LU_NB, n - j0), m = n - j0, ld = m | 1;
+  for (int j0 = 0; j0 < n; j0 += nb) {
+    const int w = std::min(nb, n - j0), m = n - j0, ld = m | 1;
     const size_t smem = (size_t)ld * w * sizeof(double);
     cudaError_t e = set_smem((const void *)k_getrf_panel, smem);
     if (e != cudaSuccess) return e;
@@ -737,7 +907,8 @@ cudaError_t launch_getrf_blocked(int batch, int n, Op C, OpW D, int *ipiv, long 
 cudaError_t launch_getrf(int batch, int n, Op C, OpW D, int *ipiv, long long sipiv, int *info, cudaStream_t s) {
   const int forced = layout_forced(ROUTINE_GETRF, n, batch);
   const int lay = (forced > 0 && getrf_layout_ok(forced, n)) ? forced : getrf_layout_rule(batch, n);
-  if (lay == LAYOUT_LU_BLOCKED) return launch_getrf_blocked(batch, n, C, D, ipiv, sipiv, info, s);
+  if (lay == LAYOUT_LU_BLOCKED) return launch_getrf_blocked(32, batch, n, C, D, ipiv, sipiv, info, s);
+  if (lay == LAYOUT_LU_BLOCKED16) return launch_getrf_blocked(16, batch, n, C, D, ipiv, sipiv, info, s);
   if (lay == LAYOUT_LU_ROWS) {
     const int ld = n | 1;
     const size_t smem = (size_t)ld * n * sizeof(double);
@@ -757,8 +928,65 @@ cudaError_t launch_getrf(int batch, int n, Op C, OpW D, int *ipiv, long long sip
   }
 }
 
+int gelqf_layout_rule(int batch, int m, int n) {
+  (void)batch;
+  if ((long long)m * n > GELQF_ONE_CTA_MAX_MN || (m >= BF_LQ_BLOCKED_MIN && n >= BF_LQ_BLOCKED_MIN))
+    return LAYOUT_LQ_BLOCKED16;
+  return m < BF_LQ_ROWS_MIN ? LAYOUT_LQ_WARP : LAYOUT_LQ_ROWS;
+}
+
+bool gelqf_layout_ok(int layout, int m, int n) {
+  switch (layout) {
+    case LAYOUT_LQ_WARP: case LAYOUT_LQ_ROWS: return (long long)m * n <= GELQF_ONE_CTA_MAX_MN;
+    case LAYOUT_LQ_BLOCKED: case LAYOUT_LQ_BLOCKED16: return m <= GELQF_MAX_DIM && n <= GELQF_MAX_DIM;
+    default: return false;
+  }
+}
+
+namespace {
+
+// Blocked gelqf: per block of nb (16 or 32) rows the panel by k_gelqf_rows, then
+// the block reflector applied to the rows below by k_gelqf_apply; in place
+// in D (C copied there first unless the two coincide).
+cudaError_t launch_gelqf_blocked(int nb, int batch, int m, int n, Op C, OpW D, double *tau, long long stau,
+                                 cudaStream_t s) {
+  if (!same_op(C, D)) copy_sub(batch, m, n, C, D, s);
+  const int k = std::min(m, n);
+  for (int i = 0; i < k; i += nb) {
+    const int ib = std::min(nb, k - i), nc = n - i, ld = ib | 1;
+    const size_t smem = (size_t)ld * nc * sizeof(double);
+    cudaError_t e = set_smem((const void *)k_gelqf_rows, smem);
+    if (e != cudaSuccess) return e;
+    const long long mn = (long long)ib * nc;
+    k_gelqf_rows<<<batch, mn > 9216 ? LU_BIG_THREADS : (mn > 4096 ? 256 : 128), smem, s>>>(
+        ib, nc, ld, Op{D.p, D.stride, D.cn, D.i0 + i, D.j0 + i}, OpW{D.p, D.stride, D.cn, D.i0 + i, D.j0 + i},
+        tau + i, stau);
+    const int m2 = m - i - ib;
+    if (m2 > 0) {
+      const size_t sa = lq_apply_smem(nb, nc);
+      const dim3 grid(batch, (m2 + LQ_RPC - 1) / LQ_RPC);
+      if (nb == 16) {
+        e = set_smem((const void *)k_gelqf_apply<16>, sa);
+        if (e != cudaSuccess) return e;
+        k_gelqf_apply<16><<<grid, LQ_T, sa, s>>>(m, n, i, ib, D, tau, stau);
+      } else {
+        e = set_smem((const void *)k_gelqf_apply<32>, sa);
+        if (e != cudaSuccess) return e;
+        k_gelqf_apply<32><<<grid, LQ_T, sa, s>>>(m, n, i, ib, D, tau, stau);
+      }
+    }
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
 cudaError_t launch_gelqf(int batch, int m, int n, Op C, OpW D, double *tau, long long stau, cudaStream_t s) {
-  if (m >= BF_LQ_ROWS_MIN) {
+  const int forced = layout_forced(ROUTINE_GELQF, n, batch);
+  const int lay = (forced > 0 && gelqf_layout_ok(forced, m, n)) ? forced : gelqf_layout_rule(batch, m, n);
+  if (lay == LAYOUT_LQ_BLOCKED) return launch_gelqf_blocked(32, batch, m, n, C, D, tau, stau, s);
+  if (lay == LAYOUT_LQ_BLOCKED16) return launch_gelqf_blocked(16, batch, m, n, C, D, tau, stau, s);
+  if (lay == LAYOUT_LQ_ROWS) {
     const int ld = m | 1;
     const size_t smem = (size_t)ld * n * sizeof(double);
     cudaError_t e = set_smem((const void *)k_gelqf_rows, smem);

@@ -20,7 +20,8 @@ from dataclasses import dataclass, field
 
 from ._abi import load
 
-ROUTINE_IDS = {"dgemm_nt": 0, "dsyrk_ln": 1, "dpotrf_l": 2, "dtrsm_rltn": 3, "dsyrk_dpotrf_ln": 4, "dgetrf": 5}
+ROUTINE_IDS = {"dgemm_nt": 0, "dsyrk_ln": 1, "dpotrf_l": 2, "dtrsm_rltn": 3, "dsyrk_dpotrf_ln": 4, "dgetrf": 5,
+              "dgelqf": 6}
 
 LAYOUT_NAMES = {
     "dgemm_nt": {1: "ks1", 2: "ks2", 3: "ks4"},
@@ -28,9 +29,11 @@ LAYOUT_NAMES = {
     "dpotrf_l": {1: "tiny", 2: "small_g2", 3: "small_g4", 4: "small_g8", 5: "small_g16", 6: "small_g32", 7: "rows",
                  8: "latency", 9: "split", 10: "blocked"},
     "dtrsm_rltn": {1: "rows", 2: "latency_r2", 3: "latency_r4", 4: "latency_r8"},
-    "dgetrf": {1: "warp", 2: "rows", 3: "blocked"},
+    "dgetrf": {1: "warp", 2: "rows", 3: "blocked", 4: "blocked16"},
+    "dgelqf": {1: "warp", 2: "rows", 3: "blocked", 4: "blocked16"},
 }
 LAYOUT_NAMES["dsyrk_dpotrf_ln"] = LAYOUT_NAMES["dpotrf_l"]
+GELQF_ONE_CTA_MAX_MN = 16384  # the one-CTA gelqf kernels hold m * n <= 16384 doubles
 
 
 def _rid(routine: str) -> int:
@@ -40,7 +43,7 @@ def _rid(routine: str) -> int:
 
 
 def _order(routine: str, m: int, n: int) -> int:
-    return n if routine == "dtrsm_rltn" else m
+    return n if routine in ("dtrsm_rltn", "dgelqf") else m
 
 
 def rule_layout(routine: str, batch: int, m: int, n: int = 0, k: int = 0) -> int:
@@ -56,12 +59,16 @@ def current_layout(routine: str, batch: int, m: int, n: int = 0, k: int = 0) -> 
     return load().bf_layout_get(_rid(routine), batch, m, n, k)
 
 
-def candidates(routine: str, order: int, batch: int) -> list[int]:
-    """Layouts that have a kernel for this order (leaves the entry at the rule)."""
+def candidates(routine: str, order: int, batch: int, m: int | None = None) -> list[int]:
+    """Layouts that have a kernel for this order (leaves the entry at the rule).
+    gelqf is keyed by its column count; with the row count `m` given, the
+    one-CTA layouts that cannot hold an m x order matrix are left out."""
     lib = load()
     rid = _rid(routine)
     out = [lay for lay in range(1, lib.bf_layout_count(rid)) if lib.bf_layout_set(rid, order, batch, lay) == 0]
     lib.bf_layout_set(rid, order, batch, 0)
+    if routine == "dgelqf" and m is not None and m * order > GELQF_ONE_CTA_MAX_MN:
+        out = [lay for lay in out if LAYOUT_NAMES[routine][lay].startswith("blocked")]
     return out
 
 
@@ -100,7 +107,7 @@ def tune(routine: str, batch: int, m: int, n: int, k: int, run, stream=None, rep
     stream = stream if stream is not None else torch.cuda.current_stream()
     rule = rule_layout(routine, batch, m, n, k)
     times = {}
-    for lay in candidates(routine, order, batch):
+    for lay in candidates(routine, order, batch, m):
         if skip is not None and lay != rule and skip(lay):
             continue
         lib.bf_layout_set(rid, order, batch, lay)

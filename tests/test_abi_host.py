@@ -129,7 +129,8 @@ def test_argument_errors_are_reported_before_launch(lib):
     # sizes beyond what the factorization kernels implement
     big = _desc(600, 600)
     assert lib.bf_dgetrf_batched(1, 513, r(big), 0, 0, 0, r(big), 0, 0, 0, ip, 0, None, None) == _abi.BF_ERR_UNSUPPORTED
-    assert lib.bf_dgelqf_batched(1, 129, 128, r(big), 0, 0, 0, r(big), 0, 0, 0, ip, 0, None) == _abi.BF_ERR_UNSUPPORTED
+    assert lib.bf_dgelqf_batched(1, 513, 40, r(big), 0, 0, 0, r(big), 0, 0, 0, ip, 0, None) == _abi.BF_ERR_UNSUPPORTED
+    assert lib.bf_dgelqf_batched(1, 30, 600, r(big), 0, 0, 0, r(big), 0, 0, 0, ip, 0, None) == _abi.BF_ERR_UNSUPPORTED
     assert lib.bf_dpotrf_l_batched(1, 600, r(big), 0, 0, 0, r(big), 0, 0, 0, None, 0, None, None) == _abi.BF_ERR_UNSUPPORTED
 
 
@@ -306,9 +307,10 @@ def test_single_problem_pack_reports_its_own_positions(lib):
 def test_layout_table(lib):
     # the autotuner's hook: candidates per routine, refused where a layout has
     # no kernel for the order, and the rule restored by layout 0 / reset
-    assert [lib.bf_layout_count(r) for r in range(6)] == [4, 4, 11, 5, 11, 4]
-    assert lib.bf_layout_count(6) == 0
-    assert lib.bf_layout_set(6, 24, 128, 1) == -1
+    assert [lib.bf_layout_count(r) for r in range(7)] == [4, 4, 11, 5, 11, 5, 5]
+    assert lib.bf_layout_count(7) == 0
+    assert lib.bf_layout_set(7, 24, 128, 1) == -1
+    assert lib.bf_layout_set(6, 513, 128, 3) == _abi.BF_ERR_UNSUPPORTED  # blocked gelqf: n <= 512
     assert lib.bf_layout_set(5, 129, 128, 2) == _abi.BF_ERR_UNSUPPORTED  # getrf in shared memory: n <= 128
     assert lib.bf_layout_set(5, 513, 128, 3) == _abi.BF_ERR_UNSUPPORTED  # blocked getrf: n <= 512
     assert lib.bf_layout_set(2, -1, 128, 1) == -2
@@ -336,6 +338,13 @@ def test_layout_table(lib):
         assert lib.bf_layout_get(5, 64, 200, 0, 0) == 3
         assert lib.bf_layout_set(5, 100, 64, 3) == 0
         assert lib.bf_layout_get(5, 64, 100, 0, 0) == 3
+        assert lib.bf_layout_get(6, 64, 16, 16, 0) == 1      # gelqf rule: warp, rows, blocked
+        assert lib.bf_layout_get(6, 64, 80, 80, 0) == 2
+        assert lib.bf_layout_get(6, 64, 128, 128, 0) == 4
+        assert lib.bf_layout_get(6, 64, 200, 200, 0) == 4
+        assert lib.bf_layout_set(6, 200, 64, 2) == 0         # forced, but 300 x 200 has no one-CTA kernel
+        assert lib.bf_layout_get(6, 64, 300, 200, 0) == 4
+        assert lib.bf_layout_get(6, 64, 20, 200, 0) == 2
     finally:
         lib.bf_layout_reset()
     assert lib.bf_layout_get(3, 128, 24, 24, 0) == lib.bf_layout_get(3, 129, 24, 24, 0)

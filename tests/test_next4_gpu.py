@@ -184,7 +184,7 @@ def test_getrf_nan_entries_follow_the_oracles_pivot_rule(n):
 # so every layout is checked against the oracle on the same inputs.
 
 GETRF = 5
-LU_WARP, LU_ROWS, LU_BLOCKED = 1, 2, 3
+LU_WARP, LU_ROWS, LU_BLOCKED, LU_BLOCKED16 = 1, 2, 3, 4
 
 
 def _getrf_forced(lay, n, bt, *args, **kw):
@@ -198,7 +198,7 @@ def _getrf_forced(lay, n, bt, *args, **kw):
 
 
 @pytest.mark.parametrize("n", [2, 31, 32, 33, 63, 64, 65, 100, 128])
-@pytest.mark.parametrize("lay", [LU_WARP, LU_ROWS, LU_BLOCKED])
+@pytest.mark.parametrize("lay", [LU_WARP, LU_ROWS, LU_BLOCKED, LU_BLOCKED16])
 def test_getrf_every_layout_matches_oracle(lay, n):
     bt = 5
     A = inputs.normal((bt, n, n), 1900 + n)
@@ -227,7 +227,7 @@ def _int_lu(n, rng, zero_at=None):
     return (L @ U).astype(float), L, U
 
 
-@pytest.mark.parametrize("n,forced", [(40, True), (136, False), (200, False)])
+@pytest.mark.parametrize("n,forced", [(40, LU_BLOCKED), (136, 0), (200, 0), (150, LU_BLOCKED16)])
 def test_blocked_getrf_integer_exact_and_zero_pivot(n, forced):
     rng = np.random.default_rng(7 + n)
     As, Ls, Us = zip(*[_int_lu(n, rng) for _ in range(3)])
@@ -239,7 +239,7 @@ def test_blocked_getrf_integer_exact_and_zero_pivot(n, forced):
     info = torch.full((bt,), -7, dtype=torch.int32, device="cuda")
     args = (put(A, 3, 2), 3, 2, dD, 3, 1, ipiv)
     if forced:
-        _getrf_forced(LU_BLOCKED, n, bt, *args, info=info)
+        _getrf_forced(forced, n, bt, *args, info=info)
     else:
         bf.dgetrf(n, *args, info=info)
     whole = get(dD)
@@ -306,9 +306,10 @@ def test_blocked_getrf_full_size_sampled():
 # -------------------------------------------------------------------- gelqf
 
 @pytest.mark.parametrize("m,n", [(1, 1), (3, 5), (8, 8), (12, 20), (20, 12), (31, 31), (33, 40), (40, 3), (64, 64),
-                                 (100, 160), (200, 60), (2, 4000)])
+                                 (100, 160), (200, 60), (2, 4000), (129, 128), (192, 192), (256, 256), (300, 100),
+                                 (100, 300), (40, 500), (161, 33)])
 def test_gelqf_matches_oracle(m, n):
-    bt = 9 if m * n <= 1600 else 3
+    bt = 9 if m * n <= 1600 else (3 if m * n <= 16384 else 2)
     A = inputs.normal((bt, m, n), 1600 + m + n)
     dD = bf.DMatBatch(bt, m, n)
     k = min(m, n)
@@ -324,6 +325,73 @@ def test_gelqf_matches_oracle(m, n):
         Lfull = np.zeros((m, n))
         Lfull[:, :k] = np.tril(F[b])[:, :k]
         assert np.linalg.norm(Lfull @ Q - A[b].numpy()) <= 1e-13 * n * np.linalg.norm(A[b].numpy())
+
+
+GELQF = 6
+LQ_WARP, LQ_ROWS, LQ_BLOCKED, LQ_BLOCKED16 = 1, 2, 3, 4
+
+
+@pytest.mark.parametrize("m,n", [(5, 9), (33, 40), (40, 33), (64, 64), (100, 120), (128, 128)])
+@pytest.mark.parametrize("lay", [LQ_WARP, LQ_ROWS, LQ_BLOCKED, LQ_BLOCKED16])
+def test_gelqf_every_layout_matches_oracle(lay, m, n):
+    """The blocked form (panels of 32 rows, block reflector on the rows
+    below) forced at sizes the one-CTA kernels also take."""
+    bt = 4
+    A = inputs.normal((bt, m, n), 2100 + m + n)
+    dD = bf.DMatBatch(bt, m, n, fill=np.nan)
+    k = min(m, n)
+    tau = torch.full((bt, k), np.nan, dtype=torch.float64, device="cuda")
+    lib = bf.load()
+    assert lib.bf_layout_set(GELQF, n, bt, lay) == 0
+    try:
+        bf.dgelqf(m, n, put(A), 0, 0, dD, 0, 0, tau)
+        torch.cuda.synchronize()
+    finally:
+        lib.bf_layout_set(GELQF, n, bt, 0)
+    F, t = get(dD), tau.cpu().numpy()
+    for b in range(bt):
+        Fo, to = oracle.dgelqf(A[b].numpy())
+        assert np.linalg.norm(F[b] - Fo) <= 1e-12 * np.linalg.norm(Fo), lay
+        assert np.allclose(t[b], to, rtol=1e-12, atol=1e-15), lay
+
+
+@pytest.mark.parametrize("m,n", [(200, 200), (150, 260)])
+def test_blocked_gelqf_in_place_with_offsets(m, n):
+    """In place at a sub-matrix offset off a panel top; the rest untouched;
+    the zero tail of a rank-deficient block gives tau = 0 there."""
+    bt = 2
+    A = inputs.normal((bt, m, n), 2200 + m).numpy().copy()
+    A[1, 40:72, :] = 0.0  # a whole panel of zero rows in problem 1
+    At = torch.from_numpy(A)
+    dA = put(At, 3, 1, fill=-2.0)
+    tau = torch.full((bt, min(m, n)), np.nan, dtype=torch.float64, device="cuda")
+    bf.dgelqf(m, n, dA, 3, 1, dA, 3, 1, tau)
+    whole = get(dA)
+    for b in range(bt):
+        Fo, to = oracle.dgelqf(A[b])
+        assert np.linalg.norm(whole[b, 3:, 1:] - Fo) <= 1e-12 * np.linalg.norm(Fo)
+        assert np.allclose(tau[b].cpu().numpy(), to, rtol=1e-12, atol=1e-15)
+    assert np.all(whole[:, :3, :] == -2.0) and np.all(whole[:, :, :1] == -2.0)
+
+
+def test_blocked_gelqf_full_size_sampled():
+    """The bench's largest gelqf workload (512 problems of order 256, one
+    call): sampled problems against the oracle, and L L^T = A A^T (Q is
+    orthogonal) for every problem."""
+    bt, n = 512, 256
+    A = inputs.normal((bt, n, n), 2300)
+    dD = bf.DMatBatch(bt, n, n)
+    tau = torch.zeros((bt, n), dtype=torch.float64, device="cuda")
+    bf.dgelqf(n, n, put(A), 0, 0, dD, 0, 0, tau)
+    F, t = get(dD), tau.cpu().numpy()
+    for b in (0, 1, 300, 511):
+        Fo, to = oracle.dgelqf(A[b].numpy())
+        assert np.linalg.norm(F[b] - Fo) <= 1e-12 * np.linalg.norm(Fo)
+        assert np.allclose(t[b], to, rtol=1e-12, atol=1e-15)
+    L = torch.from_numpy(np.tril(F))
+    G = torch.bmm(A, A.transpose(1, 2))
+    res = torch.linalg.matrix_norm(torch.bmm(L, L.transpose(1, 2)) - G) / torch.linalg.matrix_norm(G)
+    assert float(res.max()) <= 1e-13 * n
 
 
 @pytest.mark.parametrize("n", [12, 64])
