@@ -1319,7 +1319,8 @@ def next4_flops(routine: str, n: int) -> float:
 
 
 NEXT4_POINTS = [("dgemm_nn", 64, 4096), ("dtrmm_rlnn", 64, 4096), ("dgetrf", 16, 65536), ("dgetrf", 64, 8192),
-                ("dgetrf", 128, 2048), ("dgelqf", 16, 65536), ("dgelqf", 64, 8192), ("dgelqf", 128, 2048)]
+                ("dgetrf", 128, 2048), ("dgetrf", 192, 1024), ("dgetrf", 256, 512), ("dgelqf", 16, 65536),
+                ("dgelqf", 64, 8192), ("dgelqf", 128, 2048), ("dgelqf", 192, 1024), ("dgelqf", 256, 512)]
 
 
 def run_next4(args, dev):
@@ -1330,7 +1331,7 @@ def run_next4(args, dev):
     import torch
 
     import paper_1704_02457_gb300 as bf
-    from paper_1704_02457_gb300 import inputs
+    from paper_1704_02457_gb300 import inputs, tune
 
     stream = torch.cuda.current_stream()
     out = {}
@@ -1365,6 +1366,8 @@ def run_next4(args, dev):
         g = bt * next4_flops(r, n) / (ms * 1e-3) / 1e9
         out[f"{r}@{n}"] = {"batch": bt, "ms": round(ms, 4), "gflops": round(g, 2),
                            "frac_of_fp64_alu_peak": round(g / FP64_PEAK_GFLOPS, 4)}
+        if r in tune.ROUTINE_IDS:
+            out[f"{r}@{n}"]["layout"] = tune.LAYOUT_NAMES[r][tune.current_layout(r, bt, n, n, 0)]
         del A, D
         torch.cuda.empty_cache()
     return out
