@@ -1395,6 +1395,7 @@ def run_vbatched(args, dev, batch=4096, nmin=8, nmax=128):
     D = bf.DMatBatch(batch, nmax, nmax, device=dev, tight=True)
     info = torch.zeros(batch, dtype=torch.int32, device=dev)
     status = torch.zeros(batch, dtype=torch.int32, device=dev)
+    vorder = torch.zeros(batch, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
     calls = {}
     # the records in generation order, and sorted by decreasing order (a
@@ -1412,6 +1413,14 @@ def run_vbatched(args, dev, batch=4096, nmin=8, nmax=128):
         calls["dsyrk_dpotrf_ln" + tag] = (
             lambda sizes=sizes, rA=rA, rQ=rQ, rD=rD: bf.dsyrk_dpotrf_ln_vbatched(
                 batch, sizes, rA, rA, rQ, rD, nmax, info=info, status=status, stream=stream),
+            float(sum(flops("dsyrk_dpotrf_ln", int(n)) for n in ns)))
+        # the ordered form: the records sorted by size on the device (inside
+        # the timed call), then problems of one size class sharing a CTA
+        calls["dsyrk_dpotrf_ln_ordered" + tag] = (
+            lambda sizes=sizes, rA=rA, rQ=rQ, rD=rD: (
+                bf.vbatched_order(batch, sizes, nmax, vorder, stream=stream),
+                bf.dsyrk_dpotrf_ln_vbatched_ordered(batch, sizes, vorder, rA, rA, rQ, rD, nmax, info=info,
+                                                    status=status, stream=stream)),
             float(sum(flops("dsyrk_dpotrf_ln", int(n)) for n in ns)))
     out = {}
     for name, (fn, fl) in calls.items():
@@ -1431,7 +1440,9 @@ def run_vbatched(args, dev, batch=4096, nmin=8, nmax=128):
     out["status_all_zero"] = bool((status == 0).all())
     out["info_all_zero"] = bool((info == 0).all())
     out["workload"] = ("4096 problems, n ~ U{8..128}, k = n, descriptor-array forms (one launch per routine); "
-                       "_sorted: the same problems, records sorted by decreasing order")
+                       "_sorted: the same problems, records sorted by decreasing order; _ordered: the records "
+                       "sorted by size on the device (bf_vbatched_order, inside the timed call), then the ordered "
+                       "form (problems of one size class sharing a CTA, one launch per class)")
     return out
 
 

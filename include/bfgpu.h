@@ -613,6 +613,35 @@ int bf_dsyrk_dpotrf_ln_vbatched(int batch, const bf_dsize *size, const bf_dsub *
                                 const bf_dsub *C, const bf_dsub *D, int want_dinv, int *info,
                                 int max_m, int *status, void *stream);
 
+/* Order of the records by decreasing size, for the *_vbatched_ordered calls
+ * below: order (device, batch ints, 4-byte aligned) receives a permutation
+ * of 0..batch-1 with size[order[q]].m non-increasing in q (records of equal
+ * m in any order); records whose m is negative or above max_m come first.
+ * One CTA (a counting sort over max_m + 2 keys in shared memory), no
+ * workspace; its time grows with batch / 1024.  max_m <= 512. */
+int bf_vbatched_order(int batch, const bf_dsize *size, int max_m, int *order, void *stream);
+
+/* potrf_l and syrk_potrf_ln per problem, as bf_dpotrf_l_vbatched and
+ * bf_dsyrk_dpotrf_ln_vbatched (same records, checks, status codes, info and
+ * inverse diagonal), with the records taken in the order given by `order`
+ * (device, a permutation of 0..batch-1, e.g. from bf_vbatched_order; NULL:
+ * the records in their own order, which should then be sorted by size).
+ * Consecutive records share a CTA when their sizes are of the same class:
+ * four problems per CTA up to order 64, two up to 256, one above -- one
+ * launch per class present below max_m, each over the whole array.  Sorting
+ * matters: problems of very different orders in one CTA idle the smaller
+ * ones' lanes.  Entries of order outside 0..batch-1 are skipped; an order
+ * that repeats a record computes it twice, concurrently (undefined).
+ * Argument errors: -1 batch, -2 size, -3 order (misaligned), then the
+ * remaining arguments in signature order (-4 ..). */
+int bf_dpotrf_l_vbatched_ordered(int batch, const bf_dsize *size, const int *order, const bf_dsub *C,
+                                 const bf_dsub *D, int want_dinv, int *info, int max_m, int *status,
+                                 void *stream);
+
+int bf_dsyrk_dpotrf_ln_vbatched_ordered(int batch, const bf_dsize *size, const int *order, const bf_dsub *A,
+                                        const bf_dsub *B, const bf_dsub *C, const bf_dsub *D, int want_dinv,
+                                        int *info, int max_m, int *status, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -21,7 +21,8 @@ __all__ = [
     "dgemm_nt", "dsyrk_ln", "dpotrf_l", "dtrsm_rltn", "dsyrk_dpotrf_ln", "pack", "unpack",
     "dpotrs_l", "dposv_mixed", "dposv_mixed_worksize", "dposv_mixed_tc", "dposv_mixed_tc_worksize", "dgemm_nn", "dtrmm_rlnn", "dgetrf", "dgelqf",
     "dsub_records", "dsize_records", "dgemm_nt_vbatched", "dsyrk_ln_vbatched", "dpotrf_l_vbatched",
-    "dtrsm_rltn_vbatched", "dsyrk_dpotrf_ln_vbatched",
+    "dtrsm_rltn_vbatched", "dsyrk_dpotrf_ln_vbatched", "vbatched_order", "dpotrf_l_vbatched_ordered",
+    "dsyrk_dpotrf_ln_vbatched_ordered",
 ]
 
 
@@ -356,3 +357,28 @@ def dsyrk_dpotrf_ln_vbatched(batch, size, A, B, C, D, max_m, want_dinv=False, in
     _check("bf_dsyrk_dpotrf_ln_vbatched", load().bf_dsyrk_dpotrf_ln_vbatched(
         batch, _vp(size), _vp(A), _vp(B), _vp(C), _vp(D), int(want_dinv), _vp(info), max_m, _vp(status),
         _stream(stream)))
+
+
+def vbatched_order(batch, size, max_m, order, stream=None):
+    """order (int32 device tensor, batch) <- the records by decreasing size
+    (bf_vbatched_order)."""
+    _check("bf_vbatched_order", load().bf_vbatched_order(batch, _vp(size), max_m, _vp(order), _stream(stream)))
+
+
+def dpotrf_l_vbatched_ordered(batch, size, order, C, D, max_m, want_dinv=False, info=None, status=None,
+                              stream=None):
+    """dpotrf_l_vbatched with the records taken in `order` (None: their own
+    order), problems of similar size sharing a CTA (bf_dpotrf_l_vbatched_ordered)."""
+    _check("bf_dpotrf_l_vbatched_ordered", load().bf_dpotrf_l_vbatched_ordered(
+        batch, _vp(size), _vp(order), _vp(C), _vp(D), int(want_dinv), _vp(info), max_m, _vp(status),
+        _stream(stream)))
+
+
+def dsyrk_dpotrf_ln_vbatched_ordered(batch, size, order, A, B, C, D, max_m, want_dinv=False, info=None,
+                                     status=None, stream=None):
+    """dsyrk_dpotrf_ln_vbatched with the records taken in `order` (None: their
+    own order), problems of similar size sharing a CTA
+    (bf_dsyrk_dpotrf_ln_vbatched_ordered)."""
+    _check("bf_dsyrk_dpotrf_ln_vbatched_ordered", load().bf_dsyrk_dpotrf_ln_vbatched_ordered(
+        batch, _vp(size), _vp(order), _vp(A), _vp(B), _vp(C), _vp(D), int(want_dinv), _vp(info), max_m,
+        _vp(status), _stream(stream)))

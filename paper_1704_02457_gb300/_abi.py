@@ -88,6 +88,11 @@ SIGNATURES = {
                                         _c_vp]),
     "bf_dsyrk_dpotrf_ln_vbatched": (_c_int, [_c_int, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_int, _c_vp, _c_int,
                                              _c_vp, _c_vp]),
+    "bf_vbatched_order": (_c_int, [_c_int, _c_vp, _c_int, _c_vp, _c_vp]),
+    "bf_dpotrf_l_vbatched_ordered": (_c_int, [_c_int, _c_vp, _c_vp, _c_vp, _c_vp, _c_int, _c_vp, _c_int, _c_vp,
+                                              _c_vp]),
+    "bf_dsyrk_dpotrf_ln_vbatched_ordered": (_c_int, [_c_int, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_int,
+                                                     _c_vp, _c_int, _c_vp, _c_vp]),
     "bf_layout_count": (_c_int, [_c_int]),
     "bf_layout_set": (_c_int, [_c_int, _c_int, _c_int, _c_int]),
     "bf_layout_get": (_c_int, [_c_int, _c_int, _c_int, _c_int, _c_int]),

@@ -649,6 +649,49 @@ int bf_dsyrk_dpotrf_ln_vbatched(int batch, const bf_dsize *size, const bf_dsub *
                               (cudaStream_t)stream));
 }
 
+int bf_vbatched_order(int batch, const bf_dsize *size, int max_m, int *order, void *stream) {
+  if (batch < 0) return -1;
+  if (batch > 0 && !size) return -2;
+  if (max_m < 0) return -3;
+  if (max_m > CHOL_MAX_N) return BF_ERR_UNSUPPORTED;
+  if (batch > 0 && (!order || !aligned_to(order, 4))) return -4;
+  if (batch == 0) return 0;
+  return status(launch_vbatched_order(batch, size, max_m, order, (cudaStream_t)stream));
+}
+
+int bf_dpotrf_l_vbatched_ordered(int batch, const bf_dsize *size, const int *order, const bf_dsub *C,
+                                 const bf_dsub *D, int want_dinv, int *info, int max_m, int *st, void *stream) {
+  if (batch < 0) return -1;
+  if (batch > 0 && !size) return -2;
+  if (order && !aligned_to(order, 4)) return -3;
+  if (batch > 0 && !C) return -4;
+  if (batch > 0 && !D) return -5;
+  if (info && !aligned_to(info, 4)) return -7;
+  if (max_m < 0) return -8;
+  if (max_m > CHOL_MAX_N) return BF_ERR_UNSUPPORTED;
+  if (batch == 0 || max_m == 0) return 0;
+  return status(launch_chol_vp(false, batch, order, size, nullptr, nullptr, C, D, want_dinv != 0, info, max_m, st,
+                               (cudaStream_t)stream));
+}
+
+int bf_dsyrk_dpotrf_ln_vbatched_ordered(int batch, const bf_dsize *size, const int *order, const bf_dsub *A,
+                                        const bf_dsub *B, const bf_dsub *C, const bf_dsub *D, int want_dinv,
+                                        int *info, int max_m, int *st, void *stream) {
+  if (batch < 0) return -1;
+  if (batch > 0 && !size) return -2;
+  if (order && !aligned_to(order, 4)) return -3;
+  if (batch > 0 && !A) return -4;
+  if (batch > 0 && !B) return -5;
+  if (batch > 0 && !C) return -6;
+  if (batch > 0 && !D) return -7;
+  if (info && !aligned_to(info, 4)) return -9;
+  if (max_m < 0) return -10;
+  if (max_m > CHOL_MAX_N) return BF_ERR_UNSUPPORTED;
+  if (batch == 0 || max_m == 0) return 0;
+  return status(launch_chol_vp(true, batch, order, size, A, B, C, D, want_dinv != 0, info, max_m, st,
+                               (cudaStream_t)stream));
+}
+
 // ---------------------------------------------------------------- Riccati
 
 int bf_driccati_sqrt_batched(int batch, int N, const bf_riccati_prob *probs, const int *order,

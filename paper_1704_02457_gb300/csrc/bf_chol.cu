@@ -785,16 +785,23 @@ k_chol_rows4(int batch, int n, int k, Op A, Op B, Op C, OpWT<T> D, T *dinv, long
 // launch of syrk_potrf in two launches (the syrk kernel has formed
 // C + A B^T in D): the record is checked with the fused routine's rules, as
 // the syrk launch checked it, and D is factored in place.
+// With `order`, CTA q takes record order[q], and only when its order m lies
+// in (lo, hi] (or, with report_bad, when its sizes are out of range): the
+// one-problem class of the ordered form.
 template <int BW, bool FUSED, bool AFTER_SYRK = false>
 __global__ void __launch_bounds__(512)
 k_chol_rows_v(int batch, const bf_dsize *size, const bf_dsub *A, const bf_dsub *B, const bf_dsub *C,
-              const bf_dsub *D, int want_dinv, int *info, int max_m, int *status) {
+              const bf_dsub *D, int want_dinv, int *info, int max_m, int *status, const int *order = nullptr,
+              int lo = -1, int hi = CHOL_MAX_N, int report_bad = 1) {
   constexpr bool REC = FUSED || AFTER_SYRK;  // the record has the fused operands
-  const int b = blockIdx.x;
-  if (b >= batch) return;
+  if ((int)blockIdx.x >= batch) return;
+  const int b = order ? order[blockIdx.x] : (int)blockIdx.x;
+  if (b < 0 || b >= batch) return;
   const int m = size[b].m, k = REC ? size[b].k : 0;
+  const bool sized = m >= 0 && k >= 0 && m <= max_m;
+  if (sized ? !(m > lo && m <= hi) : report_bad == 0) return;  // another class's record
   int err = 0;
-  if (m < 0 || k < 0 || m > max_m)
+  if (!sized)
     err = -1;
   else if (m > 0) {
     if (REC && k > 0 && !dsub_ok(A[b], m, k))
@@ -821,6 +828,332 @@ k_chol_rows_v(int batch, const bf_dsize *size, const bf_dsub *A, const bf_dsub *
   double *dv = (want_dinv && dm.dA && D[b].j + m <= min(dm.m, dm.n)) ? dm.dA + D[b].j : nullptr;
   chol_rows_body<BW, 1, FUSED, false, double, BF_ROWS_SPLIT_P1 != 0>(0, 1, m, k, a, bb, c, d, dv, 0,
                                                                     info ? info + b : nullptr);
+}
+
+// ---------------------------------------------------------------------------
+// Descriptor-array Cholesky with P problems per CTA, the records taken in a
+// given order -- best by decreasing size, so that the problems sharing a CTA
+// have similar orders.  Each problem keeps its own sizes and operands; the
+// CTA runs its block columns to the largest order among its problems, and a
+// problem's rows idle once it is done.  The steps are those of rows_block,
+// with the diagonal warp's triangle split (the warp holds BW = 32/P rows of
+// each problem's diagonal block).  On GB300 an FP64 warp instruction costs
+// the same with 1 or 32 active lanes, and one problem per CTA leaves a
+// problem's last warp partly empty; with P problems of similar order per
+// CTA a warp carries 32/P rows of each.
+// ---------------------------------------------------------------------------
+
+// One problem of a CTA (n = 0: an empty slot).
+struct VProb {
+  const double *a, *b, *c;
+  double *d, *dinv;
+  int ai, aj, acn, bi, bj, bcn, ci, cj, ccn, di, dj, dcn;
+  int n, k;
+};
+
+template <int W, int BW, int P, bool FUSED>
+__device__ __forceinline__ void rows_block_vp(RowsSmem<double, BW, P> &S, const VProb *V, const RowMap<P> &rm,
+                                              int c0, int kmax) {
+  constexpr int RPW = RowMap<P>::RPW;
+  const int t = threadIdx.x, T_ = blockDim.x;
+  const int i = rm.i, p = rm.p;
+  const VProb &me = V[p];
+  const int n = me.n;
+  const int w = min(BW, n - c0);
+  const bool active = i < n && i >= c0;
+  const int ir = min(i, max(n - 1, 0));  // a row to address (read only when active)
+  double acc[W];
+  // The warp of the diagonal blocks (BW rows of each of the P problems, a
+  // full warp) computes only the blocks' lower triangles in (a') and (b),
+  // spread over its lanes by split_slot, and gathers its rows before (c), as
+  // the strided kernels do.
+  constexpr int H = BW / 2, NSLOT = H + 1;
+  constexpr bool SPLIT = BF_ROWS_SPLIT && W == BW && BW >= 8;
+  const bool dwarp = SPLIT && (t >> 5) == c0 / RPW;  // warp-uniform
+  const int sb = rm.lane & (BW - 1);                 // row within the diagonal block
+
+  // (a) C[i][c0 + jj] on and below the diagonal (the diagonal warp adds C
+  // when it gathers its rows)
+#pragma unroll
+  for (int jj = 0; jj < W; jj++) {
+    const int col = c0 + jj;
+    acc[jj] = (!dwarp && active && jj < w && i >= col) ? me.c[pm_off(me.ci + i, me.cj + col, me.ccn)] : 0.0;
+  }
+
+  // (a') syrk_potrf: += A[i][:] B[c0..c0+w)[:]^T, B rows of every problem staged per chunk
+  if (FUSED) {
+    const double *arow = me.a + pm_off(me.ai + ir, me.aj, me.acn);
+    for (int l0 = 0; l0 < kmax; l0 += KC) {
+      const int kc = min(KC, kmax - l0);
+      __syncthreads();
+      for (int x = t; x < P * BW * KC; x += T_) {
+        const int px = x / (BW * KC), xr = x - px * (BW * KC);
+        const int r4 = xr % PS, ll = (xr / PS) % KC, pnl = xr / (PS * KC);
+        const int jj = pnl * PS + r4;
+        const VProb &q = V[px];
+        S.stage[px][ll][jj] = (jj < q.n - c0 && ll < kc && ll < q.k - l0)
+                                  ? __ldg(q.b + pm_off(q.bi + c0 + jj, q.bj + l0 + ll, q.bcn))
+                                  : 0.0;
+      }
+      __syncthreads();
+      const int kme = min(kc, me.k - l0);
+      if (dwarp) {
+        const int ro = BW - 1 - sb, smax = min(sb, H);  // slots m <= smax are on the lane's own row
+        const bool own_ok = sb < w, oth_ok = sb <= H - 2 && ro < w;
+        const double *arow_o = me.a + pm_off(me.ai + min(c0 + ro, max(n - 1, 0)), me.aj, me.acn);
+        const int obase = max(0, H - sb);  // other-row slot m reads column H + m - sb
+        for (int ll = 0; ll < kme; ll++) {
+          const double xo = own_ok ? __ldg(arow + (long long)(l0 + ll) * PS) : 0.0;
+          const double xt = oth_ok ? __ldg(arow_o + (long long)(l0 + ll) * PS) : 0.0;
+          const double *st = S.stage[p][ll];
+#pragma unroll
+          for (int m = 0; m < NSLOT; m++) {
+            const bool own = m <= smax;
+            acc[m] = fma(own ? xo : xt, own ? st[m] : st[min(obase + m, BW - 1)], acc[m]);
+          }
+        }
+      } else if (active) {
+        for (int ll = 0; ll < kme; ll++) {
+          const double x = __ldg(arow + (long long)(l0 + ll) * PS);
+#pragma unroll
+          for (int jj = 0; jj < W; jj += 2) {
+            const double2 bv = *(const double2 *)&S.stage[p][ll][jj];
+            acc[jj] = fma(x, bv.x, acc[jj]);
+            if (jj + 1 < W) acc[jj + 1] = fma(x, bv.y, acc[jj + 1]);
+          }
+        }
+      }
+    }
+  }
+
+  // (b) downdate with the columns of L already computed
+  {
+    const double *lrow = me.d + pm_off(me.di + ir, me.dj, me.dcn);
+    for (int l0 = 0; l0 < c0; l0 += KC) {
+      const int kc = min(KC, c0 - l0);
+      __syncthreads();
+      for (int x = t; x < P * BW * KC; x += T_) {
+        const int px = x / (BW * KC), xr = x - px * (BW * KC);
+        const int r4 = xr % PS, ll = (xr / PS) % KC, pnl = xr / (PS * KC);
+        const int jj = pnl * PS + r4;
+        const VProb &q = V[px];
+        S.stage[px][ll][jj] =
+            (jj < q.n - c0 && ll < kc) ? q.d[pm_off(q.di + c0 + jj, q.dj + l0 + ll, q.dcn)] : 0.0;
+      }
+      __syncthreads();
+      if (dwarp) {
+        const int smax = min(sb, H), obase = max(0, H - sb);
+        for (int ll = 0; ll < kc; ll++) {
+          const double *st = S.stage[p][ll];
+          const double xo = st[sb], xt = st[BW - 1 - sb];
+#pragma unroll
+          for (int m = 0; m < NSLOT; m++) {
+            const bool own = m <= smax;
+            acc[m] = fma(-(own ? xo : xt), own ? st[m] : st[min(obase + m, BW - 1)], acc[m]);
+          }
+        }
+      } else if (active) {
+#pragma unroll 2
+        for (int ll = 0; ll < kc; ll++) {
+          const double x = lrow[(long long)(l0 + ll) * PS];
+#pragma unroll
+          for (int jj = 0; jj < W; jj += 2) {
+            const double2 lv = *(const double2 *)&S.stage[p][ll][jj];
+            acc[jj] = fma(-x, lv.x, acc[jj]);
+            if (jj + 1 < W) acc[jj + 1] = fma(-x, lv.y, acc[jj + 1]);
+          }
+        }
+      }
+    }
+  }
+
+  // the diagonal warp: slots to shared memory, then each lane its row, plus C
+  if (dwarp) {
+#pragma unroll
+    for (int m = 0; m < NSLOT; m++) {
+      int row, col;
+      bool ok;
+      split_slot<BW>(sb, m, row, col, ok);
+      if (ok) S.Ls[p][row][col] = acc[m];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int jj = 0; jj < W; jj++) {
+      const bool lower = jj <= sb;
+      const double cv =
+          (sb < w && jj < w && lower) ? me.c[pm_off(me.ci + c0 + sb, me.cj + c0 + jj, me.ccn)] : 0.0;
+      acc[jj] = cv + (lower ? S.Ls[p][sb][jj] : 0.0);
+    }
+    __syncwarp();
+  }
+
+  // (c) diagonal blocks: problem p's rows c0..c0+BW-1 are lanes
+  // p*RPW + (0..BW-1) of warp c0/RPW (BW == RPW), factored in registers
+  const int base = p * RPW + (c0 % RPW);
+  const int dl = rm.lane - base;
+  if ((t >> 5) == c0 / RPW && dl >= 0 && dl < BW) {
+    int bad = 0;
+#pragma unroll
+    for (int j = 0; j < W; j++) {
+      const double d = __shfl_sync(0xffffffffu, acc[j], base + j);
+      const double r = rsqrt(d);
+      if (j < w && !(d > 0.0) && bad == 0) bad = c0 + j + 1;
+      if (dl == j) {
+        acc[j] = d * r;
+        S.rinv[p][j] = r;
+      } else {
+        acc[j] *= r;
+      }
+#pragma unroll
+      for (int jj = j + 1; jj < W; jj++) {
+        const double v = __shfl_sync(0xffffffffu, acc[j], base + jj);
+        acc[jj] = fma(-acc[j], v, acc[jj]);
+      }
+    }
+#pragma unroll
+    for (int jj = 0; jj < W; jj++) S.Ls[p][dl][jj] = acc[jj];
+    if (dl == 0 && bad != 0 && S.bad[p] == 0) S.bad[p] = bad;
+  }
+  __syncthreads();
+
+  // (d) rows below the diagonal block
+  if (active && i >= c0 + BW) {
+#pragma unroll
+    for (int j = 0; j < W; j++) {
+      acc[j] *= S.rinv[p][j];
+#pragma unroll
+      for (int jj = j + 1; jj < W; jj++) acc[jj] = fma(-acc[j], S.Ls[p][jj][j], acc[jj]);
+    }
+  }
+
+  // (e) store the block column, and 1/L_jj
+  if (active) {
+    double *drow = me.d + pm_off(me.di + i, me.dj, me.dcn);
+#pragma unroll
+    for (int jj = 0; jj < W; jj++) {
+      const int col = c0 + jj;
+      if (jj < w && i >= col) drow[(long long)col * PS] = acc[jj];
+    }
+  }
+  if (t < P * BW) {
+    const int px = t / BW, j = t - px * BW;
+    const VProb &q = V[px];
+    if (q.dinv && j < q.n - c0) q.dinv[c0 + j] = S.rinv[px][j];
+  }
+  __syncthreads();
+}
+
+// CTA b takes the records at positions P*b .. P*b + P-1 of `order` (NULL:
+// the records themselves), and of those the ones whose order m lies in
+// (lo, hi]; the launch with report_bad set also reports the records whose
+// sizes are out of range.  Records are checked as in k_chol_rows_v.
+template <int P, int BW, bool FUSED, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB)
+k_chol_rows_vp(int batch, const int *order, const bf_dsize *size, const bf_dsub *A, const bf_dsub *B,
+               const bf_dsub *C, const bf_dsub *D, int want_dinv, int *info, int max_m, int *status, int lo,
+               int hi, int report_bad) {
+  static_assert(BW == 32 / P, "a warp holds one diagonal block of each problem");
+  __shared__ RowsSmem<double, BW, P> S;
+  __shared__ VProb V[P];
+  __shared__ int rec[P];
+  const RowMap<P> rm;
+  const int t = threadIdx.x;
+  if (t < P) {
+    const long long pos = (long long)blockIdx.x * P + t;
+    VProb v{};
+    int r = -1;
+    if (pos < batch) {
+      r = order ? order[pos] : (int)pos;
+      if (r < 0 || r >= batch) r = -1;
+    }
+    int use = -1;
+    if (r >= 0) {
+      const int m = size[r].m, k = FUSED ? size[r].k : 0;
+      const bool sized = m >= 0 && m <= max_m && k >= 0;
+      if (sized ? (m > lo && m <= hi) : report_bad != 0) {
+        int err = sized ? 0 : -1;
+        if (err == 0 && m > 0) {
+          if (FUSED && k > 0 && !dsub_ok(A[r], m, k))
+            err = -2;
+          else if (FUSED && k > 0 && !dsub_ok(B[r], m, k))
+            err = -3;
+          else if (!dsub_ok(C[r], m, m))
+            err = FUSED ? -4 : -2;
+          else if (!dsub_ok(D[r], m, m))
+            err = FUSED ? -5 : -3;
+        }
+        if (status) status[r] = err;
+        if (err == 0 && m == 0 && info) info[r] = 0;
+        if (err == 0 && m > 0) {
+          const bf_dsub &c = C[r], &d = D[r];
+          const bf_dsub &a = (FUSED && k > 0) ? A[r] : c;  // k == 0: A and B are never read
+          const bf_dsub &bb = (FUSED && k > 0) ? B[r] : c;
+          v.a = a.mat.pA; v.ai = a.i; v.aj = a.j; v.acn = a.mat.cn;
+          v.b = bb.mat.pA; v.bi = bb.i; v.bj = bb.j; v.bcn = bb.mat.cn;
+          v.c = c.mat.pA; v.ci = c.i; v.cj = c.j; v.ccn = c.mat.cn;
+          v.d = d.mat.pA; v.di = d.i; v.dj = d.j; v.dcn = d.mat.cn;
+          // the inverse-diagonal array holds min(m, n) entries of its matrix
+          v.dinv = (want_dinv && d.mat.dA && d.j + m <= min(d.mat.m, d.mat.n)) ? d.mat.dA + d.j : nullptr;
+          v.n = m;
+          v.k = k;
+          use = r;
+        }
+      }
+    }
+    V[t] = v;
+    rec[t] = use;
+    S.bad[t] = 0;
+  }
+  __syncthreads();
+  int nmax = 0, kmax = 0;
+#pragma unroll
+  for (int q = 0; q < P; q++) {
+    nmax = max(nmax, V[q].n);
+    kmax = max(kmax, V[q].k);
+  }
+  if (nmax == 0) return;  // CTA-uniform
+  for (int c0 = 0; c0 < nmax; c0 += BW) {
+    if constexpr (BW == 8) {
+      rows_block_vp<8, 8, P, FUSED>(S, V, rm, c0, kmax);
+    } else {
+      if (min(BW, nmax - c0) <= 8)
+        rows_block_vp<8, BW, P, FUSED>(S, V, rm, c0, kmax);
+      else
+        rows_block_vp<16, BW, P, FUSED>(S, V, rm, c0, kmax);
+    }
+  }
+  if (info && t < P && rec[t] >= 0) info[rec[t]] = S.bad[t];
+}
+
+// Counting sort of the records by decreasing order m, on one CTA: a
+// histogram over the keys, the running offsets from the largest key down,
+// then every record takes the next slot of its key (atomically, so records
+// of equal order land in any order).  Out-of-range sizes sort first.
+constexpr int ORDER_T = 1024;
+
+__global__ void __launch_bounds__(ORDER_T) k_vbatched_order(int batch, const bf_dsize *size, int max_m, int *order) {
+  __shared__ int cnt[CHOL_MAX_N + 2];
+  const int nkey = max_m + 2;  // key m for 0 <= m <= max_m, max_m + 1 for out of range
+  for (int x = threadIdx.x; x < nkey; x += ORDER_T) cnt[x] = 0;
+  __syncthreads();
+  for (int b = threadIdx.x; b < batch; b += ORDER_T) {
+    const int m = size[b].m;
+    atomicAdd(&cnt[(m < 0 || m > max_m) ? max_m + 1 : m], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {  // exclusive offsets, largest key first (at most 514 keys)
+    int run = 0;
+    for (int x = nkey - 1; x >= 0; x--) {
+      const int c = cnt[x];
+      cnt[x] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < batch; b += ORDER_T) {
+    const int m = size[b].m;
+    order[atomicAdd(&cnt[(m < 0 || m > max_m) ? max_m + 1 : m], 1)] = b;
+  }
 }
 
 // Block width of k_chol_rows: 16-column blocks halve the work the diagonal
@@ -1244,6 +1577,53 @@ cudaError_t launch_chol_v(bool fused, int batch, const bf_dsize *size, const bf_
     k_chol_rows_v<ROWS_BW, true><<<batch, threads, 0, s>>>(batch, size, A, B, C, D, want_dinv, info, max_m, status);
   else
     k_chol_rows_v<ROWS_BW, false><<<batch, threads, 0, s>>>(batch, size, A, B, C, D, want_dinv, info, max_m, status);
+  return cudaGetLastError();
+}
+
+// The ordered descriptor-array form: one launch per size class, each over
+// the whole array (a CTA skips the records of the other classes): four
+// problems per CTA with 8-column blocks up to order 32 (128 threads) and up
+// to 64 (256 threads), two with 16-column blocks up to 256, one above.  The
+// first launch also reports the records whose sizes are out of range.
+cudaError_t launch_chol_vp(bool fused, int batch, const int *order, const bf_dsize *size, const bf_dsub *A,
+                           const bf_dsub *B, const bf_dsub *C, const bf_dsub *D, bool want_dinv, int *info,
+                           int max_m, int *status, cudaStream_t s) {
+  const int wd = want_dinv ? 1 : 0;
+  const unsigned g4 = (unsigned)((batch + 3) / 4), g2 = (unsigned)((batch + 1) / 2);
+#define BF_VP(P_, BW_, MAXT_, MINB_, grid, threads, lo, hi, bad)                                                \
+  do {                                                                                                         \
+    if (fused)                                                                                                 \
+      k_chol_rows_vp<P_, BW_, true, MAXT_, MINB_><<<grid, threads, 0, s>>>(batch, order, size, A, B, C, D, wd,  \
+                                                                          info, max_m, status, lo, hi, bad);    \
+    else                                                                                                       \
+      k_chol_rows_vp<P_, BW_, false, MAXT_, MINB_><<<grid, threads, 0, s>>>(batch, order, size, A, B, C, D, wd, \
+                                                                           info, max_m, status, lo, hi, bad);   \
+  } while (0)
+  // register bounds that leave the two-problem class without spills
+  BF_VP(4, 8, 128, 8, g4, 128, -1, 32, 1);
+  if (max_m > 32) BF_VP(4, 8, 256, 4, g4, 256, 32, 64, 0);
+  if (max_m > 64) {
+    const int threads = ((std::min(max_m, 256) + 15) / 16) * 32;
+    if (threads <= 256)
+      BF_VP(2, 16, 256, 2, g2, threads, 64, 256, 0);
+    else
+      BF_VP(2, 16, 512, 1, g2, threads, 64, 256, 0);
+  }
+#undef BF_VP
+  if (max_m > 256) {
+    const int threads = ((max_m + 31) / 32) * 32;
+    if (fused)
+      k_chol_rows_v<ROWS_BW, true><<<batch, threads, 0, s>>>(batch, size, A, B, C, D, wd, info, max_m, status,
+                                                              order, 256, CHOL_MAX_N, 0);
+    else
+      k_chol_rows_v<ROWS_BW, false><<<batch, threads, 0, s>>>(batch, size, A, B, C, D, wd, info, max_m, status,
+                                                               order, 256, CHOL_MAX_N, 0);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vbatched_order(int batch, const bf_dsize *size, int max_m, int *order, cudaStream_t s) {
+  k_vbatched_order<<<1, ORDER_T, 0, s>>>(batch, size, max_m, order);
   return cudaGetLastError();
 }
 

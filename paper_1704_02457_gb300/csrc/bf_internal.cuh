@@ -149,6 +149,13 @@ cudaError_t launch_gemm_nt_v(bool syrk, int batch, const bf_dsize *size, double 
 cudaError_t launch_chol_v(bool fused, int batch, const bf_dsize *size, const bf_dsub *A, const bf_dsub *B,
                           const bf_dsub *C, const bf_dsub *D, bool want_dinv, int *info, int max_m, int *status,
                           cudaStream_t s);
+// The ordered form (records taken in `order`, NULL: their own order; P
+// problems of similar size per CTA) and the counting sort that gives the
+// order by decreasing size.
+cudaError_t launch_chol_vp(bool fused, int batch, const int *order, const bf_dsize *size, const bf_dsub *A,
+                           const bf_dsub *B, const bf_dsub *C, const bf_dsub *D, bool want_dinv, int *info,
+                           int max_m, int *status, cudaStream_t s);
+cudaError_t launch_vbatched_order(int batch, const bf_dsize *size, int max_m, int *order, cudaStream_t s);
 cudaError_t launch_trsm_rltn_v(int batch, const bf_dsize *size, double alpha, const bf_dsub *L, bool use_dinv,
                                const bf_dsub *B, const bf_dsub *D, int max_m, int max_n, int *status,
                                cudaStream_t s);

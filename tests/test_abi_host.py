@@ -304,6 +304,28 @@ def test_single_problem_pack_reports_its_own_positions(lib):
     assert lib.bf_unpack_dmat(8, 0, None, 0, 0, None, 0, None) == 0
 
 
+def test_ordered_vbatched_argument_checks(lib):
+    # host-side argument checks of the ordered descriptor-array forms and of
+    # the device sort: refused before any launch (no device pointer is read)
+    p = ctypes.c_void_p(0x10000)
+    odd = ctypes.c_void_p(0x10002)
+    assert lib.bf_vbatched_order(-1, p, 8, p, None) == -1
+    assert lib.bf_vbatched_order(4, None, 8, p, None) == -2
+    assert lib.bf_vbatched_order(4, p, -1, p, None) == -3
+    assert lib.bf_vbatched_order(4, p, 513, p, None) == _abi.BF_ERR_UNSUPPORTED
+    assert lib.bf_vbatched_order(4, p, 8, odd, None) == -4
+    assert lib.bf_vbatched_order(0, None, 8, None, None) == 0
+    assert lib.bf_dpotrf_l_vbatched_ordered(4, p, odd, p, p, 0, None, 8, None, None) == -3
+    assert lib.bf_dpotrf_l_vbatched_ordered(4, p, None, None, p, 0, None, 8, None, None) == -4
+    assert lib.bf_dpotrf_l_vbatched_ordered(4, p, None, p, p, 0, odd, 8, None, None) == -7
+    assert lib.bf_dpotrf_l_vbatched_ordered(4, p, None, p, p, 0, None, 600, None, None) == _abi.BF_ERR_UNSUPPORTED
+    assert lib.bf_dsyrk_dpotrf_ln_vbatched_ordered(4, p, None, p, None, p, p, 0, None, 8, None, None) == -5
+    assert lib.bf_dsyrk_dpotrf_ln_vbatched_ordered(4, p, None, p, p, p, p, 0, odd, 8, None, None) == -9
+    assert lib.bf_dsyrk_dpotrf_ln_vbatched_ordered(4, p, None, p, p, p, p, 0, None, -2, None, None) == -10
+    assert lib.bf_dsyrk_dpotrf_ln_vbatched_ordered(0, None, None, None, None, None, None, 0, None, 8, None,
+                                                   None) == 0
+
+
 def test_layout_table(lib):
     # the autotuner's hook: candidates per routine, refused where a layout has
     # no kernel for the order, and the rule restored by layout 0 / reset

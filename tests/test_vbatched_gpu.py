@@ -258,3 +258,175 @@ def _syrk_potrf_bad_records(rng, nb, max_m):
         if b != 5:
             assert inf[b] == 0
             assert np.linalg.norm(np.tril(got) - np.tril(want[b][0])) <= 1e-12 * np.linalg.norm(want[b][0])
+
+
+# ------------------------------------------------ ordered forms (P per CTA)
+#
+# bf_vbatched_order sorts the records by decreasing size on the device; the
+# *_vbatched_ordered calls take the records in that order, problems of one
+# size class sharing a CTA (four up to order 64, two up to 256, one above).
+# The results and reports are those of the unordered forms; with no order
+# (records in their own, unsorted order) they stay correct.
+
+def test_vbatched_order_is_a_decreasing_permutation():
+    rng = np.random.default_rng(40)
+    for batch, max_m in ((1, 8), (37, 40), (5000, 300)):
+        ms = rng.integers(0, max_m + 1, size=batch)
+        ms[::7] = -3            # out of range: first
+        ms[1::11] = max_m + 5
+        sizes = bf.dsize_records([(int(m), 0, 0) for m in ms])
+        order = torch.full((batch,), -1, dtype=torch.int32, device="cuda")
+        bf.vbatched_order(batch, sizes, max_m, order)
+        o = order.cpu().numpy()
+        assert np.array_equal(np.sort(o), np.arange(batch))
+        key = np.where((ms < 0) | (ms > max_m), max_m + 1, ms)[o]
+        assert np.all(np.diff(key) <= 0)
+
+
+def _ordered_case(rng, nb, max_m, fused):
+    """Problems of orders spread over every size class up to max_m (integer
+    factors with power-of-two diagonals, so that every class computes the
+    factor exactly), and one record above max_m."""
+    sizes, A, C, D, want = [], [], [], [], []
+    classes = [c for c in (0, 5, 16, 31, 32, 33, 47, 64, 65, 100, 128, 129, 200, 256, 257, 300) if c <= max_m]
+    for b in range(nb):
+        m = int(classes[b % len(classes)]) if b < len(classes) else int(rng.integers(0, max_m + 1))
+        k = int(rng.integers(1, 12)) if fused else 0
+        L = inputs.int_lower_pow2(1, m, 900 + b)[0].numpy() if m else np.zeros((0, 0))
+        if fused:
+            M = ints(rng, (m, k), -2, 2)
+            Q = L @ L.T - M @ M.T    # C + M M^T = L L^T, exact in FP64
+            A.append(put(M, b % 3, 1))
+        else:
+            Q = L @ L.T
+        C.append(put(Q, 1, b % 2))
+        D.append(blank(m, m, b % 4, 0, fill=np.nan))
+        sizes.append((m, 0, k))
+        want.append(L)
+    sizes[2] = (max_m + 3, 0, sizes[2][2])
+    return sizes, A, C, D, want, {2: -1}
+
+
+@pytest.mark.parametrize("fused", [False, True])
+@pytest.mark.parametrize("max_m,nb,sort", [(40, 60, True), (128, 300, True), (300, 40, True), (128, 90, False)])
+def test_ordered_forms_match_the_oracle(fused, max_m, nb, sort):
+    rng = np.random.default_rng(41 + max_m)
+    sizes, A, C, D, want, bads = _ordered_case(rng, nb, max_m, fused)
+    sz = bf.dsize_records(sizes)
+    order = None
+    if sort:
+        order = torch.empty((nb,), dtype=torch.int32, device="cuda")
+        bf.vbatched_order(nb, sz, max_m, order)
+    info = torch.full((nb,), -7, dtype=torch.int32, device="cuda")
+    status = torch.full((nb,), 99, dtype=torch.int32, device="cuda")
+    Cr = bf.dsub_records([(X, 0, 1, b % 2) for b, X in enumerate(C)])
+    Dr = bf.dsub_records([(X, 0, b % 4, 0) for b, X in enumerate(D)])
+    if fused:
+        Ar = bf.dsub_records([(X, 0, b % 3, 1) for b, X in enumerate(A)])
+        bf.dsyrk_dpotrf_ln_vbatched_ordered(nb, sz, order, Ar, Ar, Cr, Dr, max_m, want_dinv=True, info=info,
+                                            status=status)
+    else:
+        bf.dpotrf_l_vbatched_ordered(nb, sz, order, Cr, Dr, max_m, want_dinv=True, info=info, status=status)
+    st, inf = status.cpu().numpy(), info.cpu().numpy()
+    for b in range(nb):
+        got = get(D[b])
+        if b in bads:
+            assert st[b] == bads[b] and inf[b] == -7
+            assert np.all(np.isnan(got))
+            continue
+        m, o = sizes[b][0], b % 4
+        assert st[b] == 0 and inf[b] == 0, (b, m, st[b], inf[b])
+        blk = got[o:o + m, :m]
+        assert np.array_equal(np.tril(blk), want[b]), (b, m)
+        assert np.all(np.isnan(blk[np.triu(np.ones((m, m), dtype=bool), 1)]))
+        rest = np.ones(got.shape, dtype=bool)
+        rest[o:o + m, :m] = False
+        assert np.all(np.isnan(got[rest]))
+
+
+@pytest.mark.parametrize("fused", [False, True])
+def test_ordered_forms_report_like_the_unordered(fused):
+    """Bad records and failing pivots in every size class: the same status
+    and info as the unordered call, the refused outputs untouched."""
+    rng = np.random.default_rng(43)
+    nb, max_m = 24, 150
+    sizes, A, C = [], [], []
+    for b in range(nb):
+        m = [3, 20, 40, 60, 90, 150][b % 6]
+        k = 5 if fused else 0
+        M = rng.standard_normal((m, k))
+        Q = m * np.eye(m)
+        if b % 5 == 1:
+            Q[m // 2, m // 2] = -1e6
+        sizes.append((m, 0, k))
+        A.append(put(M, 0, 0))
+        C.append(put(Q, 0, 0))
+    c_rec = [(X, 0, 0, 0) for X in C]
+    c_rec[7] = (C[7], 0, 3, 0)      # C's rows run past the matrix
+    sizes[13] = (-1, 0, 5)
+    runs = {}
+    for ordered in (False, True):
+        Dc = [blank(max(s[0], 1), max(s[0], 1), fill=np.nan) for s in sizes]
+        dr = [(X, 0, 0, 0) for X in Dc]
+        dr[10] = (Dc[10], 0, 0, 5)  # D's columns run past the matrix
+        info = torch.full((nb,), -7, dtype=torch.int32, device="cuda")
+        status = torch.full((nb,), 99, dtype=torch.int32, device="cuda")
+        sz = bf.dsize_records(sizes)
+        Cr, Dr = bf.dsub_records(c_rec), bf.dsub_records(dr)
+        Ar = bf.dsub_records([(X, 0, 0, 0) for X in A])
+        if ordered:
+            order = torch.empty((nb,), dtype=torch.int32, device="cuda")
+            bf.vbatched_order(nb, sz, max_m, order)
+            if fused:
+                bf.dsyrk_dpotrf_ln_vbatched_ordered(nb, sz, order, Ar, Ar, Cr, Dr, max_m, info=info, status=status)
+            else:
+                bf.dpotrf_l_vbatched_ordered(nb, sz, order, Cr, Dr, max_m, info=info, status=status)
+        elif fused:
+            bf.dsyrk_dpotrf_ln_vbatched(nb, sz, Ar, Ar, Cr, Dr, max_m, info=info, status=status)
+        else:
+            bf.dpotrf_l_vbatched(nb, sz, Cr, Dr, max_m, info=info, status=status)
+        runs[ordered] = (status.cpu().numpy(), info.cpu().numpy(), [get(X) for X in Dc])
+    st0, inf0, D0 = runs[False]
+    st1, inf1, D1 = runs[True]
+    assert np.array_equal(st0, st1) and np.array_equal(inf0, inf1)
+    assert st1[7] == (-4 if fused else -2) and st1[10] == (-5 if fused else -3) and st1[13] == -1
+    assert all(inf1[b] > 0 for b in range(nb) if b % 5 == 1 and st1[b] == 0)
+    for b in range(nb):
+        if st1[b] != 0:
+            assert np.all(np.isnan(D1[b]))
+        elif inf1[b] == 0:
+            m = sizes[b][0]
+            assert np.allclose(np.tril(D1[b][:m, :m]), np.tril(D0[b][:m, :m]), rtol=1e-13, atol=1e-13)
+
+
+def test_ordered_full_size_workload():
+    """The bench's descriptor-array workload (4096 problems, n ~ U{8..128},
+    k = n, 128 x 128 slots), sorted on the device: sampled problems against
+    the oracle, info and status zero for all."""
+    batch, nmax = 4096, 128
+    rng = np.random.default_rng(14000)
+    ns = rng.integers(8, nmax + 1, size=batch)
+    dev = torch.device("cuda")
+    A = bf.DMatBatch.from_colmajor(inputs.normal((batch, nmax, nmax), 14001, dev), tight=True)
+    Q = torch.zeros(batch, nmax, nmax, dtype=torch.float64, device=dev)
+    Q.diagonal(dim1=1, dim2=2).copy_(torch.from_numpy(np.repeat(ns[:, None], nmax, 1)).to(dev).double())
+    Qd = bf.DMatBatch.from_colmajor(Q, tight=True)
+    del Q
+    D = bf.DMatBatch(batch, nmax, nmax, device=dev, tight=True)
+    sz = bf.dsize_records([(int(n), int(n), int(n)) for n in ns], device=dev)
+    rec = lambda M: bf.dsub_records([(M, b, 0, 0) for b in range(batch)], device=dev)  # noqa: E731
+    rA, rQ, rD = rec(A), rec(Qd), rec(D)
+    order = torch.empty((batch,), dtype=torch.int32, device=dev)
+    info = torch.full((batch,), -7, dtype=torch.int32, device=dev)
+    status = torch.full((batch,), 99, dtype=torch.int32, device=dev)
+    bf.vbatched_order(batch, sz, nmax, order)
+    bf.dsyrk_dpotrf_ln_vbatched_ordered(batch, sz, order, rA, rA, rQ, rD, nmax, info=info, status=status)
+    torch.cuda.synchronize()
+    assert np.all(info.cpu().numpy() == 0) and np.all(status.cpu().numpy() == 0)
+    Acm, Dcm, Qcm = A.to_colmajor(), D.to_colmajor(), Qd.to_colmajor()
+    for b in (0, 1, 2047, 4095) + tuple(int(x) for x in np.argsort(ns)[:2]):
+        n = int(ns[b])
+        M = Acm[b, :n, :n].cpu().numpy()
+        Lo, _, _ = oracle.dsyrk_dpotrf_ln(M, M, Qcm[b, :n, :n].cpu().numpy())
+        got = np.tril(Dcm[b, :n, :n].cpu().numpy())
+        assert np.linalg.norm(got - np.tril(Lo)) <= 1e-12 * np.linalg.norm(Lo), (b, n)
