@@ -1442,7 +1442,7 @@ def run_vbatched(args, dev, batch=4096, nmin=8, nmax=128):
     out["workload"] = ("4096 problems, n ~ U{8..128}, k = n, descriptor-array forms (one launch per routine); "
                        "_sorted: the same problems, records sorted by decreasing order; _ordered: the records "
                        "sorted by size on the device (bf_vbatched_order, inside the timed call), then the ordered "
-                       "form (problems of one size class sharing a CTA, one launch per class)")
+                       "form (two problems of neighbouring sizes per CTA, one launch)")
     return out
 
 

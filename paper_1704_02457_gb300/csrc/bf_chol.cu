@@ -1580,10 +1580,10 @@ cudaError_t launch_chol_v(bool fused, int batch, const bf_dsize *size, const bf_
   return cudaGetLastError();
 }
 
-// The ordered descriptor-array form: one launch per size class, each over
-// the whole array (a CTA skips the records of the other classes): four
-// problems per CTA with 8-column blocks up to order 32 (128 threads) and up
-// to 64 (256 threads), two with 16-column blocks up to 256, one above.  The
+// The ordered descriptor-array form: one launch for the orders up to 256
+// (four problems per CTA with 8-column blocks when max_m <= 64, else two
+// with 16-column blocks), and one problem per CTA above 256 (a second launch
+// over the whole array; each CTA skips the records of the other class).  The
 // first launch also reports the records whose sizes are out of range.
 cudaError_t launch_chol_vp(bool fused, int batch, const int *order, const bf_dsize *size, const bf_dsub *A,
                            const bf_dsub *B, const bf_dsub *C, const bf_dsub *D, bool want_dinv, int *info,
@@ -1599,15 +1599,20 @@ cudaError_t launch_chol_vp(bool fused, int batch, const int *order, const bf_dsi
       k_chol_rows_vp<P_, BW_, false, MAXT_, MINB_><<<grid, threads, 0, s>>>(batch, order, size, A, B, C, D, wd, \
                                                                            info, max_m, status, lo, hi, bad);   \
   } while (0)
-  // register bounds that leave the two-problem class without spills
-  BF_VP(4, 8, 128, 8, g4, 128, -1, 32, 1);
-  if (max_m > 32) BF_VP(4, 8, 256, 4, g4, 256, 32, 64, 0);
-  if (max_m > 64) {
+  // One launch for all orders up to 256, so that the small problems' CTAs
+  // (latency-bound: few FP64 instructions each) run beside the large ones
+  // instead of after them: four problems per CTA when max_m <= 64, else two.
+  // Register bounds that leave the two-problem build without spills.
+  if (max_m <= 32) {
+    BF_VP(4, 8, 128, 8, g4, 128, -1, 256, 1);
+  } else if (max_m <= 64) {
+    BF_VP(4, 8, 256, 4, g4, 256, -1, 256, 1);
+  } else {
     const int threads = ((std::min(max_m, 256) + 15) / 16) * 32;
     if (threads <= 256)
-      BF_VP(2, 16, 256, 2, g2, threads, 64, 256, 0);
+      BF_VP(2, 16, 256, 2, g2, threads, -1, 256, 1);
     else
-      BF_VP(2, 16, 512, 1, g2, threads, 64, 256, 0);
+      BF_VP(2, 16, 512, 1, g2, threads, -1, 256, 1);
   }
 #undef BF_VP
   if (max_m > 256) {

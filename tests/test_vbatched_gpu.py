@@ -263,8 +263,9 @@ def _syrk_potrf_bad_records(rng, nb, max_m):
 # ------------------------------------------------ ordered forms (P per CTA)
 #
 # bf_vbatched_order sorts the records by decreasing size on the device; the
-# *_vbatched_ordered calls take the records in that order, problems of one
-# size class sharing a CTA (four up to order 64, two up to 256, one above).
+# *_vbatched_ordered calls take the records in that order, consecutive
+# problems sharing a CTA (four when max_m <= 64, else two up to order 256,
+# one above).
 # The results and reports are those of the unordered forms; with no order
 # (records in their own, unsorted order) they stay correct.
 
@@ -308,7 +309,8 @@ def _ordered_case(rng, nb, max_m, fused):
 
 
 @pytest.mark.parametrize("fused", [False, True])
-@pytest.mark.parametrize("max_m,nb,sort", [(40, 60, True), (128, 300, True), (300, 40, True), (128, 90, False)])
+@pytest.mark.parametrize("max_m,nb,sort", [(30, 40, True), (40, 60, True), (128, 300, True), (300, 40, True),
+                                            (128, 90, False)])
 def test_ordered_forms_match_the_oracle(fused, max_m, nb, sort):
     rng = np.random.default_rng(41 + max_m)
     sizes, A, C, D, want, bads = _ordered_case(rng, nb, max_m, fused)
