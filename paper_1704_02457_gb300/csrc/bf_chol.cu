@@ -1602,7 +1602,9 @@ cudaError_t launch_chol_vp(bool fused, int batch, const int *order, const bf_dsi
   // One launch for all orders up to 256, so that the small problems' CTAs
   // (latency-bound: few FP64 instructions each) run beside the large ones
   // instead of after them: four problems per CTA when max_m <= 64, else two.
-  // Register bounds that leave the two-problem build without spills.
+  // Register bounds: 64 a thread.  On 4096 problems of order U{8..128} the
+  // two-problem build measured 724 (128 registers, two CTAs per SM), 822
+  // (85, three), 935 (64, four; a few spills) and 905 GFLOP/s (51, five).
   if (max_m <= 32) {
     BF_VP(4, 8, 128, 8, g4, 128, -1, 256, 1);
   } else if (max_m <= 64) {
@@ -1610,9 +1612,9 @@ cudaError_t launch_chol_vp(bool fused, int batch, const int *order, const bf_dsi
   } else {
     const int threads = ((std::min(max_m, 256) + 15) / 16) * 32;
     if (threads <= 256)
-      BF_VP(2, 16, 256, 2, g2, threads, -1, 256, 1);
+      BF_VP(2, 16, 256, 4, g2, threads, -1, 256, 1);
     else
-      BF_VP(2, 16, 512, 1, g2, threads, -1, 256, 1);
+      BF_VP(2, 16, 512, 2, g2, threads, -1, 256, 1);
   }
 #undef BF_VP
   if (max_m > 256) {
