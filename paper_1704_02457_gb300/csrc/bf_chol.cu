@@ -1580,6 +1580,16 @@ cudaError_t launch_chol_v(bool fused, int batch, const bf_dsize *size, const bf_
   return cudaGetLastError();
 }
 
+// Problems per SM below which the ordered form keeps one problem per CTA
+// (the records still in the given order): two per CTA halve the CTAs, and
+// a small batch then leaves SMs short of warps.  Measured on orders
+// U{8..128}, sorted records, GFLOP/s one per CTA / two per CTA: 1024
+// problems 499 / 465, 1536 696 / 617, 2048 710 / 712, 3072 718 / 937, 4096
+// 723 / 936.
+#ifndef BF_CHOL_VP_MIN_BATCH_PER_SM
+#define BF_CHOL_VP_MIN_BATCH_PER_SM 12
+#endif
+
 // The ordered descriptor-array form: one launch for the orders up to 256
 // (four problems per CTA with 8-column blocks when max_m <= 64, else two
 // with 16-column blocks), and one problem per CTA above 256 (a second launch
@@ -1589,6 +1599,17 @@ cudaError_t launch_chol_vp(bool fused, int batch, const int *order, const bf_dsi
                            const bf_dsub *B, const bf_dsub *C, const bf_dsub *D, bool want_dinv, int *info,
                            int max_m, int *status, cudaStream_t s) {
   const int wd = want_dinv ? 1 : 0;
+  if ((long long)batch < (long long)BF_CHOL_VP_MIN_BATCH_PER_SM * device_sm_count()) {
+    // too few problems to pair: one per CTA, in the given order
+    const int threads = ((max_m + 31) / 32) * 32;
+    if (fused)
+      k_chol_rows_v<ROWS_BW, true><<<batch, threads, 0, s>>>(batch, size, A, B, C, D, wd, info, max_m, status,
+                                                              order, -1, CHOL_MAX_N, 1);
+    else
+      k_chol_rows_v<ROWS_BW, false><<<batch, threads, 0, s>>>(batch, size, A, B, C, D, wd, info, max_m, status,
+                                                               order, -1, CHOL_MAX_N, 1);
+    return cudaGetLastError();
+  }
   const unsigned g4 = (unsigned)((batch + 3) / 4), g2 = (unsigned)((batch + 1) / 2);
 #define BF_VP(P_, BW_, MAXT_, MINB_, grid, threads, lo, hi, bad)                                                \
   do {                                                                                                         \

@@ -432,3 +432,64 @@ def test_ordered_full_size_workload():
         Lo, _, _ = oracle.dsyrk_dpotrf_ln(M, M, Qcm[b, :n, :n].cpu().numpy())
         got = np.tril(Dcm[b, :n, :n].cpu().numpy())
         assert np.linalg.norm(got - np.tril(Lo)) <= 1e-12 * np.linalg.norm(Lo), (b, n)
+
+
+@pytest.mark.parametrize("fused", [False, True])
+@pytest.mark.parametrize("max_m", [24, 40, 128, 200, 300])
+def test_ordered_forms_paired_batches_exact(fused, max_m):
+    """Batches large enough for problems to share CTAs (more than 12 per SM):
+    2400 problems of orders 0..max_m (integer factors with power-of-two
+    diagonals: every layout computes them exactly), one record out of range.
+    max_m 24 and 40: four per CTA; 128 and 200: two per CTA (256 and 512
+    threads); 300: two per CTA plus the one-problem class above 256."""
+    nb, kmax = 2400, 9
+    rng = np.random.default_rng(2000 + max_m)
+    ms = rng.integers(0, max_m + 1, size=nb)
+    ms[:5] = [0, 1, max_m, max_m // 2, 16]
+    ks = rng.integers(0, kmax + 1, size=nb) if fused else np.zeros(nb, dtype=int)
+    L = inputs.int_lower_pow2(nb, max_m, 3000 + max_m)
+    mask = torch.from_numpy(np.arange(max_m)[None, :] < ms[:, None])
+    L = L * mask[:, :, None] * mask[:, None, :]
+    S = torch.bmm(L, L.transpose(1, 2))
+    if fused:
+        M = torch.from_numpy(ints(rng, (nb, max_m, kmax), -2, 2))
+        M = M * mask[:, :, None] * torch.from_numpy(np.arange(kmax)[None, :] < ks[:, None])[:, None, :]
+        S = S - torch.bmm(M, M.transpose(1, 2))
+    ms_rec = ms.copy()
+    ms_rec[7] = max_m + 1                      # out of range: status -1, untouched
+    dev = torch.device("cuda")
+    dC = bf.DMatBatch(nb, max_m + 1, max_m, device=dev)
+    bf.pack(S.to(dev).transpose(1, 2).contiguous(), dC, 1, 0)
+    dD = bf.DMatBatch(nb, max_m, max_m + 2, fill=np.nan, device=dev)
+    Cr = bf.dsub_records([(dC, b, 1, 0) for b in range(nb)], device=dev)
+    Dr = bf.dsub_records([(dD, b, 0, 2) for b in range(nb)], device=dev)
+    sz = bf.dsize_records([(int(m), 0, int(k)) for m, k in zip(ms_rec, ks)], device=dev)
+    order = torch.empty((nb,), dtype=torch.int32, device=dev)
+    info = torch.full((nb,), -7, dtype=torch.int32, device=dev)
+    status = torch.full((nb,), 99, dtype=torch.int32, device=dev)
+    bf.vbatched_order(nb, sz, max_m, order)
+    if fused:
+        dA = bf.DMatBatch(nb, max_m, kmax, device=dev)
+        bf.pack(M.to(dev).transpose(1, 2).contiguous(), dA)
+        Ar = bf.dsub_records([(dA, b, 0, 0) for b in range(nb)], device=dev)
+        bf.dsyrk_dpotrf_ln_vbatched_ordered(nb, sz, order, Ar, Ar, Cr, Dr, max_m, info=info, status=status)
+    else:
+        bf.dpotrf_l_vbatched_ordered(nb, sz, order, Cr, Dr, max_m, info=info, status=status)
+    torch.cuda.synchronize()
+    st, inf = status.cpu().numpy(), info.cpu().numpy()
+    assert st[7] == -1 and inf[7] == -7
+    ok = np.arange(nb) != 7
+    assert np.all(st[ok] == 0) and np.all(inf[ok] == 0)
+    got = dD.to_colmajor().cpu().numpy()
+    Ln = L.numpy()
+    assert np.all(np.isnan(got[7]))
+    for b in np.flatnonzero(ok):
+        m = ms[b]
+        blk = got[b, :m, 2:2 + m]
+        assert np.array_equal(np.tril(blk), Ln[b, :m, :m]), (b, m)
+        assert np.all(np.isnan(blk[np.triu(np.ones((m, m), dtype=bool), 1)]))
+    rest = np.ones(got.shape[1:], dtype=bool)
+    for b in np.flatnonzero(ok)[:50]:
+        r = rest.copy()
+        r[:ms[b], 2:2 + ms[b]] = False
+        assert np.all(np.isnan(got[b][r]))
