@@ -626,10 +626,10 @@ int bf_vbatched_order(int batch, const bf_dsize *size, int max_m, int *order, vo
  * inverse diagonal), with the records taken in the order given by `order`
  * (device, a permutation of 0..batch-1, e.g. from bf_vbatched_order; NULL:
  * the records in their own order, which should then be sorted by size).
- * Consecutive records share a CTA: four problems per CTA when max_m <= 64,
- * else two for the orders up to 256 (one launch), and one per CTA above 256
- * (a second launch); below 12 problems per SM, one problem per CTA in the
- * given order.  Sorting matters: problems of very different orders in one
+ * Consecutive records share a CTA: four problems per CTA when max_m <= 64
+ * (or <= 128 from 24 problems per SM), else two for the orders up to 256
+ * (one launch), and one per CTA above 256 (a second launch); below 12
+ * problems per SM, one problem per CTA in the given order.  Sorting matters: problems of very different orders in one
  * CTA idle the smaller ones' lanes.  Entries of order outside 0..batch-1 are skipped; an order
  * that repeats a record computes it twice, concurrently (undefined).
  * Argument errors: -1 batch, -2 size, -3 order (misaligned), then the

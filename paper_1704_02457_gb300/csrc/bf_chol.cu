@@ -1586,15 +1586,27 @@ cudaError_t launch_chol_v(bool fused, int batch, const bf_dsize *size, const bf_
 // U{8..128}, sorted records, GFLOP/s one per CTA / two per CTA: 1024
 // problems 499 / 465, 1536 696 / 617, 2048 710 / 712, 3072 718 / 937, 4096
 // 723 / 936.
+// Four problems per CTA (8 rows of each per warp: a problem's last warp
+// wastes at most 7 rows' lanes instead of 15) also for max_m up to 128, at
+// 512 threads and 64 registers, from 24 problems per SM.  Measured on
+// orders U{8..128}, sorted, GFLOP/s two / four per CTA: 2048 problems
+// 712 / 632, 3072 937 / 926, 4096 936 / 994.
+#ifndef BF_CHOL_VP_P4_MAX_M
+#define BF_CHOL_VP_P4_MAX_M 128
+#endif
+#ifndef BF_CHOL_VP_P4_MIN_BATCH_PER_SM
+#define BF_CHOL_VP_P4_MIN_BATCH_PER_SM 24
+#endif
 #ifndef BF_CHOL_VP_MIN_BATCH_PER_SM
 #define BF_CHOL_VP_MIN_BATCH_PER_SM 12
 #endif
 
 // The ordered descriptor-array form: one launch for the orders up to 256
-// (four problems per CTA with 8-column blocks when max_m <= 64, else two
-// with 16-column blocks), and one problem per CTA above 256 (a second launch
-// over the whole array; each CTA skips the records of the other class).  The
-// first launch also reports the records whose sizes are out of range.
+// (four problems per CTA with 8-column blocks when max_m <= 64, or <= 128 in
+// large batches, else two with 16-column blocks), and one problem per CTA
+// above 256 (a second launch over the whole array; each CTA skips the
+// records of the other class).  The first launch also reports the records
+// whose sizes are out of range.
 cudaError_t launch_chol_vp(bool fused, int batch, const int *order, const bf_dsize *size, const bf_dsub *A,
                            const bf_dsub *B, const bf_dsub *C, const bf_dsub *D, bool want_dinv, int *info,
                            int max_m, int *status, cudaStream_t s) {
@@ -1630,6 +1642,9 @@ cudaError_t launch_chol_vp(bool fused, int batch, const int *order, const bf_dsi
     BF_VP(4, 8, 128, 8, g4, 128, -1, 256, 1);
   } else if (max_m <= 64) {
     BF_VP(4, 8, 256, 4, g4, 256, -1, 256, 1);
+  } else if (max_m <= BF_CHOL_VP_P4_MAX_M &&
+             (long long)batch >= (long long)BF_CHOL_VP_P4_MIN_BATCH_PER_SM * device_sm_count()) {
+    BF_VP(4, 8, 512, 2, g4, ((max_m + 7) / 8) * 32, -1, 256, 1);
   } else {
     const int threads = ((std::min(max_m, 256) + 15) / 16) * 32;
     if (threads <= 256)

@@ -435,14 +435,16 @@ def test_ordered_full_size_workload():
 
 
 @pytest.mark.parametrize("fused", [False, True])
-@pytest.mark.parametrize("max_m", [24, 40, 128, 200, 300])
-def test_ordered_forms_paired_batches_exact(fused, max_m):
-    """Batches large enough for problems to share CTAs (more than 12 per SM):
-    2400 problems of orders 0..max_m (integer factors with power-of-two
-    diagonals: every layout computes them exactly), one record out of range.
-    max_m 24 and 40: four per CTA; 128 and 200: two per CTA (256 and 512
-    threads); 300: two per CTA plus the one-problem class above 256."""
-    nb, kmax = 2400, 9
+@pytest.mark.parametrize("max_m,nb", [(24, 2400), (40, 2400), (128, 2400), (100, 3700), (200, 2400), (300, 2400)])
+def test_ordered_forms_paired_batches_exact(fused, max_m, nb):
+    """Batches large enough for problems to share CTAs (more than 12 per SM
+    on a 152-SM GB300): problems of orders 0..max_m (integer factors with
+    power-of-two diagonals: every layout computes them exactly), one record
+    out of range.  max_m 24 and 40: four per CTA; 128 and 200: two per CTA
+    (256 and 512 threads); 100 with 3700 problems (more than 24 per SM):
+    four per CTA at 512 threads; 300: two per CTA plus the one-problem class
+    above 256."""
+    kmax = 9
     rng = np.random.default_rng(2000 + max_m)
     ms = rng.integers(0, max_m + 1, size=nb)
     ms[:5] = [0, 1, max_m, max_m // 2, 16]
