@@ -36,6 +36,26 @@ __device__ __forceinline__ long long pivot_key(double x) {
   return a > 0x7ff0000000000000LL ? -1LL : a;
 }
 
+// The scalars of the reflector that annihilates x, from alpha and
+// ss = ||x||^2 > 0: beta = -sign(alpha) sqrt(alpha^2 + ss), tau = (beta -
+// alpha) / beta and scal = 1 / (alpha - beta), by one reciprocal square
+// root and one reciprocal instead of a square root and two divisions (the
+// sequential part of each row, which on GB300 costs a warp the same FP64
+// issue time whatever its active lanes).  With s = alpha^2 + ss and
+// r = 1/sqrt(s): beta = -sign(alpha) s r, tau = 1 + |alpha| r, and
+// alpha - beta = sign(alpha) (|alpha| + s r).  The reciprocal is the
+// library's (rcp.approx refined by two Newton steps): a row whose
+// |alpha| + ||(alpha, x)|| is subnormal gives NaN.
+__device__ __forceinline__ void reflector_scalars(double alpha, double ss, double &beta, double &tau, double &scal) {
+  const double s = fma(alpha, alpha, ss);
+  const double r = rsqrt(s);
+  const double rt = s * r;
+  const double sg = copysign(1.0, alpha);
+  beta = -sg * rt;
+  tau = fma(fabs(alpha), r, 1.0);
+  scal = sg * recip_newton(fabs(alpha) + rt);
+}
+
 // whole m x n matrices of the warp's problems in and out of shared memory
 template <int Q>
 __device__ __forceinline__ void load_all(double *sm, int b0, int batch, int m, int n, const Op &C) {
@@ -147,9 +167,8 @@ k_gelqf(int batch, int m, int n, Op C, OpW D, double *tau, long long stau) {
     double t = 0.0;
     __syncwarp();
     if (ss != 0.0) {
-      const double beta = -copysign(sqrt(fma(alpha, alpha, ss)), alpha);
-      t = (beta - alpha) / beta;
-      const double scal = 1.0 / (alpha - beta);
+      double beta, scal;
+      reflector_scalars(alpha, ss, beta, t, scal);
       for (int c = i + 1 + s; c < n; c += G) A_(i, c) *= scal;
       if (s == 0) A_(i, i) = beta;
     }
@@ -580,9 +599,8 @@ k_gelqf_rows(int m, int n, int ld, Op C, OpW D, double *tau, long long stau) {
       double tv = 0.0;
       __syncwarp();
       if (ss != 0.0) {
-        const double beta = -copysign(sqrt(fma(alpha, alpha, ss)), alpha);
-        tv = (beta - alpha) / beta;
-        const double scal = 1.0 / (alpha - beta);
+        double beta, scal;
+        reflector_scalars(alpha, ss, beta, tv, scal);
         for (int c = i + 1 + t; c < n; c += 32) sm[c * ld + i] *= scal;
         if (t == 0) sm[i * ld + i] = beta;
       }
