@@ -134,6 +134,31 @@ __host__ __device__ __forceinline__ bool dsub_ok(const bf_dsub &s, int rows, int
 __device__ __forceinline__ Op dsub_op(const bf_dsub &s) { return Op{s.mat.pA, 0, s.mat.cn, s.i, s.j}; }
 __device__ __forceinline__ OpW dsub_opw(const bf_dsub &s) { return OpW{s.mat.pA, 0, s.mat.cn, s.i, s.j}; }
 
+// Programmatic dependent launch (griddepcontrol, sm_90 and later).  A kernel
+// launched by launch_pdl may be scheduled while the kernel before it on the
+// stream is still running; pdl_wait() returns once that kernel has completed
+// and its writes are visible, so it comes before the first access to memory
+// another kernel may have written.  pdl_allow() lets the next such kernel be
+// scheduled once every CTA of this one has called it (or exited).  Both are
+// no-ops in a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_allow() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 // 8-byte asynchronous global -> shared copy (cp.async, bypasses registers)
 __device__ __forceinline__ void cp_async8(double *dst, const double *src) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);

@@ -123,6 +123,7 @@ k_chol_lat(int n, int k, Op A, Op B, Op C, OpW D, double *dinv, long long sdinv,
   const double *crow = lane < n ? row_base(C, b, lane) : nullptr;
   const double *arow = FUSED && lane < n && k > 0 ? row_base(A, b, lane) : nullptr;
   const double *brow = FUSED && lane < n && k > 0 ? row_base(B, b, lane) : nullptr;
+  pdl_wait();  // launched as a programmatic dependent: the previous kernel's writes first
   for (int j = warp; j < n; j += LAT_T / 32)
     if (lane < n && lane >= j) cp_async8(&S[lane * LP + j], crow + PS * j);
   auto stage = [&](int l0, int kc) {
@@ -280,6 +281,7 @@ k_chol_lat(int n, int k, Op A, Op B, Op C, OpW D, double *dinv, long long sdinv,
     for (int r = 0; r < RO; r++)
       if (tid + LAT_OFF * r < nod) *elem(D, b, ei[r], em[r]) = v[r] * rs[em[r]];
   }
+  pdl_allow();  // the next kernel may be scheduled once every CTA is here
 }
 
 // NB: the order rounded up to the instantiated width; R lanes per row.
@@ -302,6 +304,7 @@ k_trsm_lat(int m, int n, double alpha, Op L, const double *dinv, long long sdinv
   // L's lower triangle (a warp per column, a lane per row) and the inverse
   // diagonal go to shared memory asynchronously while the rows of B load
   const double *lrow = lane < n ? row_base(L, b, lane) : nullptr;
+  pdl_wait();  // launched as a programmatic dependent: the previous kernel's writes first
   for (int j = warp; j < n; j += LAT_T / 32)
     if (lane < n && lane >= j) cp_async8(&Ls[lane * PITCH + j], lrow + PS * j);
   if (dinv)
@@ -352,6 +355,7 @@ k_trsm_lat(int m, int n, double alpha, Op L, const double *dinv, long long sdinv
       if (c < n) drow[PS * c] = t[s] * dv[c];
     }
   }
+  pdl_allow();  // the next kernel may be scheduled once every CTA is here
 }
 
 template <int NB, int R>
@@ -361,8 +365,8 @@ cudaError_t launch_trsm_lat_nb(int batch, int m, int n, double alpha, Op L, cons
   const int chunks = (m + ROWS - 1) / ROWS;
   const long long blocks = (long long)batch * chunks;
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-  k_trsm_lat<NB, R><<<(unsigned)blocks, LAT_T, 0, s>>>(m, n, alpha, L, dinv, sdinv, B, D, chunks);
-  return cudaGetLastError();
+  return launch_pdl(k_trsm_lat<NB, R>, dim3((unsigned)blocks), dim3(LAT_T), 0, s, m, n, alpha, L, dinv, sdinv, B, D,
+                    chunks);
 }
 
 template <int R>
@@ -381,15 +385,11 @@ constexpr int CHOL_LAT_MAX_N = LAT_N;
 template <bool FUSED>
 cudaError_t launch_chol_lat_f(int batch, int n, int k, Op A, Op B, Op C, OpW D, double *dinv, long long sdinv,
                               int *info, cudaStream_t s) {
-  if (n <= 8)
-    k_chol_lat<FUSED, 8><<<(unsigned)batch, LAT_T, 0, s>>>(n, k, A, B, C, D, dinv, sdinv, info);
-  else if (n <= 16)
-    k_chol_lat<FUSED, 16><<<(unsigned)batch, LAT_T, 0, s>>>(n, k, A, B, C, D, dinv, sdinv, info);
-  else if (n <= 24)
-    k_chol_lat<FUSED, 24><<<(unsigned)batch, LAT_T, 0, s>>>(n, k, A, B, C, D, dinv, sdinv, info);
-  else
-    k_chol_lat<FUSED, 32><<<(unsigned)batch, LAT_T, 0, s>>>(n, k, A, B, C, D, dinv, sdinv, info);
-  return cudaGetLastError();
+  const dim3 grid((unsigned)batch), block(LAT_T);
+  if (n <= 8) return launch_pdl(k_chol_lat<FUSED, 8>, grid, block, 0, s, n, k, A, B, C, D, dinv, sdinv, info);
+  if (n <= 16) return launch_pdl(k_chol_lat<FUSED, 16>, grid, block, 0, s, n, k, A, B, C, D, dinv, sdinv, info);
+  if (n <= 24) return launch_pdl(k_chol_lat<FUSED, 24>, grid, block, 0, s, n, k, A, B, C, D, dinv, sdinv, info);
+  return launch_pdl(k_chol_lat<FUSED, 32>, grid, block, 0, s, n, k, A, B, C, D, dinv, sdinv, info);
 }
 
 cudaError_t launch_chol_lat(bool fused, int batch, int n, int k, Op A, Op B, Op C, OpW D, double *dinv,
