@@ -1634,7 +1634,8 @@ cudaError_t launch_chol_vp(bool fused, int batch, const int *order, const bf_dsi
   } while (0)
   // One launch for all orders up to 256, so that the small problems' CTAs
   // (latency-bound: few FP64 instructions each) run beside the large ones
-  // instead of after them: four problems per CTA when max_m <= 64, else two.
+  // instead of after them: four problems per CTA when max_m <= 64 (or <= 128
+  // from BF_CHOL_VP_P4_MIN_BATCH_PER_SM problems per SM), else two.
   // Register bounds: 64 a thread.  On 4096 problems of order U{8..128} the
   // two-problem build measured 724 (128 registers, two CTAs per SM), 822
   // (85, three), 935 (64, four; a few spills) and 905 GFLOP/s (51, five).
