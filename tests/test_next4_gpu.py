@@ -419,3 +419,36 @@ def test_getrf_gelqf_in_place_with_offsets(n):
         assert np.linalg.norm(whole[b, 1:, :] - Fo) <= 1e-12 * np.linalg.norm(Fo)
         assert np.allclose(tau[b].cpu().numpy(), to, rtol=1e-12, atol=1e-15)
     assert np.all(whole[:, :1, :] == -1.0)
+
+
+def test_blocked_getrf_gelqf_at_the_maximum_order():
+    """Order 512, the largest the blocked forms take (getrf: panels of up to
+    512 rows on 512 threads; gelqf: 16-row panels of 512 columns), against
+    the oracle; order 513 is refused."""
+    bt, n = 2, 512
+    A = inputs.normal((bt, n, n), 2400)
+    dD = bf.DMatBatch(bt, n, n)
+    ipiv = torch.full((bt, n), -1, dtype=torch.int32, device="cuda")
+    info = torch.full((bt,), -7, dtype=torch.int32, device="cuda")
+    bf.dgetrf(n, put(A), 0, 0, dD, 0, 0, ipiv, info=info)
+    LU, piv = get(dD), ipiv.cpu().numpy()
+    assert np.all(info.cpu().numpy() == 0)
+    for b in range(bt):
+        LUo, pivo, _ = oracle.dgetrf(A[b].numpy())
+        assert np.array_equal(piv[b], pivo)
+        assert np.linalg.norm(LU[b] - LUo) <= 1e-12 * np.linalg.norm(LUo)
+    dF = bf.DMatBatch(bt, n, n)
+    tau = torch.zeros((bt, n), dtype=torch.float64, device="cuda")
+    bf.dgelqf(n, n, put(A), 0, 0, dF, 0, 0, tau)
+    F, t = get(dF), tau.cpu().numpy()
+    for b in range(bt):
+        Fo, to = oracle.dgelqf(A[b].numpy())
+        assert np.linalg.norm(F[b] - Fo) <= 1e-12 * np.linalg.norm(Fo)
+        assert np.allclose(t[b], to, rtol=1e-12, atol=1e-15)
+        L = np.tril(F[b])
+        G = A[b].numpy() @ A[b].numpy().T
+        assert np.linalg.norm(L @ L.T - G) <= 1e-13 * n * np.linalg.norm(G)
+    big = bf.DMatBatch(1, n + 1, n + 1)
+    with pytest.raises(bf.BfError) as err:
+        bf.dgetrf(n + 1, big, 0, 0, big, 0, 0, torch.zeros((1, n + 1), dtype=torch.int32, device="cuda"))
+    assert err.value.code == bf.BF_ERR_UNSUPPORTED
