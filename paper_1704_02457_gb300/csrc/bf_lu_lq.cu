@@ -628,10 +628,15 @@ k_gelqf_rows(int m, int n, int ld, Op C, OpW D, double *tau, long long stau) {
         if (ok) {
           const double tw = tv * w;
           if (sub == 0) sm[i * ld + r] -= tw;
-          for (int c = i + 1 + sub; c < n; c += S) {
-            const double y = fma(-tw, sm[c * ld + i], sm[c * ld + r]);
-            sm[c * ld + r] = y;
-            if (c >= i + 2) nx = fma(y, y, nx);
+          if (it == 0 && t < 32) {  // the warp of row i+1 (group 0): also the next norm
+            for (int c = i + 1 + sub; c < n; c += S) {
+              const double y = fma(-tw, sm[c * ld + i], sm[c * ld + r]);
+              sm[c * ld + r] = y;
+              if (c >= i + 2) nx = fma(y, y, nx);
+            }
+          } else {  // an FP64 instruction costs a warp the same for any active lanes:
+                    // the other warps skip the squares
+            for (int c = i + 1 + sub; c < n; c += S) sm[c * ld + r] = fma(-tw, sm[c * ld + i], sm[c * ld + r]);
           }
         }
         if (r == i + 1) {  // the first group only; its S lanes share r
@@ -667,6 +672,24 @@ constexpr int LQ_RPC = 128;  // rows of A2 per CTA
 size_t lq_apply_smem(int nb, int nc) {
   const int ldv = nc | 1;
   return ((size_t)nb * ldv + (size_t)(2 * nb + LQ_RB) * (nb + 1)) * sizeof(double);
+}
+
+// One row's columns c, c + 8, ..., c + 8(K-1) of A2 -= W V (columns past nc
+// read a valid V entry and are not stored).
+template <int K>
+__device__ __forceinline__ void lq_update_chunk(double *arow, const double *wrow, const double *Vs, int ldv, int ib,
+                                                int c, int nc) {
+  double acc[K];
+#pragma unroll
+  for (int k = 0; k < K; k++) acc[k] = c + 8 * k < nc ? arow[(c + 8 * k) * PS] : 0.0;
+  for (int s = 0; s < ib; s++) {
+    const double w = wrow[s];
+#pragma unroll
+    for (int k = 0; k < K; k++) acc[k] = fma(-w, Vs[s * ldv + min(c + 8 * k, nc - 1)], acc[k]);
+  }
+#pragma unroll
+  for (int k = 0; k < K; k++)
+    if (c + 8 * k < nc) arow[(c + 8 * k) * PS] = acc[k];
 }
 
 // The apply step for panel i (NB = 16 or 32 rows per panel): CTA (b, y)
@@ -782,28 +805,22 @@ k_gelqf_apply(int m, int n, int i, int ib, OpW D, const double *tau, long long s
 #pragma unroll
     for (int q = 0; q < NQ; q++) Wt[wr * LDT + ws + 8 * q] = u4[q];
     __syncthreads();
-    // A2 <- A2 - W V, thread (row ur, columns uc + 8k of each chunk of 64)
+    // A2 <- A2 - W V, thread (row ur, columns uc + 8k of each chunk of 64);
+    // the last chunk runs only the column groups it has (a warp-uniform
+    // count), so a narrow tail issues no FMAs on padding columns
     const int ur = t >> 3, uc = t & 7;
     if (ur < rows) {
+      double *arow = pd + pm_off(D.i0 + rg + ur, D.j0 + i, D.cn);  // column c at arow + c * PS
       for (int c0 = 0; c0 < nc; c0 += 64) {
-        double acc[8];
-#pragma unroll
-        for (int k = 0; k < 8; k++) {
-          const int c = c0 + uc + 8 * k;
-          acc[k] = c < nc ? at(rg + ur, i + c) : 0.0;
-        }
-        for (int s = 0; s < ib; s++) {
-          const double w = Wt[ur * LDT + s];
-#pragma unroll
-          for (int k = 0; k < 8; k++) {
-            const int c = min(c0 + uc + 8 * k, nc - 1);
-            acc[k] = fma(-w, Vs[s * ldv + c], acc[k]);
-          }
-        }
-#pragma unroll
-        for (int k = 0; k < 8; k++) {
-          const int c = c0 + uc + 8 * k;
-          if (c < nc) at(rg + ur, i + c) = acc[k];
+        switch (min(8, (nc - c0 + 7) >> 3)) {
+          case 8: lq_update_chunk<8>(arow, Wt + ur * LDT, Vs, ldv, ib, c0 + uc, nc); break;
+          case 7: lq_update_chunk<7>(arow, Wt + ur * LDT, Vs, ldv, ib, c0 + uc, nc); break;
+          case 6: lq_update_chunk<6>(arow, Wt + ur * LDT, Vs, ldv, ib, c0 + uc, nc); break;
+          case 5: lq_update_chunk<5>(arow, Wt + ur * LDT, Vs, ldv, ib, c0 + uc, nc); break;
+          case 4: lq_update_chunk<4>(arow, Wt + ur * LDT, Vs, ldv, ib, c0 + uc, nc); break;
+          case 3: lq_update_chunk<3>(arow, Wt + ur * LDT, Vs, ldv, ib, c0 + uc, nc); break;
+          case 2: lq_update_chunk<2>(arow, Wt + ur * LDT, Vs, ldv, ib, c0 + uc, nc); break;
+          default: lq_update_chunk<1>(arow, Wt + ur * LDT, Vs, ldv, ib, c0 + uc, nc); break;
         }
       }
     }
