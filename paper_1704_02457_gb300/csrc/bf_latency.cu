@@ -30,6 +30,8 @@
 //   row's other lanes with a shuffle, and each lane downdates its own later
 //   columns: the substitution merged with the downdate (Sec. 4.6), with the
 //   downdate of a row split over R lanes.
+#include <type_traits>
+
 #include "bf_internal.cuh"
 
 namespace bf {
@@ -53,6 +55,14 @@ __device__ __forceinline__ double recip3(double d) {
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
   const double e = fma(-d, r, 1.0);
   return fma(fma(e, e, e), r, r);
+}
+
+// 1 when x is not zero and its magnitude lies outside 2^-480 .. 2^480
+// (subnormal, inf and NaN included), from the exponent field.
+__device__ __forceinline__ int far_from_one(double x) {
+  const int hi = __double2hiint(x), lo = __double2loint(x);
+  const int e = (hi >> 20) & 0x7ff;
+  return (((hi & 0x7fffffff) | lo) != 0) && (e < 1023 - 480 || e > 1023 + 480);
 }
 
 // Columns of A and B staged per pass of the fused update.
@@ -224,44 +234,62 @@ k_chol_lat(int n, int k, Op A, Op B, Op C, OpW D, double *dinv, long long sdinv,
     dg = start_value(lane, lane);
   }
 
-  // column 0, and 1 / d_0
+  // column 0, and 1 / d_0; whether any entry lies outside 2^-480 .. 2^480
+  // in magnitude (zeros aside), where the square of an entry could leave the
+  // normal range
+  int far = 0;
   if (!diag_warp) {
 #pragma unroll
     for (int r = 0; r < RO; r++)
-      if (tid + LAT_OFF * r < nod && em[r] == 0) colb[0][ei[r]] = v[r];
-  } else if (lane == 0) {
-    iv[0] = recip3(dg);
+      if (tid + LAT_OFF * r < nod) {
+        far |= far_from_one(v[r]);
+        if (em[r] == 0) colb[0][ei[r]] = v[r];
+      }
+  } else if (lane < n) {
+    far = far_from_one(dg);
+    if (lane == 0) iv[0] = recip3(dg);
   }
-  __syncthreads();
+  const bool wide = __syncthreads_or(far) != 0;
 
   // Right-looking, square-root free.  Step j: every owned element (i, m),
   // j < m <= i, takes S[i][m] -= S[i][j] (1/d_j) S[m][j], with column j read
   // from colb; the owners of column j+1 publish it.  The diagonal lanes take
   // S[m][m] -= S[m][j]^2 (1/d_j), and lane j+1, whose pivot is then final,
   // forms 1/d_{j+1} for the next step: the chain from pivot to pivot is two
-  // FP64 operations and one reciprocal, with one barrier per column.
-  for (int j = 0; j + 1 < n; j++) {
-    const double invd = iv[j];
-    const double *cj = colb[j & 1];
-    double *cn = colb[(j + 1) & 1];
-    if (diag_warp) {
-      if (lane > j && lane < n) {
-        const double x = cj[lane];
-        dg = fma(-(x * x), invd, dg);
-        if (lane == j + 1) iv[lane] = recip3(dg);
-      }
-    } else {
-      const int c = (n - j - 1) * (n - j - 2) / 2;
+  // FP64 operations and one reciprocal, with one barrier per column.  The
+  // square S[m][j]^2 is formed before the pivot's reciprocal arrives; a
+  // problem with entries far from unit size (wide) takes
+  // (S[m][j] (1/d_j)) S[m][j] instead, which stays in range as the plain
+  // form's other updates do, at one more FP64 operation on the chain.
+  auto steps = [&](auto wide_tag) {
+    constexpr bool WIDE = decltype(wide_tag)::value;
+    for (int j = 0; j + 1 < n; j++) {
+      const double invd = iv[j];
+      const double *cj = colb[j & 1];
+      double *cn = colb[(j + 1) & 1];
+      if (diag_warp) {
+        if (lane > j && lane < n) {
+          const double x = cj[lane];
+          dg = WIDE ? fma(-(x * invd), x, dg) : fma(-(x * x), invd, dg);
+          if (lane == j + 1) iv[lane] = recip3(dg);
+        }
+      } else {
+        const int c = (n - j - 1) * (n - j - 2) / 2;
 #pragma unroll
-      for (int r = 0; r < RO; r++) {
-        if (tid + LAT_OFF * r < c) {
-          v[r] = fma(-(cj[ei[r]] * invd), cj[em[r]], v[r]);
-          if (em[r] == j + 1) cn[ei[r]] = v[r];
+        for (int r = 0; r < RO; r++) {
+          if (tid + LAT_OFF * r < c) {
+            v[r] = fma(-(cj[ei[r]] * invd), cj[em[r]], v[r]);
+            if (em[r] == j + 1) cn[ei[r]] = v[r];
+          }
         }
       }
+      __syncthreads();
     }
-    __syncthreads();
-  }
+  };
+  if (wide)
+    steps(std::true_type{});
+  else
+    steps(std::false_type{});
 
   // L[i][m] = S[i][m] rsqrt(d_m); dinv = rsqrt(d_m); info = 1 + the first
   // pivot that is not > 0
@@ -284,23 +312,37 @@ k_chol_lat(int n, int k, Op A, Op B, Op C, OpW D, double *dinv, long long sdinv,
   pdl_allow();  // the next kernel may be scheduled once every CTA is here
 }
 
-// NB: the order rounded up to the instantiated width; R lanes per row.
+// NB: the order rounded up to the instantiated width; R lanes per row, a
+// warp holding 32/R rows.
 // The columns of L below the diagonal are scaled by the inverse diagonal in
 // shared memory, L'[c][j] = L[c][j] / L[j][j], so that a lane carries the
-// unscaled t_j = (alpha B - sum_{l<j} X_l L^T_l)_j, the downdate reads
-// t_c -= t_j L'[c][j], and X_j = t_j / L[j][j] is formed once at the end:
-// the chain from one column to the next is one shuffle and one FMA.
+// unscaled t_j = (B - sum_{l<j} X_l L^T_l)_j, the downdate reads
+// t_c -= t_j L'[c][j], and X_j = alpha t_j / L[j][j] is formed once at the
+// end (alpha folded into the inverse diagonal: one product per column of L
+// instead of one per element of B): the chain from one column to the next
+// is one shuffle and one FMA.
 template <int NB, int R>
 __global__ void __launch_bounds__(LAT_T)
 k_trsm_lat(int m, int n, double alpha, Op L, const double *dinv, long long sdinv, Op B, OpW D, int chunks) {
-  constexpr int S = NB / R;          // column slots per lane
-  constexpr int ROWS = LAT_T / R;    // rows per CTA
+  constexpr int S = (NB + R - 1) / R;     // column slots per lane
+  constexpr int RPW = 32 / R;             // rows per warp
+  constexpr int ROWS = (LAT_T / 32) * RPW;  // rows per CTA
   constexpr int PITCH = NB + 1;
+  constexpr int NT = (NB * (NB - 1) / 2 + LAT_T - 1) / LAT_T;  // strictly lower entries per thread
   __shared__ double Ls[NB * PITCH];
-  __shared__ double dv[NB];
+  __shared__ double dv[NB], adv[NB];
   const int b = blockIdx.x / chunks;
   const int row0 = (blockIdx.x % chunks) * ROWS;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nod = n * (n - 1) / 2;
+  // the strictly lower entries this thread scales (a constant table, read
+  // before the wait for the previous kernel)
+  int si[NT], sj[NT];
+#pragma unroll
+  for (int r = 0; r < NT; r++) {
+    si[r] = sj[r] = 0;
+    if (tid + LAT_T * r < nod) off_entry(tid + LAT_T * r, n, si[r], sj[r]);
+  }
   // L's lower triangle (a warp per column, a lane per row) and the inverse
   // diagonal go to shared memory asynchronously while the rows of B load
   const double *lrow = lane < n ? row_base(L, b, lane) : nullptr;
@@ -309,18 +351,18 @@ k_trsm_lat(int m, int n, double alpha, Op L, const double *dinv, long long sdinv
     if (lane < n && lane >= j) cp_async8(&Ls[lane * PITCH + j], lrow + PS * j);
   if (dinv)
     for (int j = tid; j < n; j += LAT_T) cp_async8(&dv[j], dinv + (long long)b * sdinv + j);
+  const int q = lane % R, rw = lane / R;
+  const int row = row0 + warp * RPW + rw;
   // a warp whose rows all lie past m only helps with the set-up
-  const bool warp_rows = row0 + (tid & ~31) / R < m;
-  const int q = tid % R;
-  const int row = row0 + tid / R;
-  const bool active = row < m;
+  const bool warp_rows = row0 + warp * RPW < m;
+  const bool active = rw < RPW && row < m;
   double t[S];
   {
     const double *brow = active ? row_base(B, b, row) : nullptr;
 #pragma unroll
     for (int s = 0; s < S; s++) {
       const int c = q + R * s;
-      t[s] = (active && c < n) ? alpha * brow[PS * c] : 0.0;
+      t[s] = (active && c < n) ? brow[PS * c] : 0.0;
     }
   }
   cp_async_wait_all();
@@ -329,18 +371,18 @@ k_trsm_lat(int m, int n, double alpha, Op L, const double *dinv, long long sdinv
     for (int j = tid; j < n; j += LAT_T) dv[j] = recip3(Ls[j * PITCH + j]);
     __syncthreads();
   }
-  for (int e = tid; e < n * n; e += LAT_T) {
-    const int c = e / n, j = e - c * n;
-    if (c > j) Ls[c * PITCH + j] *= dv[j];
-  }
+#pragma unroll
+  for (int r = 0; r < NT; r++)
+    if (tid + LAT_T * r < nod) Ls[si[r] * PITCH + sj[r]] *= dv[sj[r]];
+  if (tid < n) adv[tid] = alpha * dv[tid];
   __syncthreads();
   if (!warp_rows) return;
 
-  const int base = lane & ~(R - 1);
+  const int base = lane - q;
 #pragma unroll
   for (int j = 0; j < NB; j++) {
     if (j >= n) break;
-    const double x = __shfl_sync(0xffffffffu, t[j / R], base + j % R);
+    const double x = __shfl_sync(0xffffffffu, t[j / R], (base + j % R) & 31);
 #pragma unroll
     for (int s = (j + 1) / R; s < S; s++) {
       const int c = q + R * s;
@@ -352,7 +394,7 @@ k_trsm_lat(int m, int n, double alpha, Op L, const double *dinv, long long sdinv
 #pragma unroll
     for (int s = 0; s < S; s++) {
       const int c = q + R * s;
-      if (c < n) drow[PS * c] = t[s] * dv[c];
+      if (c < n) drow[PS * c] = t[s] * adv[c];
     }
   }
   pdl_allow();  // the next kernel may be scheduled once every CTA is here
@@ -361,7 +403,7 @@ k_trsm_lat(int m, int n, double alpha, Op L, const double *dinv, long long sdinv
 template <int NB, int R>
 cudaError_t launch_trsm_lat_nb(int batch, int m, int n, double alpha, Op L, const double *dinv, long long sdinv,
                                Op B, OpW D, cudaStream_t s) {
-  constexpr int ROWS = LAT_T / R;
+  constexpr int ROWS = (LAT_T / 32) * (32 / R);
   const int chunks = (m + ROWS - 1) / ROWS;
   const long long blocks = (long long)batch * chunks;
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;

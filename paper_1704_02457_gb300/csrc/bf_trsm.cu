@@ -242,16 +242,18 @@ cudaError_t launch_trsm_rltn_v(int batch, const bf_dsize *size, double alpha, co
 
 // The latency kernel (R lanes per row) where one thread per row would
 // leave SM sub-partitions idle: at most BF_TRSM_LAT_ROWS_PER_SM rows of X
-// per SM over the batch, eight lanes per row for orders above 24 with at
+// per SM over the batch, eight lanes per row for orders above 20 with at
 // most a quarter of that.  Measured single launches (n = 8..32, batch
 // 64..2048): four lanes per row fastest up to 512 x 24 rows, eight lanes at
-// n = 32 with 64 or 128 problems (10.1 against 14.3 us at 64).
+// n = 32 with 64 or 128 problems (10.1 against 14.3 us at 64).  In a CUDA
+// graph, 128 problems of order 24: eight lanes 5.0, five lanes (six rows a
+// warp) 5.05-5.27, four lanes 5.7 us per launch.
 #ifndef BF_TRSM_LAT_ROWS_PER_SM
 #define BF_TRSM_LAT_ROWS_PER_SM 128
 #endif
 int trsm_layout_rule(int batch, int m, int n) {
   const long long rows = (long long)batch * m, cap = (long long)BF_TRSM_LAT_ROWS_PER_SM * device_sm_count();
-  if (n <= 32 && n > 24 && rows * 4 <= cap) return LAYOUT_TRSM_LAT8;
+  if (n <= 32 && n > 20 && rows * 4 <= cap) return LAYOUT_TRSM_LAT8;
   if (n <= 32 && rows <= cap) return LAYOUT_TRSM_LAT4;
   return LAYOUT_TRSM_ROWS;
 }

@@ -127,6 +127,85 @@ def test_latency_cholesky_failing_pivots_and_offsets(lib, n):
         lib.bf_layout_set(POTRF, n, bt, 0)
 
 
+def _scaled_cases(bt, n, seed):
+    """SPD inputs far from unit scale, with zeros, and with entries whose
+    squares or scaled values leave the normal range.  The latency Cholesky
+    works on the unnormalized Schur complements and squares their entries;
+    a problem with entries outside 2^-480 .. 2^480 takes its range-safe
+    update.  The block-diagonal case stays on the fast path."""
+    S = inputs.spd(bt, n, seed).numpy()
+    big, small = S * 2.0 ** 900, S * 2.0 ** -900
+    blk = S.copy()  # block diagonal: exact zeros in every column
+    h = n // 2
+    blk[:, h:, :h] = 0.0
+    blk[:, :h, h:] = 0.0
+    # a large first pivot (2^20 * 1.5) whose column holds 2^-1010 and a
+    # subnormal entry: scaled by 2^-20 they leave the normal range
+    tiny = S.copy()
+    tiny[:, 0, 0] = 1.5 * 2.0 ** 20
+    tiny[:, 1:3, 0] = tiny[:, 0, 1:3] = 2.0 ** -1010
+    if n > 3:
+        tiny[:, 3, 0] = tiny[:, 0, 3] = 1e-310
+    # congruence by powers of two over a wide range: pivots from 2^-600 to 2^600
+    Q = 2.0 ** np.linspace(-300, 300, n).round()
+    wide = S * Q[None, :, None] * Q[None, None, :]
+    return {"big": big, "small": small, "block": blk, "tiny": tiny, "wide": wide}
+
+
+@pytest.mark.parametrize("n", [3, 8, 24, 31, 48])
+def test_cholesky_scaled_inputs_every_layout(lib, n):
+    bt = 6
+    cases = _scaled_cases(bt, n, 350 + n)
+    for lay in _layouts(lib, POTRF, n, bt):
+        _check_scaled_cases(lib, n, bt, lay, cases)
+
+
+def _check_scaled_cases(lib, n, bt, lay, cases):
+    _force(lib, POTRF, n, bt, lay)
+    try:
+        for name, S in cases.items():
+            name = (name, lay)
+            want, dinv_want, info_want = oracle.dpotrf_l(S)
+            assert np.all(info_want == 0), name
+            dD = bf.DMatBatch(bt, n, n, fill=np.nan)
+            info = torch.full((bt,), -7, dtype=torch.int32, device="cuda")
+            bf.dpotrf_l(n, put(torch.from_numpy(S)), 0, 0, dD, 0, 0, info=info)
+            got = get(dD)
+            assert np.all(info.cpu().numpy() == 0), name
+            assert np.all(np.isfinite(np.tril(got))), name
+            # ||L L^T - S|| / ||S|| with both scaled by a power of two near
+            # max |S|, so that the squares in the norms stay in range
+            sc = 2.0 ** np.floor(np.log2(np.abs(S).max(axis=(1, 2))))[:, None, None]
+            Lt = np.tril(got) / np.sqrt(sc)
+            assert np.all(fro(Lt @ Lt.transpose(0, 2, 1) - S / sc) <= 1e-13 * fro(S / sc)), name
+            # column by column against the oracle, each relative to its own
+            # column's size (the columns span hundreds of binary orders)
+            Lw, Lg = np.tril(want), np.tril(got)
+            colw = np.linalg.norm(Lw, axis=1)
+            assert np.all(np.linalg.norm(Lg - Lw, axis=1) <= 1e-12 * colw), name
+            dv = dD.dinv().cpu().numpy()[:, :n]
+            assert np.all(np.abs(dv - dinv_want) <= 1e-12 * np.abs(dinv_want)), name
+    finally:
+        lib.bf_layout_set(POTRF, n, bt, 0)
+
+
+@pytest.mark.parametrize("n", [8, 24])
+def test_latency_cholesky_power_of_four_pivots_exact(lib, n):
+    """An integer factor with power-of-two diagonal (pivots powers of four)
+    comes back exactly from the latency kernel, with its inverse diagonal."""
+    bt = 9
+    Li = inputs.int_lower_pow2(bt, n, 360 + n)
+    Si = torch.bmm(Li, Li.transpose(1, 2))
+    _force(lib, POTRF, n, bt, CHOL_LAT)
+    try:
+        dE = bf.DMatBatch(bt, n, n, fill=0.0)
+        bf.dpotrf_l(n, put(Si), 0, 0, dE, 0, 0)
+        assert np.array_equal(np.tril(get(dE)), Li.numpy())
+        assert np.array_equal(dE.dinv().cpu().numpy()[:, :n], 1.0 / np.diagonal(Li.numpy(), axis1=1, axis2=2))
+    finally:
+        lib.bf_layout_set(POTRF, n, bt, 0)
+
+
 TRSM_CASES = [(3, 1), (24, 5), (45, 8), (24, 16), (24, 24), (70, 31), (33, 32), (9, 40)]
 
 
