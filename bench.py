@@ -142,6 +142,9 @@ def kernel_of(routine, n, layout=None):
         return f"k_chol_small<{layout[7:]},{fused},1>"
     if layout == "tiny":
         return f"k_chol_tiny<{n},{fused},1>"
+    if layout == "rows8":
+        t, b = (256, 4) if n <= 32 else ((384, 3) if n <= 48 else (512, 2))
+        return f"k_chol_rows8<{fused},1,double,{t},{b}>"
     if layout == "split":
         return ("k_gemm_nt<1,1,1>+" if fused else "") + kernel_of("dpotrf_l", n, "rows")
     if layout == "blocked":

@@ -515,6 +515,8 @@ int bf_dposv_mixed_batched_noalloc(int batch, int n, int nrhs, const bf_dmat *sA
  *                         into D, then layout 7 on D (order >= 48)
  *                       10 blocked: two diagonal blocks, potrf, trsm,
  *                         syrk, potrf (order >= 32)
+ *                       11 one thread per row, eight problems per CTA,
+ *                         blocks of 4 columns (order <= 64)
  *   trsm_rltn:          1 one thread per row of X
  *                       2, 3, 4 = 2, 4, 8 lanes per row (order <= 32)
  *   getrf:              1 a warp shared by 32 / G problems (order <= 128)

@@ -220,7 +220,7 @@ k_chol_small(int batch, int n, int k, Op A, Op B, Op C, OpW D, double *dinv, lon
     // pivot of problem q comes from its sub-lane that owns row j
     const double d = (G == 1) ? dval : __shfl_sync(FULL, dval, q * G + (j % G));
     const double r = rsqrt(d);
-    if (!(d > 0.0) && first_bad == 0) first_bad = j + 1;
+    if (first_bad == 0 && not_positive(d)) first_bad = j + 1;
     for (int ii = istart; ii < n; ii += G) {
       if (ii == j)
         sm[(cj + ii) * QP + q] = d * r;
@@ -341,7 +341,7 @@ k_chol_tiny(int batch, int k, Op A, Op B, Op C, OpW D, double *dinv, long long s
   for (int j = 0; j < N; j++) {
     const double d = c[j][j];
     const double r = rsqrt(d);
-    if (!(d > 0.0) && bad == 0) bad = j + 1;
+    if (bad == 0 && not_positive(d)) bad = j + 1;
     c[j][j] = d * r;
     if (dv) dv[j] = r;
 #pragma unroll
@@ -679,7 +679,7 @@ __device__ __forceinline__ void rows_block(RowsSmem<T, BW, P> &S, const RowMap<P
     for (int j = 0; j < W; j++) {
       const T d = __shfl_sync(dmask, acc[j], base + j);
       const T r = rsqrt_t(d);
-      if (j < w && !(d > (T)0) && bad == 0) bad = c0 + j + 1;
+      if (j < w && bad == 0 && not_positive(d)) bad = c0 + j + 1;
       if (dl == j) {
         acc[j] = d * r;
         S.rinv[p][j] = r;
@@ -740,7 +740,10 @@ __device__ __forceinline__ void chol_rows_body(int b0, int batch, int n, int k, 
   if (threadIdx.x < P) S.bad[threadIdx.x] = 0;
   __syncthreads();
   for (int c0 = 0; c0 < n; c0 += BW) {
-    if constexpr (BW == 8) {
+    if constexpr (BW == 4) {
+      rows_block<4, 4, P, FUSED, ALIGNED, T, S1>(S, rm, c0, n, k, b0, batch, me_valid, pa, pc, pd, A, B, C, D,
+                                                 dinv, sdinv);
+    } else if constexpr (BW == 8) {
       rows_block<8, 8, P, FUSED, ALIGNED, T, S1>(S, rm, c0, n, k, b0, batch, me_valid, pa, pc, pd, A, B, C, D,
                                                  dinv, sdinv);
     } else {
@@ -778,6 +781,16 @@ template <bool FUSED, bool ALIGNED, typename T, int MAXT, int MINB>
 __global__ void __launch_bounds__(MAXT, MINB)
 k_chol_rows4(int batch, int n, int k, Op A, Op B, Op C, OpWT<T> D, T *dinv, long long sdinv, int *info) {
   chol_rows_body<8, 4, FUSED, ALIGNED, T>(blockIdx.x * 4, batch, n, k, A, B, C, D, dinv, sdinv, info);
+}
+
+// Eight problems per CTA with 4-column blocks: a warp holds 4 rows of each
+// of eight problems, so the diagonal block's rsqrt, pivot test and scaling
+// serve eight problems per warp instruction, at one block column (and its
+// barriers) per four columns.  Up to MAXT/8 rows.
+template <bool FUSED, bool ALIGNED, typename T, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB)
+k_chol_rows8(int batch, int n, int k, Op A, Op B, Op C, OpWT<T> D, T *dinv, long long sdinv, int *info) {
+  chol_rows_body<4, 8, FUSED, ALIGNED, T>(blockIdx.x * 8, batch, n, k, A, B, C, D, dinv, sdinv, info);
 }
 
 // Descriptor-array form: CTA b factors problem b of its own order (rows past
@@ -997,7 +1010,7 @@ __device__ __forceinline__ void rows_block_vp(RowsSmem<double, BW, P> &S, const 
     for (int j = 0; j < W; j++) {
       const double d = __shfl_sync(0xffffffffu, acc[j], base + j);
       const double r = rsqrt(d);
-      if (j < w && !(d > 0.0) && bad == 0) bad = c0 + j + 1;
+      if (j < w && bad == 0 && not_positive(d)) bad = c0 + j + 1;
       if (dl == j) {
         acc[j] = d * r;
         S.rinv[p][j] = r;
@@ -1188,6 +1201,28 @@ cudaError_t launch_rows4(bool aligned, int batch, int n, int k, Op A, Op B, Op C
   else
     k_chol_rows4<FUSED, false, T, MAXT, MINB><<<blocks, threads, 0, s>>>(batch, n, k, A, B, C, D, dinv, sdinv, info);
   return cudaGetLastError();
+}
+
+template <int MAXT, int MINB, bool FUSED, typename T>
+cudaError_t launch_rows8_t(bool aligned, int batch, int n, int k, Op A, Op B, Op C, OpWT<T> D, T *dinv,
+                           long long sdinv, int *info, cudaStream_t s) {
+  const int threads = ((n + 3) / 4) * 32;
+  const unsigned blocks = (unsigned)((batch + 7) / 8);
+  if (aligned)
+    k_chol_rows8<FUSED, true, T, MAXT, MINB><<<blocks, threads, 0, s>>>(batch, n, k, A, B, C, D, dinv, sdinv, info);
+  else
+    k_chol_rows8<FUSED, false, T, MAXT, MINB><<<blocks, threads, 0, s>>>(batch, n, k, A, B, C, D, dinv, sdinv, info);
+  return cudaGetLastError();
+}
+
+// The eight-problem kernel (orders up to 64), built per CTA size for 64
+// registers a thread.
+template <bool FUSED>
+cudaError_t launch_rows8(bool aligned, int batch, int n, int k, Op A, Op B, Op C, OpW D, double *dinv,
+                         long long sdinv, int *info, cudaStream_t s) {
+  if (n <= 32) return launch_rows8_t<256, 4, FUSED, double>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
+  if (n <= 48) return launch_rows8_t<384, 3, FUSED, double>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
+  return launch_rows8_t<512, 2, FUSED, double>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
 }
 
 template <int MAXT, int MINB, bool FUSED, typename T>
@@ -1406,12 +1441,31 @@ cudaError_t launch_tiny(bool aligned, int batch, int n, int k, Op A, Op B, Op C,
 #define BF_CHOL_SPLIT_MIN_N 48
 #endif
 
+// Orders factored eight problems per CTA in 4-column blocks (k_chol_rows8),
+// for batches that give every SM at least four such CTAs.  Measured on the
+// sweep's batches against the previous choice (ms): potrf n = 24 1.723 ->
+// 1.512 (small kernel, G = 4), n = 32 1.965 -> 1.744, n = 48 2.416 -> 2.360
+// (four-problem row kernel); n = 16 ties, n = 64 4% slower.  syrk_potrf
+// n = 24 2.379 -> 2.297; at n = 32 and 48 the syrk-first form stays faster.
+#ifndef BF_ROWS8_MIN_N
+#define BF_ROWS8_MIN_N 21
+#endif
+#ifndef BF_ROWS8_MAX_N
+#define BF_ROWS8_MAX_N 56
+#endif
+#ifndef BF_ROWS8_MAX_N_FUSED
+#define BF_ROWS8_MAX_N_FUSED 28
+#endif
+
 template <bool FUSED>
 int chol_rule(int batch, int n) {
   // few problems of a small order: one problem per CTA over an SM's four
   // sub-partitions (the latency kernel)
   if (n <= BF_CHOL_LAT_MAX_N && (long long)batch <= (long long)BF_CHOL_LAT_MAX_BATCH_PER_SM * device_sm_count())
     return LAYOUT_CHOL_LAT;
+  if (n >= BF_ROWS8_MIN_N && n <= (FUSED ? BF_ROWS8_MAX_N_FUSED : BF_ROWS8_MAX_N) &&
+      (long long)batch >= 32LL * device_sm_count())
+    return LAYOUT_CHOL_ROWS8;
   const bool full = (long long)batch >= 2LL * device_sm_count();
   if (full && n >= BF_CHOL_BLOCKED_MIN_N) return LAYOUT_CHOL_BLOCKED;
   if (FUSED && full && n >= BF_CHOL_SPLIT_MIN_N) return LAYOUT_CHOL_SPLIT;
@@ -1512,6 +1566,7 @@ cudaError_t launch_chol_t(bool aligned, int batch, int n, int k, Op A, Op B, Op 
     case LAYOUT_CHOL_SMALL_G32:
       return launch_small_g<32, FUSED>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
     case LAYOUT_CHOL_LAT: return launch_chol_lat(FUSED, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
+    case LAYOUT_CHOL_ROWS8: return launch_rows8<FUSED>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
     default: return launch_rows<FUSED, double>(aligned, batch, n, k, A, B, C, D, dinv, sdinv, info, s);
   }
 }
@@ -1535,6 +1590,7 @@ bool chol_layout_ok(int layout, int n) {
     case LAYOUT_CHOL_LAT: return n <= BF_CHOL_LAT_MAX_N;
     case LAYOUT_CHOL_SPLIT: return n <= CHOL_MAX_N;
     case LAYOUT_CHOL_BLOCKED: return n >= 32 && n <= CHOL_MAX_N;
+    case LAYOUT_CHOL_ROWS8: return n <= 64;
     default: return false;
   }
 }

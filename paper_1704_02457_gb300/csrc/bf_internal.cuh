@@ -159,6 +159,21 @@ cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t sme
   return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
 }
 
+// !(d > 0) from the bit pattern on the integer pipes: negative (-0 and
+// NaNs with the sign bit included), +0, or NaN.  On GB300 a double compare
+// issues on the narrow FP64 pipe like an FMA; the pivot test of every
+// factorization column runs here instead.
+__device__ __forceinline__ bool not_positive(double d) {
+  const int hi = __double2hiint(d), lo = __double2loint(d);
+  return hi < 0 || (hi | lo) == 0 || hi > 0x7ff00000 || (hi == 0x7ff00000 && lo != 0);
+}
+__device__ __forceinline__ bool not_positive(float f) { return !(f > 0.0f); }
+
+// d == 0 (either sign) from the bit pattern, for the same reason.
+__device__ __forceinline__ bool is_zero(double d) {
+  return ((__double2hiint(d) & 0x7fffffff) | __double2loint(d)) == 0;
+}
+
 // 8-byte asynchronous global -> shared copy (cp.async, bypasses registers)
 __device__ __forceinline__ void cp_async8(double *dst, const double *src) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
@@ -267,7 +282,8 @@ enum {
   LAYOUT_CHOL_LAT = 8,       // one problem per CTA of four warps (n <= 32)
   LAYOUT_CHOL_SPLIT = 9,     // syrk_potrf: the sum by the syrk kernel, then the row kernels
   LAYOUT_CHOL_BLOCKED = 10,  // two diagonal blocks: potrf, trsm, syrk, potrf (n >= 32)
-  LAYOUT_CHOL_COUNT = 11
+  LAYOUT_CHOL_ROWS8 = 11,    // one thread per row, eight problems per CTA, 4-column blocks (n <= 64)
+  LAYOUT_CHOL_COUNT = 12
 };
 // trsm_rltn
 enum { LAYOUT_TRSM_ROWS = 1, LAYOUT_TRSM_LAT2 = 2, LAYOUT_TRSM_LAT4 = 3, LAYOUT_TRSM_LAT8 = 4, LAYOUT_TRSM_COUNT = 5 };

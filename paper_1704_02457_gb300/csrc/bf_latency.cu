@@ -300,7 +300,7 @@ k_chol_lat(int n, int k, Op A, Op B, Op C, OpW D, double *dinv, long long sdinv,
       *elem(D, b, lane, lane) = dg * r;
       if (dinv) dinv[(long long)b * sdinv + lane] = r;
     }
-    const unsigned badm = __ballot_sync(0xffffffffu, lane < n && !(dg > 0.0));
+    const unsigned badm = __ballot_sync(0xffffffffu, lane < n && not_positive(dg));
     if (lane == 0 && info) info[b] = badm ? __ffs(badm) : 0;
   }
   __syncthreads();

@@ -130,7 +130,7 @@ k_getrf(int batch, int n, Op C, OpW D, int *ipiv, long long sipiv, int *info) {
     __syncwarp();
     const double piv = A_(j, j);
     if (valid && s == 0) ipiv[b * sipiv + j] = p;
-    if (piv == 0.0) {
+    if (is_zero(piv)) {
       if (first_zero == 0) first_zero = j + 1;
     } else {
       const double r = recip_newton(piv);
@@ -166,7 +166,7 @@ k_gelqf(int batch, int m, int n, Op C, OpW D, double *tau, long long stau) {
     const double alpha = A_(i, i);
     double t = 0.0;
     __syncwarp();
-    if (ss != 0.0) {
+    if (!is_zero(ss)) {
       double beta, scal;
       reflector_scalars(alpha, ss, beta, t, scal);
       for (int c = i + 1 + s; c < n; c += G) A_(i, c) *= scal;
@@ -284,7 +284,7 @@ k_getrf_rows(int n, int ld, Op C, OpW D, int *ipiv, long long sipiv, int *info) 
     const int pr = keep ? j : p;
     const double piv = keep ? djj : pv;
     if (t == 0) ipiv[b * sipiv + j] = pr;
-    if (piv == 0.0) {
+    if (is_zero(piv)) {
       if (first_zero == 0) first_zero = j + 1;
       // column j is zero at and below the diagonal: no swap, no update
       __syncthreads();
@@ -356,7 +356,7 @@ k_getrf_panel(int m, int w, int ld, int j0, OpW D, int *ipiv, long long sipiv, i
     const int pr = keep ? j : p;
     const double piv = keep ? djj : pv;
     if (t == 0) ipiv[b * sipiv + j0 + j] = j0 + pr;
-    if (piv == 0.0) {
+    if (is_zero(piv)) {
       if (first_zero == 0) first_zero = j0 + j + 1;
       __syncthreads();
       continue;
@@ -458,7 +458,7 @@ k_getrf_swap_solve(int n, int w, int j0, OpW D, const int *ipiv, long long sipiv
       mv_from[q] = srcB;
     }
     if (lane == 0) n_mv = __popc(bA) + __popc(bB);
-    if (lane < w) nz[lane] = at(j0 + lane, j0 + lane) != 0.0;
+    if (lane < w) nz[lane] = !is_zero(at(j0 + lane, j0 + lane));
   }
   for (int e = t; e < w * w; e += SWAP_T) {
     const int r = e / w, c = e % w;
@@ -598,7 +598,7 @@ k_gelqf_rows(int m, int n, int ld, Op C, OpW D, double *tau, long long stau) {
       const double alpha = sm[i * ld + i];
       double tv = 0.0;
       __syncwarp();
-      if (ss != 0.0) {
+      if (!is_zero(ss)) {
         double beta, scal;
         reflector_scalars(alpha, ss, beta, tv, scal);
         for (int c = i + 1 + t; c < n; c += 32) sm[c * ld + i] *= scal;
@@ -612,7 +612,7 @@ k_gelqf_rows(int m, int n, int ld, Op C, OpW D, double *tau, long long stau) {
     __syncthreads();
     const double tv = sc[0];
     const int R = m - i - 1;
-    if (tv != 0.0 && R > 0) {
+    if (!is_zero(tv) && R > 0) {
       int S = 1;
       while (S < 32 && 2 * S * R <= T_) S *= 2;
       const int sub = t & (S - 1), groups = T_ / S;

@@ -113,7 +113,7 @@ k_riccati(int batch, int N, const bf_riccati_prob *probs, const int *order, int 
           if (t == 0) {
             rv[j] = r;
             M[cj + j] = d * r;
-            if (!(d > 0.0) && s_bad == 0) s_bad = j + 1;
+            if (s_bad == 0 && not_positive(d)) s_bad = j + 1;
           }
           for (int i = j + 1 + t; i < m; i += 32) M[cj + i] *= r;
           __syncwarp();

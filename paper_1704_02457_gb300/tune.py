@@ -27,7 +27,7 @@ LAYOUT_NAMES = {
     "dgemm_nt": {1: "ks1", 2: "ks2", 3: "ks4"},
     "dsyrk_ln": {1: "ks1", 2: "ks2", 3: "ks4"},
     "dpotrf_l": {1: "tiny", 2: "small_g2", 3: "small_g4", 4: "small_g8", 5: "small_g16", 6: "small_g32", 7: "rows",
-                 8: "latency", 9: "split", 10: "blocked"},
+                 8: "latency", 9: "split", 10: "blocked", 11: "rows8"},
     "dtrsm_rltn": {1: "rows", 2: "latency_r2", 3: "latency_r4", 4: "latency_r8"},
     "dgetrf": {1: "warp", 2: "rows", 3: "blocked", 4: "blocked16"},
     "dgelqf": {1: "warp", 2: "rows", 3: "blocked", 4: "blocked16"},

@@ -329,7 +329,7 @@ def test_ordered_vbatched_argument_checks(lib):
 def test_layout_table(lib):
     # the autotuner's hook: candidates per routine, refused where a layout has
     # no kernel for the order, and the rule restored by layout 0 / reset
-    assert [lib.bf_layout_count(r) for r in range(7)] == [4, 4, 11, 5, 11, 5, 5]
+    assert [lib.bf_layout_count(r) for r in range(7)] == [4, 4, 12, 5, 12, 5, 5]
     assert lib.bf_layout_count(7) == 0
     assert lib.bf_layout_set(7, 24, 128, 1) == -1
     assert lib.bf_layout_set(6, 513, 128, 3) == _abi.BF_ERR_UNSUPPORTED  # blocked gelqf: n <= 512
@@ -337,7 +337,8 @@ def test_layout_table(lib):
     assert lib.bf_layout_set(5, 513, 128, 3) == _abi.BF_ERR_UNSUPPORTED  # blocked getrf: n <= 512
     assert lib.bf_layout_set(2, -1, 128, 1) == -2
     assert lib.bf_layout_set(2, 24, 0, 1) == -3
-    assert lib.bf_layout_set(2, 24, 128, 11) == -4
+    assert lib.bf_layout_set(2, 24, 128, 12) == -4
+    assert lib.bf_layout_set(2, 65, 128, 11) == _abi.BF_ERR_UNSUPPORTED  # eight problems per CTA: order <= 64
     assert lib.bf_layout_set(2, 24, 128, 1) == _abi.BF_ERR_UNSUPPORTED  # registers: order <= 8
     assert lib.bf_layout_set(2, 40, 128, 8) == _abi.BF_ERR_UNSUPPORTED  # latency kernel: order <= 32
     assert lib.bf_layout_set(3, 40, 128, 3) == _abi.BF_ERR_UNSUPPORTED

@@ -181,6 +181,8 @@ def test_layout_labels_and_launch_counts():
     assert bench.kernel_of("dpotrf_l", 24, "latency") == "k_chol_lat<0,24>"
     assert bench.kernel_of("dtrsm_rltn", 24, "latency_r4") == "k_trsm_lat<24,4>"
     assert bench.kernel_of("dpotrf_l", 16, "small_g8") == "k_chol_small<8,0,1>"
+    assert bench.kernel_of("dpotrf_l", 32, "rows8") == "k_chol_rows8<0,1,double,256,4>"
+    assert bench.kernel_of("dsyrk_dpotrf_ln", 48, "rows8") == "k_chol_rows8<1,1,double,384,3>"
     assert bench.kernel_of("dgemm_nt", 4, "ks1") == bench.kernel_of("dgemm_nt", 4)
 
 
