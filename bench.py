@@ -126,11 +126,27 @@ def small_g(n):
     return 16 if ne * 2 * 8 <= 48 * 1024 else 0
 
 
-def kernel_of(routine, n, layout=None):
+def potrf_block_layout(h, batch, sms=152):
+    """The layout the library's rule picks for a diagonal block of order h of
+    the blocked Cholesky (the non-fused rule for the block's order and the
+    batch): "blocked" again for a large block, "rows8", "latency", or None
+    for the order's default kernel."""
+    if h <= 32 and batch <= 4 * sms:
+        return "latency"
+    if 21 <= h <= 56 and batch >= 32 * sms:
+        return "rows8"
+    if h >= 128 and batch >= 2 * sms:
+        return "blocked"
+    return None
+
+
+def kernel_of(routine, n, layout=None, batch=None, sms=152):
     """Name of the kernel the library launches for (routine, n) at this sweep
     in `layout` (a tune.LAYOUT_NAMES name; None: the row kernels of the
     Cholesky, the built-in choice of the other routines).  Layouts made of
-    several launches are named by their parts."""
+    several launches are named by their parts; with `batch` given, the
+    blocked layout's diagonal blocks are named by the layout the rule picks
+    for them."""
     fused = int(routine == "dsyrk_dpotrf_ln")
     if layout in ("ks2", "ks4"):
         return f"k_gemm_nt<{int(routine == 'dsyrk_ln')},1,1>/{layout}"
@@ -149,8 +165,13 @@ def kernel_of(routine, n, layout=None):
         return ("k_gemm_nt<1,1,1>+" if fused else "") + kernel_of("dpotrf_l", n, "rows")
     if layout == "blocked":
         h = (n // 2) & ~3
-        return (("k_gemm_nt<1,1,1>+" if fused else "") + "blocked[" + kernel_of("dpotrf_l", h, "rows") + "+" +
-                kernel_of("dtrsm_rltn", h) + "+k_gemm_nt<1,1,1>+" + kernel_of("dpotrf_l", n - h, "rows") + "]")
+
+        def block(o):
+            if batch is None:
+                return kernel_of("dpotrf_l", o, "rows")
+            return kernel_of("dpotrf_l", o, potrf_block_layout(o, batch, sms), batch, sms)
+        return (("k_gemm_nt<1,1,1>+" if fused else "") + "blocked[" + block(h) + "+" +
+                kernel_of("dtrsm_rltn", h) + "+k_gemm_nt<1,1,1>+" + block(n - h) + "]")
     if routine == "dgemm_nt":
         return "k_gemm_nt<0,1,1>"
     if routine == "dsyrk_ln":
@@ -188,7 +209,14 @@ def launches_of(routine, n, batch, sms=152, layout=None):
     if layout == "split":
         return int(fused) + launches_of("dpotrf_l", n, batch, sms)
     if layout == "blocked":
-        return int(fused) + 5
+        # each diagonal block in the layout the rule picks for its order (a
+        # nested blocked block adds no info launch of its own)
+        h = (n // 2) & ~3
+
+        def block(o):
+            lay = potrf_block_layout(o, batch, sms)
+            return launches_of("dpotrf_l", o, batch, sms, lay) - (lay == "blocked")
+        return int(fused) + block(h) + 2 + block(n - h) + 1
     if routine in ("dpotrf_l", "dsyrk_dpotrf_ln") and 192 < n <= 256:
         slots, pairs = 2 * sms, (batch + 1) // 2
         rest = pairs % slots
@@ -745,7 +773,7 @@ def run_gpu(args):
     by_kernel = {}
     for j, p in enumerate(pts):
         times = [evs[s][j][0].elapsed_time(evs[s][j][1]) for s in range(K)]
-        by_kernel.setdefault(kernel_of(p.routine, p.n, p.layout), []).append((statistics.mean(times), p))
+        by_kernel.setdefault(kernel_of(p.routine, p.n, p.layout, p.batch, sms), []).append((statistics.mean(times), p))
     step_ms = sum(t for v in by_kernel.values() for t, _ in v)
     dom = max(by_kernel, key=lambda kname: sum(t for t, _ in by_kernel[kname]))
     t_big, p_big = max(by_kernel[dom], key=lambda x: x[0])

@@ -1515,13 +1515,31 @@ inline Op as_op(const OpW &d) { return Op{d.p, d.stride, d.cn, d.i0, d.j0}; }
 // Blocked potrf of D (in place; the first half read from C): with h = n/2
 // rounded down to a panel top,
 //   L11 = chol(C11);  L21 = C21 L11^{-T};  D22 = C22 - L21 L21^T;  L22 = chol(D22)
-// on the row kernels, the merged trsm and the syrk kernel.  info is rebuilt
-// from the diagonal at the end.
+// with the merged trsm and the syrk kernel, each diagonal block factored in
+// the layout the rule picks for its own order and the batch (blocked again
+// from order 128, eight problems per CTA at 21..56).  info is rebuilt from
+// the diagonal at the end.
+cudaError_t launch_chol_blocked(bool aligned, int batch, int n, Op C, OpW D, double *dinv, long long sdinv, int *info,
+                                cudaStream_t s);
+
+// potrf of a diagonal block of the blocked form, in the layout the rule picks
+// for its own order and the batch (the blocked form again for a large
+// block); info is left to the caller, which rebuilds it from the diagonal.
+cudaError_t launch_potrf_block(bool aligned, int batch, int h, Op C, OpW D, double *dinv, long long sdinv,
+                               cudaStream_t s) {
+  const Op none{nullptr, 0, 0, 0, 0};
+  switch (chol_rule<false>(batch, h)) {
+    case LAYOUT_CHOL_BLOCKED: return launch_chol_blocked(aligned, batch, h, C, D, dinv, sdinv, nullptr, s);
+    case LAYOUT_CHOL_ROWS8: return launch_rows8<false>(aligned, batch, h, 0, none, none, C, D, dinv, sdinv, nullptr, s);
+    case LAYOUT_CHOL_LAT: return launch_chol_lat(false, batch, h, 0, none, none, C, D, dinv, sdinv, nullptr, s);
+    default: return launch_rows<false, double>(aligned, batch, h, 0, none, none, C, D, dinv, sdinv, nullptr, s);
+  }
+}
+
 cudaError_t launch_chol_blocked(bool aligned, int batch, int n, Op C, OpW D, double *dinv, long long sdinv, int *info,
                                 cudaStream_t s) {
   const int h = (n / 2) & ~(PS - 1);
-  const Op none{nullptr, 0, 0, 0, 0};
-  cudaError_t e = launch_rows<false, double>(aligned, batch, h, 0, none, none, C, D, dinv, sdinv, nullptr, s);
+  cudaError_t e = launch_potrf_block(aligned, batch, h, C, D, dinv, sdinv, s);
   if (e != cudaSuccess) return e;
   const Op L11{D.p, D.stride, D.cn, D.i0, D.j0};
   const Op C21{C.p, C.stride, C.cn, C.i0 + h, C.j0};
@@ -1533,8 +1551,7 @@ cudaError_t launch_chol_blocked(bool aligned, int batch, int n, Op C, OpW D, dou
   const OpW D22{D.p, D.stride, D.cn, D.i0 + h, D.j0 + h};
   e = launch_gemm_nt(true, batch, n - h, n - h, h, -1.0, L21, L21, 1.0, C22, D22, aligned, s);
   if (e != cudaSuccess) return e;
-  e = launch_rows<false, double>(aligned, batch, n - h, 0, none, none, as_op(D22), D22, dinv ? dinv + h : nullptr, sdinv,
-                                 nullptr, s);
+  e = launch_potrf_block(aligned, batch, n - h, as_op(D22), D22, dinv ? dinv + h : nullptr, sdinv, s);
   if (e != cudaSuccess || !info) return e;
   k_info_from_diag<<<(batch + 127) / 128, 128, 0, s>>>(batch, n, D, info);
   return cudaGetLastError();

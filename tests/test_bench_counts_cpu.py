@@ -173,8 +173,13 @@ def test_layout_labels_and_launch_counts():
     # trsm, syrk, potrf and the info rebuild (plus the fused routine's syrk)
     assert bench.launches_of("dsyrk_dpotrf_ln", 96, 7281, layout="split") == 2
     assert bench.launches_of("dsyrk_dpotrf_ln", 256, 1024, layout="split") == 3  # with the tail split
-    assert bench.launches_of("dpotrf_l", 256, 2048, layout="blocked") == 5
-    assert bench.launches_of("dsyrk_dpotrf_ln", 256, 1024, layout="blocked") == 6
+    # the diagonal blocks take the rule's layout for their order: at n = 256
+    # the blocks of order 128 are blocked again (potrf, trsm, syrk, potrf)
+    assert bench.launches_of("dpotrf_l", 128, 8192, layout="blocked") == 5
+    assert bench.launches_of("dpotrf_l", 256, 2048, layout="blocked") == 4 + 2 + 4 + 1
+    assert bench.launches_of("dsyrk_dpotrf_ln", 256, 1024, layout="blocked") == 1 + 4 + 2 + 4 + 1
+    assert bench.potrf_block_layout(32, 32768) == "rows8" and bench.potrf_block_layout(64, 8192) is None
+    assert bench.potrf_block_layout(128, 2048) == "blocked" and bench.potrf_block_layout(24, 128) == "latency"
     assert bench.launches_of("dgemm_nt", 256, 682, layout="ks1") == 1
     k = bench.kernel_of("dsyrk_dpotrf_ln", 256, "blocked")
     assert k.startswith("k_gemm_nt<1,1,1>+blocked[") and "k_trsm_rltn" in k
