@@ -316,7 +316,8 @@ int bf_dsyrk_dpotrf_ln(int m, int k, const bf_dmat *sA, int ai, int aj,
  * The two triangular solves are the right-hand-side forms of trsm (trsv_lnn
  * and trsv_ltn of the paper's BLAS level-2 list, Appendix A.3).
  * L is the n x n lower triangle of sL at (li, lj); B and X are n x nrhs and
- * may coincide.  Supports n <= 160 and 1 <= nrhs <= 8. */
+ * may coincide.  Supports n <= 216 and 1 <= nrhs <= 8 (the factor and the
+ * right-hand sides of a system held in one CTA's shared memory). */
 int bf_dpotrs_l_batched(int batch, int n, int nrhs, const bf_dmat *sL, int li, int lj,
                         long long strideL, const bf_dmat *sB, int bi, int bj, long long strideB,
                         const bf_dmat *sX, int xi, int xj, long long strideX, void *stream);
@@ -327,7 +328,7 @@ int bf_dpotrs_l_batched(int batch, int n, int nrhs, const bf_dmat *sL, int li, i
  *     Bbar = A^{-1} Xbar                  (d loss / d B)
  *     Abar = -(Bbar X^T + X Bbar^T) / 2   (d loss / d A for symmetric A)
  * Bbar is n x nrhs, Abar n x n (written in full).  Outputs must not overlap
- * the inputs.  Supports n <= 160 and 1 <= nrhs <= 8. */
+ * the inputs.  Supports n <= 208 and 1 <= nrhs <= 8. */
 int bf_dposv_adjoint_batched(int batch, int n, int nrhs, const bf_dmat *sL, int li, int lj,
                              long long strideL, const bf_dmat *sX, int xi, int xj, long long strideX,
                              const bf_dmat *sXbar, int xbi, int xbj, long long strideXbar,
@@ -354,7 +355,7 @@ size_t bf_dposv_mixed_worksize(int batch, int n);
  * resid (device, may be NULL): the final relative residual per system.
  * work: device memory of at least bf_dposv_mixed_worksize(batch, n) bytes,
  *   256-byte aligned, owned by the caller; its contents are scratch.
- * Supports n <= 160 and 1 <= nrhs <= 8. */
+ * Supports n <= 256 and 1 <= nrhs <= 8. */
 int bf_dposv_mixed_batched(int batch, int n, int nrhs, const bf_dmat *sA, int ai, int aj,
                            long long strideA, const bf_dmat *sB, int bi, int bj, long long strideB,
                            const bf_dmat *sX, int xi, int xj, long long strideX, double tol,
@@ -380,7 +381,8 @@ size_t bf_dposv_mixed_tc_worksize(int batch, int n);
  * well below one; the others report -1.
  * Arguments 1..19 as for bf_dposv_mixed_batched; work: device memory of at
  * least bf_dposv_mixed_tc_worksize(batch, n) bytes, 256-byte aligned, owned
- * by the caller.  Supports n <= 160 and 1 <= nrhs <= 8. */
+ * by the caller.  Supports n <= 160 (its first trailing update, n - 32 rows,
+ * is one 128-row tensor-core tile) and 1 <= nrhs <= 8. */
 int bf_dposv_mixed_tc_batched(int batch, int n, int nrhs, const bf_dmat *sA, int ai, int aj,
                               long long strideA, const bf_dmat *sB, int bi, int bj, long long strideB,
                               const bf_dmat *sX, int xi, int xj, long long strideX, double tol,

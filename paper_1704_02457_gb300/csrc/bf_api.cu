@@ -377,7 +377,7 @@ int bf_dpotrs_l_batched(int batch, int n, int nrhs, const bf_dmat *sL, int li, i
   if (n < 0) return -2;
   if (nrhs < 0) return -3;
   if (batch == 0 || n == 0 || nrhs == 0) return 0;
-  if (n > POSV_MAX_N || nrhs > POSV_MAX_NRHS) return BF_ERR_UNSUPPORTED;
+  if (n > POTRS_MAX_N || nrhs > POSV_MAX_NRHS) return BF_ERR_UNSUPPORTED;
   if (int w = check_op(sL, li, lj, n, n, strideL, batch, false)) return pos_err(w, 4);
   if (int w = check_op(sB, bi, bj, n, nrhs, strideB, batch, false)) return pos_err(w, 8);
   if (int w = check_op(sX, xi, xj, n, nrhs, strideX, batch, true)) return pos_err(w, 12);
@@ -395,7 +395,7 @@ int bf_dposv_adjoint_batched(int batch, int n, int nrhs, const bf_dmat *sL, int 
   if (n < 0) return -2;
   if (nrhs < 0) return -3;
   if (batch == 0 || n == 0 || nrhs == 0) return 0;
-  if (n > POSV_MAX_N || nrhs > POSV_MAX_NRHS) return BF_ERR_UNSUPPORTED;
+  if (n > ADJOINT_MAX_N || nrhs > POSV_MAX_NRHS) return BF_ERR_UNSUPPORTED;
   if (int w = check_op(sL, li, lj, n, n, strideL, batch, false)) return pos_err(w, 4);
   if (int w = check_op(sX, xi, xj, n, nrhs, strideX, batch, false)) return pos_err(w, 8);
   if (int w = check_op(sXbar, xbi, xbj, n, nrhs, strideXbar, batch, false)) return pos_err(w, 12);
@@ -480,6 +480,7 @@ int bf_dposv_mixed_tc_batched(int batch, int n, int nrhs, const bf_dmat *sA, int
     return r;
   if (prec < 0 || prec > 2) return -20;
   if (batch == 0 || n == 0 || nrhs == 0) return 0;
+  if (n > POSV_TC_MAX_N) return BF_ERR_UNSUPPORTED;
   if (!work || !aligned_to(work, BF_ALIGN)) return -21;
   if (work_bytes < bf_dposv_mixed_tc_worksize(batch, n)) return -22;
   const size_t pm = ((size_t)n + PS - 1) / PS * PS, nblk = ((size_t)n + 31) / 32, bt = (size_t)batch;

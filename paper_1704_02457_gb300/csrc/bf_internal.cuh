@@ -326,7 +326,16 @@ cudaError_t launch_trsm_lat(int lanes, int batch, int m, int n, double alpha, Op
 // Largest order the factorization kernels accept.
 constexpr int CHOL_MAX_N = 512;
 constexpr int TRSM_MAX_N = 4096;
-constexpr int POSV_MAX_N = 160;
+// Orders of the solves, set by what one CTA holds in shared memory (at most
+// 200 KB, eight right-hand sides): the mixed refinement keeps the FP32 factor
+// and two FP64 copies of the right-hand sides (165 KB at n = 256); the FP64
+// solve the FP64 factor and one copy (199 KB at 216); the adjoint the FP64
+// factor and two copies (198 KB at 208).  The blocked tensor-core form's
+// first trailing update must fit one 128-row MMA tile: n - 32 <= 128.
+constexpr int POSV_MAX_N = 256;
+constexpr int POTRS_MAX_N = 216;
+constexpr int ADJOINT_MAX_N = 208;
+constexpr int POSV_TC_MAX_N = 160;
 constexpr int POSV_MAX_NRHS = 8;
 
 }  // namespace bf

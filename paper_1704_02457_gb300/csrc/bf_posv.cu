@@ -306,7 +306,10 @@ k_posv(int n, int nrhs, Op A, const float *l32, long long sl32, const int *info3
           case 2: warp_solve_refine<2>(L, dinv, r64, x64, n, nrhs, k0); break;
           case 3: warp_solve_refine<3>(L, dinv, r64, x64, n, nrhs, k0); break;
           case 4: warp_solve_refine<4>(L, dinv, r64, x64, n, nrhs, k0); break;
-          default: warp_solve_refine<5>(L, dinv, r64, x64, n, nrhs, k0); break;
+          case 5: warp_solve_refine<5>(L, dinv, r64, x64, n, nrhs, k0); break;
+          case 6: warp_solve_refine<6>(L, dinv, r64, x64, n, nrhs, k0); break;
+          case 7: warp_solve_refine<7>(L, dinv, r64, x64, n, nrhs, k0); break;
+          default: warp_solve_refine<8>(L, dinv, r64, x64, n, nrhs, k0); break;
         }
       }
     }

@@ -274,7 +274,7 @@ def test_noalloc_solver_reports_argument_errors_before_size(lib):
     g = lib.bf_dposv_mixed_batched_noalloc
     A, B, X = _desc(200, 200), _desc(200, 8), _desc(200, 8, addr=0x20000)
     sa, sb = 200 * 200, 200 * 8
-    assert g(4096, 161, 4, r(A), 0, 0, sa, r(B), 0, 0, sb, r(X), 0, 0, sb, 1e-12, 10, None, None,
+    assert g(4096, 257, 4, r(A), 0, 0, sa, r(B), 0, 0, sb, r(X), 0, 0, sb, 1e-12, 10, None, None,
              None) == _abi.BF_ERR_UNSUPPORTED
     assert g(4096, 128, 4, None, 0, 0, sa, r(B), 0, 0, sb, r(X), 0, 0, sb, 1e-12, 10, None, None, None) == -4
     assert g(4096, 128, 4, r(A), 0, 0, sa, r(B), 0, 0, sb, r(X), 0, 0, sb, -1.0, 10, None, None, None) == -16
@@ -282,6 +282,32 @@ def test_noalloc_solver_reports_argument_errors_before_size(lib):
     assert g(4096, 128, 4, r(A), 0, 0, sa, r(B), 0, 0, sb, r(X), 0, 0, sb, 1e-12, 10, None, None,
              None) == _abi.BF_ERR_TOO_LARGE
     assert g(0, 128, 4, None, 0, 0, 0, None, 0, 0, 0, None, 0, 0, 0, 1e-12, 10, None, None, None) == 0
+
+
+def test_solver_order_limits(lib):
+    # what one CTA holds in shared memory sets each solve's largest order:
+    # potrs 216, the adjoint 208, the mixed refinement 256; the tensor-core
+    # form 160 (its first trailing update is one 128-row tile)
+    r = ctypes.byref
+    L, B, X, Xb, Bb, Ab = (_desc(300, 300), _desc(300, 8), _desc(300, 8, 0x20000), _desc(300, 8, 0x30000),
+                           _desc(300, 8, 0x40000), _desc(300, 300, 0x50000))
+    sl, sb = 300 * 300, 300 * 8
+    assert lib.bf_dpotrs_l_batched(2, 217, 4, r(L), 0, 0, sl, r(B), 0, 0, sb, r(X), 0, 0, sb,
+                                   None) == _abi.BF_ERR_UNSUPPORTED
+    assert lib.bf_dpotrs_l_batched(2, 216, 9, r(L), 0, 0, sl, r(B), 0, 0, sb, r(X), 0, 0, sb,
+                                   None) == _abi.BF_ERR_UNSUPPORTED
+    assert lib.bf_dposv_adjoint_batched(2, 209, 1, r(L), 0, 0, sl, r(X), 0, 0, sb, r(Xb), 0, 0, sb, r(Bb), 0, 0, sb,
+                                        r(Ab), 0, 0, sl, None) == _abi.BF_ERR_UNSUPPORTED
+    work = ctypes.c_void_p(0x1000000)
+    mixed = lib.bf_dposv_mixed_batched
+    assert mixed(2, 257, 4, r(L), 0, 0, sl, r(B), 0, 0, sb, r(X), 0, 0, sb, 1e-12, 10, None, None, work, 1 << 30,
+                 None) == _abi.BF_ERR_UNSUPPORTED
+    tc = lib.bf_dposv_mixed_tc_batched
+    assert tc(2, 161, 4, r(L), 0, 0, sl, r(B), 0, 0, sb, r(X), 0, 0, sb, 1e-12, 10, None, None, 2, work, 1 << 30,
+              None) == _abi.BF_ERR_UNSUPPORTED
+    # the argument checks still come first
+    assert tc(2, 161, 4, None, 0, 0, sl, r(B), 0, 0, sb, r(X), 0, 0, sb, 1e-12, 10, None, None, 2, work, 1 << 30,
+              None) == -4
 
 
 def test_single_problem_pack_reports_its_own_positions(lib):

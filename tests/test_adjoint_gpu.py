@@ -34,7 +34,7 @@ def get(D):
     return D.to_colmajor().cpu().numpy()
 
 
-@pytest.mark.parametrize("n,nrhs", [(1, 1), (8, 3), (64, 1), (100, 8), (160, 2)])
+@pytest.mark.parametrize("n,nrhs", [(1, 1), (8, 3), (64, 1), (100, 8), (160, 2), (208, 8)])
 def test_adjoint_kernel_matches_oracle(n, nrhs):
     bt = 4
     S = inputs.spd(bt, n, 1200 + n)

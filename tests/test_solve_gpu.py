@@ -49,7 +49,8 @@ def rel_resid(A, X, B):
     return fro(B - A @ X) / (fro(A) * fro(X))
 
 
-@pytest.mark.parametrize("n,nrhs", [(1, 1), (5, 2), (24, 4), (33, 3), (64, 4), (100, 8), (128, 4), (160, 1)])
+@pytest.mark.parametrize("n,nrhs", [(1, 1), (5, 2), (24, 4), (33, 3), (64, 4), (100, 8), (128, 4), (160, 1),
+                                    (200, 3), (216, 8)])
 def test_potrs_matches_oracle(n, nrhs):
     bt = 5
     S = inputs.spd(bt, n, 400 + n)
@@ -75,7 +76,8 @@ def test_potrs_integer_exact_and_in_place():
     assert np.array_equal(get(dB), X.numpy())
 
 
-@pytest.mark.parametrize("n,nrhs,bt", [(8, 1, 33), (32, 4, 40), (97, 6, 20), (128, 4, 64), (150, 2, 9), (160, 8, 12)])
+@pytest.mark.parametrize("n,nrhs,bt", [(8, 1, 33), (32, 4, 40), (97, 6, 20), (128, 4, 64), (150, 2, 9), (160, 8, 12),
+                                       (193, 5, 7), (224, 4, 5), (256, 8, 6), (256, 1, 4)])
 def test_mixed_reaches_1e12_on_cond_up_to_1e6(n, nrhs, bt):
     A, cond = inputs.spd_cond(bt, n, 420 + n, log10_cond=(2.0, 6.0))
     B = inputs.normal((bt, n, nrhs), 421)
