@@ -214,6 +214,19 @@ __device__ __forceinline__ double recip_newton(double d) {
   return fma(r, e, r);
 }
 
+// 1/d in three FP64 operations: the hardware approximation r0 (relative
+// error e = 1 - d r0 below 2^-22), then r0 (1 + e + e^2), whose error is of
+// order e^3.  A subnormal d gives NaN, as for recip_newton.
+__device__ __forceinline__ double recip3(double d) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+  const double e = fma(-d, r, 1.0);
+  return fma(fma(e, e, e), r, r);
+}
+
+// x == 1.0 from the bit pattern (a double compare issues on the FP64 pipe)
+__device__ __forceinline__ bool is_one(double x) { return __double_as_longlong(x) == 0x3FF0000000000000LL; }
+
 // Argument checks shared by bf_dposv_mixed_batched and its allocation-free
 // form (argument positions 1..19 of both signatures).
 int posv_mixed_check(int batch, int n, int nrhs, const bf_dmat *sA, int ai, int aj, long long strideA,

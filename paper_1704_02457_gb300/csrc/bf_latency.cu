@@ -48,14 +48,6 @@ __device__ __forceinline__ double *elem(const OpW &o, int b, int r, int c) {
   return o.p + (long long)b * o.stride + pm_off(o.i0 + r, o.j0 + c, o.cn);
 }
 
-// 1/d: the hardware approximation r0 (relative error e = 1 - d r0 below
-// 2^-22), then r0 (1 + e + e^2), whose error is of order e^3.
-__device__ __forceinline__ double recip3(double d) {
-  double r;
-  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
-  const double e = fma(-d, r, 1.0);
-  return fma(fma(e, e, e), r, r);
-}
 
 // 1 when x is not zero and its magnitude lies outside 2^-480 .. 2^480
 // (subnormal, inf and NaN included), from the exponent field.

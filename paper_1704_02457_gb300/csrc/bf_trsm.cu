@@ -78,7 +78,7 @@ __device__ __forceinline__ void trsm_block(double *smem, int P, int R, int c0, i
       if (dinv)
         r = __ldg(dinv + bb * sdinv + c0 + j);
       else
-        r = recip_newton(__ldg(L.p + bb * L.stride + pm_off(L.i0 + c0 + j, L.j0 + c0 + j, L.cn)));
+        r = recip3(__ldg(L.p + bb * L.stride + pm_off(L.i0 + c0 + j, L.j0 + c0 + j, L.cn)));
     }
     smem[(size_t)pp * RS + W * (W + 1) + j] = r;
   }
@@ -89,7 +89,7 @@ __device__ __forceinline__ void trsm_block(double *smem, int P, int R, int c0, i
   double *xrow = D.p + (active ? b : 0) * D.stride + pm_off(D.i0 + (active ? row : 0), D.j0, D.cn);
 #pragma unroll
   for (int jj = 0; jj < W; jj++) acc[jj] = (active && jj < w) ? brow[(long long)(c0 + jj) * PS] : 0.0;
-  if (alpha != 1.0) {
+  if (!is_one(alpha)) {
 #pragma unroll
     for (int jj = 0; jj < W; jj++) acc[jj] *= alpha;
   }
