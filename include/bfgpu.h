@@ -283,7 +283,7 @@ int bf_dgetrf(int n, const bf_dmat *sC, int ci, int cj, const bf_dmat *sD, int d
  * the rows below at once as the block reflector I - V^T T V (compact WY form,
  * T upper triangular), so the results agree with the row-by-row order up to
  * rounding.  The reflector's scalars come from a reciprocal square root and
- * a reciprocal (rcp.approx refined by Newton steps): a row whose
+ * a reciprocal (rcp.approx and one third-order correction): a row whose
  * |alpha| + ||(alpha, x)|| is subnormal yields NaN. */
 int bf_dgelqf_batched(int batch, int m, int n, const bf_dmat *sC, int ci, int cj, long long strideC,
                       const bf_dmat *sD, int di, int dj, long long strideD, double *tau,

@@ -200,23 +200,11 @@ cudaError_t launch_trsm_rltn_v(int batch, const bf_dsize *size, double alpha, co
                                const bf_dsub *B, const bf_dsub *D, int max_m, int max_n, int *status,
                                cudaStream_t s);
 
-// 1/d by Newton-Raphson iteration r <- r + r (1 - d r) from the hardware's
-// approximate reciprocal (rcp.approx.ftz.f64); two steps take it to full
-// double precision.  Used where one reciprocal is shared by a column of
-// multiplications, instead of an IEEE divide.  The approximation flushes a
-// subnormal d to zero, and the result is then NaN (tested).
-__device__ __forceinline__ double recip_newton(double d) {
-  double r;
-  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
-  double e = fma(-d, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-d, r, 1.0);
-  return fma(r, e, r);
-}
-
 // 1/d in three FP64 operations: the hardware approximation r0 (relative
 // error e = 1 - d r0 below 2^-22), then r0 (1 + e + e^2), whose error is of
-// order e^3.  A subnormal d gives NaN, as for recip_newton.
+// order e^3.  Used where one reciprocal is shared by a column of
+// multiplications, instead of an IEEE divide.  The approximation flushes a
+// subnormal d to zero, and the result is then NaN (tested).
 __device__ __forceinline__ double recip3(double d) {
   double r;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));

@@ -43,17 +43,17 @@ __device__ __forceinline__ long long pivot_key(double x) {
 // sequential part of each row, which on GB300 costs a warp the same FP64
 // issue time whatever its active lanes).  With s = alpha^2 + ss and
 // r = 1/sqrt(s): beta = -sign(alpha) s r, tau = 1 + |alpha| r, and
-// alpha - beta = sign(alpha) (|alpha| + s r).  The reciprocal is the
-// library's (rcp.approx refined by two Newton steps): a row whose
+// alpha - beta = sign(alpha) (|alpha| + s r).  The signs are applied on the
+// bit patterns (copysign), not by FP64 products.  The reciprocal is the
+// library's (rcp.approx and one third-order correction): a row whose
 // |alpha| + ||(alpha, x)|| is subnormal gives NaN.
 __device__ __forceinline__ void reflector_scalars(double alpha, double ss, double &beta, double &tau, double &scal) {
   const double s = fma(alpha, alpha, ss);
   const double r = rsqrt(s);
   const double rt = s * r;
-  const double sg = copysign(1.0, alpha);
-  beta = -sg * rt;
+  beta = copysign(rt, -alpha);
   tau = fma(fabs(alpha), r, 1.0);
-  scal = sg * recip_newton(fabs(alpha) + rt);
+  scal = copysign(recip3(fabs(alpha) + rt), alpha);
 }
 
 // whole m x n matrices of the warp's problems in and out of shared memory
@@ -133,7 +133,7 @@ k_getrf(int batch, int n, Op C, OpW D, int *ipiv, long long sipiv, int *info) {
     if (is_zero(piv)) {
       if (first_zero == 0) first_zero = j + 1;
     } else {
-      const double r = recip_newton(piv);
+      const double r = recip3(piv);
       for (int i = j + 1 + s; i < n; i += G) {
         const double l = A_(i, j) * r;
         A_(i, j) = l;
@@ -296,7 +296,7 @@ k_getrf_rows(int n, int ld, Op C, OpW D, int *ipiv, long long sipiv, int *info) 
       sm[t * ld + pr] = y;
     }
     if (t < 32) {  // one warp forms the reciprocal and the multipliers (FP64 work is issued per warp)
-      const double r = recip_newton(piv);
+      const double r = recip3(piv);
       for (int i = j + 1 + t; i < n; i += 32) sm[j * ld + i] = ((i == pr) ? djj : sm[j * ld + i]) * r;
       if (t == 0) sm[j * ld + j] = piv;
     }
@@ -367,7 +367,7 @@ k_getrf_panel(int m, int w, int ld, int j0, OpW D, int *ipiv, long long sipiv, i
       sm[t * ld + pr] = y;
     }
     if (t < 32) {
-      const double r = recip_newton(piv);
+      const double r = recip3(piv);
       for (int i = j + 1 + t; i < m; i += 32) sm[j * ld + i] = ((i == pr) ? djj : sm[j * ld + i]) * r;
       if (t == 0) sm[j * ld + j] = piv;
     }
