@@ -139,7 +139,8 @@ def _chol_defaults():
                             "paper_1704_02457_gb300", "csrc", "bf_chol.cu")).read()
     vals = {}
     for name in ("BF_CHOL_TINY_MAX_N", "BF_CHOL_SMALL_MAX_N", "BF_ROWS_P4_MIN_N", "BF_ROWS_P4_MAX_N",
-                 "BF_ROWS_P4_FUSED_MIN_N8", "BF_SMALL_SMEM_BUDGET_KB", "BF_ROWS_P2_MAX_N"):
+                 "BF_ROWS_P4_FUSED_MIN_N8", "BF_SMALL_SMEM_BUDGET_KB", "BF_ROWS_P2_MAX_N", "BF_ROWS8_MIN_N",
+                 "BF_ROWS8_MAX_N", "BF_CHOL_BLOCKED_MIN_N"):
         m = re.search(r"#define %s (\d+)" % name, src)
         assert m, name
         vals[name] = int(m.group(1))
@@ -166,6 +167,19 @@ def test_kernel_labels_match_the_launchers_thresholds():
     for n in range(v["BF_CHOL_TINY_MAX_N"] + 1, v["BF_CHOL_SMALL_MAX_N"] + 1):
         g = bench.small_g(n)
         assert n * (n + 1) // 2 * (32 // g) * 8 <= v["BF_SMALL_SMEM_BUDGET_KB"] * 1024 or g == 16
+
+
+def test_blocked_halves_follow_the_launchers_rule():
+    # bench.potrf_block_layout mirrors the rule the blocked Cholesky applies
+    # to its halves; it must move with the rule's thresholds
+    v = _chol_defaults()
+    big = 10 ** 6
+    assert bench.potrf_block_layout(v["BF_ROWS8_MIN_N"], big) == "rows8"
+    assert bench.potrf_block_layout(v["BF_ROWS8_MIN_N"] - 1, big) != "rows8"
+    assert bench.potrf_block_layout(v["BF_ROWS8_MAX_N"], big) == "rows8"
+    assert bench.potrf_block_layout(v["BF_ROWS8_MAX_N"] + 1, big) is None
+    assert bench.potrf_block_layout(v["BF_CHOL_BLOCKED_MIN_N"], big) == "blocked"
+    assert bench.potrf_block_layout(v["BF_CHOL_BLOCKED_MIN_N"] - 4, big) is None
 
 
 def test_layout_labels_and_launch_counts():
