@@ -221,12 +221,9 @@ k_chol_small(int batch, int n, int k, Op A, Op B, Op C, OpW D, double *dinv, lon
     const double d = (G == 1) ? dval : __shfl_sync(FULL, dval, q * G + (j % G));
     const double r = rsqrt(d);
     if (first_bad == 0 && not_positive(d)) first_bad = j + 1;
-    for (int ii = istart; ii < n; ii += G) {
-      if (ii == j)
-        sm[(cj + ii) * QP + q] = d * r;
-      else
-        sm[(cj + ii) * QP + q] *= r;
-    }
+    // the pivot's own entry holds d, so one product serves every row (no
+    // divergent second FP64 instruction for the pivot row)
+    for (int ii = istart; ii < n; ii += G) sm[(cj + ii) * QP + q] *= r;
     if (dinv && valid && s == (j % G)) dinv[b * sdinv + j] = r;
     __syncwarp();
   }
@@ -680,12 +677,10 @@ __device__ __forceinline__ void rows_block(RowsSmem<T, BW, P> &S, const RowMap<P
       const T d = __shfl_sync(dmask, acc[j], base + j);
       const T r = rsqrt_t(d);
       if (j < w && bad == 0 && not_positive(d)) bad = c0 + j + 1;
-      if (dl == j) {
-        acc[j] = d * r;
-        S.rinv[p][j] = r;
-      } else {
-        acc[j] *= r;
-      }
+      // lane j's own acc[j] is d: one product for every lane gives its
+      // L_jj = d r and the others' entries, with no divergent FP64 branch
+      acc[j] *= r;
+      if (dl == j) S.rinv[p][j] = r;
 #pragma unroll
       for (int jj = j + 1; jj < W; jj++) {
         const T v = __shfl_sync(dmask, acc[j], base + jj);
@@ -1011,12 +1006,10 @@ __device__ __forceinline__ void rows_block_vp(RowsSmem<double, BW, P> &S, const 
       const double d = __shfl_sync(0xffffffffu, acc[j], base + j);
       const double r = rsqrt(d);
       if (j < w && bad == 0 && not_positive(d)) bad = c0 + j + 1;
-      if (dl == j) {
-        acc[j] = d * r;
-        S.rinv[p][j] = r;
-      } else {
-        acc[j] *= r;
-      }
+      // lane j's own acc[j] is d: one product for every lane gives its
+      // L_jj = d r and the others' entries, with no divergent FP64 branch
+      acc[j] *= r;
+      if (dl == j) S.rinv[p][j] = r;
 #pragma unroll
       for (int jj = j + 1; jj < W; jj++) {
         const double v = __shfl_sync(0xffffffffu, acc[j], base + jj);
